@@ -1,0 +1,653 @@
+/*
+ * FP64 CPU oracle for the semi-Lagrangian (SL) level-set step of
+ * Preda & Semplice, arXiv 2410.22205. TEST INFRASTRUCTURE ONLY: only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg may load it.
+ *
+ * Plain C99, FP64, one node at a time, compiled with -ffp-contract=off.
+ * Optional OpenMP over independent nodes; every reduction is summed per
+ * fixed slab and then over slabs in order, so the result does not depend on
+ * the thread count. Declarations and the list of unpinned functions are in
+ * slr_oracle.h.
+ *
+ * Readings of passages the paper leaves silent or garbled (each one chosen
+ * here, not printed in the paper):
+ *  - gradients on the domain boundary: one-sided first-order differences;
+ *  - feet outside the domain: the index-space coordinate is clamped to
+ *    [0, n-1]; WENO stencil nodes outside the grid replicate the edge value;
+ *  - eq. subgrid is read as |φ_j| < γ (strict); eq. ZhaoPDECutOff drops δ,
+ *    which is kept as in eq. levelset:pde; the cut-off factor multiplies the
+ *    scale factor in both the advective and the diffusive displacement;
+ *  - "first neighbours" of eq. SL:2 are the face neighbours inside the grid,
+ *    and interpolation at a node returns the node value;
+ *  - the 3-D WENO splitting runs z-lines first, then y, then x (the 2-D text
+ *    gives y then x);
+ *  - energy: zero counts with the positive side; a 2-D cell with four edge
+ *    crossings pairs them by the sign of the mean of its four corners;
+ *  - the stop test uses k = min(n, kmax) for both running means;
+ *  - E_p == 0 with p != 1 gives the scale factor 0 (no motion).
+ */
+#include "slr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* grid helpers                                                         */
+/* ------------------------------------------------------------------ */
+
+long long or_num_nodes(const or_params* g) { return g->n[0] * g->n[1] * g->n[2]; }
+
+static void unflatten(const or_params* g, long long idx, long long ijk[3]) {
+    ijk[0] = idx % g->n[0];
+    ijk[1] = (idx / g->n[0]) % g->n[1];
+    ijk[2] = idx / (g->n[0] * g->n[1]);
+}
+
+static long long flatten(const or_params* g, long long i, long long j, long long k) {
+    return i + g->n[0] * (j + g->n[1] * k);
+}
+
+static long long clampi(long long v, long long lo, long long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* node coordinate x = lo + i*h (§3: uniform mesh width Δx) */
+void or_node_coord(const or_params* g, long long idx, double x[3]) {
+    long long ijk[3];
+    unflatten(g, idx, ijk);
+    for (int a = 0; a < 3; ++a) x[a] = (a < g->dim) ? g->lo[a] + (double)ijk[a] * g->h : 0.0;
+}
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* §2 and §3.4: distance to the cloud                                   */
+/* ------------------------------------------------------------------ */
+
+/* d(x) = min over Q in S of |x - Q|. The squared distance is summed as
+ * (x-qx)^2 + (y-qy)^2 [+ (z-qz)^2] in that order; the minimiser with the
+ * lowest index wins ties (strict < over ascending point index). */
+void or_distance(const or_params* g, const double* pts, long long npts,
+                 const long long* nodes, long long m, double* d_out, int* arg_out) {
+    long long count = nodes ? m : or_num_nodes(g);
+    int dim = g->dim;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long t = 0; t < count; ++t) {
+        long long idx = nodes ? nodes[t] : t;
+        double x[3];
+        or_node_coord(g, idx, x);
+        double best = INFINITY;
+        long long arg = -1;
+        for (long long q = 0; q < npts; ++q) {
+            const double* Q = pts + q * dim;
+            double s = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                double diff = x[a] - Q[a];
+                s = s + diff * diff;
+            }
+            if (s < best) {
+                best = s;
+                arg = q;
+            }
+        }
+        d_out[t] = sqrt(best);
+        if (arg_out) arg_out[t] = (int)arg;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* §3: centred finite differences                                       */
+/* ------------------------------------------------------------------ */
+
+void or_gradient(const or_params* g, const double* v, long long idx, double grad[3]) {
+    long long ijk[3];
+    unflatten(g, idx, ijk);
+    for (int a = 0; a < 3; ++a) grad[a] = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+        long long lo_ijk[3] = {ijk[0], ijk[1], ijk[2]};
+        long long hi_ijk[3] = {ijk[0], ijk[1], ijk[2]};
+        if (ijk[a] > 0 && ijk[a] < g->n[a] - 1) {
+            lo_ijk[a] -= 1;
+            hi_ijk[a] += 1;
+            grad[a] = (v[flatten(g, hi_ijk[0], hi_ijk[1], hi_ijk[2])] -
+                       v[flatten(g, lo_ijk[0], lo_ijk[1], lo_ijk[2])]) / (2.0 * g->h);
+        } else if (ijk[a] == 0) {
+            hi_ijk[a] += 1;
+            grad[a] = (v[flatten(g, hi_ijk[0], hi_ijk[1], hi_ijk[2])] - v[idx]) / g->h;
+        } else {
+            lo_ijk[a] -= 1;
+            grad[a] = (v[idx] - v[flatten(g, lo_ijk[0], lo_ijk[1], lo_ijk[2])]) / g->h;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* §3.2: interpolators                                                  */
+/* ------------------------------------------------------------------ */
+
+/* index-space coordinate of x on axis a, clamped to [0, n-1]; returns the
+ * cell index i0 in [0, n-2] and the local coordinate t = xi - i0 in [0, 1] */
+static void locate(const or_params* g, const double x[3], int a, long long* i0, double* t) {
+    double xi = (x[a] - g->lo[a]) / g->h;
+    double top = (double)(g->n[a] - 1);
+    if (xi < 0.0) xi = 0.0;
+    if (xi > top) xi = top;
+    long long c = (long long)floor(xi);
+    if (c > g->n[a] - 2) c = g->n[a] - 2;
+    *i0 = c;
+    *t = xi - (double)c;
+}
+
+/* eq. IQ1: Q1 finite-element interpolation. Inside the cell holding x the
+ * tensor-product shape functions reduce to linear interpolation along x, then
+ * along y, then along z. */
+double or_interp_q1(const or_params* g, const double* v, const double x[3]) {
+    long long c[3] = {0, 0, 0};
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < g->dim; ++a) locate(g, x, a, &c[a], &t[a]);
+    double vz[2];
+    int nz = (g->dim == 3) ? 2 : 1;
+    for (int dz = 0; dz < nz; ++dz) {
+        double vy[2];
+        for (int dy = 0; dy < 2; ++dy) {
+            double v0 = v[flatten(g, c[0], c[1] + dy, c[2] + dz)];
+            double v1 = v[flatten(g, c[0] + 1, c[1] + dy, c[2] + dz)];
+            vy[dy] = (1.0 - t[0]) * v0 + t[0] * v1;
+        }
+        vz[dz] = (1.0 - t[1]) * vy[0] + t[1] * vy[1];
+    }
+    if (g->dim == 2) return vz[0];
+    return (1.0 - t[2]) * vz[0] + t[2] * vz[1];
+}
+
+/* eq. IWENO with n = 2 on the cell [x_j, x_{j+1}] of a uniform mesh of
+ * width h. v = (v_{j-1}, v_j, v_{j+1}, v_{j+2}); theta = (x - x_j)/h.
+ *  - P_L interpolates v on S_L = {x_{j-1}, x_j, x_{j+1}}, P_R on
+ *    S_R = {x_j, x_{j+1}, x_{j+2}} (Lagrange form, nodes at -1,0,1 / 0,1,2);
+ *  - linear weights, eq. ckgamma: C_k(x) = γ_k (x - x̂_k)/Δx with
+ *    γ_L = -1/3, x̂_L = x_{j+2} and γ_R = 1/3, x̂_R = x_{j-1};
+ *  - regularity indicators, eq. ind:1d, as the quadratic forms
+ *    I_k = V^T A_k V / Δx^2 with the matrices A_L, A_R of §3.2;
+ *  - α_k = C_k / (I_k + ε)^2 with ε = Δx^2; w_k = α_k / Σ α; I = Σ w_k P_k.
+ * w (may be NULL) receives (w_L, w_R). */
+double or_weno1d_weights(const double v[4], double theta, double h, double w[2]) {
+    static const double A_L[4][4] = {{1, -2, 1, 0}, {-2, 4, -2, 0}, {1, -2, 1, 0}, {0, 0, 0, 0}};
+    static const double A_R[4][4] = {{0, 0, 0, 0}, {0, 1, -2, 1}, {0, -2, 4, -2}, {0, 1, -2, 1}};
+    double s = theta;
+    /* Lagrange basis on nodes -1, 0, 1 (P_L) and 0, 1, 2 (P_R) */
+    double PL = v[0] * (s * (s - 1.0) / 2.0) + v[1] * ((1.0 - s) * (1.0 + s)) + v[2] * (s * (s + 1.0) / 2.0);
+    double PR = v[1] * ((s - 1.0) * (s - 2.0) / 2.0) + v[2] * (s * (2.0 - s)) + v[3] * (s * (s - 1.0) / 2.0);
+    double IL = 0.0, IR = 0.0;
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            IL += v[r] * A_L[r][c] * v[c];
+            IR += v[r] * A_R[r][c] * v[c];
+        }
+    IL /= h * h;
+    IR /= h * h;
+    /* positions in units of h relative to x_j: x_{j-1} = -1, x_{j+2} = 2 */
+    double CL = (-1.0 / 3.0) * (s - 2.0);
+    double CR = (1.0 / 3.0) * (s - (-1.0));
+    double eps = h * h;
+    double aL = CL / ((IL + eps) * (IL + eps));
+    double aR = CR / ((IR + eps) * (IR + eps));
+    double wL = aL / (aL + aR);
+    double wR = aR / (aL + aR);
+    if (w) {
+        w[0] = wL;
+        w[1] = wR;
+    }
+    return wL * PL + wR * PR;
+}
+
+double or_weno1d(const double v[4], double theta, double h) { return or_weno1d_weights(v, theta, h, NULL); }
+
+/* §3.2, multi-dimensional WENO by dimension splitting: in 3-D, 16 one-
+ * dimensional interpolations along z (one per (x,y) stencil column), then 4
+ * along y, then 1 along x; in 2-D, 4 along y then 1 along x. Stencil nodes
+ * outside the grid take the nearest edge value. */
+double or_interp_weno(const or_params* g, const double* v, const double x[3]) {
+    long long c[3] = {0, 0, 0};
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < g->dim; ++a) locate(g, x, a, &c[a], &t[a]);
+    double colx[4];
+    for (int a = 0; a < 4; ++a) {
+        long long ii = clampi(c[0] - 1 + a, 0, g->n[0] - 1);
+        double coly[4];
+        for (int b = 0; b < 4; ++b) {
+            long long jj = clampi(c[1] - 1 + b, 0, g->n[1] - 1);
+            if (g->dim == 3) {
+                double line[4];
+                for (int e = 0; e < 4; ++e) {
+                    long long kk = clampi(c[2] - 1 + e, 0, g->n[2] - 1);
+                    line[e] = v[flatten(g, ii, jj, kk)];
+                }
+                coly[b] = or_weno1d(line, t[2], g->h);
+            } else {
+                coly[b] = v[flatten(g, ii, jj, 0)];
+            }
+        }
+        colx[a] = or_weno1d(coly, t[1], g->h);
+    }
+    return or_weno1d(colx, t[0], g->h);
+}
+
+double or_interp(const or_params* g, const double* v, const double x[3]) {
+    return g->interp == 1 ? or_interp_weno(g, v, x) : or_interp_q1(g, v, x);
+}
+
+/* ------------------------------------------------------------------ */
+/* §3.8: band, cut, cut-off                                             */
+/* ------------------------------------------------------------------ */
+
+/* γ as represented in the storage precision */
+static double gamma_s(const or_params* g) { return g->prec == 32 ? (double)(float)g->gamma : g->gamma; }
+
+/* eq. subgrid, read as |φ_j| < γ, decided in the storage precision */
+int or_in_band(const or_params* g, double u) {
+    if (g->prec == 32) return (float)fabs(u) < (float)g->gamma;
+    return fabs(u) < g->gamma;
+}
+
+/* eq. cut */
+double or_cut(const or_params* g, double u) {
+    double gm = gamma_s(g);
+    if (u > gm) return gm;
+    if (u < -gm) return -gm;
+    return u;
+}
+
+void or_cut_all(const or_params* g, double* u) {
+    long long N = or_num_nodes(g);
+    for (long long i = 0; i < N; ++i) u[i] = or_cut(g, u[i]);
+}
+
+long long or_band(const or_params* g, const double* u, long long* list_out) {
+    long long N = or_num_nodes(g), m = 0;
+    for (long long i = 0; i < N; ++i)
+        if (or_in_band(g, u[i])) {
+            if (list_out) list_out[m] = i;
+            ++m;
+        }
+    return m;
+}
+
+/* eq. cutoff */
+double or_cutoff(const or_params* g, double u) {
+    double a = fabs(u), gm = g->gamma, b = g->beta;
+    if (a <= b) return 1.0;
+    if (a <= gm) return (a - gm) * (a - gm) * (2.0 * a + gm - 3.0 * b) / ((gm - b) * (gm - b) * (gm - b));
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* §3.1: tangent directions and feet                                    */
+/* ------------------------------------------------------------------ */
+
+/* eq. sigma2d: σ = (∂2φ, -∂1φ) / |∇φ| */
+void or_sigma2d(const double grad[3], double sigma[3]) {
+    double nrm = sqrt(grad[0] * grad[0] + grad[1] * grad[1]);
+    sigma[0] = grad[1] / nrm;
+    sigma[1] = -grad[0] / nrm;
+    sigma[2] = 0.0;
+}
+
+/* eq. sigma3d with the regularisation of §3.1: ν1 = (1,0,0), ν2 = (0,0,1)
+ * when sqrt((∂1φ)^2 + (∂3φ)^2) == 0. Returns 1 when regularised. */
+int or_tangent_basis(const double grad[3], double nu1[3], double nu2[3]) {
+    double g1 = grad[0], g2 = grad[1], g3 = grad[2];
+    double r = sqrt(g1 * g1 + g3 * g3);
+    if (r == 0.0) {
+        nu1[0] = 1.0; nu1[1] = 0.0; nu1[2] = 0.0;
+        nu2[0] = 0.0; nu2[1] = 0.0; nu2[2] = 1.0;
+        return 1;
+    }
+    double nrm = sqrt(g1 * g1 + g2 * g2 + g3 * g3);
+    nu1[0] = -g3 / r;
+    nu1[1] = 0.0;
+    nu1[2] = g1 / r;
+    nu2[0] = (1.0 / nrm) * (-g1 * g2 / r);
+    nu2[1] = (1.0 / nrm) * r;
+    nu2[2] = (1.0 / nrm) * (-g2 * g3 / r);
+    return 0;
+}
+
+/* eq. SL2d / SL3d: x* = x_j + C Δt ∇d(x_j) + sqrt(C δ d(x_j) Δt / p) σ λ_i,
+ * λ over {-1, +1} (2-D) or {(-,-), (-,+), (+,-), (+,+)} (3-D), σλ = λ1 ν1 + λ2 ν2. */
+int or_feet(const or_params* g, const double xj[3], const double grad_u[3], const double grad_d[3],
+            double dj, double ct, double feet[4][3]) {
+    double base[3];
+    for (int a = 0; a < 3; ++a) base[a] = xj[a] + ct * g->dt * grad_d[a];
+    double s = sqrt(ct * g->delta * dj * g->dt / g->p);
+    if (g->dim == 2) {
+        double sigma[3];
+        or_sigma2d(grad_u, sigma);
+        static const double lam[2] = {-1.0, 1.0};
+        for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < 3; ++a) feet[i][a] = base[a] + s * sigma[a] * lam[i];
+        return 2;
+    }
+    double nu1[3], nu2[3];
+    or_tangent_basis(grad_u, nu1, nu2);
+    static const double lam[4][2] = {{-1, -1}, {-1, 1}, {1, -1}, {1, 1}};
+    for (int i = 0; i < 4; ++i)
+        for (int a = 0; a < 3; ++a) feet[i][a] = base[a] + s * (lam[i][0] * nu1[a] + lam[i][1] * nu2[a]);
+    return 4;
+}
+
+/* C^n_j = (d(x_j) / E_p(φ^n))^(p-1) (§3.1); C = 1 for p = 1 (§4) */
+double or_scale_factor(const or_params* g, double dj, double Ep) {
+    if (g->p == 1.0) return 1.0;
+    if (!(Ep > 0.0)) return 0.0;
+    return pow(dj / Ep, g->p - 1.0);
+}
+
+/* ------------------------------------------------------------------ */
+/* §3.1: one SL update                                                  */
+/* ------------------------------------------------------------------ */
+
+double or_sl_node(const or_params* g, const double* u, const double* d, double Ep, long long idx, int* flags) {
+    int f = 0;
+    double gu[3], gd[3], x[3];
+    or_gradient(g, u, idx, gu);
+    double nrm = sqrt(gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2]);
+    double thr = g->c_sing * pow(g->dt, g->alpha);
+    if (fabs(nrm - thr) <= 1e-6 * thr) f |= OR_FLAG_MARGIN;
+    if (nrm < thr) {
+        /* eq. SL:2: mean over the first (face) neighbours inside the grid */
+        long long ijk[3];
+        unflatten(g, idx, ijk);
+        double sum = 0.0;
+        int cnt = 0;
+        for (int a = 0; a < g->dim; ++a)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                long long nb[3] = {ijk[0], ijk[1], ijk[2]};
+                nb[a] += sgn;
+                if (nb[a] < 0 || nb[a] >= g->n[a]) continue;
+                sum += u[flatten(g, nb[0], nb[1], nb[2])];
+                ++cnt;
+            }
+        if (flags) *flags = f | OR_FLAG_FALLBACK;
+        return sum / (double)cnt;
+    }
+    or_gradient(g, d, idx, gd);
+    or_node_coord(g, idx, x);
+    double dj = d[idx];
+    double ct = or_scale_factor(g, dj, Ep);
+    if (g->band) ct = or_cutoff(g, u[idx]) * ct;
+    if (g->dim == 3 && gu[0] == 0.0 && gu[2] == 0.0) f |= OR_FLAG_REGULAR;
+    double feet[4][3];
+    int nf = or_feet(g, x, gu, gd, dj, ct, feet);
+    double sum = 0.0;
+    for (int i = 0; i < nf; ++i) sum += or_interp(g, u, feet[i]);
+    if (flags) *flags = f;
+    return sum / (double)nf;
+}
+
+void or_sl_nodes(const or_params* g, const double* u, const double* d, double Ep,
+                 const long long* nodes, long long m, double* out, int* flags) {
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long long t = 0; t < m; ++t) out[t] = or_sl_node(g, u, d, Ep, nodes[t], flags ? flags + t : NULL);
+}
+
+/* Algorithm 1, steps 4a, 4c and the cut of 4d (no reinitialisation) */
+double or_sl_step(const or_params* g, const double* u, const double* d, double Ep, double* u_out, int* flags_out) {
+    long long N = or_num_nodes(g);
+    long long slab = g->n[0] * g->n[1];
+    long long nslab = g->n[2];
+    double* part = (double*)calloc((size_t)nslab, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long k = 0; k < nslab; ++k) {
+        double acc = 0.0;
+        for (long long idx = k * slab; idx < (k + 1) * slab; ++idx) {
+            double v;
+            int f = 0;
+            if (!g->band || or_in_band(g, u[idx]))
+                v = or_sl_node(g, u, d, Ep, idx, &f);
+            else
+                v = u[idx];
+            if (g->band) v = or_cut(g, v);
+            u_out[idx] = v;
+            if (flags_out) flags_out[idx] = f;
+            acc += fabs(v - u[idx]);
+        }
+        part[k] = acc;
+    }
+    double total = 0.0;
+    for (long long k = 0; k < nslab; ++k) total += part[k];
+    free(part);
+    (void)N;
+    return total * pow(g->h, (double)g->dim);
+}
+
+/* ------------------------------------------------------------------ */
+/* §3.5: energy                                                         */
+/* ------------------------------------------------------------------ */
+
+static int negative(double v) { return v < 0.0; }
+
+/* 2-D: the front crosses the cell edges where φ changes sign (linear
+ * interpolation of φ along the edge); d at a crossing is interpolated
+ * linearly along the edge; trapezoid rule on the segment(s). */
+static double energy_cell_2d(const or_params* g, const double* u, const double* d, double p,
+                             long long i, long long j) {
+    /* corners in the order 00, 10, 11, 01; edge e joins corner e and e+1 */
+    long long id[4] = {flatten(g, i, j, 0), flatten(g, i + 1, j, 0), flatten(g, i + 1, j + 1, 0),
+                       flatten(g, i, j + 1, 0)};
+    double cx[4] = {0, 1, 1, 0}, cy[4] = {0, 0, 1, 1};
+    double uv[4], dv[4];
+    for (int c = 0; c < 4; ++c) {
+        uv[c] = u[id[c]];
+        dv[c] = d[id[c]];
+    }
+    double px[4], py[4], pd[4];
+    int has[4] = {0, 0, 0, 0}, nc = 0;
+    for (int e = 0; e < 4; ++e) {
+        int a = e, b = (e + 1) % 4;
+        if (negative(uv[a]) != negative(uv[b])) {
+            double t = uv[a] / (uv[a] - uv[b]);
+            px[e] = (cx[a] + t * (cx[b] - cx[a])) * g->h;
+            py[e] = (cy[a] + t * (cy[b] - cy[a])) * g->h;
+            pd[e] = dv[a] + t * (dv[b] - dv[a]);
+            has[e] = 1;
+            ++nc;
+        }
+    }
+    if (nc == 0) return 0.0;
+    int pairs[2][2], np = 0;
+    if (nc == 2) {
+        int k = 0;
+        for (int e = 0; e < 4; ++e)
+            if (has[e]) pairs[0][k++] = e;
+        np = 1;
+    } else {
+        /* four crossings: corners 00 and 11 share a sign. If the cell mean
+         * has that sign too, the segments cut off corners 10 (edges 0,1) and
+         * 01 (edges 2,3); otherwise corners 00 (edges 3,0) and 11 (edges 1,2). */
+        double mean = (uv[0] + uv[1] + uv[2] + uv[3]) / 4.0;
+        if (negative(mean) == negative(uv[0])) {
+            pairs[0][0] = 0; pairs[0][1] = 1;
+            pairs[1][0] = 2; pairs[1][1] = 3;
+        } else {
+            pairs[0][0] = 3; pairs[0][1] = 0;
+            pairs[1][0] = 1; pairs[1][1] = 2;
+        }
+        np = 2;
+    }
+    double acc = 0.0;
+    for (int s = 0; s < np; ++s) {
+        int e1 = pairs[s][0], e2 = pairs[s][1];
+        double len = sqrt((px[e1] - px[e2]) * (px[e1] - px[e2]) + (py[e1] - py[e2]) * (py[e1] - py[e2]));
+        acc += len * (pow(fabs(pd[e1]), p) + pow(fabs(pd[e2]), p)) / 2.0;
+    }
+    return acc;
+}
+
+/* 3-D, eq. energyApproxFiner: the front cell is split into R^3 subcells of
+ * width Δx' = Δx/R; a subcell counts when the reconstruction of φ at its
+ * centre (the active interpolator) satisfies |φ(x')| < (√3/2) Δx'; it adds
+ * |d(x')|^p (Δx')^2 with d interpolated by Q1. */
+static double energy_cell_3d(const or_params* g, const double* u, const double* d, double p, int R,
+                             long long i, long long j, long long k, double amb_tol, double* amb) {
+    double hp = g->h / (double)R;
+    double thr = sqrt(3.0) / 2.0 * hp;
+    or_params gq = *g;
+    gq.interp = 0;
+    double x0[3];
+    or_node_coord(g, flatten(g, i, j, k), x0);
+    double acc = 0.0;
+    for (int c = 0; c < R; ++c)
+        for (int b = 0; b < R; ++b)
+            for (int a = 0; a < R; ++a) {
+                double xp[3] = {x0[0] + ((double)a + 0.5) * hp, x0[1] + ((double)b + 0.5) * hp,
+                                x0[2] + ((double)c + 0.5) * hp};
+                double up = or_interp(g, u, xp);
+                double contrib = pow(fabs(or_interp_q1(&gq, d, xp)), p) * hp * hp;
+                if (fabs(up) < thr) acc += contrib;
+                if (fabs(fabs(up) - thr) <= amb_tol) *amb += contrib;
+            }
+    return acc;
+}
+
+static int front_cell(const or_params* g, const double* u, long long i, long long j, long long k) {
+    int nz = g->dim == 3 ? 2 : 1;
+    int seen_neg = 0, seen_pos = 0;
+    for (int dz = 0; dz < nz; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                if (negative(u[flatten(g, i + dx, j + dy, k + dz)]))
+                    seen_neg = 1;
+                else
+                    seen_pos = 1;
+            }
+    return seen_neg && seen_pos;
+}
+
+void or_energy(const or_params* g, const double* u, const double* d, double p, int R, double amb_tol, double out[4]) {
+    long long nk = g->dim == 3 ? g->n[2] - 1 : 1;
+    double* part = (double*)calloc((size_t)nk, sizeof(double));
+    double* pamb = (double*)calloc((size_t)nk, sizeof(double));
+    long long* pcnt = (long long*)calloc((size_t)nk, sizeof(long long));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long k = 0; k < nk; ++k) {
+        double acc = 0.0, amb = 0.0;
+        long long cnt = 0;
+        for (long long j = 0; j < g->n[1] - 1; ++j)
+            for (long long i = 0; i < g->n[0] - 1; ++i) {
+                if (!front_cell(g, u, i, j, k)) continue;
+                ++cnt;
+                if (g->dim == 2)
+                    acc += energy_cell_2d(g, u, d, p, i, j);
+                else
+                    acc += energy_cell_3d(g, u, d, p, R, i, j, k, amb_tol, &amb);
+            }
+        part[k] = acc;
+        pamb[k] = amb;
+        pcnt[k] = cnt;
+    }
+    double total = 0.0, amb = 0.0;
+    long long cnt = 0;
+    for (long long k = 0; k < nk; ++k) {
+        total += part[k];
+        amb += pamb[k];
+        cnt += pcnt[k];
+    }
+    free(part);
+    free(pamb);
+    free(pcnt);
+    out[0] = total;
+    out[1] = pow(total, 1.0 / p);
+    out[2] = amb;
+    out[3] = (double)cnt;
+}
+
+/* ------------------------------------------------------------------ */
+/* §4: stopping criterion, evolution loop, diagnostics                 */
+/* ------------------------------------------------------------------ */
+
+/* eq. deltaEn: ē_n = (1/k) Σ_{i=n-k+1..n} E_2(φ^i), k = min(n, kmax);
+ * stop when Δ_E^n = |ē_{n-1} - ē_n| / ē_n < tol and n >= min_iters, or when
+ * n reaches max_iters. */
+int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int max_iters, double* delta_out) {
+    double delta = -1.0;
+    if (n >= 1) {
+        int k = n < kmax ? n : kmax;
+        double en = 0.0, em = 0.0;
+        for (int i = n - k + 1; i <= n; ++i) en += E2[i];
+        for (int i = n - k; i <= n - 1; ++i) em += E2[i];
+        en /= (double)k;
+        em /= (double)k;
+        if (en > 0.0)
+            delta = fabs(em - en) / en;
+        else
+            delta = (em == en) ? 0.0 : INFINITY;
+    }
+    if (delta_out) *delta_out = delta;
+    if (n >= max_iters) return 1;
+    if (n >= min_iters && delta >= 0.0 && delta < tol) return 1;
+    return 0;
+}
+
+int or_evolve(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
+              int min_iters, int max_iters, double* E2_hist, double* dphi_hist, int* converged) {
+    long long N = or_num_nodes(g);
+    double* next = (double*)malloc((size_t)N * sizeof(double));
+    double e[4];
+    or_energy(g, u, d, 2.0, R, 0.0, e);
+    E2_hist[0] = e[1];
+    int n = 0, conv = 0;
+    for (;;) {
+        double Ep = E2_hist[n];
+        if (g->p != 2.0 && g->p != 1.0) {
+            double ep[4];
+            or_energy(g, u, d, g->p, R, 0.0, ep);
+            Ep = ep[1];
+        }
+        double dphi = or_sl_step(g, u, d, Ep, next, NULL);
+        memcpy(u, next, (size_t)N * sizeof(double));
+        dphi_hist[n] = dphi;
+        ++n;
+        or_energy(g, u, d, 2.0, R, 0.0, e);
+        E2_hist[n] = e[1];
+        double delta;
+        if (or_stop(E2_hist, n, kmax, stop_tol, min_iters, max_iters, &delta)) {
+            conv = (n >= min_iters && delta >= 0.0 && delta < stop_tol);
+            break;
+        }
+    }
+    free(next);
+    if (converged) *converged = conv;
+    return n;
+}
+
+long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out) {
+    long long N = or_num_nodes(g), m = 0;
+    for (long long i = 0; i < N; ++i)
+        if (fabs(u[i]) < width) {
+            if (idx_out) idx_out[m] = i;
+            if (u_out) u_out[m] = u[i];
+            ++m;
+        }
+    return m;
+}
+
+/* eq. errCloud */
+double or_err_cloud(const or_params* g, const double* u, const double* pts, long long npts) {
+    double acc = 0.0;
+    for (long long q = 0; q < npts; ++q) {
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < g->dim; ++a) x[a] = pts[q * g->dim + a];
+        acc += fabs(or_interp(g, u, x));
+    }
+    return acc / (double)npts;
+}
