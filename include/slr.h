@@ -1,0 +1,178 @@
+/*
+ * slr.h -- C ABI of the GB300 (sm_103a) semi-Lagrangian level-set surface
+ * reconstruction library (libslr.so).
+ *
+ * Method: Preda & Semplice, "Surface reconstruction from point cloud using a
+ * semi-Lagrangian scheme with local interpolator" (arXiv 2410.22205). The
+ * calls follow the paper's statement of the problem, Algorithm 1: build a
+ * Cartesian grid around the cloud, compute the distance d to the cloud
+ * (§3.4), set the initial level set φ^0 (§3.6), then loop { narrow band
+ * (§3.8), energy E_p (§3.5), SL update (§3.1) with the Q1 or WENO
+ * interpolator (§3.2), cut (§3.8) } until the stopping criterion of §4.
+ *
+ * Conventions
+ *  - Every call returns an slr_status; nothing aborts or throws across the
+ *    ABI. On failure, slr_last_error(ctx) holds a one-line message.
+ *  - Host arrays passed in are read during the call and not retained; the
+ *    caller keeps ownership. Output arrays are caller buffers with a stated
+ *    capacity; SLR_E_CAPACITY reports the count that would be needed.
+ *  - Device memory comes from the allocator given to slr_create (NULL: the
+ *    library uses cudaMalloc/cudaFree). All work is enqueued on the stream
+ *    given to slr_create (NULL: the legacy default stream). Calls that return
+ *    host data synchronise that stream.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *    Different contexts may be used from different threads.
+ *  - Grid layout: node (i,j,k), 0 <= i < n[0] ..., has linear index
+ *    i + n[0]*(j + n[1]*k) (x fastest); in 2-D n[2] must be 1. Node
+ *    coordinates are lo[a] + i*h with h = (hi[0]-lo[0])/(n[0]-1), which must
+ *    be the same on every axis (§3: one mesh width Δx).
+ *  - Calling out of order (e.g. slr_step before slr_init_u) returns
+ *    SLR_E_STATE.
+ */
+#ifndef SLR_H
+#define SLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slr_ctx slr_ctx;
+
+typedef enum {
+    SLR_OK = 0,
+    SLR_E_INVALID = 1,  /* bad argument or configuration */
+    SLR_E_NOMEM = 2,    /* the allocator returned NULL */
+    SLR_E_CUDA = 3,     /* a CUDA runtime call failed */
+    SLR_E_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    SLR_E_STATE = 5,    /* call out of order */
+    SLR_E_CAPACITY = 6  /* output buffer too small; the needed count is returned */
+} slr_status;
+
+/* Device allocator. alloc returns device memory of at least `bytes` bytes
+ * (NULL on failure); free releases a pointer alloc returned. `user` is passed
+ * through unchanged. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} slr_allocator;
+
+/* Run configuration. slr_config_default fills the paper's defaults. */
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int64_t n[3];       /* nodes per axis (n[2] = 1 in 2-D); at most 2^31-1 nodes in total */
+    double lo[3];       /* box corner of node (0,0,0) */
+    double hi[3];       /* box corner of the last node; equal h on every axis */
+    int precision;      /* 32 or 64: storage and arithmetic type of u, d and the SL step */
+    int interp;         /* 0 = Q1 (§3.2 eq. IQ1), 1 = WENO (§3.2 eq. IWENO) */
+    double p;           /* energy exponent p (§2 eq. energy), default 2 */
+    double delta;       /* curvature weight δ (§2 eq. levelset:pde), default 1 */
+    double dt;          /* time step; 0 -> h/4 (§4 eq. dxdt) */
+    int band;           /* 0 = update the whole grid; 1 = narrow band of §3.8 */
+    double gamma;       /* band half-width γ; 0 -> 4h (2-D) / 6h (3-D) (§3.8) */
+    double beta;        /* cut-off inner radius β; 0 -> 2h (2-D) / 3h (3-D) (§3.8 eq. cutoff) */
+    double c_sing;      /* singular-gradient test constant C (§3.1 eq. SL:2), default 1e-3 */
+    double alpha;       /* singular-gradient test exponent α, default 1 */
+    int energy_R;       /* 3-D energy subcells per axis R (§3.5), default 5, 1..8 */
+    double stop_tol;    /* Δ_E threshold (§4 eq. deltaEn), default 1e-4 */
+    int stop_k;         /* running-mean window k_max, default 10 */
+    int min_iters;      /* default 10 */
+    int max_iters;      /* default 100 */
+} slr_config;
+
+void slr_config_default(slr_config* cfg);
+
+/* Create a context for one reconstruction job. Validates cfg (equal h on
+ * all axes, at least 4 nodes per active axis, precision 32|64, ...) and
+ * allocates the dense fields u (two buffers), d and argmin plus the band and
+ * reduction buffers. alloc may be NULL (cudaMalloc/cudaFree); stream is a
+ * cudaStream_t or NULL. The context binds to the device current at this call. */
+slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out);
+
+/* Copy the point cloud S = {Q_1..Q_N} (§2) to the device. xyz: host array of
+ * n_points rows of `dim` FP64 coordinates, row-major. n_points >= 1. */
+slr_status slr_load_cloud(slr_ctx* ctx, const double* xyz, int64_t n_points);
+
+/* Algorithm 1 step 2 / §3.4: d(x_j) = min_Q |x_j - Q| on every node, exact,
+ * with argmin (the lowest point index on ties). Needs slr_load_cloud. The
+ * minimiser is decided in FP64; d is stored in the configured precision. */
+slr_status slr_build_distance(slr_ctx* ctx);
+
+/* Set d from a host FP64 array of all nodes (e.g. an analytic distance);
+ * argmin is set to -1. Rounded to the storage precision. */
+slr_status slr_set_distance(slr_ctx* ctx, const double* d_host);
+
+/* Algorithm 1 step 3: initial level set φ^0.
+ *  kind 0 (sphere): params = {cx, cy, cz, r}; φ^0 = |x - c| - r (FP64, rounded to storage);
+ *  kind 1 (array):  u0_host = FP64 values of all nodes.
+ * In band mode the cut of eq. cut is applied, so |φ^0| <= γ holds before the
+ * first step; the band G̃^0 (eq. subgrid, |φ| < γ) and the list of cells the
+ * energy quadrature may visit are built here. Resets the iteration count and
+ * the diagnostics. Needs d (build or set) first. */
+slr_status slr_init_u(slr_ctx* ctx, int kind, const double* params, const double* u0_host);
+
+/* Run n_steps iterations of Algorithm 1 step 4 (band, SL update §3.1, cut)
+ * without the stopping test, each followed by the FP64 energy of the new
+ * state. energy_override >= 0 uses that value as E_p in the scale factor
+ * (d/E_p)^(p-1) of every step; < 0 uses the computed E_p(φ^n). */
+slr_status slr_step(slr_ctx* ctx, int n_steps, double energy_override);
+
+/* Iterate until the stopping criterion of §4 (eq. deltaEn: Δ_E < stop_tol
+ * after at least min_iters iterations, or max_iters). The test and the
+ * iteration count live on the device; the host reads a 4-byte status every
+ * few iterations. iters_out / converged_out may be NULL. */
+slr_status slr_evolve(slr_ctx* ctx, int* iters_out, int* converged_out);
+
+/* Nodes with |φ| < width, in ascending linear index (the reconstructed zero
+ * level set's neighbourhood). idx/u: caller buffers of `cap` entries (either
+ * may be NULL to query the count). *n_out = number of such nodes; returns
+ * SLR_E_CAPACITY if it exceeds cap (nothing written then). */
+slr_status slr_extract(slr_ctx* ctx, double width, int64_t* idx, double* u, int64_t cap, int64_t* n_out);
+
+enum { SLR_FIELD_U = 0, SLR_FIELD_D = 1, SLR_FIELD_ARGMIN = 2 };
+
+/* Copy a whole field to the host: U and D as FP64 (widened from storage),
+ * ARGMIN as int32. cap = number of entries host_out holds (>= nodes). */
+slr_status slr_get_field(slr_ctx* ctx, int which, void* host_out, int64_t cap);
+
+/* Current narrow band G̃ (ascending node indices), as int64. In whole-grid
+ * mode the band is every node and *n_out = nodes (idx may be NULL). */
+slr_status slr_get_band(slr_ctx* ctx, int64_t* idx, int64_t cap, int64_t* n_out);
+
+/* §3.5 energy of the current state computed now: E_p with the given p and,
+ * separately, the raw sum Σ|d|^p·measure. Either output may be NULL. */
+slr_status slr_energy(slr_ctx* ctx, double p, double* E_out, double* sum_out);
+
+/* Per-iteration history since slr_init_u: e2_hist[i] = E_2(φ^i) for
+ * i = 0..iters, dphi_hist[i] = Δ_φ (§4, h^dim Σ|φ^{i+1}-φ^i|) and
+ * band_hist[i] = band size of iteration i for i < iters. Arrays may be NULL;
+ * each holds `cap` entries (entries beyond cap are dropped). *n_out = iters.
+ * err_cloud (may be NULL): Err_S of §4 eq. errCloud for the current state,
+ * needs the cloud. */
+slr_status slr_diagnostics(slr_ctx* ctx, double* e2_hist, double* dphi_hist, int64_t* band_hist, int cap,
+                           int* n_out, double* err_cloud);
+
+/* Checkpoint: serialise u, d, argmin, the band, the iteration count and the
+ * energy history into buf (host, cap bytes). buf NULL or too small ->
+ * SLR_E_CAPACITY with *n_out = bytes needed. slr_import_state restores a
+ * state exported from a context with the same configuration; continuing
+ * from it reproduces an uninterrupted run bit for bit. */
+slr_status slr_export_state(slr_ctx* ctx, void* buf, int64_t cap, int64_t* n_out);
+slr_status slr_import_state(slr_ctx* ctx, const void* buf, int64_t n);
+
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t slr_kernel_launches(const slr_ctx* ctx);
+
+/* Last error message of the context (never NULL; "" when none). */
+const char* slr_last_error(const slr_ctx* ctx);
+
+/* Release all device memory of the context and the context itself. NULL is a no-op. */
+void slr_destroy(slr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,701 @@
+// C ABI of libslr (declared in include/slr.h): context lifecycle, argument
+// validation, device memory through the injected allocator, and the
+// per-iteration loop. One iteration (fused band+SL step, energy pass,
+// record/stop kernel) is captured once as a CUDA graph and replayed; the
+// iteration counter, the stop flag and the energy history live on the
+// device, and the host reads a few status words every kChunk iterations.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "slr_internal.cuh"
+
+using namespace slr;
+
+namespace {
+
+constexpr int kChunk = 8;  // graph replays between status reads in slr_evolve
+constexpr uint32_t kStateMagic = 0x534c5231u;  // "SLR1"
+thread_local std::string g_create_error;  // reason of the last failed slr_create on this thread
+
+slr_status fail(slr_ctx* c, slr_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+slr_status cuda_fail(slr_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return fail(c, SLR_E_CUDA, m);
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void free_graphs(slr_ctx* c) {
+    if (c->g_evolve) cudaGraphExecDestroy(c->g_evolve);
+    if (c->g_step) cudaGraphExecDestroy(c->g_step);
+    c->g_evolve = nullptr;
+    c->g_step = nullptr;
+    c->g_step_override = -2.0;
+}
+
+void release(slr_ctx* c, void*& p) {
+    dev_free(c, p);
+    p = nullptr;
+}
+
+template <typename P>
+void release_t(slr_ctx* c, P*& p) {
+    void* v = (void*)p;
+    dev_free(c, v);
+    p = nullptr;
+}
+
+// capture one iteration as a graph
+slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e1 = launch_step(c, ov, evolve);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve) : e1;
+    cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
+    c->launches = l0;  // captured kernels are counted per replay
+    if (e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e2, "capture of one iteration");
+    }
+    if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaStreamEndCapture");
+    cudaError_t e4 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) return cuda_fail(c, e4, "cudaGraphInstantiate");
+    return SLR_OK;
+}
+
+constexpr int kKernelsPerIteration = 3;
+
+slr_status read_status(slr_ctx* c, int* stop, int* error, int* n) {
+    int* hp = c->host_pinned_flags;
+    CK(cudaMemcpyAsync(hp + 0, &c->ds->stop, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+    CK(cudaMemcpyAsync(hp + 1, &c->ds->error, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+    CK(cudaMemcpyAsync(hp + 2, &c->ds->n, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (stop) *stop = hp[0];
+    if (error) *error = hp[1];
+    if (n) *n = hp[2];
+    return SLR_OK;
+}
+
+slr_status check_device_error(slr_ctx* c) {
+    int err = 0;
+    slr_status s = read_status(c, nullptr, &err, nullptr);
+    if (s != SLR_OK) return s;
+    if (err & kErrLookback) return fail(c, SLR_E_TIMEOUT, "band compaction look-back wait timed out");
+    return SLR_OK;
+}
+
+// allocate the per-band buffers for a band of `count` nodes and the energy
+// partials for `ncells` candidate cells
+slr_status size_band_buffers(slr_ctx* c, long long count) {
+    long long cap = count > 0 ? count : 1;
+    release_t(c, c->band[0]);
+    release_t(c, c->band[1]);
+    release_t(c, c->part_dphi);
+    release_t(c, c->tile_status);
+    c->band[0] = (int*)dev_alloc(c, sizeof(int) * cap);
+    c->band[1] = (int*)dev_alloc(c, sizeof(int) * cap);
+    long long tiles = (cap + kStepTile - 1) / kStepTile + 1;
+    c->part_dphi = (double*)dev_alloc(c, sizeof(double) * tiles);
+    c->tile_status = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * tiles);
+    if (!c->band[0] || !c->band[1] || !c->part_dphi || !c->tile_status)
+        return fail(c, SLR_E_NOMEM, "allocation of the band buffers failed");
+    c->band_cap = cap;
+    c->n_tiles_cap = tiles;
+    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * tiles, c->stream), "memset");
+    return SLR_OK;
+}
+
+slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
+    release_t(c, c->part_e);
+    c->n_echunks = (ncells + 31) / 32;
+    c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2));
+    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy partials failed");
+    return SLR_OK;
+}
+
+bool same_config(const slr_config& a, const slr_config& b) { return memcmp(&a, &b, sizeof(slr_config)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+void slr_config_default(slr_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->dim = 3;
+    cfg->n[0] = cfg->n[1] = cfg->n[2] = 64;
+    for (int a = 0; a < 3; ++a) {
+        cfg->lo[a] = -1.0;
+        cfg->hi[a] = 1.0;
+    }
+    cfg->precision = 32;
+    cfg->interp = 1;
+    cfg->p = 2.0;
+    cfg->delta = 1.0;
+    cfg->dt = 0.0;
+    cfg->band = 1;
+    cfg->gamma = 0.0;
+    cfg->beta = 0.0;
+    cfg->c_sing = 1e-3;
+    cfg->alpha = 1.0;
+    cfg->energy_R = 5;
+    cfg->stop_tol = 1e-4;
+    cfg->stop_k = 10;
+    cfg->min_iters = 10;
+    cfg->max_iters = 100;
+}
+
+slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out) {
+    if (!cfg || !out) return SLR_E_INVALID;
+    *out = nullptr;
+    slr_ctx* c = new slr_ctx();
+    c->cfg = *cfg;
+    slr_config& k = c->cfg;
+    auto bad = [&](const char* m) {
+        g_create_error = m;
+        delete c;
+        return SLR_E_INVALID;
+    };
+    if (k.dim != 2 && k.dim != 3) return bad("dim must be 2 or 3");
+    if (k.dim == 2) {
+        if (k.n[2] != 1) return bad("n[2] must be 1 in 2-D");
+        k.lo[2] = k.hi[2] = 0.0;
+    }
+    for (int a = 0; a < k.dim; ++a)
+        if (k.n[a] < 4) return bad("need at least 4 nodes per axis");
+    long long N = k.n[0] * k.n[1] * k.n[2];
+    if (N <= 0 || N > 2147483647ll) return bad("at most 2^31-1 nodes");
+    double h = (k.hi[0] - k.lo[0]) / (double)(k.n[0] - 1);
+    if (!(h > 0.0) || !isfinite(h)) return bad("hi must exceed lo");
+    for (int a = 1; a < k.dim; ++a) {
+        double ha = (k.hi[a] - k.lo[a]) / (double)(k.n[a] - 1);
+        if (!(fabs(ha - h) <= 1e-12 * h)) return bad("mesh width must be equal on every axis");
+    }
+    if (k.precision != 32 && k.precision != 64) return bad("precision must be 32 or 64");
+    if (k.interp != 0 && k.interp != 1) return bad("interp must be 0 (Q1) or 1 (WENO)");
+    if (!(k.p >= 1.0) || !isfinite(k.p)) return bad("p must be >= 1");
+    if (!(k.delta >= 0.0)) return bad("delta must be >= 0");
+    if (!(k.dt >= 0.0)) return bad("dt must be >= 0");
+    if (k.band != 0 && k.band != 1) return bad("band must be 0 or 1");
+    if (k.energy_R < 1 || k.energy_R > kMaxR) return bad("energy_R must be in 1..8");
+    if (k.stop_k < 1 || k.max_iters < 1 || k.min_iters < 0) return bad("bad stop parameters");
+    if (k.max_iters >= kHist - 1) return bad("max_iters too large");
+    if (!(k.c_sing >= 0.0)) return bad("c_sing must be >= 0");
+    c->h = h;
+    c->dt = k.dt > 0.0 ? k.dt : h / 4.0;
+    c->gamma = k.gamma > 0.0 ? k.gamma : (k.dim == 2 ? 4.0 : 6.0) * h;
+    c->beta = k.beta > 0.0 ? k.beta : (k.dim == 2 ? 2.0 : 3.0) * h;
+    if (!(c->beta < c->gamma)) return bad("beta must be smaller than gamma");
+    c->N = N;
+    c->ncells_all = (k.n[0] - 1) * (k.n[1] - 1) * (k.dim == 3 ? (k.n[2] - 1) : 1);
+    c->tsize = k.precision == 32 ? 4 : 8;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->al = *alloc;
+        c->default_alloc = false;
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SLR_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms <= 0) c->num_sms = 1;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return SLR_E_CUDA;
+        }
+        c->own_stream = true;
+    }
+    if (cudaMallocHost((void**)&c->host_pinned_flags, 64) != cudaSuccess) {
+        cudaGetLastError();
+        slr_destroy(c);
+        return SLR_E_CUDA;
+    }
+    c->u[0] = dev_alloc(c, c->tsize * N);
+    c->u[1] = dev_alloc(c, c->tsize * N);
+    c->d = dev_alloc(c, c->tsize * N);
+    c->argmin = (int*)dev_alloc(c, sizeof(int) * N);
+    c->ds = (DevState*)dev_alloc(c, sizeof(DevState));
+    if (!c->u[0] || !c->u[1] || !c->d || !c->argmin || !c->ds) {
+        slr_destroy(c);
+        return SLR_E_NOMEM;
+    }
+    if (cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->argmin, 0xff, sizeof(int) * N, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        slr_destroy(c);
+        return SLR_E_CUDA;
+    }
+    if (!k.band) {
+        long long tiles = (N + kStepTile - 1) / kStepTile;
+        c->part_dphi = (double*)dev_alloc(c, sizeof(double) * tiles);
+        c->n_tiles_cap = tiles;
+        if (!c->part_dphi || size_energy_buffers(c, c->ncells_all) != SLR_OK) {
+            slr_destroy(c);
+            return SLR_E_NOMEM;
+        }
+    }
+    *out = c;
+    return SLR_OK;
+}
+
+slr_status slr_load_cloud(slr_ctx* c, const double* xyz, int64_t n_points) {
+    if (!c) return SLR_E_INVALID;
+    if (!xyz || n_points < 1) return fail(c, SLR_E_INVALID, "load_cloud: need at least one point");
+    if (n_points > 2147483647ll) return fail(c, SLR_E_INVALID, "load_cloud: at most 2^31-1 points");
+    DeviceGuard g(c->device);
+    release_t(c, c->pts);
+    size_t bytes = sizeof(double) * (size_t)c->cfg.dim * (size_t)n_points;
+    c->pts = (double*)dev_alloc(c, bytes);
+    if (!c->pts) return fail(c, SLR_E_NOMEM, "load_cloud: allocation failed");
+    CK(cudaMemcpyAsync(c->pts, xyz, bytes, cudaMemcpyHostToDevice, c->stream), "load_cloud copy");
+    CK(cudaStreamSynchronize(c->stream), "load_cloud sync");
+    c->npts = n_points;
+    c->have_cloud = true;
+    return SLR_OK;
+}
+
+slr_status slr_build_distance(slr_ctx* c) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_cloud) return fail(c, SLR_E_STATE, "build_distance: no cloud loaded");
+    DeviceGuard g(c->device);
+    cudaError_t e = build_distance(c);
+    if (e == cudaErrorInvalidValue) return fail(c, SLR_E_INVALID, "build_distance: non-finite point coordinates");
+    if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "build_distance: scratch allocation failed");
+    if (e != cudaSuccess) return cuda_fail(c, e, "build_distance");
+    c->have_d = true;
+    return SLR_OK;
+}
+
+slr_status slr_set_distance(slr_ctx* c, const double* d_host) {
+    if (!c) return SLR_E_INVALID;
+    if (!d_host) return fail(c, SLR_E_INVALID, "set_distance: null array");
+    DeviceGuard g(c->device);
+    double* tmp = (double*)dev_alloc(c, sizeof(double) * c->N);
+    if (!tmp) return fail(c, SLR_E_NOMEM, "set_distance: staging allocation failed");
+    cudaError_t e = cudaMemcpyAsync(tmp, d_host, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_from_double(c, tmp, c->d, c->N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->argmin, 0xff, sizeof(int) * c->N, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_distance");
+    c->have_d = true;
+    return SLR_OK;
+}
+
+slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* u0_host) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_d) return fail(c, SLR_E_STATE, "init_u: distance field not set");
+    if (kind == 0 && !params) return fail(c, SLR_E_INVALID, "init_u: sphere needs {cx,cy,cz,r}");
+    if (kind == 1 && !u0_host) return fail(c, SLR_E_INVALID, "init_u: array needs u0_host");
+    if (kind != 0 && kind != 1) return fail(c, SLR_E_INVALID, "init_u: kind must be 0 or 1");
+    DeviceGuard g(c->device);
+    free_graphs(c);
+    c->have_u = false;
+    double* tmp = nullptr;
+    double prm[4] = {0, 0, 0, 0};
+    if (kind == 0)
+        for (int a = 0; a < 4; ++a) prm[a] = params[a];
+    if (kind == 1) {
+        tmp = (double*)dev_alloc(c, sizeof(double) * c->N);
+        if (!tmp) return fail(c, SLR_E_NOMEM, "init_u: staging allocation failed");
+        cudaError_t e = cudaMemcpyAsync(tmp, u0_host, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            dev_free(c, tmp);
+            return cuda_fail(c, e, "init_u copy");
+        }
+    }
+    cudaError_t e = launch_init_u(c, kind, prm, tmp);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init_u");
+    if (c->cfg.band) {
+        long long cnt = 0;
+        CK(launch_count_band(c, &cnt), "init_u band count");
+        slr_status s = size_band_buffers(c, cnt);
+        if (s != SLR_OK) return s;
+        CK(launch_build_band(c), "init_u band list");
+        int ci = (int)cnt;
+        CK(cudaMemcpyAsync(&c->ds->band_count[0], &ci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
+        long long nc = 0;
+        CK(launch_build_ecells(c, &nc, false), "init_u cell count");
+        release_t(c, c->ecells);
+        c->ecells = (int*)dev_alloc(c, sizeof(int) * (nc > 0 ? nc : 1));
+        if (!c->ecells) return fail(c, SLR_E_NOMEM, "init_u: cell list allocation failed");
+        c->n_ecells = nc;
+        CK(launch_build_ecells(c, &nc, true), "init_u cell list");
+        s = size_energy_buffers(c, c->n_ecells);
+        if (s != SLR_OK) return s;
+    }
+    CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
+    CK(cudaStreamSynchronize(c->stream), "init_u sync");
+    c->have_u = true;
+    return SLR_OK;
+}
+
+slr_status slr_step(slr_ctx* c, int n_steps, double energy_override) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "step: initial level set not set");
+    if (n_steps < 0) return fail(c, SLR_E_INVALID, "step: negative step count");
+    DeviceGuard g(c->device);
+    double ov = energy_override >= 0.0 ? energy_override : -1.0;
+    if (!c->g_step || c->g_step_override != ov) {
+        if (c->g_step) cudaGraphExecDestroy(c->g_step);
+        c->g_step = nullptr;
+        slr_status s = capture_step(c, ov, 0, &c->g_step);
+        if (s != SLR_OK) return s;
+        c->g_step_override = ov;
+    }
+    CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "step");
+    for (int i = 0; i < n_steps; ++i) {
+        CK(cudaGraphLaunch(c->g_step, c->stream), "cudaGraphLaunch");
+        c->launches += kKernelsPerIteration;
+    }
+    CK(cudaStreamSynchronize(c->stream), "step sync");
+    return check_device_error(c);
+}
+
+slr_status slr_evolve(slr_ctx* c, int* iters_out, int* converged_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "evolve: initial level set not set");
+    DeviceGuard g(c->device);
+    if (!c->g_evolve) {
+        slr_status s = capture_step(c, -1.0, 1, &c->g_evolve);
+        if (s != SLR_OK) return s;
+    }
+    CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "evolve");
+    CK(cudaMemsetAsync(&c->ds->converged, 0, sizeof(int), c->stream), "evolve");
+    int stop = 0, err = 0, n = 0;
+    int guard = 0;
+    while (!stop) {
+        for (int i = 0; i < kChunk; ++i) {
+            CK(cudaGraphLaunch(c->g_evolve, c->stream), "cudaGraphLaunch");
+            c->launches += kKernelsPerIteration;
+        }
+        slr_status s = read_status(c, &stop, &err, &n);
+        if (s != SLR_OK) return s;
+        if (err & kErrLookback) return fail(c, SLR_E_TIMEOUT, "band compaction look-back wait timed out");
+        guard += kChunk;
+        if (guard > c->cfg.max_iters + 2 * kChunk && !stop)
+            return fail(c, SLR_E_STATE, "evolve: stop flag never set");
+    }
+    int conv = 0;
+    CK(cudaMemcpyAsync(c->host_pinned_flags + 3, &c->ds->converged, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "evolve");
+    CK(cudaStreamSynchronize(c->stream), "evolve sync");
+    conv = c->host_pinned_flags[3];
+    if (iters_out) *iters_out = n;
+    if (converged_out) *converged_out = conv;
+    return SLR_OK;
+}
+
+slr_status slr_extract(slr_ctx* c, double width, int64_t* idx, double* u, int64_t cap, int64_t* n_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "extract: no level set");
+    if (!(width > 0.0)) return fail(c, SLR_E_INVALID, "extract: width must be > 0");
+    DeviceGuard g(c->device);
+    long long cnt = 0;
+    CK(launch_extract(c, width, nullptr, nullptr, &cnt, false), "extract count");
+    if (n_out) *n_out = cnt;
+    if (!idx && !u) return SLR_OK;
+    if (cnt > cap) return fail(c, SLR_E_CAPACITY, "extract: buffer too small");
+    if (cnt == 0) return SLR_OK;
+    long long* di = (long long*)dev_alloc(c, sizeof(long long) * cnt);
+    double* dv = (double*)dev_alloc(c, sizeof(double) * cnt);
+    if (!di || !dv) {
+        dev_free(c, di);
+        dev_free(c, dv);
+        return fail(c, SLR_E_NOMEM, "extract: allocation failed");
+    }
+    cudaError_t e = launch_extract(c, width, di, dv, &cnt, true);
+    if (e == cudaSuccess && idx)
+        e = cudaMemcpyAsync(idx, di, sizeof(long long) * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, dv, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, di);
+    dev_free(c, dv);
+    if (e != cudaSuccess) return cuda_fail(c, e, "extract");
+    return SLR_OK;
+}
+
+slr_status slr_get_field(slr_ctx* c, int which, void* host_out, int64_t cap) {
+    if (!c) return SLR_E_INVALID;
+    if (!host_out) return fail(c, SLR_E_INVALID, "get_field: null buffer");
+    if (cap < c->N) return fail(c, SLR_E_CAPACITY, "get_field: buffer smaller than the grid");
+    DeviceGuard g(c->device);
+    if (which == SLR_FIELD_ARGMIN) {
+        CK(cudaMemcpyAsync(host_out, c->argmin, sizeof(int) * c->N, cudaMemcpyDeviceToHost, c->stream), "get_field");
+        CK(cudaStreamSynchronize(c->stream), "get_field");
+        return SLR_OK;
+    }
+    if (which != SLR_FIELD_U && which != SLR_FIELD_D) return fail(c, SLR_E_INVALID, "get_field: unknown field");
+    const void* src = c->d;
+    if (which == SLR_FIELD_U) {
+        int n = 0;
+        slr_status s = read_status(c, nullptr, nullptr, &n);
+        if (s != SLR_OK) return s;
+        src = c->u[n & 1];
+    }
+    double* tmp = (double*)dev_alloc(c, sizeof(double) * c->N);
+    if (!tmp) return fail(c, SLR_E_NOMEM, "get_field: staging allocation failed");
+    cudaError_t e = launch_to_double(c, src, tmp, c->N);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_field");
+    return SLR_OK;
+}
+
+slr_status slr_get_band(slr_ctx* c, int64_t* idx, int64_t cap, int64_t* n_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "get_band: no level set");
+    DeviceGuard g(c->device);
+    if (!c->cfg.band) {
+        if (n_out) *n_out = c->N;
+        if (!idx) return SLR_OK;
+        if (cap < c->N) return fail(c, SLR_E_CAPACITY, "get_band: buffer too small");
+        for (long long i = 0; i < c->N; ++i) idx[i] = i;
+        return SLR_OK;
+    }
+    int n = 0;
+    slr_status s = read_status(c, nullptr, nullptr, &n);
+    if (s != SLR_OK) return s;
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream), "get_band");
+    CK(cudaStreamSynchronize(c->stream), "get_band");
+    if (n_out) *n_out = cnt;
+    if (!idx) return SLR_OK;
+    if (cnt > cap) return fail(c, SLR_E_CAPACITY, "get_band: buffer too small");
+    int* tmp = (int*)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
+    if (!tmp) return fail(c, SLR_E_NOMEM, "get_band: host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(tmp, c->band[n & 1], sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess)
+        for (int i = 0; i < cnt; ++i) idx[i] = tmp[i];
+    free(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_band");
+    return SLR_OK;
+}
+
+slr_status slr_energy(slr_ctx* c, double p, double* E_out, double* sum_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "energy: no level set");
+    if (!(p >= 1.0)) return fail(c, SLR_E_INVALID, "energy: p must be >= 1");
+    DeviceGuard g(c->device);
+    CK(launch_energy(c, 0, p, 2, 0), "energy");
+    double rep[2] = {0, 0};
+    CK(cudaMemcpyAsync(rep, c->part_e + 2 * c->n_echunks, sizeof(rep), cudaMemcpyDeviceToHost, c->stream), "energy");
+    CK(cudaStreamSynchronize(c->stream), "energy");
+    if (sum_out) *sum_out = rep[0];
+    if (E_out) *E_out = pow(rep[0], 1.0 / p);
+    return SLR_OK;
+}
+
+slr_status slr_diagnostics(slr_ctx* c, double* e2_hist, double* dphi_hist, int64_t* band_hist, int cap, int* n_out,
+                           double* err_cloud) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "diagnostics: no level set");
+    DeviceGuard g(c->device);
+    DevState* h = (DevState*)malloc(sizeof(DevState));
+    if (!h) return fail(c, SLR_E_NOMEM, "diagnostics: host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free(h);
+        return cuda_fail(c, e, "diagnostics");
+    }
+    int n = h->n;
+    if (n_out) *n_out = n;
+    int first = n + 1 > kHist ? n + 1 - kHist : 0;
+    for (int i = 0; i <= n && i - first < cap; ++i) {
+        if (i < first) continue;
+        if (e2_hist) e2_hist[i - first] = h->e2_hist[i % kHist];
+        if (i < n) {
+            if (dphi_hist) dphi_hist[i - first] = h->dphi_hist[i % kHist];
+            if (band_hist) band_hist[i - first] = h->band_hist[i % kHist];
+        }
+    }
+    free(h);
+    if (err_cloud) {
+        if (!c->have_cloud) return fail(c, SLR_E_STATE, "diagnostics: Err_S needs the cloud");
+        double* dv = (double*)dev_alloc(c, sizeof(double));
+        if (!dv) return fail(c, SLR_E_NOMEM, "diagnostics: allocation failed");
+        cudaError_t e2 = launch_err_cloud(c, dv);
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(err_cloud, dv, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
+        dev_free(c, dv);
+        if (e2 != cudaSuccess) return cuda_fail(c, e2, "Err_S");
+    }
+    return SLR_OK;
+}
+
+// checkpoint layout: header, config, DevState, band list, cell list, u, d, argmin
+struct StateHeader {
+    uint32_t magic;
+    uint32_t tsize;
+    int64_t N;
+    int64_t band_count;
+    int64_t n_ecells;
+};
+
+slr_status slr_export_state(slr_ctx* c, void* buf, int64_t cap, int64_t* n_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "export_state: no level set");
+    DeviceGuard g(c->device);
+    int n = 0;
+    slr_status s = read_status(c, nullptr, nullptr, &n);
+    if (s != SLR_OK) return s;
+    int cnt = 0;
+    if (c->cfg.band) {
+        CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream), "export");
+        CK(cudaStreamSynchronize(c->stream), "export");
+    }
+    StateHeader hd{kStateMagic, (uint32_t)c->tsize, c->N, cnt, c->cfg.band ? c->n_ecells : 0};
+    size_t need = sizeof(hd) + sizeof(slr_config) + sizeof(DevState) + sizeof(int) * (size_t)cnt +
+                  sizeof(int) * (size_t)hd.n_ecells + c->tsize * 2 * c->N + sizeof(int) * c->N;
+    if (n_out) *n_out = (int64_t)need;
+    if (!buf || cap < (int64_t)need) return fail(c, SLR_E_CAPACITY, "export_state: buffer too small");
+    char* p = (char*)buf;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    memcpy(p, &c->cfg, sizeof(slr_config));
+    p += sizeof(slr_config);
+    CK(cudaMemcpyAsync(p, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "export");
+    p += sizeof(DevState);
+    if (cnt) CK(cudaMemcpyAsync(p, c->band[n & 1], sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream), "export");
+    p += sizeof(int) * cnt;
+    if (hd.n_ecells)
+        CK(cudaMemcpyAsync(p, c->ecells, sizeof(int) * hd.n_ecells, cudaMemcpyDeviceToHost, c->stream), "export");
+    p += sizeof(int) * hd.n_ecells;
+    CK(cudaMemcpyAsync(p, c->u[n & 1], c->tsize * c->N, cudaMemcpyDeviceToHost, c->stream), "export");
+    p += c->tsize * c->N;
+    CK(cudaMemcpyAsync(p, c->d, c->tsize * c->N, cudaMemcpyDeviceToHost, c->stream), "export");
+    p += c->tsize * c->N;
+    CK(cudaMemcpyAsync(p, c->argmin, sizeof(int) * c->N, cudaMemcpyDeviceToHost, c->stream), "export");
+    CK(cudaStreamSynchronize(c->stream), "export");
+    return SLR_OK;
+}
+
+slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
+    if (!c) return SLR_E_INVALID;
+    if (!buf || nbytes < (int64_t)(sizeof(StateHeader) + sizeof(slr_config)))
+        return fail(c, SLR_E_INVALID, "import_state: buffer too small");
+    DeviceGuard g(c->device);
+    const char* p = (const char*)buf;
+    StateHeader hd;
+    memcpy(&hd, p, sizeof(hd));
+    p += sizeof(hd);
+    slr_config cfg;
+    memcpy(&cfg, p, sizeof(cfg));
+    p += sizeof(cfg);
+    if (hd.magic != kStateMagic || hd.tsize != c->tsize || hd.N != c->N || !same_config(cfg, c->cfg))
+        return fail(c, SLR_E_INVALID, "import_state: state of a different configuration");
+    size_t need = sizeof(hd) + sizeof(slr_config) + sizeof(DevState) + sizeof(int) * (size_t)hd.band_count +
+                  sizeof(int) * (size_t)hd.n_ecells + c->tsize * 2 * c->N + sizeof(int) * c->N;
+    if (nbytes < (int64_t)need) return fail(c, SLR_E_INVALID, "import_state: truncated buffer");
+    free_graphs(c);
+    DevState* hds = (DevState*)malloc(sizeof(DevState));
+    if (!hds) return fail(c, SLR_E_NOMEM, "import_state: host allocation failed");
+    memcpy(hds, p, sizeof(DevState));
+    p += sizeof(DevState);
+    const int n = hds->n;
+    if (c->cfg.band) {
+        slr_status s = size_band_buffers(c, hd.band_count);
+        if (s == SLR_OK) {
+            release_t(c, c->ecells);
+            c->ecells = (int*)dev_alloc(c, sizeof(int) * (hd.n_ecells > 0 ? hd.n_ecells : 1));
+            c->n_ecells = hd.n_ecells;
+            if (!c->ecells) s = fail(c, SLR_E_NOMEM, "import_state: allocation failed");
+        }
+        if (s == SLR_OK) s = size_energy_buffers(c, c->n_ecells);
+        if (s != SLR_OK) {
+            free(hds);
+            return s;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(c->ds, hds, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    free(hds);
+    if (e != cudaSuccess) return cuda_fail(c, e, "import_state");
+    if (hd.band_count)
+        CK(cudaMemcpyAsync(c->band[n & 1], p, sizeof(int) * hd.band_count, cudaMemcpyHostToDevice, c->stream),
+           "import");
+    p += sizeof(int) * hd.band_count;
+    if (hd.n_ecells)
+        CK(cudaMemcpyAsync(c->ecells, p, sizeof(int) * hd.n_ecells, cudaMemcpyHostToDevice, c->stream), "import");
+    p += sizeof(int) * hd.n_ecells;
+    CK(cudaMemcpyAsync(c->u[0], p, c->tsize * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    CK(cudaMemcpyAsync(c->u[1], p, c->tsize * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    p += c->tsize * c->N;
+    CK(cudaMemcpyAsync(c->d, p, c->tsize * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    p += c->tsize * c->N;
+    CK(cudaMemcpyAsync(c->argmin, p, sizeof(int) * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    CK(cudaStreamSynchronize(c->stream), "import");
+    c->have_d = true;
+    c->have_u = true;
+    return SLR_OK;
+}
+
+int64_t slr_kernel_launches(const slr_ctx* c) { return c ? c->launches : 0; }
+
+const char* slr_last_error(const slr_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void slr_destroy(slr_ctx* c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_graphs(c);
+    release(c, c->u[0]);
+    release(c, c->u[1]);
+    release(c, c->d);
+    release_t(c, c->argmin);
+    release_t(c, c->pts);
+    release_t(c, c->band[0]);
+    release_t(c, c->band[1]);
+    release_t(c, c->ecells);
+    release_t(c, c->part_dphi);
+    release_t(c, c->part_e);
+    release_t(c, c->tile_status);
+    release_t(c, c->ds);
+    if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+    delete c;
+}
+
+}  // extern "C"

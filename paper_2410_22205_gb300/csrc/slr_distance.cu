@@ -1,0 +1,513 @@
+// Exact distance grid d(x_j) = min_Q |x_j - Q| with argmin (arXiv 2410.22205,
+// §2 and §3.4; the paper computes exact values only near the cloud and fast
+// sweeping elsewhere — here every node gets the exact value).
+//
+//  1. bounding box of the cloud (order-preserving integer atomics);
+//  2. Morton code of each point's bin on a 2^L-per-axis bin grid over the
+//     box, counting sort of the points by code (count, scan, scatter), so
+//     consecutive points are spatially close;
+//  3. a 32-ary box hierarchy over the sorted points: a leaf box per 32
+//     consecutive points, a box per 32 consecutive boxes above, up to a top
+//     level of at most 32 boxes;
+//  4. one warp per tile of 32 grid nodes (4x4x2 in 3-D, 8x4 in 2-D): a
+//     depth-first walk of the hierarchy, nearest child first, pruning boxes
+//     farther from the tile than the warp's worst current best. At the leaves
+//     each lane screens the 32 points in FP32 and re-checks in FP64 — with the
+//     oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 + (z-qz)^2 without
+//     contraction — every point whose FP32 distance is within a safety
+//     margin of its best. Ties go to the lowest point index.
+// The FP32 screen only discards points whose true distance exceeds the
+// lane's best by more than the FP32 error bound (margin 1e-6 x (extent + d),
+// ~10x the worst rounding), so the FP64 decision is exact.
+#include "slr_compact.cuh"
+#include "slr_internal.cuh"
+
+namespace slr {
+
+template <typename T>
+Params<T> make_params(const slr_ctx* c);
+
+constexpr int kMaxLevels = 8;
+constexpr int kStack = 256;
+
+__device__ __forceinline__ unsigned long long enc_double(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__host__ __device__ inline double dec_double(unsigned long long e) {
+    unsigned long long b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    double x;
+    memcpy(&x, &b, sizeof(double));
+    return x;
+}
+
+// bbox[0..2] = min, bbox[3..5] = max (encoded); flag[0] = non-finite seen
+__global__ void k_bbox(const double* pts, long long npts, int dim, unsigned long long* bbox, int* flag) {
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    int bad = 0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += (long long)gridDim.x * blockDim.x)
+        for (int a = 0; a < dim; ++a) {
+            double v = pts[q * dim + a];
+            if (!isfinite(v)) {
+                bad = 1;
+                continue;
+            }
+            unsigned long long e = enc_double(v);
+            mn[a] = e < mn[a] ? e : mn[a];
+            mx[a] = e > mx[a] ? e : mx[a];
+        }
+    for (int a = 0; a < dim; ++a) {
+        atomicMin(&bbox[a], mn[a]);
+        atomicMax(&bbox[3 + a], mx[a]);
+    }
+    if (bad) atomicOr(flag, 1);
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned spread2(unsigned v) {  // 16 bits -> every second bit
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+struct BinArgs {
+    double bmin[3];
+    double inv_bin;
+    int L;
+    int dim;
+};
+
+__global__ void k_codes(const double* pts, long long npts, BinArgs B, unsigned* codes, int* counts) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npts) return;
+    unsigned b[3] = {0, 0, 0};
+    const int top = (1 << B.L) - 1;
+    for (int a = 0; a < B.dim; ++a) {
+        double t = (pts[q * B.dim + a] - B.bmin[a]) * B.inv_bin;
+        int v = (int)floor(t);
+        b[a] = (unsigned)(v < 0 ? 0 : (v > top ? top : v));
+    }
+    unsigned code = B.dim == 3 ? (spread3(b[0]) | (spread3(b[1]) << 1) | (spread3(b[2]) << 2))
+                               : (spread2(b[0]) | (spread2(b[1]) << 1));
+    codes[q] = code;
+    atomicAdd(&counts[code], 1);
+}
+
+// exclusive scan of an int array, 4096 items per block
+__global__ void __launch_bounds__(1024) k_scan_blocks(int* a, long long M, int* tot) {
+    __shared__ int s[1024];
+    long long beg = (long long)blockIdx.x * 4096 + threadIdx.x * 4;
+    int v[4], local = 0;
+    for (int i = 0; i < 4; ++i) {
+        v[i] = beg + i < M ? a[beg + i] : 0;
+        local += v[i];
+    }
+    s[threadIdx.x] = local;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int x = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += x;
+        __syncthreads();
+    }
+    int run = threadIdx.x ? s[threadIdx.x - 1] : 0;
+    for (int i = 0; i < 4; ++i) {
+        if (beg + i < M) a[beg + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 1023) tot[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_add(int* a, long long M, const int* tot) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) a[i] += tot[i / 4096];
+}
+
+__global__ void k_scatter(const double* pts, long long npts, int dim, const unsigned* codes, int* offsets,
+                          double o0, double o1, double o2, float4* spt) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npts) return;
+    int pos = atomicAdd(&offsets[codes[q]], 1);
+    float4 r;
+    r.x = (float)(pts[q * dim + 0] - o0);
+    r.y = (float)(pts[q * dim + 1] - o1);
+    r.z = dim == 3 ? (float)(pts[q * dim + 2] - o2) : 0.0f;
+    r.w = __int_as_float((int)q);
+    spt[pos] = r;
+}
+
+// one warp per box of level `lvl` (children: points at level 0, boxes above)
+__global__ void k_boxes(const float4* spt, long long npts, float4* blo, float4* bhi, long long child_off,
+                        long long child_cnt, long long own_off, long long own_cnt, int lvl) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (w >= own_cnt) return;
+    long long ch = w * 32 + lane;
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+    if (lvl == 0) {
+        if (ch < npts) {
+            float4 p = spt[ch];
+            lx = hx = p.x;
+            ly = hy = p.y;
+            lz = hz = p.z;
+        }
+    } else if (ch < child_cnt) {
+        float4 a = blo[child_off + ch], b = bhi[child_off + ch];
+        lx = a.x; ly = a.y; lz = a.z;
+        hx = b.x; hy = b.y; hz = b.z;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+    }
+    if (lane == 0) {
+        blo[own_off + w] = make_float4(lx, ly, lz, 0.f);
+        bhi[own_off + w] = make_float4(hx, hy, hz, 0.f);
+    }
+}
+
+struct SearchArgs {
+    int n0, n1, n2;
+    int tx, ty, tz;        // tiles per axis
+    double lo0, lo1, lo2, h;
+    const float4* spt;
+    const double* pts;
+    long long npts;
+    const float4* blo;
+    const float4* bhi;
+    int nlevels;
+    long long off[kMaxLevels];
+    long long cnt[kMaxLevels];
+    double extent;         // coordinate extent used in the FP32 error margin
+    int* flag;             // bit 2: traversal stack overflow
+};
+
+__device__ __forceinline__ float box_dist2(float tlx, float tly, float tlz, float thx, float thy, float thz,
+                                           float4 lo, float4 hi) {
+    float gx = fmaxf(0.f, fmaxf(lo.x - thx, tlx - hi.x));
+    float gy = fmaxf(0.f, fmaxf(lo.y - thy, tly - hi.y));
+    float gz = fmaxf(0.f, fmaxf(lo.z - thz, tlz - hi.z));
+    return gx * gx + gy * gy + gz * gz;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_minf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int* aout) {
+    __shared__ int s_stack[8][kStack];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long ntiles = (long long)A.tx * A.ty * A.tz;
+    if (tile >= ntiles) return;
+    int* stack = s_stack[wib];
+    int ti = (int)(tile % A.tx);
+    long long r = tile / A.tx;
+    int tj = (int)(r % A.ty);
+    int tk = (int)(r / A.ty);
+    int i, j, k;
+    if (DIM == 3) {
+        i = ti * 4 + (lane & 3);
+        j = tj * 4 + ((lane >> 2) & 3);
+        k = tk * 2 + (lane >> 4);
+    } else {
+        i = ti * 8 + (lane & 7);
+        j = tj * 4 + (lane >> 3);
+        k = 0;
+    }
+    const bool valid = i < A.n0 && j < A.n1 && k < A.n2;
+    i = i < A.n0 ? i : A.n0 - 1;
+    j = j < A.n1 ? j : A.n1 - 1;
+    k = k < A.n2 ? k : A.n2 - 1;
+    // exact node coordinates (lo + i*h, no contraction) and FP32 offsets from lo
+    const double x = __dadd_rn(A.lo0, __dmul_rn((double)i, A.h));
+    const double y = __dadd_rn(A.lo1, __dmul_rn((double)j, A.h));
+    const double z = DIM == 3 ? __dadd_rn(A.lo2, __dmul_rn((double)k, A.h)) : 0.0;
+    const float xf = (float)(x - A.lo0), yf = (float)(y - A.lo1), zf = DIM == 3 ? (float)(z - A.lo2) : 0.f;
+    const float tlx = warp_minf(xf), tly = warp_minf(yf), tlz = warp_minf(zf);
+    const float thx = warp_maxf(xf), thy = warp_maxf(yf), thz = warp_maxf(zf);
+    const double mscale = 1e-6;
+
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+    float thr = INFINITY;  // squared FP32 screen
+    float wb2 = INFINITY;  // squared warp bound
+
+    int sp = 0;
+    {
+        const int top = A.nlevels - 1;
+        long long c = lane;
+        bool ex = c < A.cnt[top];
+        float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[top] + c], A.bhi[A.off[top] + c]) : INFINITY;
+        unsigned m = __ballot_sync(0xffffffffu, ex);
+        int np = __popc(m);
+        int rank = 0;
+        for (int s = 0; s < 32; ++s) {
+            float o = __shfl_sync(0xffffffffu, d2, s);
+            bool oex = (m >> s) & 1u;
+            if (oex && (o < d2 || (o == d2 && s < lane))) ++rank;
+        }
+        if (ex) stack[np - 1 - rank] = (top << 27) | (int)c;
+        sp = np;
+        __syncwarp();
+    }
+    while (sp > 0) {
+        --sp;
+        const int ent = stack[sp];
+        __syncwarp();
+        const int lvl = ent >> 27;
+        const long long id = ent & ((1 << 27) - 1);
+        const float bd2 = box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]);
+        if (bd2 > wb2) continue;
+        if (lvl == 0) {
+            const long long base = id * 32;
+            long long rem = A.npts - base;
+            const int cnt = rem < 32 ? (int)rem : 32;
+            float4 mine = lane < cnt ? A.spt[base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int s = 0; s < cnt; ++s) {
+                const float px = __shfl_sync(0xffffffffu, mine.x, s);
+                const float py = __shfl_sync(0xffffffffu, mine.y, s);
+                const float pz = __shfl_sync(0xffffffffu, mine.z, s);
+                const int pid = __float_as_int(__shfl_sync(0xffffffffu, mine.w, s));
+                const float dx = xf - px, dy = yf - py, dz = zf - pz;
+                const float d2f = dx * dx + dy * dy + dz * dz;
+                if (d2f <= thr) {
+                    const double* Q = A.pts + (long long)pid * DIM;
+                    const double ex = __dsub_rn(x, Q[0]);
+                    const double ey = __dsub_rn(y, Q[1]);
+                    double s2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+                    if (DIM == 3) {
+                        const double ez = __dsub_rn(z, Q[2]);
+                        s2 = __dadd_rn(s2, __dmul_rn(ez, ez));
+                    }
+                    if (s2 < best || (s2 == best && pid < bi)) {
+                        best = s2;
+                        bi = pid;
+                        const double bdist = sqrt(s2);
+                        const double lim = bdist + mscale * (A.extent + bdist);
+                        thr = (float)(lim * lim) * 1.00001f;
+                    }
+                }
+            }
+            const float mine_b = best < INFINITY ? (float)(sqrt(best) + mscale * (A.extent + sqrt(best))) * 1.00001f
+                                                 : INFINITY;
+            const float wb = warp_maxf(mine_b);
+            wb2 = wb * wb;
+        } else {
+            const int cl = lvl - 1;
+            const long long c = id * 32 + lane;
+            const bool ex = c < A.cnt[cl];
+            float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[cl] + c], A.bhi[A.off[cl] + c])
+                          : INFINITY;
+            const bool pass = ex && d2 <= wb2;
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            const int np = __popc(m);
+            if (sp + np > kStack) {
+                if (lane == 0) atomicOr(A.flag, 4);
+                break;
+            }
+            int rank = 0;
+            for (int s = 0; s < 32; ++s) {
+                const float o = __shfl_sync(0xffffffffu, d2, s);
+                if (((m >> s) & 1u) && (o < d2 || (o == d2 && s < lane))) ++rank;
+            }
+            if (pass) stack[sp + np - 1 - rank] = (cl << 27) | (int)c;
+            sp += np;
+            __syncwarp();
+        }
+    }
+    if (valid) {
+        const long long idx = (long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k);
+        dout[idx] = (T)sqrt(best);
+        aout[idx] = bi;
+    }
+}
+
+template <typename T, int DIM>
+static void launch_search(slr_ctx* c, const SearchArgs& A) {
+    long long ntiles = (long long)A.tx * A.ty * A.tz;
+    long long blocks = (ntiles * 32 + 255) / 256;
+    k_dist_search<T, DIM><<<(unsigned)blocks, 256, 0, c->stream>>>(A, (T*)c->d, c->argmin);
+    c->launches += 1;
+}
+
+cudaError_t build_distance(slr_ctx* c) {
+    const int dim = c->cfg.dim;
+    const long long npts = c->npts;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
+    // bit-grid resolution: 2^L bins per axis
+    const int L = dim == 3 ? 7 : 10;
+    const long long nbins = 1ll << (dim * L);
+    // box hierarchy sizes
+    long long cnt[kMaxLevels], off[kMaxLevels];
+    int nlevels = 0;
+    long long total_boxes = 0;
+    {
+        long long cc = (npts + 31) / 32;
+        for (;;) {
+            if (nlevels >= kMaxLevels) return cudaErrorInvalidValue;
+            cnt[nlevels] = cc;
+            off[nlevels] = total_boxes;
+            total_boxes += cc;
+            ++nlevels;
+            if (cc <= 32) break;
+            cc = (cc + 31) / 32;
+        }
+    }
+    const long long nscan_blocks = (nbins + 4095) / 4096;
+    // scratch layout
+    size_t b_bbox = 64, b_flag = 16, b_codes = sizeof(unsigned) * npts, b_counts = sizeof(int) * nbins,
+           b_tot = sizeof(int) * (nscan_blocks + 2) + 16, b_spt = sizeof(float4) * npts,
+           b_boxes = sizeof(float4) * 2 * total_boxes;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t total = al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes);
+    char* base = (char*)dev_alloc(c, total);
+    if (!base) return cudaErrorMemoryAllocation;
+    char* p = base;
+    unsigned long long* bbox = (unsigned long long*)p;
+    p += al(b_bbox);
+    int* flag = (int*)p;
+    p += al(b_flag);
+    unsigned* codes = (unsigned*)p;
+    p += al(b_codes);
+    int* counts = (int*)p;
+    p += al(b_counts);
+    int* tot = (int*)p;
+    p += al(b_tot);
+    float4* spt = (float4*)p;
+    p += al(b_spt);
+    float4* blo = (float4*)p;
+    float4* bhi = blo + total_boxes;
+
+    unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    unsigned long long hb[6];
+    int hflag = 0;
+    e = cudaMemcpyAsync(bbox, init_bbox, sizeof(init_bbox), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, b_counts, st);
+    if (e == cudaSuccess) {
+        int blocks = (int)((npts + 255) / 256);
+        if (blocks > c->num_sms * 8) blocks = c->num_sms * 8;
+        k_bbox<<<blocks, 256, 0, st>>>(c->pts, npts, dim, bbox, flag);
+        c->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(c, base);
+        return e;
+    }
+    if (hflag) {
+        dev_free(c, base);
+        return cudaErrorInvalidValue;
+    }
+    BinArgs B;
+    double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0}, ext = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        bmin[a] = dec_double(hb[a]);
+        bmax[a] = dec_double(hb[3 + a]);
+        ext = fmax(ext, bmax[a] - bmin[a]);
+    }
+    double bin = ext > 0 ? ext / (double)(1 << L) * (1.0 + 1e-9) : 1.0;
+    for (int a = 0; a < 3; ++a) B.bmin[a] = bmin[a];
+    B.inv_bin = 1.0 / bin;
+    B.L = L;
+    B.dim = dim;
+    const double o0 = c->cfg.lo[0], o1 = c->cfg.lo[1], o2 = dim == 3 ? c->cfg.lo[2] : 0.0;
+    double extent = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        double lo = c->cfg.lo[a];
+        extent = fmax(extent, fabs(c->cfg.hi[a] - lo));
+        extent = fmax(extent, fabs(bmin[a] - lo));
+        extent = fmax(extent, fabs(bmax[a] - lo));
+    }
+    {
+        int blocks = (int)((npts + 255) / 256);
+        k_codes<<<blocks, 256, 0, st>>>(c->pts, npts, B, codes, counts);
+        k_scan_blocks<<<(unsigned)nscan_blocks, 1024, 0, st>>>(counts, nbins, tot);
+        k_scan_counts<<<1, 1024, 0, st>>>(tot, (int)nscan_blocks, (long long*)(tot + ((nscan_blocks + 2) & ~1ll)));
+        k_scan_add<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, nbins, tot);
+        k_scatter<<<blocks, 256, 0, st>>>(c->pts, npts, dim, codes, counts, o0, o1, o2, spt);
+        c->launches += 5;
+        for (int l = 0; l < nlevels; ++l) {
+            long long own = cnt[l];
+            long long threads = own * 32;
+            k_boxes<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+                spt, npts, blo, bhi, l == 0 ? 0 : off[l - 1], l == 0 ? npts : cnt[l - 1], off[l], own, l);
+            c->launches += 1;
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        SearchArgs A;
+        A.n0 = (int)c->cfg.n[0];
+        A.n1 = (int)c->cfg.n[1];
+        A.n2 = (int)c->cfg.n[2];
+        if (dim == 3) {
+            A.tx = (A.n0 + 3) / 4;
+            A.ty = (A.n1 + 3) / 4;
+            A.tz = (A.n2 + 1) / 2;
+        } else {
+            A.tx = (A.n0 + 7) / 8;
+            A.ty = (A.n1 + 3) / 4;
+            A.tz = 1;
+        }
+        A.lo0 = c->cfg.lo[0];
+        A.lo1 = c->cfg.lo[1];
+        A.lo2 = dim == 3 ? c->cfg.lo[2] : 0.0;
+        A.h = c->h;
+        A.spt = spt;
+        A.pts = c->pts;
+        A.npts = npts;
+        A.blo = blo;
+        A.bhi = bhi;
+        A.nlevels = nlevels;
+        for (int l = 0; l < kMaxLevels; ++l) {
+            A.off[l] = l < nlevels ? off[l] : 0;
+            A.cnt[l] = l < nlevels ? cnt[l] : 0;
+        }
+        A.extent = extent;
+        A.flag = flag;
+        if (c->cfg.precision == 32) {
+            if (dim == 3) launch_search<float, 3>(c, A);
+            else launch_search<float, 2>(c, A);
+        } else {
+            if (dim == 3) launch_search<double, 3>(c, A);
+            else launch_search<double, 2>(c, A);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(c, base);
+    if (e == cudaSuccess && (hflag & 4)) return cudaErrorLaunchOutOfResources;
+    return e;
+}
+
+}  // namespace slr

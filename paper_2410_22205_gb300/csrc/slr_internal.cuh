@@ -1,0 +1,428 @@
+// Internal declarations of libslr: context, device state, launch wrappers
+// and the device-side numerics shared by the kernels (centred differences,
+// cut-off, tangent directions, Q1 and WENO interpolation).
+//
+// Method: Preda & Semplice, arXiv 2410.22205 (§3 numerical scheme).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/slr.h"
+
+namespace slr {
+
+// ---------------------------------------------------------------------------
+// sizes
+// ---------------------------------------------------------------------------
+constexpr int kHist = 4096;          // ring size of the per-iteration history
+constexpr int kStepBlock = 256;      // threads per block of the fused SL step
+constexpr int kStepTile = 256;       // band entries per look-back tile (1 per thread)
+constexpr int kEnergyBlock = 256;    // 8 warps; one warp per chunk of 32 candidate cells
+constexpr int kMaxR = 8;             // largest supported energy subcell count per axis
+constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: ~0.3 s with 64 ns sleeps
+
+// error bits written to DevState::error by device code
+constexpr int kErrLookback = 1;      // a look-back wait gave up
+
+// ---------------------------------------------------------------------------
+// device-resident state of one job (one allocation)
+// ---------------------------------------------------------------------------
+struct DevState {
+    int n;               // iterations completed since init
+    int stop;            // nonzero: step kernels return at entry
+    int converged;       // the Δ_E test stopped the loop
+    int error;           // kErr* bits
+    int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
+    unsigned ticket;     // tile ticket of the fused step kernel (reset by the stop kernel)
+    unsigned epoch;      // tags look-back status words; advanced once per step
+    double Ep;           // E_p(φ^n) used by step n
+    double e2_hist[kHist];
+    double dphi_hist[kHist];
+    long long band_hist[kHist];
+};
+
+// grid and scheme parameters passed by value to the kernels
+template <typename T>
+struct Params {
+    int n0, n1, n2;        // nodes per axis
+    long long s1, s2;      // strides of axes 1 and 2
+    T inv_h;               // 1/h
+    T inv_2h;              // 1/(2h)
+    T h4;                  // h^4 (WENO: ε = h^2 folded into the weights)
+    T dt;
+    T delta, p, inv_p;
+    T gamma, beta, inv_gb3;  // γ, β, 1/(γ-β)^3
+    T sing_thr;            // C Δt^α of the singular-gradient test
+    int band;              // narrow band on
+    int p_kind;            // 1: p == 1, 2: p == 2, 0: general
+};
+
+// ---------------------------------------------------------------------------
+// host-side context
+// ---------------------------------------------------------------------------
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace slr
+
+struct slr_ctx {
+    slr_config cfg;
+    slr_allocator al;
+    bool default_alloc = true;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+    double h = 0, dt = 0, gamma = 0, beta = 0;
+    long long N = 0;          // nodes
+    long long ncells_all = 0; // cells of the whole grid
+    size_t tsize = 4;         // bytes of the storage type
+
+    void* u[2] = {nullptr, nullptr};
+    void* d = nullptr;
+    int* argmin = nullptr;
+    double* pts = nullptr;
+    long long npts = 0;
+
+    int* band[2] = {nullptr, nullptr};  // band lists (capacity band_cap)
+    long long band_cap = 0;
+    int* ecells = nullptr;     // candidate cells of the energy quadrature (lower-corner node index)
+    long long n_ecells = 0;
+    double* part_dphi = nullptr;   // one per step tile
+    long long n_tiles_cap = 0;
+    double* part_e = nullptr;      // two per energy chunk
+    long long n_echunks = 0;
+    unsigned long long* tile_status = nullptr;  // look-back words of the step kernel
+    slr::DevState* ds = nullptr;
+    int* host_pinned_flags = nullptr;  // pinned host words for status readback
+
+    bool have_cloud = false, have_d = false, have_u = false;
+    std::string err;
+    long long launches = 0;
+
+    cudaGraphExec_t g_evolve = nullptr;
+    cudaGraphExec_t g_step = nullptr;
+    double g_step_override = -2.0;
+};
+
+namespace slr {
+
+// allocation through the context's allocator
+void* dev_alloc(slr_ctx* c, size_t bytes);
+void dev_free(slr_ctx* c, void* p);
+
+// kernel launch wrappers (defined in the .cu files); each returns the CUDA
+// error of the launch and adds the number of kernels it launched to *launches
+cudaError_t launch_init_u(slr_ctx* c, int kind, const double* params, const double* u0_dev);
+cudaError_t launch_count_band(slr_ctx* c, long long* count_out);
+cudaError_t launch_build_band(slr_ctx* c);
+cudaError_t launch_build_ecells(slr_ctx* c, long long* count_out, bool write);
+cudaError_t launch_step(slr_ctx* c, double energy_override, int evolve_mode);
+cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode);
+cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double* u_dev, long long* count_out,
+                           bool write);
+cudaError_t launch_err_cloud(slr_ctx* c, double* out_dev);
+cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long n);
+cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long long n);
+cudaError_t build_distance(slr_ctx* c);
+
+// ---------------------------------------------------------------------------
+// device numerics
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) {
+    return __ldg(p);
+}
+
+// §3: centred difference along one axis; one-sided first order on the
+// domain boundary (the paper is silent there).
+template <typename T>
+__device__ __forceinline__ T diff_axis(const T* __restrict__ v, long long idx, int i, int n, long long stride,
+                                       T inv_2h, T inv_h) {
+    if (i > 0 && i < n - 1) return (ld(v + idx + stride) - ld(v + idx - stride)) * inv_2h;
+    if (i == 0) return (ld(v + idx + stride) - ld(v + idx)) * inv_h;
+    return (ld(v + idx) - ld(v + idx - stride)) * inv_h;
+}
+
+// §3.8 eq. cutoff
+template <typename T>
+__device__ __forceinline__ T cutoff(const Params<T>& P, T u) {
+    T a = fabs(u);
+    if (a <= P.beta) return T(1);
+    if (a <= P.gamma) {
+        T m = a - P.gamma;
+        return m * m * (T(2) * a + P.gamma - T(3) * P.beta) * P.inv_gb3;
+    }
+    return T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T fast_div(T a, T b) {
+    return a / b;
+}
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) {
+    return __fdividef(a, b);
+}
+
+// cell index and local coordinate along one axis for a foot at node index
+// `i` plus a displacement `r` in units of h; the index-space coordinate is
+// clamped to [0, n-1] and the cell to [0, n-2].
+template <typename T>
+__device__ __forceinline__ void locate_rel(int i, T r, int n, int& c, T& t) {
+    const T big = T(4) * T(n) + T(8);
+    r = fmin(fmax(r, -big), big);
+    T f = floor(r);
+    c = i + (int)f;
+    t = r - f;
+    if (c < 0) {
+        c = 0;
+        t = T(0);
+    } else if (c >= n - 1) {
+        c = n - 2;
+        t = T(1);
+    }
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Per-axis WENO coefficients at local coordinate θ: linear weights
+// C_L = (2-θ)/3, C_R = (1+θ)/3 (eq. ckgamma) and q = θ(θ-1)/2.
+template <typename T>
+struct WenoAxis {
+    T th, q, cl, cr;
+    __device__ __forceinline__ void set(T t) {
+        th = t;
+        q = T(0.5) * t * (t - T(1));
+        cl = (T(2) - t) * T(1.0 / 3.0);
+        cr = (T(1) + t) * T(1.0 / 3.0);
+    }
+};
+
+// One-dimensional third-order WENO of §3.2 (eq. IWENO, n = 2) on the cell
+// [x_j, x_{j+1}] with data v0..v3 = v_{j-1}..v_{j+2}. Algebraically equal to
+// Σ w_k P_k with α_k = C_k/(I_k + h^2)^2 and I_k = D_k^2/h^2 (the quadratic
+// forms A_L, A_R give the squared second differences D_L, D_R):
+//   P_k(θ) = v_j + θ (v_{j+1} - v_j) + D_k θ(θ-1)/2,
+//   w_L = C_L (D_R^2 + h^4)^2 / (C_L (D_R^2 + h^4)^2 + C_R (D_L^2 + h^4)^2).
+template <typename T>
+__device__ __forceinline__ T weno1(T v0, T v1, T v2, T v3, const WenoAxis<T>& w, T h4) {
+    T dl = (v0 + v2) - (v1 + v1);
+    T dr = (v1 + v3) - (v2 + v2);
+    T sl = dl * dl + h4;
+    T sr = dr * dr + h4;
+    T gl = w.cl * (sr * sr);
+    T gr = w.cr * (sl * sl);
+    T num = gl * dl + gr * dr;
+    T den = gl + gr;
+    T lin = v1 + w.th * (v2 - v1);
+    return lin + w.q * fast_div(num, den);
+}
+
+// eq. IQ1 at node (i,j,k) + displacement r (units of h): multilinear
+// interpolation in the cell holding the foot, along x, then y, then z.
+template <typename T, int DIM>
+__device__ __forceinline__ T interp_q1(const Params<T>& P, const T* __restrict__ u, int i, int j, int k,
+                                       const T r[3]) {
+    int cx, cy, cz = 0;
+    T tx, ty, tz = T(0);
+    locate_rel(i, r[0], P.n0, cx, tx);
+    locate_rel(j, r[1], P.n1, cy, ty);
+    if (DIM == 3) locate_rel(k, r[2], P.n2, cz, tz);
+    long long b = (long long)cx + P.s1 * cy + P.s2 * cz;
+    T v00 = ld(u + b), v10 = ld(u + b + 1), v01 = ld(u + b + P.s1), v11 = ld(u + b + P.s1 + 1);
+    T a0 = v00 + tx * (v10 - v00);
+    T a1 = v01 + tx * (v11 - v01);
+    T s0 = a0 + ty * (a1 - a0);
+    if (DIM == 2) return s0;
+    long long b2 = b + P.s2;
+    T w00 = ld(u + b2), w10 = ld(u + b2 + 1), w01 = ld(u + b2 + P.s1), w11 = ld(u + b2 + P.s1 + 1);
+    T c0 = w00 + tx * (w10 - w00);
+    T c1 = w01 + tx * (w11 - w01);
+    T s1 = c0 + ty * (c1 - c0);
+    return s0 + tz * (s1 - s0);
+}
+
+// §3.2 WENO by dimension splitting: 16 lines along z, then 4 along y, then
+// 1 along x (2-D: 4 along y, then 1 along x). Stencil nodes outside the grid
+// repeat the edge node.
+template <typename T, int DIM>
+__device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict__ u, int i, int j, int k,
+                                         const T r[3]) {
+    int cx, cy, cz = 0;
+    T tx, ty, tz = T(0);
+    locate_rel(i, r[0], P.n0, cx, tx);
+    locate_rel(j, r[1], P.n1, cy, ty);
+    if (DIM == 3) locate_rel(k, r[2], P.n2, cz, tz);
+    WenoAxis<T> wx, wy, wz;
+    wx.set(tx);
+    wy.set(ty);
+    long long ox[4], oy[4], oz[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ox[a] = clampi(cx - 1 + a, 0, P.n0 - 1);
+        oy[a] = P.s1 * clampi(cy - 1 + a, 0, P.n1 - 1);
+    }
+    if (DIM == 3) {
+        wz.set(tz);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) oz[a] = P.s2 * clampi(cz - 1 + a, 0, P.n2 - 1);
+    }
+    T xv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        T yv[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            long long base = ox[a] + oy[b];
+            if (DIM == 3) {
+                T z0 = ld(u + base + oz[0]), z1 = ld(u + base + oz[1]);
+                T z2 = ld(u + base + oz[2]), z3 = ld(u + base + oz[3]);
+                yv[b] = weno1(z0, z1, z2, z3, wz, P.h4);
+            } else {
+                yv[b] = ld(u + base);
+            }
+        }
+        xv[a] = weno1(yv[0], yv[1], yv[2], yv[3], wy, P.h4);
+    }
+    return weno1(xv[0], xv[1], xv[2], xv[3], wx, P.h4);
+}
+
+template <typename T, int DIM, int INTERP>
+__device__ __forceinline__ T interp_at(const Params<T>& P, const T* __restrict__ u, int i, int j, int k,
+                                       const T r[3]) {
+    if (INTERP == 1) return interp_weno<T, DIM>(P, u, i, j, k, r);
+    return interp_q1<T, DIM>(P, u, i, j, k, r);
+}
+
+// §3.1: SL update of band node idx = (i,j,k) with value uc, before the cut.
+// Scale factor C = (d_j/E_p)^(p-1) (1 for p = 1, 0 when E_p <= 0), times the
+// cut-off c(φ_j) in band mode; feet x_j + C Δt ∇d + sqrt(C δ d Δt / p) σ λ
+// (eq. SL2d / SL3d, σ of eq. sigma2d, ν1 ν2 of eq. sigma3d with the
+// regularisation of §3.1); eq. SL:2 when |∇φ| < C_sing Δt^α.
+template <typename T, int DIM, int INTERP>
+__device__ T sl_update(const Params<T>& P, const T* __restrict__ u, const T* __restrict__ d, T Ep, int i, int j,
+                       int k, long long idx, T uc) {
+    T gx = diff_axis(u, idx, i, P.n0, 1ll, P.inv_2h, P.inv_h);
+    T gy = diff_axis(u, idx, j, P.n1, P.s1, P.inv_2h, P.inv_h);
+    T gz = DIM == 3 ? diff_axis(u, idx, k, P.n2, P.s2, P.inv_2h, P.inv_h) : T(0);
+    T gn = sqrt(gx * gx + gy * gy + gz * gz);
+    if (gn < P.sing_thr) {
+        // eq. SL:2: mean of the face neighbours inside the grid (-x,+x,-y,+y,-z,+z)
+        T s = T(0);
+        int cnt = 0;
+        if (i > 0) { s += ld(u + idx - 1); ++cnt; }
+        if (i < P.n0 - 1) { s += ld(u + idx + 1); ++cnt; }
+        if (j > 0) { s += ld(u + idx - P.s1); ++cnt; }
+        if (j < P.n1 - 1) { s += ld(u + idx + P.s1); ++cnt; }
+        if (DIM == 3) {
+            if (k > 0) { s += ld(u + idx - P.s2); ++cnt; }
+            if (k < P.n2 - 1) { s += ld(u + idx + P.s2); ++cnt; }
+        }
+        return s / T(cnt);
+    }
+    T dj = ld(d + idx);
+    T C;
+    if (P.p_kind == 1)
+        C = T(1);
+    else if (!(Ep > T(0)))
+        C = T(0);
+    else if (P.p_kind == 2)
+        C = dj / Ep;
+    else
+        C = pow(dj / Ep, P.p - T(1));
+    if (P.band) C *= cutoff(P, uc);
+    T ddx = diff_axis(d, idx, i, P.n0, 1ll, P.inv_2h, P.inv_h);
+    T ddy = diff_axis(d, idx, j, P.n1, P.s1, P.inv_2h, P.inv_h);
+    T ddz = DIM == 3 ? diff_axis(d, idx, k, P.n2, P.s2, P.inv_2h, P.inv_h) : T(0);
+    // displacements in units of h
+    T adv = C * P.dt * P.inv_h;
+    T bx = adv * ddx, by = adv * ddy, bz = adv * ddz;
+    T s = sqrt(C * P.delta * dj * P.dt * P.inv_p) * P.inv_h;
+    if (DIM == 2) {
+        T sx = gy / gn, sy = -gx / gn;  // eq. sigma2d
+        T r0[3] = {bx - s * sx, by - s * sy, T(0)};
+        T r1[3] = {bx + s * sx, by + s * sy, T(0)};
+        T a = interp_at<T, DIM, INTERP>(P, u, i, j, k, r0);
+        T b = interp_at<T, DIM, INTERP>(P, u, i, j, k, r1);
+        return (a + b) * T(0.5);
+    }
+    T n1x, n1y, n1z, n2x, n2y, n2z;
+    if (gx == T(0) && gz == T(0)) {
+        n1x = T(1); n1y = T(0); n1z = T(0);
+        n2x = T(0); n2y = T(0); n2z = T(1);
+    } else {
+        T rr = sqrt(gx * gx + gz * gz);
+        n1x = -gz / rr; n1y = T(0); n1z = gx / rr;
+        T ig = T(1) / gn;
+        n2x = ig * (-gx * gy / rr);
+        n2y = ig * rr;
+        n2z = ig * (-gy * gz / rr);
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        T l1 = (f & 2) ? T(1) : T(-1);
+        T l2 = (f & 1) ? T(1) : T(-1);
+        T r[3] = {bx + s * (l1 * n1x + l2 * n2x), by + s * (l1 * n1y + l2 * n2y), bz + s * (l1 * n1z + l2 * n2z)};
+        acc += interp_at<T, DIM, INTERP>(P, u, i, j, k, r);
+    }
+    return acc * T(0.25);
+}
+
+// ordered block compaction helpers --------------------------------------------
+
+// inclusive-exclusive prefix of one flag per thread across the block.
+// Returns the exclusive offset of this thread; *total receives the block sum.
+template <int BLOCK>
+__device__ __forceinline__ int block_exclusive_flag(int flag, int* smem_warp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned m = __ballot_sync(0xffffffffu, flag);
+    int within = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) smem_warp[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < BLOCK / 32; ++w) {
+            int c = smem_warp[w];
+            smem_warp[w] = run;
+            run += c;
+        }
+        smem_warp[BLOCK / 32] = run;
+    }
+    __syncthreads();
+    *total = smem_warp[BLOCK / 32];
+    return smem_warp[warp] + within;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// fixed-order block sum (result valid in thread 0)
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < BLOCK / 32; ++w) r += smem[w];
+    __syncthreads();
+    return r;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace slr

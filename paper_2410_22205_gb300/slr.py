@@ -1,0 +1,392 @@
+"""Python binding of libslr (include/slr.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does no
+numerical work: arrays are converted to contiguous FP64/int64 numpy buffers
+and passed by pointer; every step of the method runs in the CUDA library.
+PyTorch supplies the device memory (its caching allocator, injected through
+the slr_allocator callbacks) and the CUDA stream.
+
+There is no CPU fallback: if libslr.so is missing or fails to load,
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libslr.so")
+_lock = threading.Lock()
+_lib = None
+
+SLR_OK, SLR_E_INVALID, SLR_E_NOMEM, SLR_E_CUDA, SLR_E_TIMEOUT, SLR_E_STATE, SLR_E_CAPACITY = range(7)
+STATUS_NAMES = ["SLR_OK", "SLR_E_INVALID", "SLR_E_NOMEM", "SLR_E_CUDA", "SLR_E_TIMEOUT", "SLR_E_STATE",
+                "SLR_E_CAPACITY"]
+SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
+
+# every entry point declared in include/slr.h
+EXPORTS = [
+    "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
+    "slr_step", "slr_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
+    "slr_export_state", "slr_import_state", "slr_kernel_launches", "slr_last_error", "slr_destroy",
+]
+
+
+class SlrError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+class slr_config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("n", C.c_int64 * 3),
+        ("lo", C.c_double * 3),
+        ("hi", C.c_double * 3),
+        ("precision", C.c_int),
+        ("interp", C.c_int),
+        ("p", C.c_double),
+        ("delta", C.c_double),
+        ("dt", C.c_double),
+        ("band", C.c_int),
+        ("gamma", C.c_double),
+        ("beta", C.c_double),
+        ("c_sing", C.c_double),
+        ("alpha", C.c_double),
+        ("energy_R", C.c_int),
+        ("stop_tol", C.c_double),
+        ("stop_k", C.c_int),
+        ("min_iters", C.c_int),
+        ("max_iters", C.c_int),
+    ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class slr_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_vp, _dp, _i64p, _ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int)
+
+
+def lib():
+    """Load libslr.so (raises if it is absent: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libslr.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+            L = C.CDLL(LIB_PATH)
+            P = C.POINTER(slr_config)
+            sig = {
+                "slr_config_default": (None, [P]),
+                "slr_create": (C.c_int, [P, C.POINTER(slr_allocator), _vp, C.POINTER(_vp)]),
+                "slr_load_cloud": (C.c_int, [_vp, _dp, C.c_int64]),
+                "slr_build_distance": (C.c_int, [_vp]),
+                "slr_set_distance": (C.c_int, [_vp, _dp]),
+                "slr_init_u": (C.c_int, [_vp, C.c_int, _dp, _dp]),
+                "slr_step": (C.c_int, [_vp, C.c_int, C.c_double]),
+                "slr_evolve": (C.c_int, [_vp, _ip, _ip]),
+                "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
+                "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
+                "slr_get_band": (C.c_int, [_vp, _i64p, C.c_int64, _i64p]),
+                "slr_energy": (C.c_int, [_vp, C.c_double, _dp, _dp]),
+                "slr_diagnostics": (C.c_int, [_vp, _dp, _dp, _i64p, C.c_int, _ip, _dp]),
+                "slr_export_state": (C.c_int, [_vp, _vp, C.c_int64, _i64p]),
+                "slr_import_state": (C.c_int, [_vp, _vp, C.c_int64]),
+                "slr_kernel_launches": (C.c_int64, [_vp]),
+                "slr_last_error": (C.c_char_p, [_vp]),
+                "slr_destroy": (None, [_vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != SLR_OK:
+        msg = lib().slr_last_error(ctx)
+        raise SlrError(status, msg.decode() if msg else "")
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def slr_config_default(**overrides) -> slr_config:
+    cfg = slr_config()
+    lib().slr_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if k in ("n", "lo", "hi"):
+            v = list(v) + [1 if k == "n" else 0.0] * (3 - len(v))
+            arr = getattr(cfg, k)
+            for a in range(3):
+                arr[a] = v[a]
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class _TorchAllocator:
+    """slr_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, _user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, _user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.c_alloc = ALLOC_FN(_alloc)
+        self.c_free = FREE_FN(_free)
+        self.struct = slr_allocator(self.c_alloc, self.c_free, None)
+
+
+def slr_create(cfg: slr_config, allocator=None, stream=None):
+    """Returns an opaque context handle (int). ``allocator`` is an
+    slr_allocator (or an object with a ``.struct``), ``stream`` a raw
+    cudaStream_t value (int) or None."""
+    h = C.c_void_p()
+    al = None
+    if allocator is not None:
+        al = C.byref(allocator.struct if hasattr(allocator, "struct") else allocator)
+    st = C.c_void_p(stream) if stream else None
+    s = lib().slr_create(C.byref(cfg), al, st, C.byref(h))
+    _check(None, s)
+    return h.value
+
+
+def slr_load_cloud(ctx, xyz):
+    xyz = _f64(xyz)
+    _check(ctx, lib().slr_load_cloud(ctx, _ptr(xyz), xyz.shape[0]))
+
+
+def slr_build_distance(ctx):
+    _check(ctx, lib().slr_build_distance(ctx))
+
+
+def slr_set_distance(ctx, d):
+    d = _f64(d)
+    _check(ctx, lib().slr_set_distance(ctx, _ptr(d)))
+
+
+def slr_init_u(ctx, kind, params=None, u0=None):
+    p = _f64(params) if params is not None else None
+    u = _f64(u0) if u0 is not None else None
+    _check(ctx, lib().slr_init_u(ctx, int(kind), _ptr(p) if p is not None else None,
+                                 _ptr(u) if u is not None else None))
+
+
+def slr_step(ctx, n_steps=1, energy_override=-1.0):
+    _check(ctx, lib().slr_step(ctx, int(n_steps), float(energy_override)))
+
+
+def slr_evolve(ctx):
+    it, conv = C.c_int(0), C.c_int(0)
+    _check(ctx, lib().slr_evolve(ctx, C.byref(it), C.byref(conv)))
+    return it.value, bool(conv.value)
+
+
+def slr_extract(ctx, width):
+    n = C.c_int64(0)
+    _check(ctx, lib().slr_extract(ctx, float(width), None, None, 0, C.byref(n)))
+    idx = np.empty(max(n.value, 1), np.int64)
+    val = np.empty(max(n.value, 1), np.float64)
+    _check(ctx, lib().slr_extract(ctx, float(width), _ptr(idx, _i64p), _ptr(val), idx.size, C.byref(n)))
+    return idx[: n.value], val[: n.value]
+
+
+def slr_get_field(ctx, which, num_nodes):
+    if which == SLR_FIELD_ARGMIN:
+        out = np.empty(num_nodes, np.int32)
+    else:
+        out = np.empty(num_nodes, np.float64)
+    _check(ctx, lib().slr_get_field(ctx, int(which), out.ctypes.data_as(_vp), num_nodes))
+    return out
+
+
+def slr_get_band(ctx):
+    n = C.c_int64(0)
+    _check(ctx, lib().slr_get_band(ctx, None, 0, C.byref(n)))
+    out = np.empty(max(n.value, 1), np.int64)
+    _check(ctx, lib().slr_get_band(ctx, _ptr(out, _i64p), out.size, C.byref(n)))
+    return out[: n.value]
+
+
+def slr_energy(ctx, p=2.0):
+    E, S = C.c_double(0), C.c_double(0)
+    _check(ctx, lib().slr_energy(ctx, float(p), C.byref(E), C.byref(S)))
+    return E.value, S.value
+
+
+def slr_diagnostics(ctx, cap=4096, err_cloud=False):
+    e2 = np.zeros(cap)
+    dphi = np.zeros(cap)
+    band = np.zeros(cap, np.int64)
+    n = C.c_int(0)
+    ec = C.c_double(0)
+    _check(ctx, lib().slr_diagnostics(ctx, _ptr(e2), _ptr(dphi), _ptr(band, _i64p), cap, C.byref(n),
+                                      C.byref(ec) if err_cloud else None))
+    k = n.value
+    return dict(iters=k, e2=e2[: min(k + 1, cap)], dphi=dphi[: min(k, cap)], band=band[: min(k, cap)],
+                err_cloud=ec.value if err_cloud else None)
+
+
+def slr_export_state(ctx) -> bytes:
+    n = C.c_int64(0)
+    lib().slr_export_state(ctx, None, 0, C.byref(n))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, lib().slr_export_state(ctx, C.cast(buf, _vp), n.value, C.byref(n)))
+    return buf.raw
+
+
+def slr_import_state(ctx, data: bytes):
+    buf = C.create_string_buffer(data, len(data))
+    _check(ctx, lib().slr_import_state(ctx, C.cast(buf, _vp), len(data)))
+
+
+def slr_kernel_launches(ctx) -> int:
+    return int(lib().slr_kernel_launches(ctx))
+
+
+def slr_last_error(ctx) -> str:
+    m = lib().slr_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def slr_destroy(ctx):
+    if ctx:
+        lib().slr_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper: one reconstruction job
+# ---------------------------------------------------------------------------
+
+class Reconstruction:
+    """One reconstruction job on the current CUDA device.
+
+    Device memory comes from torch's caching allocator; work is queued on
+    ``stream`` (a torch.cuda.Stream; default: a new stream owned by the job,
+    so that the allocator and the kernels agree on the stream).
+    """
+
+    def __init__(self, dim=3, n=64, lo=-1.0, hi=1.0, precision=32, interp=1, band=1, stream=None, allocator="torch",
+                 **cfg):
+        import torch
+
+        if isinstance(n, int):
+            n = (n,) * dim + ((1,) if dim == 2 else ())
+        if isinstance(lo, (int, float)):
+            lo = (lo,) * dim
+        if isinstance(hi, (int, float)):
+            hi = (hi,) * dim
+        self.cfg = slr_config_default(dim=dim, n=n, lo=lo, hi=hi, precision=precision, interp=interp, band=band,
+                                      **cfg)
+        self.dim = dim
+        self.shape = tuple(int(x) for x in n)
+        self.num_nodes = int(np.prod(self.shape))
+        dev = torch.cuda.current_device()
+        s = stream if stream is not None else torch.cuda.Stream(dev)
+        self.stream = s
+        self._alloc = _TorchAllocator(dev, s.cuda_stream) if allocator == "torch" else None
+        self.ctx = slr_create(self.cfg, self._alloc, s.cuda_stream)
+
+    # Algorithm 1 calls
+    def load_cloud(self, xyz):
+        slr_load_cloud(self.ctx, xyz)
+
+    def build_distance(self):
+        slr_build_distance(self.ctx)
+
+    def set_distance(self, d):
+        slr_set_distance(self.ctx, d)
+
+    def init_sphere(self, radius, center=(0.0, 0.0, 0.0)):
+        c = list(center) + [0.0] * (3 - len(center))
+        slr_init_u(self.ctx, 0, params=[c[0], c[1], c[2], radius])
+
+    def init_array(self, u0):
+        slr_init_u(self.ctx, 1, u0=u0)
+
+    def step(self, n=1, energy_override=-1.0):
+        slr_step(self.ctx, n, energy_override)
+
+    def evolve(self):
+        return slr_evolve(self.ctx)
+
+    def extract(self, width):
+        return slr_extract(self.ctx, width)
+
+    def u(self):
+        return slr_get_field(self.ctx, SLR_FIELD_U, self.num_nodes)
+
+    def d(self):
+        return slr_get_field(self.ctx, SLR_FIELD_D, self.num_nodes)
+
+    def argmin(self):
+        return slr_get_field(self.ctx, SLR_FIELD_ARGMIN, self.num_nodes)
+
+    def band(self):
+        return slr_get_band(self.ctx)
+
+    def energy(self, p=2.0):
+        return slr_energy(self.ctx, p)
+
+    def diagnostics(self, err_cloud=False):
+        return slr_diagnostics(self.ctx, err_cloud=err_cloud)
+
+    def export_state(self):
+        return slr_export_state(self.ctx)
+
+    def import_state(self, data):
+        slr_import_state(self.ctx, data)
+
+    @property
+    def kernel_launches(self):
+        return slr_kernel_launches(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            slr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,343 @@
+"""GPU parity: every kernel through the C ABI against the FP64 oracle.
+
+Bars (written in each test):
+  - distance argmin and band / extract index lists: bit-exact;
+  - d: bit-exact (same FP64 arithmetic, same rounding to the storage type);
+  - u after one SL step from identical inputs: max-abs <= 1e-12 (FP64 mode),
+    <= 1e-5 * h (FP32 mode; the FP32 input is widened exactly for the
+    oracle), excluding the nodes the oracle flags as within 1e-6 of the
+    singular-gradient threshold (a discontinuous branch);
+  - energy: relative 1e-12 (FP64) or within the ambiguous mass the oracle
+    reports for subcells near the inclusion threshold plus relative 1e-5
+    (FP32).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_22205_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _slr():
+    from paper_2410_22205_gb300 import slr
+
+    return slr
+
+
+def tol_u(prec, h):
+    return 1e-12 if prec == 64 else 1e-5 * h
+
+
+def make(dim, n, prec, interp, band, lo=-1.0, hi=1.0, **kw):
+    slr = _slr()
+    shape = (n,) * dim if isinstance(n, int) else tuple(n)
+    if dim == 2:
+        shape = shape[:2] + (1,)
+    los = (lo,) * dim
+    his = tuple(lo + (hi - lo) * (shape[a] - 1) / (shape[0] - 1) for a in range(dim))
+    rec = slr.Reconstruction(dim=dim, n=shape, lo=los, hi=his, precision=prec, interp=interp, band=band, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("p", "delta", "dt", "gamma", "beta", "c_sing", "alpha")}
+    P = O.params(dim, shape[:dim], los, his, interp=interp, band=band, prec=prec, **okw)
+    return rec, P
+
+
+def step_parity(rec, P, Ep, prec):
+    """One GPU step from the current GPU state vs the oracle from the same input."""
+    u0 = rec.u()
+    d = rec.d()
+    rec.step(1, energy_override=Ep)
+    u1 = rec.u()
+    ref, flags, _ = O.sl_step(P, u0, d, Ep)
+    ok = (flags & O.FLAG_MARGIN) == 0
+    err = np.abs(u1 - ref)
+    return float(err[ok].max()), int((~ok).sum()), u0, u1, ref
+
+
+# ---------------------------------------------------------------- distance
+
+@pytest.mark.parametrize("dim,n,npts", [(2, 64, 200), (3, 33, 500), (2, (37, 29), 57), (3, (19, 23, 17), 300)])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_distance_grid_bit_exact(dim, n, npts, prec):
+    rng = np.random.default_rng(npts)
+    rec, P = make(dim, n, prec, 0, 1)
+    pts = rng.uniform(-1.2, 1.2, (npts, dim))
+    rec.load_cloud(pts)
+    rec.build_distance()
+    d_o, a_o = O.distance(P, pts)
+    d_o = d_o.astype(np.float32).astype(np.float64) if prec == 32 else d_o
+    assert np.array_equal(rec.argmin(), a_o)
+    assert np.array_equal(rec.d(), d_o)
+
+
+def test_distance_ties_and_duplicates_lowest_index():
+    """Symmetric and duplicated points give exact ties; the lowest index wins."""
+    rec, P = make(3, 21, 64, 0, 1)
+    base = np.array([[0.3, 0.0, 0.0], [-0.3, 0.0, 0.0], [0.0, 0.3, 0.0], [0.0, -0.3, 0.0], [0.0, 0.0, 0.3],
+                     [0.0, 0.0, -0.3], [0.5, 0.5, 0.5], [-0.5, -0.5, -0.5]])
+    pts = np.concatenate([base, base[::-1], base])  # duplicates at several indices
+    rec.load_cloud(pts)
+    rec.build_distance()
+    d_o, a_o = O.distance(P, pts)
+    assert np.array_equal(rec.argmin(), a_o)
+    assert np.array_equal(rec.d(), d_o)
+
+
+def test_distance_single_point_and_far_cloud():
+    rec, P = make(3, 17, 64, 0, 1)
+    pts = np.array([[5.0, -3.0, 7.0]])
+    rec.load_cloud(pts)
+    rec.build_distance()
+    d_o, a_o = O.distance(P, pts)
+    assert np.array_equal(rec.argmin(), a_o) and np.array_equal(rec.d(), d_o)
+
+
+def test_distance_torus_128_sampled():
+    """Torus workload size (20k points, 128^3): sampled nodes vs brute force."""
+    g = synth.cube_grid(3, 128)
+    pts = synth.torus_cloud(20000, 0.5, 0.2, 0.002, 1)
+    rec, P = make(3, 128, 32, 1, 1)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    nodes = np.random.default_rng(0).choice(g.num_nodes, 3000, replace=False)
+    d_o, a_o = O.distance(P, pts, nodes)
+    assert np.array_equal(rec.argmin()[nodes], a_o)
+    assert np.array_equal(rec.d()[nodes], d_o.astype(np.float32).astype(np.float64))
+
+
+# ---------------------------------------------------------------- init, band
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_init_sphere_and_band_bit_exact(prec, dim):
+    n = 48 if dim == 3 else 96
+    rec, P = make(dim, n, prec, 1, 1)
+    g = synth.cube_grid(dim, n)
+    rec.set_distance(np.full(g.num_nodes, 0.3))
+    rec.init_sphere(0.7)
+    ref = synth.sphere_sdf(g, 0.7)
+    if prec == 32:
+        ref = ref.astype(np.float32).astype(np.float64)
+    ref = O.cut(P, ref)
+    assert np.array_equal(rec.u(), ref)
+    assert np.array_equal(rec.band(), O.band(P, ref))
+
+
+def test_empty_band_steps_are_no_ops():
+    rec, P = make(3, 24, 32, 0, 1)
+    rec.set_distance(np.full(24 ** 3, 0.2))
+    rec.init_sphere(5.0)  # front far outside the grid: every node cut to -γ
+    assert rec.band().size == 0
+    u0 = rec.u()
+    rec.step(3, energy_override=1.0)
+    assert np.array_equal(rec.u(), u0)
+    assert rec.band().size == 0
+
+
+# ---------------------------------------------------------------- SL step
+
+@pytest.mark.parametrize("interp", [0, 1])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("dim,n", [(2, 64), (3, 40), (3, (33, 41, 29))])
+def test_sl_step_band_parity(dim, n, prec, interp):
+    rec, P = make(dim, n, prec, interp, 1)
+    rng = np.random.default_rng(1)
+    pts = (synth.sphere_cloud(800, 0.5, 0.01, 2) if dim == 3 else synth.circle_noisy(300, 0.5, 0.01, 2))
+    pts = pts + rng.normal(0, 0.02, pts.shape) * 0
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.62)
+    for s in range(3):
+        band_gpu_before = rec.band()
+        err, nflag, u0, u1, ref = step_parity(rec, P, 0.37, prec)
+        assert err <= tol_u(prec, P.h), (s, err)
+        assert nflag < 5
+        # the band used by this step is G^n of the state it started from
+        assert np.array_equal(rec.band(), O.band(P, u0))
+        assert set(rec.band()) <= set(band_gpu_before)
+
+
+@pytest.mark.parametrize("interp", [0, 1])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sl_step_full_grid_parity(dim, prec, interp):
+    n = 48 if dim == 2 else 26
+    rec, P = make(dim, n, prec, interp, 0)
+    pts = synth.sphere_cloud(300, 0.45, 0.0, 5) if dim == 3 else synth.circle_noisy(200, 0.5, 0.005, 0)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.9)
+    for s in range(2):
+        err, nflag, *_ = step_parity(rec, P, 0.21, prec)
+        assert err <= tol_u(prec, P.h), (s, err)
+
+
+@pytest.mark.parametrize("p,delta", [(1.0, 0.0), (1.0, 1.0), (3.0, 0.5), (2.0, 0.0)])
+def test_sl_step_parameters(p, delta):
+    rec, P = make(3, 30, 64, 1, 1, p=p, delta=delta)
+    rec.load_cloud(synth.torus_cloud(3000, 0.5, 0.2, 0.002, 4))
+    rec.build_distance()
+    rec.init_sphere(0.7)
+    err, *_ = step_parity(rec, P, 0.8, 64)
+    assert err <= 1e-12
+
+
+def test_singular_fallback_node_at_centre():
+    """Odd n puts a node at the sphere centre: eq. SL:2 on both sides."""
+    rec, P = make(3, 9, 64, 1, 0, p=1.0)
+    rec.set_distance(np.full(9 ** 3, 0.2))
+    rec.init_sphere(0.5)
+    err, nflag, u0, u1, ref = step_parity(rec, P, 1.0, 64)
+    c = 4 + 9 * (4 + 9 * 4)
+    assert err <= 1e-12 and u1[c] == pytest.approx(P.h - 0.5, abs=1e-15)
+
+
+def test_step_is_deterministic():
+    outs = []
+    for _ in range(2):
+        rec, P = make(3, 40, 32, 1, 1)
+        rec.load_cloud(synth.sphere_cloud(2000, 0.5, 0.01, 9))
+        rec.build_distance()
+        rec.init_sphere(0.62)
+        rec.step(4)
+        outs.append((rec.u(), rec.band(), rec.diagnostics()["e2"]))
+        rec.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+# ---------------------------------------------------------------- energy
+
+@pytest.mark.parametrize("interp", [0, 1])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("band", [0, 1])
+def test_energy_parity(dim, prec, interp, band):
+    n = 64 if dim == 2 else 36
+    rec, P = make(dim, n, prec, interp, band)
+    pts = synth.sphere_cloud(1500, 0.5, 0.01, 3) if dim == 3 else synth.circle_noisy(200, 0.5, 0.005, 0)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.61)
+    if band:
+        rec.step(2, energy_override=0.4)
+    u, d = rec.u(), rec.d()
+    for p in (2.0, 1.0, 3.0):
+        E, S = rec.energy(p)
+        amb_tol = 0.0 if prec == 64 else 1e-5 * P.h / 5
+        ref = O.energy(P, u, d, p, 5, amb_tol)
+        if prec == 64:
+            assert S == pytest.approx(ref["sum"], rel=1e-12, abs=1e-300)
+        else:
+            assert abs(S - ref["sum"]) <= ref["amb"] + 1e-5 * ref["sum"]
+
+
+def test_energy_2d_paper_circle():
+    """The paper's 64-point unit circle with the exact SDF: GPU E_2 matches
+    the oracle to 1e-12 and approaches 7.1035e-2."""
+    n = 201
+    rec, P = make(2, n, 64, 1, 0, lo=-1.3, hi=1.3)
+    pts = synth.circle_uniform(64, 1.0)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    g = synth.cube_grid(2, n, -1.3, 1.3)
+    rec.init_array(synth.sphere_sdf(g, 1.0))
+    E, S = rec.energy(2.0)
+    ref = O.energy(P, rec.u(), rec.d(), 2.0)
+    assert S == pytest.approx(ref["sum"], rel=1e-12)
+    assert E == pytest.approx(7.103510780002126e-02, rel=2e-2)
+
+
+# ---------------------------------------------------------------- evolve, extract, diagnostics
+
+def test_circle64_workload_100_steps_fp64_q1():
+    """Small 2-D workload: 200 noisy circle points, 64^2 on [-1,1]^2,
+    u0 = circle r = 0.9, 100 SL steps, whole grid, FP64 Q1. GPU vs oracle
+    stepping with its own energies; drift reported, gated at 1e-9."""
+    wl = synth.workload_circle64()
+    g = wl["grid"]
+    rec, P = make(2, 64, 64, 0, 0)
+    rec.load_cloud(wl["cloud"])
+    rec.build_distance()
+    rec.init_sphere(0.9)
+    d = rec.d()
+    u = rec.u()
+    rec.step(100)
+    diag = rec.diagnostics()
+    e2 = []
+    for s in range(100):
+        E = O.energy(P, u, d, 2.0)["E"]
+        e2.append(E)
+        u, _, _ = O.sl_step(P, u, d, E)
+    e2.append(O.energy(P, u, d, 2.0)["E"])
+    drift = np.abs(rec.u() - u).max()
+    assert drift <= 1e-9, drift
+    np.testing.assert_allclose(diag["e2"][:101], e2, rtol=1e-9)
+
+
+def test_evolve_matches_oracle_stop_rule():
+    rec, P = make(2, 48, 64, 1, 1, p=1.0, delta=0.0)
+    pts = synth.circle_noisy(150, 0.5, 0.0, 0)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.8)
+    u0, d = rec.u(), rec.d()
+    iters, conv = rec.evolve()
+    ref = O.evolve(P, u0, d)
+    assert iters == ref["iters"] and conv == ref["converged"]
+    assert np.abs(rec.u() - ref["u"]).max() <= 1e-10
+    np.testing.assert_allclose(rec.diagnostics()["e2"], ref["E2"], rtol=1e-10)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_extract_and_err_cloud(prec):
+    rec, P = make(3, 40, prec, 1, 1)
+    pts = synth.sphere_cloud(1000, 0.5, 0.0, 1)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.55)
+    rec.step(2, energy_override=0.5)
+    u = rec.u()
+    idx, val = rec.extract(2 * P.h)
+    ridx, rval = O.extract(P, u, 2 * P.h)
+    assert np.array_equal(idx, ridx) and np.array_equal(val, rval)
+    es = rec.diagnostics(err_cloud=True)["err_cloud"]
+    assert es == pytest.approx(O.err_cloud(P, u, pts), rel=1e-12 if prec == 64 else 1e-5, abs=1e-7 * P.h)
+
+
+def test_checkpoint_resume_bit_identical():
+    rec, P = make(3, 36, 32, 1, 1)
+    pts = synth.torus_cloud(5000, 0.5, 0.2, 0.002, 1)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.7)
+    rec.step(3)
+    blob = rec.export_state()
+    rec.step(4)
+    u_ref, diag_ref = rec.u(), rec.diagnostics()
+    rec2, _ = make(3, 36, 32, 1, 1)
+    rec2.import_state(blob)
+    rec2.step(4)
+    assert np.array_equal(rec2.u(), u_ref)
+    assert np.array_equal(rec2.diagnostics()["e2"], diag_ref["e2"])
+
+
+def test_invalid_inputs_and_order():
+    slr = _slr()
+    rec, P = make(3, 16, 32, 0, 1)
+    with pytest.raises(slr.SlrError) as e:
+        rec.step(1)
+    assert e.value.status == slr.SLR_E_STATE
+    with pytest.raises(slr.SlrError) as e:
+        rec.build_distance()
+    assert e.value.status == slr.SLR_E_STATE
+    with pytest.raises(slr.SlrError) as e:
+        rec.load_cloud(np.array([[np.nan, 0.0, 0.0]]))
+        rec.build_distance()
+    assert e.value.status == slr.SLR_E_INVALID
+    with pytest.raises(slr.SlrError):
+        slr.Reconstruction(dim=3, n=(16, 16, 16), lo=(-1, -1, -1), hi=(1, 1, 2))
