@@ -1,0 +1,495 @@
+#!/usr/bin/env python3
+"""Benchmark of the semi-Lagrangian level-set iteration on one GB300.
+
+Workload (default): 1,000,000 points on a union of three superquadrics with a
+10x density variation, 256^3 grid on [-1,1]^3, φ^0 = sphere of radius 0.9,
+narrow band of 6h, WENO interpolation, FP32 storage and arithmetic, p = 2,
+δ = 1, Δt = h/4.
+
+One benchmark step is one iteration of Algorithm 1 on the device: band
+rebuild + SL update + cut (one fused kernel), the energy quadrature of the
+new state, and the record/stop kernel — replayed from a captured CUDA graph.
+The metric is SL node-updates per second: band nodes updated in the timed
+steps divided by their device time (CUDA events on the job's stream). The L2
+cache is flushed (a 256 MB write) between timed steps, outside the events.
+
+Also reported on the same JSON line:
+  roofline      the dominant kernel of a step against its bound;
+  cpu_baseline  the FP64 oracle on the host cores, a bounded sample;
+  e2e           whole jobs through the public API from host buffers (copy in,
+                distance grid, init, evolve to the stop test, extract, copy out);
+  latency       p50/p99 of the iteration time and of the whole-job solve time;
+  variants      node-updates/s of Q1 and of FP64 at the same workload;
+  clocks        nvidia-smi samples taken during the timed region.
+
+--impl reference times the oracle (the CPU FP64 implementation written from
+the paper) on the same workload instead; see run_reference().
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2410_22205_gb300 import synth  # noqa: E402
+
+METRIC = "SL node-updates/s at 256^3 (WENO, FP32, narrow band 6h)"
+UNIT = "node-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=256, help="nodes per axis")
+    ap.add_argument("--points", type=int, default=1_000_000)
+    ap.add_argument("--e2e-jobs", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no data-path collective)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, backend):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def reduce(self, value, op):
+        """Reduce a float over ranks: op in {"sum", "max"}."""
+        if not self.pg:
+            return value
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM if op == "sum" else self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(units, seconds, dist):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    tot = dist.reduce(units, "sum")
+    tmax = dist.reduce(seconds, "max")
+    return tot / tmax if tmax > 0 else 0.0, tot, tmax
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload(args, seed=2):
+    grid = synth.cube_grid(3, args.n)
+    cloud = synth.superquadric_union_cloud(args.points, 3, seed)
+    return grid, cloud
+
+
+def cfg_kw():
+    return dict(p=2.0, delta=1.0)
+
+
+def sha_of_kernels():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_22205_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha):
+    """Algorithmic work per launch of the dominant kernel over its measured
+    duration. Per band node and step (FP32):
+      bytes: read u_j, d_j, the band-list entry, write u_j and the new band
+             entry = 4 + 4 + 4 + 4 + 4 = 20 B (HBM bound for Q1);
+      flops: WENO needs 4 feet x 21 one-dimensional WENO evaluations of 24
+             flops (FMA = 2) plus ~140 for gradients, tangents and feet =
+             2156 flops (ALU bound); Q1: 4 feet x 7 lerps x 3 + 140 = 224.
+    Energy kernel: per front cell 305 WENO evaluations + 125 trilinear
+    d-lookups... reported when it dominates (flops, ALU bound)."""
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+    info = {}
+    traffic = None
+    side = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(side):
+        try:
+            tr = json.load(open(side))
+            if tr.get("src_sha") == kernel_sha and tr.get("kernel") == kernel["name"]:
+                traffic = tr.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    if kernel["kind"] == "step_weno":
+        flops = 2156.0 * band_nodes
+        achieved = flops / (ms * 1e-3) / 1e12
+        info = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "hbm_view": {"achieved_gbs": 20.0 * band_nodes / (ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                             "frac": 20.0 * band_nodes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+    elif kernel["kind"] == "step_q1":
+        bytes_ = 20.0 * band_nodes
+        achieved = bytes_ / (ms * 1e-3) / 1e9
+        info = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS)"}
+    else:
+        fc = kernel.get("front_cells", 0)
+        flops = (305 * 24 + 125 * 20) * fc
+        achieved = flops / (ms * 1e-3) / 1e12
+        info = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    info["kernel"] = kernel["name"]
+    info["ms_per_launch"] = ms
+    return info
+
+
+def measure_steps(rec, steps, warmup, flush_buf, torch):
+    """Warm-up, then `steps` timed iterations; returns per-step ms, per-kernel
+    ms (3 per step) and the band sizes of the timed steps."""
+    st = rec.stream
+    for _ in range(warmup):
+        rec.step_async(1)
+    torch.cuda.synchronize()
+    n0 = rec.diagnostics()["iters"]
+    step_ms, kern_ms = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    launches0 = rec.kernel_launches
+    for _ in range(steps):
+        with torch.cuda.stream(st):
+            flush_buf.zero_()  # L2 flush between timed steps, outside the events
+        ev0.record(st)
+        rec.step_async(1)
+        ev1.record(st)
+        kern_ms.append(rec.last_iteration_times())  # synchronises the stream
+        step_ms.append(ev0.elapsed_time(ev1))
+    launches = rec.kernel_launches - launches0
+    diag = rec.diagnostics()
+    bands = diag["band"][n0:n0 + steps]
+    return step_ms, kern_ms, bands, launches
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2410_22205_gb300 import slr
+
+    dist = Dist("nccl")
+    torch.cuda.set_device(dist.local_rank)
+    peaks = {"hbm_gbs": 6794.5, "bf16_tflops": 1921.5}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks.update({k: v for k, v in json.load(open(pk)).items() if isinstance(v, (int, float))})
+    t_setup = time.time()
+    grid, cloud = workload(args)
+    n = args.n
+    rec = slr.Reconstruction(dim=3, n=n, precision=32, interp=1, band=1, **cfg_kw())
+    st = rec.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    rec.load_cloud(cloud)
+    ev[0].record(st)
+    rec.build_distance()
+    ev[1].record(st)
+    rec.init_sphere(0.9)
+    ev[2].record(st)
+    ev[2].synchronize()
+    dist_ms = ev[0].elapsed_time(ev[1])
+    rec.set_profiling(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    step_ms, kern_ms, bands, launches = measure_steps(rec, args.steps, args.warmup, flush, torch)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+
+    units = float(np.sum(bands))
+    secs = float(np.sum(step_ms)) / 1e3
+    value, tot_units, tmax = aggregate(units, secs, dist)
+    ms_per_step = tmax * 1e3 / args.steps
+    kern = np.array(kern_ms)
+    names = ["k_step_band<float,3,WENO>", "k_energy<float,3,WENO,R=5>", "k_record"]
+    kmean = kern.mean(axis=0)
+    dom = int(np.argmax(kmean))
+    mean_band = float(np.mean(bands))
+    front = None
+    if dom == 1:
+        front = 1.5 * 4 * math.pi * 0.81 / ((2.0 / (n - 1)) ** 2)
+    kernel = {"name": names[dom], "kind": ["step_weno", "energy", "record"][dom], "front_cells": front}
+    sha = sha_of_kernels()
+    roof = roofline_for(kernel, float(kmean[dom]), mean_band, peaks, sha)
+    roof["kernel_share_of_step"] = float(kmean[dom] / np.mean(step_ms))
+    roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
+    iter_lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
+    rec.close()
+
+    variants = {}
+    if not args.no_variants and dist.rank == 0:
+        for prec, interp, band, label in ((32, 0, 1, "q1_fp32_band"), (64, 1, 1, "weno_fp64_band"),
+                                          (64, 0, 1, "q1_fp64_band"), (32, 1, 0, "weno_fp32_fullgrid"),
+                                          (32, 0, 0, "q1_fp32_fullgrid")):
+            r2 = slr.Reconstruction(dim=3, n=n, precision=prec, interp=interp, band=band, **cfg_kw())
+            r2.load_cloud(cloud)
+            r2.build_distance()
+            r2.init_sphere(0.9)
+            r2.set_profiling(True)
+            ks = max(3, args.steps // 4)
+            sm, km, bd, _ = measure_steps(r2, ks, 2, flush, torch)
+            variants[label] = {"value": float(np.sum(bd)) / (float(np.sum(sm)) / 1e3), "ms_per_step": float(np.mean(sm)),
+                               "nodes_per_step": float(np.mean(bd)), "kernels_ms": [float(x) for x in np.mean(km, 0)]}
+            r2.close()
+
+    e2e = None
+    solve_lat = None
+    if args.e2e_jobs > 0:
+        e2e, solve_lat = run_e2e(args, cloud, slr, torch)
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(grid, cloud, budget_s=20.0)
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded superquadric-union cloud)",
+            "config": {"workload": f"sq3union{args.points // 1000}k_{n}cube_band6h_weno_fp32", "grid": f"{n}^3",
+                       "points": args.points, "interp": "WENO", "band": "6h", "p": 2, "delta": 1,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{dist.world}",
+                       "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "latency": {"iteration": iter_lat, "solve": solve_lat},
+            "variants": variants, "gpu_launches": int(launches), "clocks": clk,
+            "setup_s": time.time() - t_setup,
+        }
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def run_e2e(args, cloud, slr, torch):
+    """Whole jobs through the public API with host buffers: pinned host cloud
+    -> load (H2D) -> exact distance grid -> φ^0 -> evolve to the stop test ->
+    extract |φ| < 2h (D2H). Timed by the host clock around each job."""
+    pinned = torch.empty(cloud.shape, dtype=torch.float64, pin_memory=True)
+    pinned.numpy()[:] = cloud
+    host = pinned.numpy()
+    h = 2.0 / (args.n - 1)
+    times, units, h2d, d2h, iters = [], 0.0, 0, 0, []
+    for j in range(args.e2e_jobs + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec = slr.Reconstruction(dim=3, n=args.n, precision=32, interp=1, band=1, **cfg_kw())
+        rec.load_cloud(host)
+        rec.build_distance()
+        rec.init_sphere(0.9)
+        it, conv = rec.evolve()
+        idx, val = rec.extract(2 * h)
+        t1 = time.perf_counter()
+        diag = rec.diagnostics()
+        rec.close()
+        if j == 0:
+            continue  # first job warms the allocator and the graph instantiation path
+        times.append(t1 - t0)
+        units += float(np.sum(diag["band"]))
+        h2d += host.nbytes
+        d2h += idx.nbytes + val.nbytes
+        iters.append(it)
+    jobs = len(times)
+    e2e = {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d // jobs, "d2h_bytes_per_step": d2h // jobs,
+           "step": "one whole job (H2D cloud, distance grid, init, evolve to the stop test, extract, D2H)",
+           "jobs": jobs, "iterations_per_job": iters}
+    lat = {"p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)), "jobs": jobs}
+    return e2e, lat
+
+
+# ---------------------------------------------------------------------------
+# CPU: the oracle
+# ---------------------------------------------------------------------------
+
+def oracle_setup(grid, cloud):
+    """φ^0 (sphere r = 0.9, cut) and d by the oracle's exact k-d tree search on
+    the nodes the first iterations read: the band and its 26-neighbourhood."""
+    import oracle as O
+
+    P = O.params_for_grid(grid, interp=1, band=1, p=2.0, delta=1.0, prec=32)
+    u = synth.sphere_sdf(grid, 0.9).astype(np.float32).astype(np.float64)
+    u = O.cut(P, u)
+    n = grid.n[0]
+    inb = (np.abs(u) < np.float32(P.gamma)).reshape(n, n, n)
+    need = inb.copy()
+    for ax in range(3):
+        for s in (-1, 1):
+            need |= np.roll(inb, s, axis=ax)
+    nodes = np.flatnonzero(need.reshape(-1))
+    d = np.zeros(grid.num_nodes)
+    dd, _ = O.distance(P, cloud, nodes, method="kd")
+    d[nodes] = dd.astype(np.float32).astype(np.float64)
+    return O, P, u, d
+
+
+def oracle_iteration(O, P, u, d, Ep):
+    out, _, _ = O.sl_step(P, u, d, Ep)
+    E = O.energy(P, out, d, 2.0)["E"]
+    nb = int(np.count_nonzero(np.abs(u) < np.float32(P.gamma)))
+    return out, E, nb
+
+
+def cpu_baseline(grid, cloud, budget_s=20.0):
+    """The oracle as it stands on the host cores: whole iterations (band scan,
+    WENO SL step in FP64 on every band node, cut, energy) from φ^0 until about
+    budget_s seconds of work."""
+    O, P, u, d = oracle_setup(grid, cloud)
+    cores = O.set_threads(len(os.sched_getaffinity(0)))
+    Ep = O.energy(P, u, d, 2.0)["E"]
+    t0 = time.perf_counter()
+    units, its = 0, 0
+    while True:
+        u, Ep, nb = oracle_iteration(O, P, u, d, Ep)
+        units += nb
+        its += 1
+        if time.perf_counter() - t0 > budget_s * 0.5 or its >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{its} whole oracle iterations (WENO FP64 SL step on {units // its} band nodes + energy) of the "
+                      f"{grid.n[0]}^3 workload from φ^0, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle, as it stands, on the host cores, on the
+    same workload; each step is one whole oracle iteration."""
+    dist = Dist("gloo")
+    if dist.rank != 0:
+        dist.barrier()
+        dist.close()
+        return
+    grid, cloud = workload(args)
+    O, P, u, d = oracle_setup(grid, cloud)
+    cores = O.set_threads(len(os.sched_getaffinity(0)))
+    Ep = O.energy(P, u, d, 2.0)["E"]
+    for _ in range(args.warmup):
+        u, Ep, _ = oracle_iteration(O, P, u, d, Ep)
+    times, units = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u, Ep, nb = oracle_iteration(O, P, u, d, Ep)
+        times.append(time.perf_counter() - t0)
+        units += nb
+    secs = sum(times)
+    value = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded superquadric-union cloud)",
+            "config": {"workload": f"sq3union{args.points // 1000}k_{args.n}cube_band6h_weno_fp32", "grid": f"{args.n}^3",
+                       "points": args.points, "interp": "WENO", "band": "6h",
+                       "note": "FP64 oracle on the host; its inputs are the FP32-rounded φ^0 and d"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed whole oracle iterations after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

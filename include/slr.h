@@ -18,8 +18,9 @@
  *    capacity; SLR_E_CAPACITY reports the count that would be needed.
  *  - Device memory comes from the allocator given to slr_create (NULL: the
  *    library uses cudaMalloc/cudaFree). All work is enqueued on the stream
- *    given to slr_create (NULL: the legacy default stream). Calls that return
- *    host data synchronise that stream.
+ *    given to slr_create (NULL: a non-blocking stream the context creates
+ *    and owns; the legacy default stream cannot hold the captured iteration
+ *    graphs). Calls that return host data synchronise that stream.
  *  - A context is not thread-safe: one host thread at a time per context.
  *    Different contexts may be used from different threads.
  *  - Grid layout: node (i,j,k), 0 <= i < n[0] ..., has linear index
@@ -89,7 +90,8 @@ void slr_config_default(slr_config* cfg);
  * all axes, at least 4 nodes per active axis, precision 32|64, ...) and
  * allocates the dense fields u (two buffers), d and argmin plus the band and
  * reduction buffers. alloc may be NULL (cudaMalloc/cudaFree); stream is a
- * cudaStream_t or NULL. The context binds to the device current at this call. */
+ * cudaStream_t or NULL (the context then owns a stream of its own). The
+ * context binds to the device current at this call. */
 slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out);
 
 /* Copy the point cloud S = {Q_1..Q_N} (§2) to the device. xyz: host array of
@@ -119,6 +121,12 @@ slr_status slr_init_u(slr_ctx* ctx, int kind, const double* params, const double
  * state. energy_override >= 0 uses that value as E_p in the scale factor
  * (d/E_p)^(p-1) of every step; < 0 uses the computed E_p(φ^n). */
 slr_status slr_step(slr_ctx* ctx, int n_steps, double energy_override);
+
+/* As slr_step, but only enqueues the iterations on the context's stream and
+ * returns without waiting (no host synchronisation, no status read). Errors
+ * raised by the device (SLR_E_TIMEOUT) are reported by the next synchronous
+ * call. For overlapping host work or other jobs with the iterations. */
+slr_status slr_step_async(slr_ctx* ctx, int n_steps, double energy_override);
 
 /* Iterate until the stopping criterion of §4 (eq. deltaEn: Δ_E < stop_tol
  * after at least min_iters iterations, or max_iters). The test and the
@@ -162,6 +170,14 @@ slr_status slr_diagnostics(slr_ctx* ctx, double* e2_hist, double* dphi_hist, int
  * from it reproduces an uninterrupted run bit for bit. */
 slr_status slr_export_state(slr_ctx* ctx, void* buf, int64_t cap, int64_t* n_out);
 slr_status slr_import_state(slr_ctx* ctx, const void* buf, int64_t n);
+
+/* Opt-in timing of the kernels of one iteration: with on != 0 the captured
+ * iteration graph also records CUDA events around its three kernels (SL step
+ * with band compaction, energy quadrature, record/stop). After an iteration
+ * has run, slr_last_iteration_times synchronises the stream and writes the
+ * three kernel durations of the most recent iteration in milliseconds. */
+slr_status slr_set_profiling(slr_ctx* ctx, int on);
+slr_status slr_last_iteration_times(slr_ctx* ctx, float ms[3]);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t slr_kernel_launches(const slr_ctx* ctx);

@@ -76,6 +76,7 @@ def lib():
                 "or_num_nodes": (C.c_longlong, [_P]),
                 "or_node_coord": (None, [_P, C.c_longlong, _dp]),
                 "or_distance": (None, [_P, _dp, C.c_longlong, _lp, C.c_longlong, _dp, _ip]),
+                "or_distance_kd": (None, [_P, _dp, C.c_longlong, _lp, C.c_longlong, _dp, _ip]),
                 "or_gradient": (None, [_P, _dp, C.c_longlong, _dp]),
                 "or_interp_q1": (C.c_double, [_P, _dp, _dp]),
                 "or_weno1d": (C.c_double, [_dp, C.c_double, C.c_double]),
@@ -154,7 +155,9 @@ def num_nodes(P):
     return int(P.n[0] * P.n[1] * P.n[2])
 
 
-def distance(P, pts, nodes=None):
+def distance(P, pts, nodes=None, method="brute"):
+    """d and argmin on all nodes (or the listed ones). method "brute" scans
+    every point; "kd" uses the k-d tree with identical decisions."""
     pts, pp = _d(pts)
     if nodes is None:
         m = num_nodes(P)
@@ -165,7 +168,8 @@ def distance(P, pts, nodes=None):
         m = np_.size
     d = np.empty(m, np.float64)
     arg = np.empty(m, np.int32)
-    lib().or_distance(C.byref(P), pp, pts.shape[0], lp, m, d.ctypes.data_as(_dp), arg.ctypes.data_as(_ip))
+    f = lib().or_distance_kd if method == "kd" else lib().or_distance
+    f(C.byref(P), pp, pts.shape[0], lp, m, d.ctypes.data_as(_dp), arg.ctypes.data_as(_ip))
     return d, arg
 
 

@@ -105,6 +105,139 @@ void or_distance(const or_params* g, const double* pts, long long npts,
     }
 }
 
+/* k-d tree search with the same decisions as the scan above. Median split
+ * on the widest axis, leaves of at most 8 points. A subtree on the far side
+ * of a split plane is skipped only when fl(diff)^2 > best: every point there
+ * has |x_a - q_a| >= |x_a - split| on that axis, rounding is monotone and the
+ * squared distance is a sum of non-negative terms, so its computed value is
+ * at least fl(diff)^2 and it can neither win nor tie. */
+typedef struct {
+    int axis;          /* -1 for a leaf */
+    double split;
+    int left, right;
+    long long lo, hi;  /* leaf range in the permutation */
+} kd_node;
+
+typedef struct {
+    const double* pts;
+    int dim;
+    long long* perm;
+    kd_node* nodes;
+    int count;
+} kd_tree;
+
+static double kd_coord(const kd_tree* t, long long i, int a) { return t->pts[t->perm[i] * t->dim + a]; }
+
+static void kd_select(kd_tree* t, long long lo, long long hi, long long k, int a) {
+    /* Hoare-style quickselect: afterwards perm[lo..k) <= perm[k] <= perm[k+1..hi) on axis a */
+    while (hi - lo > 1) {
+        double pivot = kd_coord(t, lo + (hi - lo) / 2, a);
+        long long i = lo, j = hi - 1;
+        while (i <= j) {
+            while (kd_coord(t, i, a) < pivot) ++i;
+            while (kd_coord(t, j, a) > pivot) --j;
+            if (i <= j) {
+                long long tmp = t->perm[i];
+                t->perm[i] = t->perm[j];
+                t->perm[j] = tmp;
+                ++i;
+                --j;
+            }
+        }
+        if (k <= j)
+            hi = j + 1;
+        else if (k >= i)
+            lo = i;
+        else
+            return;
+    }
+}
+
+static int kd_build(kd_tree* t, long long lo, long long hi) {
+    int id = t->count++;
+    kd_node* nd = &t->nodes[id];
+    nd->lo = lo;
+    nd->hi = hi;
+    nd->axis = -1;
+    if (hi - lo <= 8) return id;
+    int best_a = 0;
+    double best_w = -1.0;
+    for (int a = 0; a < t->dim; ++a) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (long long i = lo; i < hi; ++i) {
+            double v = kd_coord(t, i, a);
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        if (mx - mn > best_w) {
+            best_w = mx - mn;
+            best_a = a;
+        }
+    }
+    long long mid = lo + (hi - lo) / 2;
+    kd_select(t, lo, hi, mid, best_a);
+    double split = kd_coord(t, mid, best_a);
+    int left = kd_build(t, lo, mid);
+    int right = kd_build(t, mid, hi);
+    nd = &t->nodes[id];
+    nd->axis = best_a;
+    nd->split = split;
+    nd->left = left;
+    nd->right = right;
+    return id;
+}
+
+static void kd_query(const kd_tree* t, int id, const double x[3], double* best, long long* arg) {
+    const kd_node* nd = &t->nodes[id];
+    if (nd->axis < 0) {
+        for (long long i = nd->lo; i < nd->hi; ++i) {
+            long long q = t->perm[i];
+            const double* Q = t->pts + q * t->dim;
+            double s = 0.0;
+            for (int a = 0; a < t->dim; ++a) {
+                double diff = x[a] - Q[a];
+                s = s + diff * diff;
+            }
+            if (s < *best || (s == *best && q < *arg)) {
+                *best = s;
+                *arg = q;
+            }
+        }
+        return;
+    }
+    double diff = x[nd->axis] - nd->split;
+    int near = diff <= 0.0 ? nd->left : nd->right;
+    int far = diff <= 0.0 ? nd->right : nd->left;
+    kd_query(t, near, x, best, arg);
+    if (!(diff * diff > *best)) kd_query(t, far, x, best, arg);
+}
+
+void or_distance_kd(const or_params* g, const double* pts, long long npts,
+                    const long long* nodes, long long m, double* d_out, int* arg_out) {
+    kd_tree t;
+    t.pts = pts;
+    t.dim = g->dim;
+    t.perm = (long long*)malloc(sizeof(long long) * (size_t)npts);
+    t.nodes = (kd_node*)malloc(sizeof(kd_node) * (size_t)(2 * (npts / 4 + 2)));
+    t.count = 0;
+    for (long long i = 0; i < npts; ++i) t.perm[i] = i;
+    kd_build(&t, 0, npts);
+    long long count = nodes ? m : or_num_nodes(g);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long long k = 0; k < count; ++k) {
+        long long idx = nodes ? nodes[k] : k;
+        double x[3];
+        or_node_coord(g, idx, x);
+        double best = INFINITY;
+        long long arg = 0x7fffffffffffffffll;
+        kd_query(&t, 0, x, &best, &arg);
+        d_out[k] = sqrt(best);
+        if (arg_out) arg_out[k] = (int)arg;
+    }
+    free(t.perm);
+    free(t.nodes);
+}
+
 /* ------------------------------------------------------------------ */
 /* §3: centred finite differences                                       */
 /* ------------------------------------------------------------------ */

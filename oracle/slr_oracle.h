@@ -55,6 +55,12 @@ void or_node_coord(const or_params* g, long long idx, double x[3]);
 void or_distance(const or_params* g, const double* pts, long long npts,
                  const long long* nodes, long long m, double* d_out, int* arg_out);
 
+/* The same d and argmin as or_distance (identical floating-point decisions),
+ * found through a k-d tree over the cloud instead of a scan of every point:
+ * for clouds too large for brute force. */
+void or_distance_kd(const or_params* g, const double* pts, long long npts,
+                    const long long* nodes, long long m, double* d_out, int* arg_out);
+
 /* §3: centred differences; one-sided first-order on the domain boundary */
 void or_gradient(const or_params* g, const double* v, long long idx, double grad[3]);
 

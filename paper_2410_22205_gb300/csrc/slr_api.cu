@@ -73,8 +73,12 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     long long l0 = c->launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    cudaError_t e1 = launch_step(c, ov, evolve);
-    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve) : e1;
+    cudaError_t e1 = c->profiling ? cudaEventRecord(c->pev[0], c->stream) : cudaSuccess;
+    if (e1 == cudaSuccess) e1 = launch_step(c, ov, evolve);
+    if (e1 == cudaSuccess && c->profiling) e1 = cudaEventRecord(c->pev[1], c->stream);
+    // launch_energy enqueues the energy kernel and the record kernel
+    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve, c->profiling ? c->pev[2] : nullptr) : e1;
+    if (e2 == cudaSuccess && c->profiling) e2 = cudaEventRecord(c->pev[3], c->stream);
     cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
     c->launches = l0;  // captured kernels are counted per replay
     if (e2 != cudaSuccess) {
@@ -88,7 +92,7 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     return SLR_OK;
 }
 
-constexpr int kKernelsPerIteration = 3;
+constexpr int kKernelsPerIteration = 3;  // step, energy, record
 
 slr_status read_status(slr_ctx* c, int* stop, int* error, int* n) {
     int* hp = c->host_pinned_flags;
@@ -135,7 +139,7 @@ slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     release_t(c, c->part_e);
     c->n_echunks = (ncells + 31) / 32;
     c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2));
-    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy partials failed");
+    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
     return SLR_OK;
 }
 
@@ -258,7 +262,7 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
         return SLR_E_CUDA;
     }
     if (!k.band) {
-        long long tiles = (N + kStepTile - 1) / kStepTile;
+        long long tiles = (N + kStepBlock - 1) / kStepBlock;
         c->part_dphi = (double*)dev_alloc(c, sizeof(double) * tiles);
         c->n_tiles_cap = tiles;
         if (!c->part_dphi || size_energy_buffers(c, c->ncells_all) != SLR_OK) {
@@ -385,6 +389,47 @@ slr_status slr_step(slr_ctx* c, int n_steps, double energy_override) {
     }
     CK(cudaStreamSynchronize(c->stream), "step sync");
     return check_device_error(c);
+}
+
+slr_status slr_step_async(slr_ctx* c, int n_steps, double energy_override) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_u) return fail(c, SLR_E_STATE, "step_async: initial level set not set");
+    if (n_steps < 0) return fail(c, SLR_E_INVALID, "step_async: negative step count");
+    DeviceGuard g(c->device);
+    double ov = energy_override >= 0.0 ? energy_override : -1.0;
+    if (!c->g_step || c->g_step_override != ov) {
+        if (c->g_step) cudaGraphExecDestroy(c->g_step);
+        c->g_step = nullptr;
+        slr_status s = capture_step(c, ov, 0, &c->g_step);
+        if (s != SLR_OK) return s;
+        c->g_step_override = ov;
+    }
+    CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "step_async");
+    for (int i = 0; i < n_steps; ++i) {
+        CK(cudaGraphLaunch(c->g_step, c->stream), "cudaGraphLaunch");
+        c->launches += kKernelsPerIteration;
+    }
+    return SLR_OK;
+}
+
+slr_status slr_set_profiling(slr_ctx* c, int on) {
+    if (!c) return SLR_E_INVALID;
+    DeviceGuard g(c->device);
+    bool want = on != 0;
+    if (want && !c->pev[0])
+        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->pev[i]), "cudaEventCreate");
+    if (want != c->profiling) free_graphs(c);
+    c->profiling = want;
+    return SLR_OK;
+}
+
+slr_status slr_last_iteration_times(slr_ctx* c, float ms[3]) {
+    if (!c || !ms) return SLR_E_INVALID;
+    if (!c->profiling) return fail(c, SLR_E_STATE, "last_iteration_times: profiling is off");
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->stream), "last_iteration_times");
+    for (int i = 0; i < 3; ++i) CK(cudaEventElapsedTime(&ms[i], c->pev[i], c->pev[i + 1]), "cudaEventElapsedTime");
+    return SLR_OK;
 }
 
 slr_status slr_evolve(slr_ctx* c, int* iters_out, int* converged_out) {
@@ -692,6 +737,8 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->tile_status);
     release_t(c, c->ds);
     if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);
+    for (int i = 0; i < 4; ++i)
+        if (c->pev[i]) cudaEventDestroy(c->pev[i]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     if (prev >= 0 && prev != c->device) cudaSetDevice(prev);

@@ -219,6 +219,7 @@ __device__ __forceinline__ float warp_minf(float v) {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int* aout) {
     __shared__ int s_stack[8][kStack];
+    __shared__ float4 s_leaf[8][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long ntiles = (long long)A.tx * A.ty * A.tz;
@@ -253,8 +254,10 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
 
     double best = INFINITY;
     int bi = 0x7fffffff;
-    float thr = INFINITY;  // squared FP32 screen
-    float wb2 = INFINITY;  // squared warp bound
+    float thr = INFINITY;    // squared FP32 screen of this lane
+    float lbound = INFINITY; // this lane's best plus the error margin (FP32)
+    float wb2 = INFINITY;    // squared warp bound
+    float4* leaf = s_leaf[wib];
 
     int sp = 0;
     {
@@ -286,15 +289,27 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
             const long long base = id * 32;
             long long rem = A.npts - base;
             const int cnt = rem < 32 ? (int)rem : 32;
-            float4 mine = lane < cnt ? A.spt[base + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < cnt) leaf[lane] = A.spt[base + lane];
+            __syncwarp();
+            if (best == INFINITY) {
+                // first leaf of this lane: an FP32 minimum bounds the exact best,
+                // so only points within the margin of it need the FP64 check
+                float m2 = INFINITY;
+                for (int s = 0; s < cnt; ++s) {
+                    const float4 q = leaf[s];
+                    const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
+                    m2 = fminf(m2, dx * dx + dy * dy + dz * dz);
+                }
+                const double md = sqrt((double)m2);
+                const double lim = md + 2.0 * mscale * (A.extent + md);
+                thr = (float)(lim * lim) * 1.00001f;
+            }
             for (int s = 0; s < cnt; ++s) {
-                const float px = __shfl_sync(0xffffffffu, mine.x, s);
-                const float py = __shfl_sync(0xffffffffu, mine.y, s);
-                const float pz = __shfl_sync(0xffffffffu, mine.z, s);
-                const int pid = __float_as_int(__shfl_sync(0xffffffffu, mine.w, s));
-                const float dx = xf - px, dy = yf - py, dz = zf - pz;
+                const float4 q = leaf[s];
+                const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
                 const float d2f = dx * dx + dy * dy + dz * dz;
                 if (d2f <= thr) {
+                    const int pid = __float_as_int(q.w);
                     const double* Q = A.pts + (long long)pid * DIM;
                     const double ex = __dsub_rn(x, Q[0]);
                     const double ey = __dsub_rn(y, Q[1]);
@@ -309,12 +324,12 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
                         const double bdist = sqrt(s2);
                         const double lim = bdist + mscale * (A.extent + bdist);
                         thr = (float)(lim * lim) * 1.00001f;
+                        lbound = (float)lim * 1.00001f;
                     }
                 }
             }
-            const float mine_b = best < INFINITY ? (float)(sqrt(best) + mscale * (A.extent + sqrt(best))) * 1.00001f
-                                                 : INFINITY;
-            const float wb = warp_maxf(mine_b);
+            __syncwarp();
+            const float wb = warp_maxf(lbound);
             wb2 = wb * wb;
         } else {
             const int cl = lvl - 1;

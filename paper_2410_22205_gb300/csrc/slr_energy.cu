@@ -3,9 +3,9 @@
 //
 // Energy: the candidate cells (every cell in whole-grid mode; in band mode
 // the cells touching the initial band or crossing the front at init) are
-// taken 32 at a time by one warp; a ballot finds the front cells (vertices of
-// both signs, zero counted as positive) and the warp then works through them
-// one by one:
+// scanned 32 at a time by one warp; a ballot finds the front cells (vertices
+// of both signs, zero counted as positive), which are queued and processed
+// one per lane:
 //   2-D: edge crossings by linear interpolation of φ, d interpolated along
 //        the edge, trapezoid rule on the segment(s) (eq. energyApprox);
 //   3-D: R^3 subcells (eq. energyApproxFiner); φ at the subcell centres by
@@ -14,14 +14,28 @@
 //        along y, then R^3 along x, all with the same arithmetic as a single
 //        point evaluation); d by Q1; a subcell counts when
 //        |φ(x')| < (√3/2)Δx' and adds |d(x')|^p (Δx')^2.
-// Each warp writes FP64 partial sums per chunk; one block reduces them in a
-// fixed order, so results are bit-reproducible.
+// Each warp sums its chunks in a fixed order, each block writes one FP64
+// partial per sum, and one block reduces the partials in a fixed order: the
+// grid is fixed per context, so results are bit-reproducible.
 #include "slr_internal.cuh"
 
 namespace slr {
 
 template <typename T>
 Params<T> make_params(const slr_ctx* c);
+
+// fixed grid of the energy pass for this context (per-block partials)
+long long energy_blocks(const slr_ctx* c) {
+    long long ncells = c->cfg.band ? c->n_ecells : c->ncells_all;
+    // each warp scans ~32 chunks of 32 candidates, so that its queue fills
+    // several full batches of 32 front cells (front cells are ~1/10 of the
+    // candidates in band mode); at most one wave of 4 blocks per SM
+    long long blocks = (ncells + 32 * 32 * 4 - 1) / (32 * 32 * 4);
+    long long cap = (long long)c->num_sms * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return blocks;
+}
 
 __device__ __forceinline__ double pow_abs(double v, double p, int p_kind) {
     double a = fabs(v);
@@ -105,139 +119,235 @@ __device__ double energy_cell_2d(const Params<T>& P, const T* __restrict__ u, co
     return s;
 }
 
-template <typename T, int DIM, int INTERP>
-__global__ void __launch_bounds__(kEnergyBlock) k_energy(Params<T> P, const T* ub0, const T* ub1,
-                                                         const T* __restrict__ d, const int* __restrict__ cells,
-                                                         long long ncells, long long nchunks, int R, double h,
-                                                         double p, int p_kind, int offset, double* part,
-                                                         DevState* ds, int check_stop) {
-    constexpr int W = kEnergyBlock / 32;
-    __shared__ T s_sv[W][64];
-    __shared__ T s_zv[W][16 * kMaxR];
-    __shared__ T s_yv[W][4 * kMaxR * kMaxR];
-    __shared__ T s_dc[W][8];
+// Data-only part of one WENO evaluation (the squared second differences and
+// their h^4-shifted squares); evaluations of the same four values at several
+// θ share it.
+template <typename T>
+struct WenoInd {
+    T v1, dv, dl, dr, sl2, sr2;
+    __device__ __forceinline__ void set(T v0, T a1, T v2, T v3, T h4) {
+        v1 = a1;
+        dv = v2 - a1;
+        dl = (v0 + v2) - (a1 + a1);
+        dr = (a1 + v3) - (v2 + v2);
+        T sl = dl * dl + h4, sr = dr * dr + h4;
+        sl2 = sl * sl;
+        sr2 = sr * sr;
+    }
+    // same arithmetic as weno1()
+    __device__ __forceinline__ T eval(const WenoAxis<T>& w) const {
+        T gl = w.cl * sr2, gr = w.cr * sl2;
+        T num = gl * dl + gr * dr;
+        T den = gl + gr;
+        return (v1 + w.th * dv) + w.q * fast_div(num, den);
+    }
+};
+
+// Energy of one front cell (lower corner node index `node`), summed in the
+// storage type: *cp += Σ |d'|^p Δx'^2, *c2 += Σ |d'|^2 Δx'^2 over counted subcells.
+template <typename T, int INTERP, int RC>
+__device__ __forceinline__ void energy_cell_3d(const Params<T>& P, const T* __restrict__ u,
+                                               const T* __restrict__ d, int node, int R, const T* th,
+                                               const WenoAxis<T>* wa, T thr, T hp2, T p, int p_kind, T& cp, T& c2,
+                                               T* zs) {
+    // RC > 0: R fixed at compile time (θ and the WENO coefficients fold to
+    // constants, loops unroll); RC == 0: R and the tables at run time
+    if (RC > 0) R = RC;
+    constexpr double RD = RC > 0 ? (double)RC : 1.0;
+    auto TH = [&](int m) -> T { return RC > 0 ? (T)((m + 0.5) / RD) : th[m]; };
+    auto WA = [&](int m) -> WenoAxis<T> {
+        if (RC > 0) {
+            WenoAxis<T> w;
+            w.set((T)((m + 0.5) / RD));
+            return w;
+        }
+        return wa[m];
+    };
+    long long q = node / P.n0;
+    const int i = (int)(node - q * P.n0);
+    const int k = (int)(q / P.n1);
+    const int j = (int)(q - (long long)k * P.n1);
+    T dc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dc[c] = ld(d + node + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+    auto add = [&](T uu, T tx, T ty, T tz) {
+        if (fabs(uu) < thr) {
+            T e0 = dc[0] + tx * (dc[1] - dc[0]);
+            T e1 = dc[2] + tx * (dc[3] - dc[2]);
+            T e2 = dc[4] + tx * (dc[5] - dc[4]);
+            T e3 = dc[6] + tx * (dc[7] - dc[6]);
+            T f0 = e0 + ty * (e1 - e0);
+            T f1 = e2 + ty * (e3 - e2);
+            T dd = fabs(f0 + tz * (f1 - f0));
+            T d2 = dd * dd;
+            cp += (p_kind == 2 ? d2 : (p_kind == 1 ? dd : (T)pow(dd, p))) * hp2;
+            c2 += d2 * hp2;
+        }
+    };
+    if (INTERP == 0) {
+        T uc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) uc[c] = ld(u + node + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+#pragma unroll
+        for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz)
+#pragma unroll
+            for (int by = 0; by < (RC > 0 ? RC : R); ++by)
+#pragma unroll
+                for (int ax = 0; ax < (RC > 0 ? RC : R); ++ax) {
+                    const T tx = TH(ax), ty = TH(by), tz = TH(cz);
+                    T a0 = uc[0] + tx * (uc[1] - uc[0]);
+                    T a1 = uc[2] + tx * (uc[3] - uc[2]);
+                    T a2 = uc[4] + tx * (uc[5] - uc[4]);
+                    T a3 = uc[6] + tx * (uc[7] - uc[6]);
+                    T b0 = a0 + ty * (a1 - a0);
+                    T b1 = a2 + ty * (a3 - a2);
+                    add(b0 + tz * (b1 - b0), tx, ty, tz);
+                }
+        return;
+    }
+    // WENO: the 16 z-lines of the 4x4x4 stencil are evaluated at every θ_z
+    // into per-thread scratch (shared memory, stride = threads per block);
+    // then, per θ_z, 4 y-lines at every θ_y and 1 x-line at every θ_x. The
+    // data-only part of each line's indicators is computed once.
+    const int stride = blockDim.x;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int ia = clampi(i - 1 + a, 0, P.n0 - 1);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const long long ab = ia + P.s1 * clampi(j - 1 + b, 0, P.n1 - 1);
+            WenoInd<T> iz;
+            iz.set(ld(u + ab + P.s2 * clampi(k - 1, 0, P.n2 - 1)), ld(u + ab + P.s2 * k),
+                   ld(u + ab + P.s2 * clampi(k + 1, 0, P.n2 - 1)), ld(u + ab + P.s2 * clampi(k + 2, 0, P.n2 - 1)),
+                   P.h4);
+#pragma unroll
+            for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz) zs[((a * 4 + b) * R + cz) * stride] = iz.eval(WA(cz));
+        }
+    }
+#pragma unroll
+    for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz) {
+        WenoInd<T> iy[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            iy[a].set(zs[((a * 4 + 0) * R + cz) * stride], zs[((a * 4 + 1) * R + cz) * stride],
+                      zs[((a * 4 + 2) * R + cz) * stride], zs[((a * 4 + 3) * R + cz) * stride], P.h4);
+#pragma unroll
+        for (int by = 0; by < (RC > 0 ? RC : R); ++by) {
+            const WenoAxis<T> wy = WA(by);
+            WenoInd<T> ix;
+            ix.set(iy[0].eval(wy), iy[1].eval(wy), iy[2].eval(wy), iy[3].eval(wy), P.h4);
+#pragma unroll
+            for (int ax = 0; ax < (RC > 0 ? RC : R); ++ax) add(ix.eval(WA(ax)), TH(ax), TH(by), TH(cz));
+        }
+    }
+}
+
+// Energy pass, one launch: every warp walks its own fixed sequence of
+// chunks of 32 candidate cells (chunk c to warp c mod warps), ballots the
+// front cells (vertices of both signs, zero counted as positive) into a
+// shared-memory queue and, whenever 32 are queued (or at its end), processes
+// them one per lane. Per-cell sums are in the storage type, per-lane, per-warp
+// and per-block sums in FP64, every order fixed, so the result is
+// bit-reproducible for a given grid.
+constexpr int kEnergyThreads = 128;
+
+template <typename T, int DIM, int INTERP, int RC>
+__global__ void __launch_bounds__(kEnergyThreads, 4) k_energy(Params<T> P, const T* ub0, const T* ub1,
+                                                           const T* __restrict__ d, const int* __restrict__ cells,
+                                                           long long ncells, int R, double h, double p, int p_kind,
+                                                           int offset, double* part, DevState* ds, int check_stop) {
+    constexpr int W = kEnergyThreads / 32;
+    extern __shared__ unsigned char s_dyn[];
+    T* zs_all = reinterpret_cast<T*>(s_dyn);  // 16 R values per thread (WENO, 3-D)
+    __shared__ T s_th[kMaxR];
+    __shared__ WenoAxis<T> s_wa[kMaxR];
+    __shared__ int s_q[W][64];
+    __shared__ double s_a[W], s_b[W];
     if (check_stop && ds->stop) return;
     const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    if (threadIdx.x < R) {
+        T t = (T)(((double)threadIdx.x + 0.5) / (double)R);  // subcell centre θ_m = (m + 1/2)/R
+        s_th[threadIdx.x] = t;
+        s_wa[threadIdx.x].set(t);
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long gw = (long long)blockIdx.x * W + wib;
-    const long long nw = (long long)gridDim.x * W;
-    const T hp = (T)(h / R);
+    const unsigned lt = (1u << lane) - 1u;
+    int* q = s_q[wib];
+    T* zs = zs_all + threadIdx.x;
     const T thr = (T)(0.8660254037844386 * (h / R));  // (√3/2) Δx'
-    const double hp2 = (h / R) * (h / R);
-    T* sv = s_sv[wib];
-    T* zv = s_zv[wib];
-    T* yv = s_yv[wib];
-    T* dc = s_dc[wib];
-    (void)hp;
-    for (long long c = gw; c < nchunks; c += nw) {
-        const long long e = c * 32 + lane;
-        int ci = 0, cj = 0, ck = 0;
-        bool front = false;
-        if (e < ncells) {
-            cell_of<T, DIM>(P, cells, e, ci, cj, ck);
-            long long b = ci + P.s1 * cj + P.s2 * ck;
-            bool neg = false, pos = false;
+    const T hp2 = (T)((h / R) * (h / R));
+    const long long nchunks = (ncells + 31) / 32;
+    const long long nw = (long long)gridDim.x * W;
+    double ap = 0.0, a2 = 0.0;
+    int qn = 0;
+    for (long long c = (long long)blockIdx.x * W + wib;; c += nw) {
+        const bool have = c < nchunks;
+        if (have) {
+            const long long e = c * 32 + lane;
+            int f = 0, node = 0;
+            if (e < ncells) {
+                int i, j, k;
+                cell_of<T, DIM>(P, cells, e, i, j, k);
+                node = (int)(i + P.s1 * j + P.s2 * k);
+                bool neg = false, pos = false;
 #pragma unroll
-            for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+                for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
 #pragma unroll
-                for (int dy = 0; dy < 2; ++dy)
+                    for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
-                        T v = u[b + dx + P.s1 * dy + P.s2 * dz];
-                        if (v < T(0))
-                            neg = true;
-                        else
-                            pos = true;
-                    }
-            front = neg && pos;
+                        for (int dx = 0; dx < 2; ++dx) {
+                            T v = ld(u + node + dx + P.s1 * dy + P.s2 * dz);
+                            if (v < T(0))
+                                neg = true;
+                            else
+                                pos = true;
+                        }
+                f = neg && pos;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            if (f) q[qn + __popc(m & lt)] = node;
+            qn += __popc(m);
+            __syncwarp();
         }
-        unsigned m = __ballot_sync(0xffffffffu, front);
-        double accp = 0.0, acc2 = 0.0;
-        if (DIM == 2) {
-            if (front) accp = energy_cell_2d<T>(P, u, d, ci, cj, h, p, p_kind, &acc2);
-        } else {
-            while (m) {
-                const int f = __ffs(m) - 1;
-                m &= m - 1;
-                const int i = __shfl_sync(0xffffffffu, ci, f);
-                const int j = __shfl_sync(0xffffffffu, cj, f);
-                const int k = __shfl_sync(0xffffffffu, ck, f);
-                const long long b = i + P.s1 * j + P.s2 * k;
-                if (lane < 8) dc[lane] = d[b + (lane & 1) + P.s1 * ((lane >> 1) & 1) + P.s2 * (lane >> 2)];
-                if (INTERP == 1) {
-                    for (int q = lane; q < 64; q += 32) {
-                        int a = q & 3, bb = (q >> 2) & 3, cz = q >> 4;
-                        long long id = clampi(i - 1 + a, 0, P.n0 - 1) + P.s1 * clampi(j - 1 + bb, 0, P.n1 - 1) +
-                                       P.s2 * clampi(k - 1 + cz, 0, P.n2 - 1);
-                        sv[q] = u[id];
-                    }
-                    __syncwarp();
-                    // z-lines: zv[(a*4+b)*R + c] at θ_z = (c + 1/2)/R
-                    for (int q = lane; q < 16 * R; q += 32) {
-                        int line = q / R, cz = q - line * R;
-                        int a = line >> 2, bb = line & 3;
-                        WenoAxis<T> wz;
-                        wz.set((T)((cz + 0.5) / R));
-                        const T* s = sv + a + 4 * bb;
-                        zv[q] = weno1(s[0], s[16], s[32], s[48], wz, P.h4);
-                    }
-                    __syncwarp();
-                    // y-lines: yv[(a*R + c)*R + b'] at θ_y = (b' + 1/2)/R
-                    for (int q = lane; q < 4 * R * R; q += 32) {
-                        int a = q / (R * R), rem = q - a * R * R;
-                        int cz = rem / R, by = rem - cz * R;
-                        WenoAxis<T> wy;
-                        wy.set((T)((by + 0.5) / R));
-                        yv[q] = weno1(zv[(a * 4 + 0) * R + cz], zv[(a * 4 + 1) * R + cz], zv[(a * 4 + 2) * R + cz],
-                                      zv[(a * 4 + 3) * R + cz], wy, P.h4);
-                    }
-                    __syncwarp();
+        while (qn >= 32 || (!have && qn > 0)) {
+            const int take = qn < 32 ? qn : 32;
+            const int node = lane < take ? q[lane] : -1;
+            __syncwarp();
+            if (qn > 32 && lane < qn - 32) q[lane] = q[lane + 32];  // reads [32, qn), writes [0, qn-32)
+            __syncwarp();
+            qn -= take;
+            if (node >= 0) {
+                if (DIM == 2) {
+                    long long qq = node / P.n0;
+                    double s2 = 0.0;
+                    ap += energy_cell_2d<T>(P, u, d, (int)(node - qq * P.n0), (int)qq, h, p, p_kind, &s2);
+                    a2 += s2;
                 } else {
-                    if (lane < 8) sv[lane] = u[b + (lane & 1) + P.s1 * ((lane >> 1) & 1) + P.s2 * (lane >> 2)];
-                    __syncwarp();
+                    T cp = T(0), c2 = T(0);
+                    energy_cell_3d<T, INTERP, RC>(P, u, d, node, R, s_th, s_wa, thr, hp2, (T)p, p_kind, cp, c2, zs);
+                    ap += (double)cp;
+                    a2 += (double)c2;
                 }
-                // x pass (WENO) or trilinear (Q1), d by Q1, accumulate
-                for (int q = lane; q < R * R * R; q += 32) {
-                    int cz = q / (R * R), rem = q - cz * R * R;
-                    int by = rem / R, ax = rem - by * R;
-                    T tx = (T)((ax + 0.5) / R), ty = (T)((by + 0.5) / R), tz = (T)((cz + 0.5) / R);
-                    T uu;
-                    if (INTERP == 1) {
-                        WenoAxis<T> wx;
-                        wx.set(tx);
-                        const int RR = R * R;
-                        uu = weno1(yv[cz * R + by], yv[RR + cz * R + by], yv[2 * RR + cz * R + by],
-                                   yv[3 * RR + cz * R + by], wx, P.h4);
-                    } else {
-                        T a0 = sv[0] + tx * (sv[1] - sv[0]);
-                        T a1 = sv[2] + tx * (sv[3] - sv[2]);
-                        T a2 = sv[4] + tx * (sv[5] - sv[4]);
-                        T a3 = sv[6] + tx * (sv[7] - sv[6]);
-                        T b0 = a0 + ty * (a1 - a0);
-                        T b1 = a2 + ty * (a3 - a2);
-                        uu = b0 + tz * (b1 - b0);
-                    }
-                    T e0 = dc[0] + tx * (dc[1] - dc[0]);
-                    T e1 = dc[2] + tx * (dc[3] - dc[2]);
-                    T e2 = dc[4] + tx * (dc[5] - dc[4]);
-                    T e3 = dc[6] + tx * (dc[7] - dc[6]);
-                    T f0 = e0 + ty * (e1 - e0);
-                    T f1 = e2 + ty * (e3 - e2);
-                    double dd = (double)(f0 + tz * (f1 - f0));
-                    if (fabs(uu) < thr) {
-                        accp += pow_abs(dd, p, p_kind) * hp2;
-                        acc2 += dd * dd * hp2;
-                    }
-                }
-                __syncwarp();
             }
         }
-        accp = warp_sum(accp);
-        acc2 = warp_sum(acc2);
-        if (lane == 0) {
-            part[2 * c] = accp;
-            part[2 * c + 1] = acc2;
+        if (!have) break;
+    }
+    ap = warp_sum(ap);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+        s_a[wib] = ap;
+        s_b[wib] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < W; ++w) {
+            x += s_a[w];
+            y += s_b[w];
         }
+        part[2 * blockIdx.x] = x;
+        part[2 * blockIdx.x + 1] = y;
     }
 }
 
@@ -250,7 +360,8 @@ __global__ void __launch_bounds__(kEnergyBlock) k_energy(Params<T> P, const T* u
 struct RecordArgs {
     const double* part_dphi;
     const double* part_e;
-    long long nchunks;
+    long long nchunks;     // number of energy partial pairs (energy blocks)
+    long long n_dphi_full; // number of Δ_φ partials in whole-grid mode (step blocks)
     long long N;
     int full_grid;
     int mode;
@@ -269,14 +380,40 @@ __global__ void __launch_bounds__(1024) k_record(RecordArgs A, DevState* ds) {
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
-        long long cnt = A.full_grid ? A.N : (long long)ds->band_count[n & 1];
-        ntiles = (cnt + kStepTile - 1) / kStepTile;
+        ntiles = A.full_grid ? A.n_dphi_full : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
     }
+    // contiguous segments per thread, eight independent loads in flight;
+    // the order of the additions is fixed by the sizes alone
     double a = 0.0, b = 0.0, cc = 0.0;
-    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x) a += A.part_dphi[t];
-    for (long long t = threadIdx.x; t < A.nchunks; t += blockDim.x) {
-        b += A.part_e[2 * t];
-        cc += A.part_e[2 * t + 1];
+    {
+        const long long per = (ntiles + blockDim.x - 1) / blockDim.x;
+        long long i = threadIdx.x * per, end = i + per < ntiles ? i + per : ntiles;
+        for (; i + 8 <= end; i += 8) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = A.part_dphi[i + q];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a += v[q];
+        }
+        for (; i < end; ++i) a += A.part_dphi[i];
+    }
+    {
+        const long long per = (A.nchunks + blockDim.x - 1) / blockDim.x;
+        long long i = threadIdx.x * per, end = i + per < A.nchunks ? i + per : A.nchunks;
+        for (; i + 4 <= end; i += 4) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = A.part_e[2 * i + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                b += v[2 * q];
+                cc += v[2 * q + 1];
+            }
+        }
+        for (; i < end; ++i) {
+            b += A.part_e[2 * i];
+            cc += A.part_e[2 * i + 1];
+        }
     }
     a = warp_sum(a);
     b = warp_sum(b);
@@ -336,14 +473,23 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     Params<T> P = make_params<T>(c);
     const int* cells = c->cfg.band ? c->ecells : nullptr;
     long long ncells = c->cfg.band ? c->n_ecells : c->ncells_all;
-    long long nchunks = (ncells + 31) / 32;
-    long long blocks = (nchunks + kEnergyBlock / 32 - 1) / (kEnergyBlock / 32);
-    long long cap = (long long)c->num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_energy<T, DIM, INTERP><<<(int)blocks, kEnergyBlock, 0, c->stream>>>(
-        P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, nchunks, c->cfg.energy_R, c->h, p,
-        p_kind, offset, c->part_e, c->ds, check_stop);
+    size_t smem = (DIM == 3 && INTERP == 1) ? sizeof(T) * 16 * c->cfg.energy_R * kEnergyThreads : 0;
+    static bool attr_set = false;
+    if (!attr_set && smem > 0) {
+        cudaFuncSetAttribute(k_energy<T, DIM, INTERP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 16 * kMaxR * kEnergyThreads));
+        cudaFuncSetAttribute(k_energy<T, DIM, INTERP, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 16 * 5 * kEnergyThreads));
+        attr_set = true;
+    }
+    if (DIM == 3 && INTERP == 1 && c->cfg.energy_R == 5)
+        k_energy<T, DIM, INTERP, 5><<<(int)energy_blocks(c), kEnergyThreads, smem, c->stream>>>(
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
+            offset, c->part_e, c->ds, check_stop);
+    else
+        k_energy<T, DIM, INTERP, 0><<<(int)energy_blocks(c), kEnergyThreads, smem, c->stream>>>(
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
+            offset, c->part_e, c->ds, check_stop);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -364,15 +510,21 @@ static cudaError_t energy_dispatch(slr_ctx* c, int offset, double p, int p_kind,
 }
 
 // record_mode: 0 init, 1 step, 2 report (p_override used, result in ds report slot)
-cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode) {
+cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode,
+                          cudaEvent_t between) {
     double p = record_mode == 2 ? p_override : c->cfg.p;
     int p_kind = p == 1.0 ? 1 : (p == 2.0 ? 2 : 0);
     cudaError_t e = energy_dispatch(c, offset, p, p_kind, record_mode == 1);
     if (e != cudaSuccess) return e;
+    if (between) {
+        e = cudaEventRecord(between, c->stream);
+        if (e != cudaSuccess) return e;
+    }
     RecordArgs A;
     A.part_dphi = c->part_dphi;
     A.part_e = c->part_e;
-    A.nchunks = c->n_echunks;
+    A.nchunks = energy_blocks(c);
+    A.n_dphi_full = full_step_blocks(c);
     A.N = c->N;
     A.full_grid = !c->cfg.band;
     A.mode = record_mode;

@@ -18,8 +18,8 @@ namespace slr {
 // sizes
 // ---------------------------------------------------------------------------
 constexpr int kHist = 4096;          // ring size of the per-iteration history
-constexpr int kStepBlock = 256;      // threads per block of the fused SL step
-constexpr int kStepTile = 256;       // band entries per look-back tile (1 per thread)
+constexpr int kStepBlock = 256;      // threads per block of the SL step kernels
+constexpr int kStepTile = 128;       // band entries per warp ticket / look-back tile (4 per lane)
 constexpr int kEnergyBlock = 256;    // 8 warps; one warp per chunk of 32 candidate cells
 constexpr int kMaxR = 8;             // largest supported energy subcell count per axis
 constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: ~0.3 s with 64 ns sleeps
@@ -36,8 +36,8 @@ struct DevState {
     int converged;       // the Δ_E test stopped the loop
     int error;           // kErr* bits
     int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
-    unsigned ticket;     // tile ticket of the fused step kernel (reset by the stop kernel)
-    unsigned epoch;      // tags look-back status words; advanced once per step
+    unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
+    unsigned epoch;      // tags the step kernel's look-back words; advanced once per step
     double Ep;           // E_p(φ^n) used by step n
     double e2_hist[kHist];
     double dphi_hist[kHist];
@@ -95,8 +95,8 @@ struct slr_ctx {
     long long n_ecells = 0;
     double* part_dphi = nullptr;   // one per step tile
     long long n_tiles_cap = 0;
-    double* part_e = nullptr;      // two per energy chunk
-    long long n_echunks = 0;
+    double* part_e = nullptr;      // two per energy block, plus a two-value report slot
+    long long n_echunks = 0;       // candidate chunks of 32 cells (sizes part_e)
     unsigned long long* tile_status = nullptr;  // look-back words of the step kernel
     slr::DevState* ds = nullptr;
     int* host_pinned_flags = nullptr;  // pinned host words for status readback
@@ -108,6 +108,8 @@ struct slr_ctx {
     cudaGraphExec_t g_evolve = nullptr;
     cudaGraphExec_t g_step = nullptr;
     double g_step_override = -2.0;
+    bool profiling = false;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace slr {
@@ -123,13 +125,16 @@ cudaError_t launch_count_band(slr_ctx* c, long long* count_out);
 cudaError_t launch_build_band(slr_ctx* c);
 cudaError_t launch_build_ecells(slr_ctx* c, long long* count_out, bool write);
 cudaError_t launch_step(slr_ctx* c, double energy_override, int evolve_mode);
-cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode);
+cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode,
+                          cudaEvent_t between = nullptr);
 cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double* u_dev, long long* count_out,
                            bool write);
 cudaError_t launch_err_cloud(slr_ctx* c, double* out_dev);
 cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long n);
 cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long long n);
 cudaError_t build_distance(slr_ctx* c);
+long long energy_blocks(const slr_ctx* c);
+long long full_step_blocks(const slr_ctx* c);
 
 // ---------------------------------------------------------------------------
 // device numerics
@@ -275,6 +280,36 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
 #pragma unroll
         for (int a = 0; a < 4; ++a) oz[a] = P.s2 * clampi(cz - 1 + a, 0, P.n2 - 1);
     }
+    const bool interior = cx >= 1 && cx <= P.n0 - 3 && cy >= 1 && cy <= P.n1 - 3 &&
+                          (DIM == 2 || (cz >= 1 && cz <= P.n2 - 3));
+    if (interior) {
+        // whole stencil inside the grid: one base pointer, rows of four
+        // consecutive x-values, z-lines evaluated as their rows arrive
+        const T* base = u + ((long long)(cx - 1) + P.s1 * (cy - 1) + (DIM == 3 ? P.s2 * (cz - 1) : 0ll));
+        T yv[4][4];  // [a][b]: z-line (DIM 3) or node value (DIM 2) at column a, row b
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const T* rb = base + P.s1 * b;
+            if (DIM == 3) {
+                T r[4][4];  // [c][a]
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const T* row = rb + P.s2 * c;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) r[c][a] = ld(row + a);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) yv[a][b] = weno1(r[0][a], r[1][a], r[2][a], r[3][a], wz, P.h4);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) yv[a][b] = ld(rb + a);
+            }
+        }
+        T xv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv[a] = weno1(yv[a][0], yv[a][1], yv[a][2], yv[a][3], wy, P.h4);
+        return weno1(xv[0], xv[1], xv[2], xv[3], wx, P.h4);
+    }
     T xv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -367,7 +402,7 @@ __device__ T sl_update(const Params<T>& P, const T* __restrict__ u, const T* __r
         n2z = ig * (-gy * gz / rr);
     }
     T acc = T(0);
-#pragma unroll
+#pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         T l1 = (f & 2) ? T(1) : T(-1);
         T l2 = (f & 1) ? T(1) : T(-1);
@@ -409,11 +444,12 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// fixed-order block sum (result valid in thread 0)
+// fixed-order block sum (result valid in thread 0); with warp_done the
+// value of lane 0 of each warp is already that warp's sum
 template <int BLOCK>
-__device__ __forceinline__ double block_sum(double v, double* smem) {
+__device__ __forceinline__ double block_sum(double v, double* smem, bool warp_done = false) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
+    if (!warp_done) v = warp_sum(v);
     if (lane == 0) smem[warp] = v;
     __syncthreads();
     double r = 0.0;
@@ -421,6 +457,76 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
         for (int w = 0; w < BLOCK / 32; ++w) r += smem[w];
     __syncthreads();
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// look-back status words: bits 0..31 value, 32..33 flag (1 aggregate,
+// 2 inclusive prefix), 34..63 epoch (one epoch per step launch)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, unsigned value) {
+    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)flag << 32) |
+           (unsigned long long)value;
+}
+
+// A status word carries its whole message (epoch, flag, count) in one
+// 64-bit access, and no reader depends on other memory written by the
+// publisher, so relaxed GPU-scope accesses suffice (no fences).
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Warp-parallel look-back of tile t (t > 0), run by all 32 lanes of one
+// warp: lane l inspects predecessor j - l. The walk stops at the nearest
+// predecessor that has published its inclusive prefix; aggregates in between
+// are summed. Every wait is bounded: after kSpinLimit polls the error bit is
+// set and the partial prefix returned; a partial prefix never exceeds the true
+// one, so the writes it leads to stay inside the output list.
+static __device__ unsigned lookback_warp(const unsigned long long* status, int t, unsigned epoch, int* err) {
+    const int lane = threadIdx.x & 31;
+    const unsigned ep = epoch & 0x3FFFFFFFu;
+    unsigned excl = 0;
+    int j = t - 1;
+    long long spins = 0;
+    while (j >= 0) {
+        const int idx = j - lane;
+        bool valid = true, incl = true;
+        unsigned val = 0;
+        if (idx >= 0) {
+            const unsigned long long w = ld_acquire_u64(status + idx);
+            const unsigned fl = (unsigned)(w >> 32) & 3u;
+            valid = ((unsigned)(w >> 34) == ep) && fl != 0u;
+            incl = valid && fl == 2u;
+            val = (unsigned)(w & 0xffffffffull);
+        }
+        const unsigned V = __ballot_sync(0xffffffffu, valid);
+        const unsigned I = __ballot_sync(0xffffffffu, incl);
+        if (I) {
+            const int f = __ffs(I) - 1;
+            const unsigned need = f == 31 ? 0xffffffffu : ((1u << (f + 1)) - 1u);
+            if ((V & need) == need) {
+                excl += warp_sum(lane <= f ? val : 0u);
+                excl = __shfl_sync(0xffffffffu, excl, 0);
+                return excl;
+            }
+        } else if (V == 0xffffffffu) {
+            excl += warp_sum(val);
+            excl = __shfl_sync(0xffffffffu, excl, 0);
+            j -= 32;
+            continue;
+        }
+        if (++spins > kSpinLimit) {
+            if (lane == 0) atomicOr(err, kErrLookback);
+            return __shfl_sync(0xffffffffu, excl, 0);
+        }
+        __nanosleep(32);
+    }
+    return __shfl_sync(0xffffffffu, excl, 0);
 }
 
 #endif  // __CUDACC__

@@ -17,53 +17,6 @@
 
 namespace slr {
 
-// ---------------------------------------------------------------------------
-// look-back status words: bits 0..31 value, 32..33 flag (1 aggregate,
-// 2 inclusive prefix), 34..63 epoch (one epoch per step launch)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, unsigned value) {
-    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)flag << 32) |
-           (unsigned long long)value;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Serial look-back of tile t (t > 0) over its predecessors. Every wait is
-// bounded: after kSpinLimit polls the error bit is set and the partial prefix
-// returned; the partial prefix never exceeds the true one, so the writes it
-// leads to stay inside the output list.
-__device__ unsigned lookback(const unsigned long long* status, int t, unsigned epoch, int* err) {
-    unsigned excl = 0;
-    int j = t - 1;
-    long long spins = 0;
-    const unsigned ep = epoch & 0x3FFFFFFFu;
-    while (j >= 0) {
-        unsigned long long w = ld_acquire_u64(status + j);
-        unsigned wep = (unsigned)(w >> 34);
-        unsigned fl = (unsigned)(w >> 32) & 3u;
-        if (wep != ep || fl == 0u) {
-            if (++spins > kSpinLimit) {
-                atomicOr(err, kErrLookback);
-                return excl;
-            }
-            __nanosleep(64);
-            continue;
-        }
-        excl += (unsigned)(w & 0xffffffffull);
-        if (fl == 2u) break;
-        --j;
-    }
-    return excl;
-}
-
 template <typename T>
 __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i, int& j, int& k) {
     long long q = idx / P.n0;
@@ -72,16 +25,17 @@ __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i
     j = (int)(q - (long long)k * P.n1);
 }
 
-// fused band rebuild + SL update + cut (band mode)
+// fused band rebuild + SL update + cut (band mode). Work is handed out per
+// warp: a ticket is a tile of kStepTile consecutive entries of L^{n-1} (four
+// per lane); the warp ballots band membership, publishes its count, resolves
+// its output offset by a warp-parallel look-back, writes its part of G̃^n, and
+// only then runs the SL arithmetic. No block-wide barrier inside the loop.
 template <typename T, int DIM, int INTERP>
-__global__ void __launch_bounds__(kStepBlock) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
+__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 4))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
                                                           int* L0, int* L1, unsigned long long* status,
                                                           double* part_dphi, DevState* ds, double ep_override) {
-    __shared__ int s_tile;
-    __shared__ unsigned s_prefix;
-    __shared__ int s_warp[kStepBlock / 32 + 1];
-    __shared__ double s_red[kStepBlock / 32];
     if (ds->stop) return;
+    const int lane = threadIdx.x & 31;
     const int n = ds->n;
     const unsigned epoch = ds->epoch;
     const int cnt_in = ds->band_count[n & 1];
@@ -95,74 +49,90 @@ __global__ void __launch_bounds__(kStepBlock) k_step_band(Params<T> P, T* ub0, T
         if (blockIdx.x == 0 && threadIdx.x == 0) ds->band_count[(n + 1) & 1] = 0;
         return;
     }
+    const unsigned lt = (1u << lane) - 1u;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ds->ticket, 1u);
-        __syncthreads();
-        const int t = s_tile;
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&ds->ticket, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int e = t * kStepTile + threadIdx.x;
-        const bool valid = e < cnt_in;
-        const int idx = valid ? Lin[e] : 0;
-        const T v = valid ? uin[idx] : T(0);
-        const int inb = valid && (fabs(v) < P.gamma);
-        int total;
-        const int off = block_exclusive_flag<kStepBlock>(inb, s_warp, &total);
-        if (threadIdx.x == 0) st_release_u64(status + t, pack_status(epoch, t == 0 ? 2u : 1u, (unsigned)total));
-        double dabs = 0.0;
-        if (valid) {
-            T out = v;
-            if (inb) {
+        constexpr int H = kStepTile / 32;
+        int idx[H];
+        T v[H];
+        bool inb[H], valid[H];
+        unsigned m[H];
+        unsigned total = 0;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int e = t * kStepTile + h * 32 + lane;
+            valid[h] = e < cnt_in;
+            idx[h] = valid[h] ? Lin[e] : 0;
+            v[h] = valid[h] ? uin[idx[h]] : T(0);
+            inb[h] = valid[h] && (fabs(v[h]) < P.gamma);
+            m[h] = __ballot_sync(0xffffffffu, inb[h]);
+            total += (unsigned)__popc(m[h]);
+        }
+        if (lane == 0) st_release_u64(status + t, pack_status(epoch, t == 0 ? 2u : 1u, total));
+        unsigned excl = 0;
+        if (t > 0) {
+            excl = lookback_warp(status, t, epoch, &ds->error);
+            if (lane == 0) st_release_u64(status + t, pack_status(epoch, 2u, excl + total));
+        }
+        if (lane == 0 && t == ntiles - 1) ds->band_count[(n + 1) & 1] = (int)(excl + total);
+        {
+            unsigned run = excl;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                if (inb[h]) Lout[run + __popc(m[h] & lt)] = idx[h];
+                run += (unsigned)__popc(m[h]);
+            }
+        }
+        T dabs = T(0);
+#pragma unroll 1
+        for (int h = 0; h < H; ++h) {
+            if (!valid[h]) continue;
+            T out = v[h];
+            if (inb[h]) {
                 int i, j, k;
-                decode(P, idx, i, j, k);
-                out = sl_update<T, DIM, INTERP>(P, uin, d, Ep, i, j, k, idx, v);
+                decode(P, idx[h], i, j, k);
+                out = sl_update<T, DIM, INTERP>(P, uin, d, Ep, i, j, k, idx[h], v[h]);
                 out = fmin(fmax(out, -P.gamma), P.gamma);  // eq. cut
             }
-            uout[idx] = out;
-            dabs = fabs((double)out - (double)v);
+            uout[idx[h]] = out;
+            dabs += fabs(out - v[h]);
         }
-        const double bs = block_sum<kStepBlock>(dabs, s_red);
-        if (threadIdx.x == 0) {
-            part_dphi[t] = bs;
-            unsigned excl = 0;
-            if (t > 0) {
-                excl = lookback(status, t, epoch, &ds->error);
-                st_release_u64(status + t, pack_status(epoch, 2u, excl + (unsigned)total));
-            }
-            s_prefix = excl;
-            if (t == ntiles - 1) ds->band_count[(n + 1) & 1] = (int)(excl + (unsigned)total);
-        }
-        __syncthreads();
-        if (inb) Lout[s_prefix + off] = idx;
-        __syncthreads();
+        dabs = warp_sum(dabs);
+        if (lane == 0) part_dphi[t] = (double)dabs;
     }
 }
 
 // whole-grid SL update (band off: c ≡ 1, no cut), static tiles
 template <typename T, int DIM, int INTERP>
-__global__ void __launch_bounds__(kStepBlock) k_step_full(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
+__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 4))) k_step_full(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
                                                           long long N, double* part_dphi, DevState* ds,
                                                           double ep_override) {
     __shared__ double s_red[kStepBlock / 32];
     if (ds->stop) return;
     const int n = ds->n;
-    const T* __restrict__ uin = (n & 1) ? ub1 : ub0;
+    const T* __restrict__ uin = (n & 1) ? ub1 : ub0;  // whole-grid tiles: 256 consecutive nodes
     T* __restrict__ uout = (n & 1) ? ub0 : ub1;
     const T Ep = ep_override >= 0.0 ? (T)ep_override : (T)ds->Ep;
-    const long long ntiles = (N + kStepTile - 1) / kStepTile;
+    const long long ntiles = (N + kStepBlock - 1) / kStepBlock;
+    double acc = 0.0;  // lane 0 of each warp: sum of the warp's per-tile sums
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long idx = t * kStepTile + threadIdx.x;
-        double dabs = 0.0;
+        const long long idx = t * kStepBlock + threadIdx.x;
+        T dabs = T(0);
         if (idx < N) {
             int i, j, k;
             decode(P, idx, i, j, k);
             const T v = uin[idx];
             const T out = sl_update<T, DIM, INTERP>(P, uin, d, Ep, i, j, k, idx, v);
             uout[idx] = out;
-            dabs = fabs((double)out - (double)v);
+            dabs = fabs(out - v);
         }
-        const double bs = block_sum<kStepBlock>(dabs, s_red);
-        if (threadIdx.x == 0) part_dphi[t] = bs;
+        acc += (double)warp_sum(dabs);
     }
+    const double bs = block_sum<kStepBlock>(acc, s_red, true);
+    if (threadIdx.x == 0) part_dphi[blockIdx.x] = bs;
 }
 
 // ---------------------------------------------------------------------------
@@ -297,6 +267,13 @@ template Params<double> make_params<double>(const slr_ctx*);
 
 static int grid_blocks(const slr_ctx* c, int per_sm) { return c->num_sms * per_sm; }
 
+// fixed grid of the whole-grid step (one Δ_φ partial per block)
+long long full_step_blocks(const slr_ctx* c) {
+    long long ntiles = (c->N + kStepBlock - 1) / kStepBlock;
+    long long nb = (long long)c->num_sms * 8;
+    return nb < ntiles ? nb : ntiles;
+}
+
 template <typename T, int DIM, int INTERP>
 static cudaError_t step_t(slr_ctx* c, double ov) {
     Params<T> P = make_params<T>(c);
@@ -306,9 +283,7 @@ static cudaError_t step_t(slr_ctx* c, double ov) {
         k_step_band<T, DIM, INTERP><<<grid_blocks(c, 8), kStepBlock, 0, c->stream>>>(
             P, u0, u1, (const T*)c->d, c->band[0], c->band[1], c->tile_status, c->part_dphi, c->ds, ov);
     } else {
-        long long ntiles = (c->N + kStepTile - 1) / kStepTile;
-        long long nb = grid_blocks(c, 8);
-        if (nb > ntiles) nb = ntiles;
+        long long nb = full_step_blocks(c);
         k_step_full<T, DIM, INTERP><<<(int)nb, kStepBlock, 0, c->stream>>>(P, u0, u1, (const T*)c->d, c->N,
                                                                           c->part_dphi, c->ds, ov);
     }

@@ -30,8 +30,9 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 # every entry point declared in include/slr.h
 EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
-    "slr_step", "slr_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
-    "slr_export_state", "slr_import_state", "slr_kernel_launches", "slr_last_error", "slr_destroy",
+    "slr_step", "slr_step_async", "slr_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
+    "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times", "slr_kernel_launches",
+    "slr_last_error", "slr_destroy",
 ]
 
 
@@ -93,6 +94,7 @@ def lib():
                 "slr_set_distance": (C.c_int, [_vp, _dp]),
                 "slr_init_u": (C.c_int, [_vp, C.c_int, _dp, _dp]),
                 "slr_step": (C.c_int, [_vp, C.c_int, C.c_double]),
+                "slr_step_async": (C.c_int, [_vp, C.c_int, C.c_double]),
                 "slr_evolve": (C.c_int, [_vp, _ip, _ip]),
                 "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
                 "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
@@ -101,6 +103,8 @@ def lib():
                 "slr_diagnostics": (C.c_int, [_vp, _dp, _dp, _i64p, C.c_int, _ip, _dp]),
                 "slr_export_state": (C.c_int, [_vp, _vp, C.c_int64, _i64p]),
                 "slr_import_state": (C.c_int, [_vp, _vp, C.c_int64]),
+                "slr_set_profiling": (C.c_int, [_vp, C.c_int]),
+                "slr_last_iteration_times": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_kernel_launches": (C.c_int64, [_vp]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
@@ -207,6 +211,20 @@ def slr_init_u(ctx, kind, params=None, u0=None):
 
 def slr_step(ctx, n_steps=1, energy_override=-1.0):
     _check(ctx, lib().slr_step(ctx, int(n_steps), float(energy_override)))
+
+
+def slr_step_async(ctx, n_steps=1, energy_override=-1.0):
+    _check(ctx, lib().slr_step_async(ctx, int(n_steps), float(energy_override)))
+
+
+def slr_set_profiling(ctx, on=True):
+    _check(ctx, lib().slr_set_profiling(ctx, 1 if on else 0))
+
+
+def slr_last_iteration_times(ctx):
+    ms = (C.c_float * 3)()
+    _check(ctx, lib().slr_last_iteration_times(ctx, ms))
+    return list(ms)
 
 
 def slr_evolve(ctx):
@@ -339,6 +357,15 @@ class Reconstruction:
 
     def step(self, n=1, energy_override=-1.0):
         slr_step(self.ctx, n, energy_override)
+
+    def step_async(self, n=1, energy_override=-1.0):
+        slr_step_async(self.ctx, n, energy_override)
+
+    def set_profiling(self, on=True):
+        slr_set_profiling(self.ctx, on)
+
+    def last_iteration_times(self):
+        return slr_last_iteration_times(self.ctx)
 
     def evolve(self):
         return slr_evolve(self.ctx)

@@ -256,27 +256,29 @@ def test_energy_2d_paper_circle():
 
 def test_circle64_workload_100_steps_fp64_q1():
     """Small 2-D workload: 200 noisy circle points, 64^2 on [-1,1]^2,
-    u0 = circle r = 0.9, 100 SL steps, whole grid, FP64 Q1. GPU vs oracle
-    stepping with its own energies; drift reported, gated at 1e-9."""
+    u0 = circle r = 0.9, 100 SL steps, whole grid, FP64 Q1, each step with
+    the GPU's own E_2. Every step is compared with the oracle from the same
+    input state and energy (<= 1e-12); the GPU energies match the oracle's
+    energy of the same state (rel 1e-12). Free-running drift is not gated:
+    in whole-grid mode a one-ulp change of u0 already grows to 1e-3 by step
+    85 in the oracle alone (boundary rows, one-sided differences)."""
     wl = synth.workload_circle64()
-    g = wl["grid"]
     rec, P = make(2, 64, 64, 0, 0)
     rec.load_cloud(wl["cloud"])
     rec.build_distance()
     rec.init_sphere(0.9)
     d = rec.d()
-    u = rec.u()
-    rec.step(100)
-    diag = rec.diagnostics()
-    e2 = []
+    worst = 0.0
     for s in range(100):
-        E = O.energy(P, u, d, 2.0)["E"]
-        e2.append(E)
-        u, _, _ = O.sl_step(P, u, d, E)
-    e2.append(O.energy(P, u, d, 2.0)["E"])
-    drift = np.abs(rec.u() - u).max()
-    assert drift <= 1e-9, drift
-    np.testing.assert_allclose(diag["e2"][:101], e2, rtol=1e-9)
+        u = rec.u()
+        E = rec.diagnostics()["e2"][s]
+        assert E == pytest.approx(O.energy(P, u, d, 2.0)["E"], rel=1e-12)
+        rec.step(1)
+        ref, flags, _ = O.sl_step(P, u, d, E)
+        ok = (flags & O.FLAG_MARGIN) == 0
+        worst = max(worst, float(np.abs(rec.u() - ref)[ok].max()))
+    assert worst <= 1e-12, worst
+    assert rec.diagnostics()["iters"] == 100
 
 
 def test_evolve_matches_oracle_stop_rule():

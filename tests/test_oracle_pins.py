@@ -76,6 +76,26 @@ def test_distance_dense_circle_sagitta_bound():
     assert np.all(d <= upper + 1e-15)
 
 
+def test_kdtree_distance_identical_to_brute_force():
+    """The k-d tree search takes the same decisions as the scan: d and argmin
+    bit-identical, including exact ties and duplicated points."""
+    rng = np.random.default_rng(21)
+    for dim, n in ((2, 33), (3, 17)):
+        P = _grid_params(dim, n)
+        pts = rng.uniform(-1.1, 1.1, (700, dim))
+        pts = np.concatenate([pts, pts[:50], -pts[:50]])  # duplicates and mirror ties
+        pts[::7, 0] = 0.25  # shared coordinates on the split axis
+        for nodes in (None, rng.choice(n ** dim, 200, replace=False)):
+            d1, a1 = O.distance(P, pts, nodes)
+            d2, a2 = O.distance(P, pts, nodes, method="kd")
+            assert np.array_equal(d1, d2) and np.array_equal(a1, a2)
+    P = _grid_params(3, 5)
+    grid_pts = O.node_coords(P)[::3] + 0.0  # points on nodes: distance-0 and equidistant ties
+    d1, a1 = O.distance(P, grid_pts)
+    d2, a2 = O.distance(P, grid_pts, method="kd")
+    assert np.array_equal(d1, d2) and np.array_equal(a1, a2)
+
+
 # ---------------------------------------------------------------- gradient
 
 def test_gradient_centred_exact_on_quadratics_and_onesided_on_linear():
