@@ -73,12 +73,13 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     cudaGraph_t g = nullptr;
     long long l0 = c->launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    cudaError_t e1 = c->profiling ? cudaEventRecord(c->pev[0], c->stream) : cudaSuccess;
+    // external event-record nodes: recorded again at every replay
+    cudaError_t e1 = c->profiling ? cudaEventRecordWithFlags(c->pev[0], c->stream, cudaEventRecordExternal) : cudaSuccess;
     if (e1 == cudaSuccess) e1 = launch_step(c, ov, evolve);
-    if (e1 == cudaSuccess && c->profiling) e1 = cudaEventRecord(c->pev[1], c->stream);
+    if (e1 == cudaSuccess && c->profiling) e1 = cudaEventRecordWithFlags(c->pev[1], c->stream, cudaEventRecordExternal);
     // launch_energy enqueues the energy kernel and the record kernel
     cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve, c->profiling ? c->pev[2] : nullptr) : e1;
-    if (e2 == cudaSuccess && c->profiling) e2 = cudaEventRecord(c->pev[3], c->stream);
+    if (e2 == cudaSuccess && c->profiling) e2 = cudaEventRecordWithFlags(c->pev[3], c->stream, cudaEventRecordExternal);
     cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
     c->launches = l0;  // captured kernels are counted per replay
     if (e2 != cudaSuccess) {

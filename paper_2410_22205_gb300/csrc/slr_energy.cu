@@ -517,7 +517,7 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     cudaError_t e = energy_dispatch(c, offset, p, p_kind, record_mode == 1);
     if (e != cudaSuccess) return e;
     if (between) {
-        e = cudaEventRecord(between, c->stream);
+        e = cudaEventRecordWithFlags(between, c->stream, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     RecordArgs A;

@@ -343,3 +343,21 @@ def test_invalid_inputs_and_order():
     assert e.value.status == slr.SLR_E_INVALID
     with pytest.raises(slr.SlrError):
         slr.Reconstruction(dim=3, n=(16, 16, 16), lo=(-1, -1, -1), hi=(1, 1, 2))
+
+
+def test_profiling_times_and_async_steps():
+    rec, P = make(3, 32, 32, 1, 1)
+    rec.load_cloud(synth.sphere_cloud(1000, 0.5, 0.01, 3))
+    rec.build_distance()
+    rec.init_sphere(0.6)
+    rec.set_profiling(True)
+    rec.step_async(2)
+    ms = rec.last_iteration_times()
+    assert len(ms) == 3 and all(m > 0 for m in ms)
+    u_async = rec.u()
+    rec2, _ = make(3, 32, 32, 1, 1)
+    rec2.load_cloud(synth.sphere_cloud(1000, 0.5, 0.01, 3))
+    rec2.build_distance()
+    rec2.init_sphere(0.6)
+    rec2.step(2)
+    assert np.array_equal(rec2.u(), u_async)
