@@ -182,7 +182,43 @@ slr_status slr_last_iteration_times(slr_ctx* ctx, float ms[3]);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t slr_kernel_launches(const slr_ctx* ctx);
 
-/* Last error message of the context (never NULL; "" when none). */
+/* Distance grid for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this call; it exists for users of this
+ * library that may not call cudaMalloc: code running while another framework
+ * owns the device memory through its own pool, real-time loops that must not
+ * allocate once running, or plug-ins that are handed pre-allocated buffers
+ * only. It computes exactly what slr_build_distance computes (d and argmin,
+ * the lowest point index on ties, d rounded to `precision`), but from
+ * caller-owned device buffers and without a context, and it allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine. Its
+ * scratch (point codes, bin counts, sorted points, box hierarchy) is one
+ * fixed array of about 2.4 MB in the library's device memory, present on
+ * every GPU that loads the library until the process exits.
+ *
+ *  dim, n, lo, h: the grid (as in slr_config; node coordinates lo + i*h;
+ *                 n[2] = 1 in 2-D); at most 2^31-1 nodes.
+ *  pts_dev:       device array of n_points rows of `dim` FP64 coordinates;
+ *                 1 <= n_points <= 65536 (larger clouds: SLR_E_INVALID,
+ *                 use slr_build_distance).
+ *  d_dev:         device output, one float (precision 32) or double (64) per node.
+ *  argmin_dev:    device output, one int32 per node.
+ *  cuda_stream:   stream for the work (NULL: the legacy default stream). The
+ *                 call returns after the stream has finished the work.
+ *
+ * The first call on each device looks up that device's address of the
+ * scratch array (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture. All calls share the one array and it
+ * keeps the last call's contents (what must start at zero is cleared at the
+ * start of each call): calls that overlap on the GPU, from different threads
+ * or streams, race. Errors are described by slr_last_error(NULL). */
+slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], const double lo[3], double h, int precision,
+                                     const double* pts_dev, int64_t n_points, void* d_dev, int32_t* argmin_dev,
+                                     void* cuda_stream);
+
+/* Last error message of the context (never NULL; "" when none). With
+ * ctx == NULL: the reason of the last failed slr_create or
+ * slr_distance_grid_noalloc on this thread. */
 const char* slr_last_error(const slr_ctx* ctx);
 
 /* Release all device memory of the context and the context itself. NULL is a no-op. */

@@ -716,7 +716,11 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
 
 int64_t slr_kernel_launches(const slr_ctx* c) { return c ? c->launches : 0; }
 
-const char* slr_last_error(const slr_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+const char* slr_last_error(const slr_ctx* c) {
+    if (c) return c->err.c_str();
+    const char* m = slr::noalloc_last_error();
+    return (m && m[0]) ? m : g_create_error.c_str();
+}
 
 void slr_destroy(slr_ctx* c) {
     if (!c) return;

@@ -19,6 +19,12 @@
 // The FP32 screen only discards points whose true distance exceeds the
 // lane's best by more than the FP32 error bound (margin 1e-6 x (extent + d),
 // ~10x the worst rounding), so the FP64 decision is exact.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
 #include "slr_compact.cuh"
 #include "slr_internal.cuh"
 
@@ -526,3 +532,240 @@ cudaError_t build_distance(slr_ctx* c) {
 }
 
 }  // namespace slr
+
+// ---------------------------------------------------------------------------
+// Distance grid for callers that cannot allocate device memory.
+//
+// Some callers of this library may not call cudaMalloc: code that runs while
+// another framework owns all of the device memory through its own pool,
+// real-time loops that must not allocate after start-up, or plug-ins handed
+// only pre-allocated buffers. slr_distance_grid_noalloc computes the same
+// d and argmin as slr_build_distance from caller-owned device buffers and
+// keeps its scratch (point codes, bin counts, sorted points, box hierarchy)
+// in the fixed array below, which every GPU that loads the library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace slr {
+namespace {
+
+constexpr long long kNoAllocMaxPoints = 1ll << 16;  // 65,536 points
+constexpr int kNoAllocL3 = 6;                         // 2^6 bins per axis in 3-D
+constexpr int kNoAllocL2 = 9;                         // 2^9 bins per axis in 2-D
+constexpr long long kNoAllocBins = 1ll << 18;         // both cases
+constexpr long long kNoAllocScanBlocks = (kNoAllocBins + 4095) / 4096;
+constexpr size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr long long kNoAllocBoxes = (kNoAllocMaxPoints + 31) / 32 + (kNoAllocMaxPoints + 1023) / 1024 + 8;
+constexpr size_t kOffBbox = 0;
+constexpr size_t kOffFlag = kOffBbox + al256(64);
+constexpr size_t kOffCodes = kOffFlag + al256(16);
+constexpr size_t kOffCounts = kOffCodes + al256(sizeof(unsigned) * kNoAllocMaxPoints);
+constexpr size_t kOffTot = kOffCounts + al256(sizeof(int) * kNoAllocBins);
+constexpr size_t kOffSpt = kOffTot + al256(sizeof(int) * (kNoAllocScanBlocks + 2) + 16);
+constexpr size_t kOffBoxes = kOffSpt + al256(sizeof(float4) * kNoAllocMaxPoints);
+constexpr size_t kNoAllocScratchBytes = kOffBoxes + al256(sizeof(float4) * 2 * kNoAllocBoxes);  // ~2.4 MB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+thread_local std::string g_noalloc_error;
+
+slr_status noalloc_fail(slr_status s, const std::string& m) {
+    g_noalloc_error = m;
+    return s;
+}
+
+}  // namespace
+
+const char* noalloc_last_error() { return g_noalloc_error.c_str(); }
+
+}  // namespace slr
+
+extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], const double lo[3], double h, int precision,
+                                                const double* pts_dev, int64_t n_points, void* d_dev,
+                                                int32_t* argmin_dev, void* cuda_stream) {
+    using namespace slr;
+    g_noalloc_error.clear();
+    if (dim != 2 && dim != 3) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: dim must be 2 or 3");
+    if (!n || !lo || !pts_dev || !d_dev || !argmin_dev)
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: null argument");
+    if (precision != 32 && precision != 64)
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: precision must be 32 or 64");
+    if (n_points < 1 || n_points > kNoAllocMaxPoints)
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: n_points must be in 1..65536 (the fixed scratch "
+                                           "holds at most 65536 points; use slr_build_distance for larger clouds)");
+    long long N = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (n[a] < 2) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: need at least 2 nodes per axis");
+        N *= n[a];
+        if (N > 2147483647ll) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: at most 2^31-1 nodes");
+    }
+    if (dim == 3 ? false : (n[2] != 1))
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: n[2] must be 1 in 2-D");
+    if (!(h > 0.0)) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: h must be > 0");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    // per-device set-up: the host-side name of the array is not a device
+    // address; ask the runtime for this device's address once
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return noalloc_fail(SLR_E_CUDA, "distance_grid_noalloc: no usable current device");
+    }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return noalloc_fail(SLR_E_CUDA, std::string("distance_grid_noalloc: cudaGetSymbolAddress: ") +
+                                                    cudaGetErrorString(e));
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = (unsigned char*)g_noalloc_ptr[dev];
+    }
+    unsigned long long* bbox = (unsigned long long*)(base + kOffBbox);
+    int* flag = (int*)(base + kOffFlag);
+    unsigned* codes = (unsigned*)(base + kOffCodes);
+    int* counts = (int*)(base + kOffCounts);
+    int* tot = (int*)(base + kOffTot);
+    float4* spt = (float4*)(base + kOffSpt);
+    float4* blo = (float4*)(base + kOffBoxes);
+
+    const long long npts = n_points;
+    const int L = dim == 3 ? kNoAllocL3 : kNoAllocL2;
+    const long long nbins = 1ll << (dim * L);
+    long long cnt[kMaxLevels], off[kMaxLevels];
+    int nlevels = 0;
+    long long total_boxes = 0;
+    {
+        long long cc = (npts + 31) / 32;
+        for (;;) {
+            cnt[nlevels] = cc;
+            off[nlevels] = total_boxes;
+            total_boxes += cc;
+            ++nlevels;
+            if (cc <= 32) break;
+            cc = (cc + 31) / 32;
+        }
+    }
+    float4* bhi = blo + total_boxes;
+    int num_sms = 0;
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (num_sms <= 0) num_sms = 1;
+
+    // the array keeps the previous call's contents: reset what must start at zero
+    unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    unsigned long long hb[6];
+    int hflag = 0;
+    e = cudaMemcpyAsync(bbox, init_bbox, sizeof(init_bbox), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * nbins, st);
+    if (e == cudaSuccess) {
+        int blocks = (int)((npts + 255) / 256);
+        if (blocks > num_sms * 8) blocks = num_sms * 8;
+        k_bbox<<<blocks, 256, 0, st>>>(pts_dev, npts, dim, bbox, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(SLR_E_CUDA, std::string("distance_grid_noalloc: ") + cudaGetErrorString(e));
+    }
+    if (hflag) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: non-finite point coordinates");
+    BinArgs B;
+    double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0}, ext = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        bmin[a] = dec_double(hb[a]);
+        bmax[a] = dec_double(hb[3 + a]);
+        ext = fmax(ext, bmax[a] - bmin[a]);
+    }
+    double bin = ext > 0 ? ext / (double)(1 << L) * (1.0 + 1e-9) : 1.0;
+    for (int a = 0; a < 3; ++a) B.bmin[a] = bmin[a];
+    B.inv_bin = 1.0 / bin;
+    B.L = L;
+    B.dim = dim;
+    const double o0 = lo[0], o1 = lo[1], o2 = dim == 3 ? lo[2] : 0.0;
+    double extent = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        double hi_a = lo[a] + (double)(n[a] - 1) * h;
+        extent = fmax(extent, fabs(hi_a - lo[a]));
+        extent = fmax(extent, fabs(bmin[a] - lo[a]));
+        extent = fmax(extent, fabs(bmax[a] - lo[a]));
+    }
+    const long long nscan = (nbins + 4095) / 4096;
+    int blocks = (int)((npts + 255) / 256);
+    k_codes<<<blocks, 256, 0, st>>>(pts_dev, npts, B, codes, counts);
+    k_scan_blocks<<<(unsigned)nscan, 1024, 0, st>>>(counts, nbins, tot);
+    k_scan_counts<<<1, 1024, 0, st>>>(tot, (int)nscan, (long long*)(tot + ((nscan + 2) & ~1ll)));
+    k_scan_add<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, nbins, tot);
+    k_scatter<<<blocks, 256, 0, st>>>(pts_dev, npts, dim, codes, counts, o0, o1, o2, spt);
+    for (int l = 0; l < nlevels; ++l) {
+        long long threads = cnt[l] * 32;
+        k_boxes<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            spt, npts, blo, bhi, l == 0 ? 0 : off[l - 1], l == 0 ? npts : cnt[l - 1], off[l], cnt[l], l);
+    }
+    SearchArgs A;
+    A.n0 = (int)n[0];
+    A.n1 = (int)n[1];
+    A.n2 = dim == 3 ? (int)n[2] : 1;
+    if (dim == 3) {
+        A.tx = (A.n0 + 3) / 4;
+        A.ty = (A.n1 + 3) / 4;
+        A.tz = (A.n2 + 1) / 2;
+    } else {
+        A.tx = (A.n0 + 7) / 8;
+        A.ty = (A.n1 + 3) / 4;
+        A.tz = 1;
+    }
+    A.lo0 = lo[0];
+    A.lo1 = lo[1];
+    A.lo2 = dim == 3 ? lo[2] : 0.0;
+    A.h = h;
+    A.spt = spt;
+    A.pts = pts_dev;
+    A.npts = npts;
+    A.blo = blo;
+    A.bhi = bhi;
+    A.nlevels = nlevels;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        A.off[l] = l < nlevels ? off[l] : 0;
+        A.cnt[l] = l < nlevels ? cnt[l] : 0;
+    }
+    A.extent = extent;
+    A.flag = flag;
+    long long ntiles = (long long)A.tx * A.ty * A.tz;
+    unsigned sblocks = (unsigned)((ntiles * 32 + 255) / 256);
+    if (precision == 32) {
+        if (dim == 3)
+            k_dist_search<float, 3><<<sblocks, 256, 0, st>>>(A, (float*)d_dev, argmin_dev);
+        else
+            k_dist_search<float, 2><<<sblocks, 256, 0, st>>>(A, (float*)d_dev, argmin_dev);
+    } else {
+        if (dim == 3)
+            k_dist_search<double, 3><<<sblocks, 256, 0, st>>>(A, (double*)d_dev, argmin_dev);
+        else
+            k_dist_search<double, 2><<<sblocks, 256, 0, st>>>(A, (double*)d_dev, argmin_dev);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(SLR_E_CUDA, std::string("distance_grid_noalloc: ") + cudaGetErrorString(e));
+    }
+    if (hflag & 4) return noalloc_fail(SLR_E_CUDA, "distance_grid_noalloc: traversal stack overflow");
+    return SLR_OK;
+}

@@ -134,6 +134,7 @@ cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long
 cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long long n);
 cudaError_t build_distance(slr_ctx* c);
 long long energy_blocks(const slr_ctx* c);
+const char* noalloc_last_error();
 long long full_step_blocks(const slr_ctx* c);
 
 // ---------------------------------------------------------------------------

@@ -32,7 +32,7 @@ EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
     "slr_step", "slr_step_async", "slr_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times", "slr_kernel_launches",
-    "slr_last_error", "slr_destroy",
+    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc",
 ]
 
 
@@ -108,6 +108,8 @@ def lib():
                 "slr_kernel_launches": (C.c_int64, [_vp]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
+                "slr_distance_grid_noalloc": (C.c_int, [C.c_int, _i64p, _dp, C.c_double, C.c_int, _vp, C.c_int64,
+                                                        _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -298,6 +300,18 @@ def slr_kernel_launches(ctx) -> int:
 def slr_last_error(ctx) -> str:
     m = lib().slr_last_error(ctx)
     return m.decode() if m else ""
+
+
+def slr_distance_grid_noalloc(dim, n, lo, h, precision, pts_dev, n_points, d_dev, argmin_dev, stream=None):
+    """Distance grid from caller-owned device buffers with no device
+    allocation (see include/slr.h): pts_dev, d_dev and argmin_dev are raw
+    device addresses (ints), stream a raw cudaStream_t value or None."""
+    nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    ll = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    s = lib().slr_distance_grid_noalloc(int(dim), nn, ll, float(h), int(precision), C.c_void_p(pts_dev),
+                                        int(n_points), C.c_void_p(d_dev), C.c_void_p(argmin_dev),
+                                        C.c_void_p(stream) if stream else None)
+    _check(None, s)
 
 
 def slr_destroy(ctx):
