@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=64, help="jobs of the batched mix (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson serving run length (0: skip)")
     return ap.parse_args()
 
 
@@ -335,6 +337,12 @@ def run_gpu(args):
     if args.e2e_jobs > 0:
         e2e, solve_lat = run_e2e(args, cloud, slr, torch)
 
+    batched = serving = None
+    if dist.rank == 0 and args.batch_jobs > 0:
+        batched = run_batched(args, slr, torch)
+    if dist.rank == 0 and args.serve_seconds > 0:
+        serving = run_serving(args, slr, torch)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(grid, cloud, budget_s=20.0)
@@ -350,7 +358,7 @@ def run_gpu(args):
                        "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "latency": {"iteration": iter_lat, "solve": solve_lat},
-            "variants": variants, "gpu_launches": int(launches), "clocks": clk,
+            "variants": variants, "batched": batched, "serving": serving, "gpu_launches": int(launches), "clocks": clk,
             "setup_s": time.time() - t_setup,
         }
         print(json.dumps(line), flush=True)
@@ -391,6 +399,155 @@ def run_e2e(args, cloud, slr, torch):
            "jobs": jobs, "iterations_per_job": iters}
     lat = {"p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)), "jobs": jobs}
     return e2e, lat
+
+
+# ---------------------------------------------------------------------------
+# batched and served forms
+# ---------------------------------------------------------------------------
+
+def _job_cfg(slr, job, **kw):
+    g = job["grid"]
+    n = tuple(g.n[: g.dim]) + ((1,) if g.dim == 2 else ())
+    return slr.slr_config_default(dim=g.dim, n=n, lo=g.lo[: g.dim], hi=g.hi[: g.dim], precision=job.get("precision", 32),
+                                  interp=job["interp"], band=job.get("band", 1), **kw)
+
+
+def _run_job(slr, job, stream=None):
+    """One whole reconstruction through the public API; returns (rec, iters)."""
+    g = job["grid"]
+    n = tuple(g.n[: g.dim]) + ((1,) if g.dim == 2 else ())
+    rec = slr.Reconstruction(dim=g.dim, n=n, lo=g.lo[: g.dim], hi=g.hi[: g.dim], precision=job.get("precision", 32),
+                             interp=job["interp"], band=job.get("band", 1), stream=stream)
+    rec.load_cloud(job["cloud"])
+    rec.build_distance()
+    rec.init_sphere(job.get("u0_radius", 0.9))
+    return rec
+
+
+def run_batched(args, slr, torch):
+    """The 64-job mix (half 2-D, half 3-D, Q1/WENO mixed, FP32): whole jobs
+    one after another versus all jobs set up on their own streams from a
+    thread pool and evolved together by slr_batch_evolve (one graph launch
+    advances every job by 8 iterations). Reconstructions per second over the
+    whole job (distance grid, φ^0, evolve to the stop test, extract)."""
+    import concurrent.futures as cf
+
+    t0 = time.time()
+    jobs = synth.batch_mix(seed=3, n_jobs=args.batch_jobs)
+    gen_s = time.time() - t0
+    h_of = lambda j: (j["grid"].hi[0] - j["grid"].lo[0]) / (j["grid"].n[0] - 1)
+    # one job at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_iters, seq_state = [], []
+    for j in jobs:
+        rec = _run_job(slr, j)
+        it, _ = rec.evolve()
+        idx, val = rec.extract(2 * h_of(j))
+        seq_iters.append(it)
+        seq_state.append((idx.size, float(val.sum())))
+        rec.close()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    # batched: set-up overlapped on per-job streams, one batched evolve
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(8) as ex:
+        recs = list(ex.map(lambda j: _run_job(slr, j, stream=torch.cuda.Stream()), jobs))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    its, _ = slr.slr_batch_evolve([r.ctx for r in recs], chunk=8)
+    t_evolve = time.perf_counter() - t0 - t_setup
+    bat_state = []
+    for j, r in zip(jobs, recs):
+        idx, val = r.extract(2 * h_of(j))
+        bat_state.append((idx.size, float(val.sum())))
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    for r in recs:
+        r.close()
+    same = its == seq_iters and bat_state == seq_state
+    return {"jobs": len(jobs), "workload": "batch mix: 32 2-D (64^2-512^2) + 32 3-D (64^3-192^3), 1k-200k points, "
+                                            "Q1/WENO mixed, FP32, band",
+            "one_at_a_time": {"reconstructions_per_s": len(jobs) / t_seq, "seconds": t_seq},
+            "batched": {"reconstructions_per_s": len(jobs) / t_bat, "seconds": t_bat, "setup_s": t_setup,
+                        "evolve_s": t_evolve},
+            "speedup": t_seq / t_bat, "identical_results": bool(same), "iterations": its,
+            "input_generation_s": gen_s}
+
+
+def run_serving(args, slr, torch):
+    """Continuous batching: requests of 3-D WENO FP32 reconstructions (grids
+    log-uniform 64^3-256^3, clouds log-uniform 5k-2M points on superquadric
+    unions, drawn from a pool of pre-generated clouds) are submitted to the
+    server. A burst first measures its capacity; then a Poisson stream at
+    0.8 x capacity runs for --serve-seconds; p50/p99 submit-to-finish
+    latency and reconstructions per second are reported."""
+    rng = np.random.default_rng(4)
+    pool_sizes = [int(round(math.exp(x))) for x in np.linspace(math.log(5000), math.log(2_000_000), 6)]
+    t0 = time.time()
+    pool = [synth.superquadric_union_cloud(nn, 3, 100 + i) for i, nn in enumerate(pool_sizes)]
+    gen_s = time.time() - t0
+
+    def draw():
+        n = int(round(math.exp(rng.uniform(math.log(64), math.log(256)))))
+        ci = int(rng.integers(0, len(pool)))
+        cfg = slr.slr_config_default(dim=3, n=(n, n, n), lo=(-1.0,) * 3, hi=(1.0,) * 3, precision=32, interp=1, band=1)
+        return cfg, pool[ci], n
+
+    srv = slr.slr_server_create(96 << 30, max_active=16)
+    done_lat = []
+
+    def drain(tickets, deadline):
+        pending = set(tickets)
+        while pending and time.time() < deadline:
+            for t in list(pending):
+                st, ctx, lat = slr.slr_server_poll(srv, t)
+                if st == 2:
+                    done_lat.append(lat)
+                    slr.slr_server_release(srv, t)
+                    pending.discard(t)
+            time.sleep(0.002)
+        return pending
+
+    try:
+        # capacity: a burst of requests submitted at once
+        burst = 24
+        t0 = time.perf_counter()
+        tickets = [slr.slr_server_submit(srv, *draw()[:2], (0.0, 0.0, 0.0, 0.9)) for _ in range(burst)]
+        left = drain(tickets, time.time() + 300)
+        cap = burst / (time.perf_counter() - t0)
+        done_lat.clear()
+        # Poisson stream at 0.8 x capacity
+        lam = 0.8 * cap
+        t_end = time.perf_counter() + args.serve_seconds
+        tickets, t_next = [], time.perf_counter()
+        pending = set()
+        while time.perf_counter() < t_end:
+            now = time.perf_counter()
+            if now >= t_next:
+                t = slr.slr_server_submit(srv, *draw()[:2], (0.0, 0.0, 0.0, 0.9))
+                tickets.append(t)
+                pending.add(t)
+                t_next += rng.exponential(1.0 / lam)
+            for t in list(pending):
+                st, ctx, lat = slr.slr_server_poll(srv, t)
+                if st == 2:
+                    done_lat.append(lat)
+                    slr.slr_server_release(srv, t)
+                    pending.discard(t)
+            time.sleep(0.001)
+        t_stream = args.serve_seconds
+        left = drain(pending, time.time() + 300)
+        n_done = len(done_lat)
+        lat = np.array(done_lat)
+        return {"workload": "3-D WENO FP32, grids 64^3-256^3, clouds 5k-2M points (superquadric unions)",
+                "capacity_burst_per_s": cap, "lambda_per_s": lam, "submitted": len(tickets), "completed": n_done,
+                "reconstructions_per_s": n_done / (t_stream + 1e-9),
+                "latency_ms": {"p50": float(np.percentile(lat, 50)) if n_done else None,
+                               "p99": float(np.percentile(lat, 99)) if n_done else None},
+                "unfinished_after_drain": len(left), "max_active": 16, "cloud_pool_generation_s": gen_s}
+    finally:
+        slr.slr_server_destroy(srv)
 
 
 # ---------------------------------------------------------------------------

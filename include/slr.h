@@ -134,6 +134,19 @@ slr_status slr_step_async(slr_ctx* ctx, int n_steps, double energy_override);
  * few iterations. iters_out / converged_out may be NULL. */
 slr_status slr_evolve(slr_ctx* ctx, int* iters_out, int* converged_out);
 
+/* Batched form of slr_evolve for independent jobs on one device: each
+ * launch of one CUDA graph advances every job by `chunk` iterations (1..64,
+ * 0 -> 8), the jobs as parallel branches, so that the iterations of many
+ * small and large reconstructions overlap on the GPU instead of running one
+ * job after another. A job whose stop test (§4) has fired turns the rest of
+ * its branch into no-ops. Returns when every job has stopped. Every job must
+ * have been initialised (slr_init_u) on the current device; jobs keep their
+ * own streams and memory; `cuda_stream` (NULL: the first job's stream) orders
+ * the batch launches. iters_out / converged_out: n_jobs entries each, may be
+ * NULL. The jobs' contexts must not be used by other threads meanwhile. */
+slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* cuda_stream, int* iters_out,
+                            int* converged_out);
+
 /* Nodes with |φ| < width, in ascending linear index (the reconstructed zero
  * level set's neighbourhood). idx/u: caller buffers of `cap` entries (either
  * may be NULL to query the count). *n_out = number of such nodes; returns
@@ -223,6 +236,47 @@ const char* slr_last_error(const slr_ctx* ctx);
 
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop (the paper has no counterpart;
+ * it reconstructs one cloud at a time). Requests are admitted in order while
+ * an active slot (max_active) and enough of the device-memory budget are
+ * free; each admitted job gets its own context and stream, its exact
+ * distance grid and φ^0 (a sphere), and then joins the round-robin of
+ * iterations of all running jobs, which overlap on the GPU. A finished job's
+ * context stays with the server until released; the client reads results
+ * from it with slr_extract / slr_get_field / slr_diagnostics meanwhile.
+ * Thread-safe: any thread may submit, poll and release.
+ * ------------------------------------------------------------------------ */
+typedef struct slr_server slr_server;
+
+/* hbm_budget: device bytes the server may hold for admitted jobs (a job is
+ * admitted alone even if its estimate exceeds the budget); max_active: jobs
+ * admitted at once; alloc: allocator for the jobs' contexts (NULL: cudaMalloc).
+ * Binds to the current device; starts the setup and iteration threads. */
+slr_status slr_server_create(size_t hbm_budget, int max_active, const slr_allocator* alloc, slr_server** out);
+
+/* Queue one reconstruction: cfg as for slr_create, the cloud (host, copied),
+ * φ^0 = |x - c| - r with sphere = {cx, cy, cz, r}; the job then runs to the
+ * stopping criterion of §4. *ticket identifies it. */
+slr_status slr_server_submit(slr_server* s, const slr_config* cfg, const double* xyz, int64_t n_points,
+                             const double sphere[4], uint64_t* ticket);
+
+/* *state: 0 queued, 1 running, 2 done, 3 failed (then SLR_E_CUDA and
+ * slr_server_last_error). result (may be NULL): the job's context once done,
+ * owned by the server. latency_ms (may be NULL): submit-to-finish time once
+ * done or failed, else -1. */
+slr_status slr_server_poll(slr_server* s, uint64_t ticket, int* state, slr_ctx** result, double* latency_ms);
+
+/* Destroy a finished (done or failed) job's context and return its budget
+ * share; SLR_E_STATE while it is queued or running. */
+slr_status slr_server_release(slr_server* s, uint64_t ticket);
+
+const char* slr_server_last_error(const slr_server* s);
+
+/* Stop the threads (running jobs are abandoned after their queued work
+ * drains) and destroy every context the server still holds. */
+void slr_server_destroy(slr_server* s);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "slr_internal.cuh"
 
@@ -66,6 +67,24 @@ void release_t(slr_ctx* c, P*& p) {
     void* v = (void*)p;
     dev_free(c, v);
     p = nullptr;
+}
+
+// capture one iteration into a graph template (not instantiated)
+slr_status capture_step_graph(slr_ctx* c, double ov, int evolve, cudaGraph_t* out) {
+    cudaGraph_t g = nullptr;
+    long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e1 = launch_step(c, ov, evolve);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve) : e1;
+    cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
+    c->launches = l0;
+    if (e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e2, "capture of one iteration");
+    }
+    if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaStreamEndCapture");
+    *out = g;
+    return SLR_OK;
 }
 
 // capture one iteration as a graph
@@ -140,13 +159,34 @@ slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     release_t(c, c->part_e);
     c->n_echunks = (ncells + 31) / 32;
     c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2));
-    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
+    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy partials failed");
     return SLR_OK;
 }
 
 bool same_config(const slr_config& a, const slr_config& b) { return memcmp(&a, &b, sizeof(slr_config)) == 0; }
 
 }  // namespace
+
+namespace slr {
+
+slr_status evolve_prepare(slr_ctx* c) {
+    if (!c->have_u) return fail(c, SLR_E_STATE, "evolve: initial level set not set");
+    if (!c->g_evolve) {
+        slr_status s = capture_step(c, -1.0, 1, &c->g_evolve);
+        if (s != SLR_OK) return s;
+    }
+    CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "evolve");
+    CK(cudaMemsetAsync(&c->ds->converged, 0, sizeof(int), c->stream), "evolve");
+    return SLR_OK;
+}
+
+slr_status evolve_launch(slr_ctx* c) {
+    CK(cudaGraphLaunch(c->g_evolve, c->stream), "cudaGraphLaunch");
+    c->launches += kKernelsPerIteration;
+    return SLR_OK;
+}
+
+}  // namespace slr
 
 extern "C" {
 
@@ -390,6 +430,115 @@ slr_status slr_step(slr_ctx* c, int n_steps, double energy_override) {
     }
     CK(cudaStreamSynchronize(c->stream), "step sync");
     return check_device_error(c);
+}
+
+slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* cuda_stream, int* iters_out,
+                            int* converged_out) {
+    if (!jobs || n_jobs < 1) return SLR_E_INVALID;
+    if (chunk == 0) chunk = 8;
+    if (chunk < 1 || chunk > 64) return fail(jobs[0], SLR_E_INVALID, "batch_evolve: chunk must be in 1..64");
+    int dev = -1;
+    for (int j = 0; j < n_jobs; ++j) {
+        slr_ctx* c = jobs[j];
+        if (!c) return SLR_E_INVALID;
+        if (!c->have_u) return fail(c, SLR_E_STATE, "batch_evolve: a job has no initial level set");
+        if (dev < 0) dev = c->device;
+        if (c->device != dev) return fail(c, SLR_E_INVALID, "batch_evolve: jobs on different devices");
+    }
+    slr_ctx* c0 = jobs[0];
+    DeviceGuard g(dev);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c0->stream;
+    // the batch graph: per job a chain of `chunk` copies of its iteration graph
+    cudaGraph_t parent = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraph_t> tmpl(n_jobs, nullptr);
+    slr_status status = SLR_OK;
+    DevState** dstates = nullptr;
+    int* dstop = nullptr;
+    int* hstop = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (parent) cudaGraphDestroy(parent);
+        for (auto t : tmpl)
+            if (t) cudaGraphDestroy(t);
+        if (dstates) dev_free(c0, dstates);
+        if (dstop) dev_free(c0, dstop);
+        if (hstop) cudaFreeHost(hstop);
+    };
+    cudaError_t e = cudaGraphCreate(&parent, 0);
+    for (int j = 0; j < n_jobs && e == cudaSuccess && status == SLR_OK; ++j) {
+        status = capture_step_graph(jobs[j], -1.0, 1, &tmpl[j]);
+        if (status != SLR_OK) break;
+        cudaGraphNode_t prev = nullptr;
+        for (int r = 0; r < chunk && e == cudaSuccess; ++r) {
+            cudaGraphNode_t node;
+            e = cudaGraphAddChildGraphNode(&node, parent, prev ? &prev : nullptr, prev ? 1 : 0, tmpl[j]);
+            prev = node;
+        }
+    }
+    if (status != SLR_OK) {
+        cleanup();
+        return status;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
+    // stop flags of all jobs gathered by one kernel into one array
+    if (e == cudaSuccess) {
+        dstates = (DevState**)dev_alloc(c0, sizeof(DevState*) * n_jobs);
+        dstop = (int*)dev_alloc(c0, sizeof(int) * 4 * n_jobs);
+        if (!dstates || !dstop) {
+            cleanup();
+            return fail(c0, SLR_E_NOMEM, "batch_evolve: allocation failed");
+        }
+        e = cudaMallocHost((void**)&hstop, sizeof(int) * 4 * n_jobs);
+    }
+    if (e == cudaSuccess) {
+        std::vector<DevState*> hs(n_jobs);
+        for (int j = 0; j < n_jobs; ++j) hs[j] = jobs[j]->ds;
+        e = cudaMemcpyAsync(dstates, hs.data(), sizeof(DevState*) * n_jobs, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    // every job's own stream must be idle before the batch stream takes over
+    for (int j = 0; j < n_jobs && e == cudaSuccess; ++j) e = cudaStreamSynchronize(jobs[j]->stream);
+    for (int j = 0; j < n_jobs && e == cudaSuccess; ++j) {
+        e = cudaMemsetAsync(&jobs[j]->ds->stop, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&jobs[j]->ds->converged, 0, sizeof(int), st);
+    }
+    int max_iters = 0;
+    for (int j = 0; j < n_jobs; ++j) max_iters = jobs[j]->cfg.max_iters > max_iters ? jobs[j]->cfg.max_iters : max_iters;
+    int rounds = 0;
+    while (e == cudaSuccess) {
+        e = cudaGraphLaunch(exec, st);
+        for (int j = 0; j < n_jobs; ++j) jobs[j]->launches += (long long)chunk * kKernelsPerIteration;
+        if (e == cudaSuccess) e = launch_gather_status(c0, dstates, n_jobs, dstop, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hstop, dstop, sizeof(int) * 4 * n_jobs, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        ++rounds;
+        bool all = true, err = false;
+        for (int j = 0; j < n_jobs; ++j) {
+            all = all && hstop[4 * j + 0];
+            err = err || (hstop[4 * j + 3] & kErrLookback);
+        }
+        if (err) {
+            cleanup();
+            return fail(c0, SLR_E_TIMEOUT, "batch_evolve: band compaction look-back wait timed out");
+        }
+        if (all) break;
+        if ((long long)rounds * chunk > max_iters + 2 * chunk) {
+            cleanup();
+            return fail(c0, SLR_E_STATE, "batch_evolve: stop flags never set");
+        }
+    }
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(c0, e, "batch_evolve");
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        if (iters_out) iters_out[j] = hstop[4 * j + 1];
+        if (converged_out) converged_out[j] = hstop[4 * j + 2];
+    }
+    cleanup();
+    return SLR_OK;
 }
 
 slr_status slr_step_async(slr_ctx* c, int n_steps, double energy_override) {

@@ -292,6 +292,15 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
         const float bd2 = box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]);
         if (bd2 > wb2) continue;
         if (lvl == 0) {
+            // per-lane test: skip the leaf when its box is beyond every lane's own bound
+            {
+                const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
+                const float gx = fmaxf(0.f, fmaxf(blo_.x - xf, xf - bhi_.x));
+                const float gy = fmaxf(0.f, fmaxf(blo_.y - yf, yf - bhi_.y));
+                const float gz = fmaxf(0.f, fmaxf(blo_.z - zf, zf - bhi_.z));
+                const bool need = !(gx * gx + gy * gy + gz * gz > lbound * lbound);
+                if (!__any_sync(0xffffffffu, need)) continue;
+            }
             const long long base = id * 32;
             long long rem = A.npts - base;
             const int cnt = rem < 32 ? (int)rem : 32;

@@ -3,9 +3,8 @@
 //
 // Energy: the candidate cells (every cell in whole-grid mode; in band mode
 // the cells touching the initial band or crossing the front at init) are
-// scanned 32 at a time by one warp; a ballot finds the front cells (vertices
-// of both signs, zero counted as positive), which are queued and processed
-// one per lane:
+// checked 256 per block for a sign change (front cells, vertices of both
+// signs, zero counted as positive), which the block then processes:
 //   2-D: edge crossings by linear interpolation of φ, d interpolated along
 //        the edge, trapezoid rule on the segment(s) (eq. energyApprox);
 //   3-D: R^3 subcells (eq. energyApproxFiner); φ at the subcell centres by
@@ -14,9 +13,8 @@
 //        along y, then R^3 along x, all with the same arithmetic as a single
 //        point evaluation); d by Q1; a subcell counts when
 //        |φ(x')| < (√3/2)Δx' and adds |d(x')|^p (Δx')^2.
-// Each warp sums its chunks in a fixed order, each block writes one FP64
-// partial per sum, and one block reduces the partials in a fixed order: the
-// grid is fixed per context, so results are bit-reproducible.
+// Each block writes one FP64 partial per sum and one block reduces the
+// partials in a fixed order, so results are bit-reproducible.
 #include "slr_internal.cuh"
 
 namespace slr {
@@ -24,17 +22,12 @@ namespace slr {
 template <typename T>
 Params<T> make_params(const slr_ctx* c);
 
-// fixed grid of the energy pass for this context (per-block partials)
+// grid of the energy pass: one block per 1024 candidate cells (one partial
+// pair per block)
 long long energy_blocks(const slr_ctx* c) {
     long long ncells = c->cfg.band ? c->n_ecells : c->ncells_all;
-    // each warp scans ~32 chunks of 32 candidates, so that its queue fills
-    // several full batches of 32 front cells (front cells are ~1/10 of the
-    // candidates in band mode); at most one wave of 4 blocks per SM
-    long long blocks = (ncells + 32 * 32 * 4 - 1) / (32 * 32 * 4);
-    long long cap = (long long)c->num_sms * 4;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    return blocks;
+    long long blocks = (ncells + 1023) / 1024;
+    return blocks < 1 ? 1 : blocks;
 }
 
 __device__ __forceinline__ double pow_abs(double v, double p, int p_kind) {
@@ -143,198 +136,185 @@ struct WenoInd {
     }
 };
 
-// Energy of one front cell (lower corner node index `node`), summed in the
-// storage type: *cp += Σ |d'|^p Δx'^2, *c2 += Σ |d'|^2 Δx'^2 over counted subcells.
-template <typename T, int INTERP, int RC>
-__device__ __forceinline__ void energy_cell_3d(const Params<T>& P, const T* __restrict__ u,
-                                               const T* __restrict__ d, int node, int R, const T* th,
-                                               const WenoAxis<T>* wa, T thr, T hp2, T p, int p_kind, T& cp, T& c2,
-                                               T* zs) {
-    // RC > 0: R fixed at compile time (θ and the WENO coefficients fold to
-    // constants, loops unroll); RC == 0: R and the tables at run time
-    if (RC > 0) R = RC;
+constexpr int kEnergyThreads = 256;
+
+template <typename T, int DIM>
+__device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict__ u, int node) {
+    bool neg = false, pos = false;
+#pragma unroll
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                T v = ld(u + node + dx + P.s1 * dy + P.s2 * dz);
+                if (v < T(0))
+                    neg = true;
+                else
+                    pos = true;
+            }
+    return neg && pos;
+}
+
+// Energy pass, one launch. Block b checks kEnergyCand consecutive candidate
+// cells for a sign change (front cells, zero counted as positive) and
+// compacts them in order into shared memory. Then:
+//   3-D: one thread per (front cell, subcell layer c along z): the 16 z-lines
+//        of the 4x4x4 stencil at θ_z(c), the 4 y-lines at the R θ_y, the R
+//        x-lines at the R θ_x (WENO; the data-only part of each y- and x-line
+//        indicator is computed once and reused for its R points), or the
+//        trilinear interpolant (Q1); d by Q1, linear along each x-line. A
+//        subcell counts when |φ(x')| < (√3/2)Δx' and adds |d(x')|^p Δx'^2.
+//   2-D: one thread per front cell (segments, FP64).
+// Many small blocks let the block scheduler even out the clustering of front
+// cells. Sums per work item in the storage type; per-thread and per-block
+// sums in FP64, in a fixed order (one partial pair per block).
+constexpr int kEnergyCand = 1024;  // candidate cells per block (4 per thread)
+
+template <typename T, int DIM, int INTERP, int RC>
+__global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T* ub0, const T* ub1,
+                                                           const T* __restrict__ d, const int* __restrict__ cells,
+                                                           long long ncells, int R_run, double h, double p,
+                                                           int p_kind, T thr, T hp2, T pT, int offset, double* part,
+                                                           DevState* ds, int check_stop) {
+    constexpr int W = kEnergyThreads / 32;
+    constexpr int PER = kEnergyCand / kEnergyThreads;
+    const int R = RC > 0 ? RC : R_run;
     constexpr double RD = RC > 0 ? (double)RC : 1.0;
-    auto TH = [&](int m) -> T { return RC > 0 ? (T)((m + 0.5) / RD) : th[m]; };
+    __shared__ int s_list[kEnergyCand];
+    __shared__ int s_warp[W + 1];
+    __shared__ T s_th[kMaxR];
+    __shared__ WenoAxis<T> s_wa[kMaxR];
+    __shared__ double s_a[W], s_b[W];
+    if (check_stop && ds->stop) return;
+    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    if (RC == 0 && threadIdx.x < R) {
+        T t = ((T)threadIdx.x + (T)0.5) / (T)R;  // subcell centre θ_m = (m + 1/2)/R
+        s_th[threadIdx.x] = t;
+        s_wa[threadIdx.x].set(t);
+    }
+    // front cells of this block's candidate range, in order (PER rounds)
+    int nf = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
+        int node = 0, f = 0;
+        if (e < ncells) {
+            int i, j, k;
+            cell_of<T, DIM>(P, cells, e, i, j, k);
+            node = (int)(i + P.s1 * j + P.s2 * k);
+            f = is_front<T, DIM>(P, u, node);
+        }
+        int tot;
+        const int off = block_exclusive_flag<kEnergyThreads>(f, s_warp, &tot);
+        if (f) s_list[nf + off] = node;
+        nf += tot;
+        __syncthreads();
+    }
+    // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
+    auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
     auto WA = [&](int m) -> WenoAxis<T> {
         if (RC > 0) {
             WenoAxis<T> w;
             w.set((T)((m + 0.5) / RD));
             return w;
         }
-        return wa[m];
+        return s_wa[m];
     };
-    long long q = node / P.n0;
-    const int i = (int)(node - q * P.n0);
-    const int k = (int)(q / P.n1);
-    const int j = (int)(q - (long long)k * P.n1);
-    T dc[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) dc[c] = ld(d + node + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
-    auto add = [&](T uu, T tx, T ty, T tz) {
-        if (fabs(uu) < thr) {
-            T e0 = dc[0] + tx * (dc[1] - dc[0]);
-            T e1 = dc[2] + tx * (dc[3] - dc[2]);
-            T e2 = dc[4] + tx * (dc[5] - dc[4]);
-            T e3 = dc[6] + tx * (dc[7] - dc[6]);
-            T f0 = e0 + ty * (e1 - e0);
-            T f1 = e2 + ty * (e3 - e2);
-            T dd = fabs(f0 + tz * (f1 - f0));
-            T d2 = dd * dd;
-            cp += (p_kind == 2 ? d2 : (p_kind == 1 ? dd : (T)pow(dd, p))) * hp2;
-            c2 += d2 * hp2;
-        }
+    auto contrib = [&](T uu, T dd, T& cp, T& c2) {
+        const T a = fabs(dd);
+        const T d2 = a * a;
+        const T keep = fabs(uu) < thr ? hp2 : T(0);
+        cp += (p_kind == 2 ? d2 : (p_kind == 1 ? a : (T)pow(a, pT))) * keep;
+        c2 += d2 * keep;
     };
-    if (INTERP == 0) {
-        T uc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) uc[c] = ld(u + node + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
-#pragma unroll
-        for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz)
-#pragma unroll
-            for (int by = 0; by < (RC > 0 ? RC : R); ++by)
-#pragma unroll
-                for (int ax = 0; ax < (RC > 0 ? RC : R); ++ax) {
-                    const T tx = TH(ax), ty = TH(by), tz = TH(cz);
-                    T a0 = uc[0] + tx * (uc[1] - uc[0]);
-                    T a1 = uc[2] + tx * (uc[3] - uc[2]);
-                    T a2 = uc[4] + tx * (uc[5] - uc[4]);
-                    T a3 = uc[6] + tx * (uc[7] - uc[6]);
-                    T b0 = a0 + ty * (a1 - a0);
-                    T b1 = a2 + ty * (a3 - a2);
-                    add(b0 + tz * (b1 - b0), tx, ty, tz);
-                }
-        return;
-    }
-    // WENO: the 16 z-lines of the 4x4x4 stencil are evaluated at every θ_z
-    // into per-thread scratch (shared memory, stride = threads per block);
-    // then, per θ_z, 4 y-lines at every θ_y and 1 x-line at every θ_x. The
-    // data-only part of each line's indicators is computed once.
-    const int stride = blockDim.x;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int ia = clampi(i - 1 + a, 0, P.n0 - 1);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const long long ab = ia + P.s1 * clampi(j - 1 + b, 0, P.n1 - 1);
-            WenoInd<T> iz;
-            iz.set(ld(u + ab + P.s2 * clampi(k - 1, 0, P.n2 - 1)), ld(u + ab + P.s2 * k),
-                   ld(u + ab + P.s2 * clampi(k + 1, 0, P.n2 - 1)), ld(u + ab + P.s2 * clampi(k + 2, 0, P.n2 - 1)),
-                   P.h4);
-#pragma unroll
-            for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz) zs[((a * 4 + b) * R + cz) * stride] = iz.eval(WA(cz));
-        }
-    }
-#pragma unroll
-    for (int cz = 0; cz < (RC > 0 ? RC : R); ++cz) {
-        WenoInd<T> iy[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            iy[a].set(zs[((a * 4 + 0) * R + cz) * stride], zs[((a * 4 + 1) * R + cz) * stride],
-                      zs[((a * 4 + 2) * R + cz) * stride], zs[((a * 4 + 3) * R + cz) * stride], P.h4);
-#pragma unroll
-        for (int by = 0; by < (RC > 0 ? RC : R); ++by) {
-            const WenoAxis<T> wy = WA(by);
-            WenoInd<T> ix;
-            ix.set(iy[0].eval(wy), iy[1].eval(wy), iy[2].eval(wy), iy[3].eval(wy), P.h4);
-#pragma unroll
-            for (int ax = 0; ax < (RC > 0 ? RC : R); ++ax) add(ix.eval(WA(ax)), TH(ax), TH(by), TH(cz));
-        }
-    }
-}
-
-// Energy pass, one launch: every warp walks its own fixed sequence of
-// chunks of 32 candidate cells (chunk c to warp c mod warps), ballots the
-// front cells (vertices of both signs, zero counted as positive) into a
-// shared-memory queue and, whenever 32 are queued (or at its end), processes
-// them one per lane. Per-cell sums are in the storage type, per-lane, per-warp
-// and per-block sums in FP64, every order fixed, so the result is
-// bit-reproducible for a given grid.
-constexpr int kEnergyThreads = 128;
-
-template <typename T, int DIM, int INTERP, int RC>
-__global__ void __launch_bounds__(kEnergyThreads, 4) k_energy(Params<T> P, const T* ub0, const T* ub1,
-                                                           const T* __restrict__ d, const int* __restrict__ cells,
-                                                           long long ncells, int R, double h, double p, int p_kind,
-                                                           int offset, double* part, DevState* ds, int check_stop) {
-    constexpr int W = kEnergyThreads / 32;
-    extern __shared__ unsigned char s_dyn[];
-    T* zs_all = reinterpret_cast<T*>(s_dyn);  // 16 R values per thread (WENO, 3-D)
-    __shared__ T s_th[kMaxR];
-    __shared__ WenoAxis<T> s_wa[kMaxR];
-    __shared__ int s_q[W][64];
-    __shared__ double s_a[W], s_b[W];
-    if (check_stop && ds->stop) return;
-    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
-    if (threadIdx.x < R) {
-        T t = (T)(((double)threadIdx.x + 0.5) / (double)R);  // subcell centre θ_m = (m + 1/2)/R
-        s_th[threadIdx.x] = t;
-        s_wa[threadIdx.x].set(t);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    int* q = s_q[wib];
-    T* zs = zs_all + threadIdx.x;
-    const T thr = (T)(0.8660254037844386 * (h / R));  // (√3/2) Δx'
-    const T hp2 = (T)((h / R) * (h / R));
-    const long long nchunks = (ncells + 31) / 32;
-    const long long nw = (long long)gridDim.x * W;
     double ap = 0.0, a2 = 0.0;
-    int qn = 0;
-    for (long long c = (long long)blockIdx.x * W + wib;; c += nw) {
-        const bool have = c < nchunks;
-        if (have) {
-            const long long e = c * 32 + lane;
-            int f = 0, node = 0;
-            if (e < ncells) {
-                int i, j, k;
-                cell_of<T, DIM>(P, cells, e, i, j, k);
-                node = (int)(i + P.s1 * j + P.s2 * k);
-                bool neg = false, pos = false;
-#pragma unroll
-                for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            T v = ld(u + node + dx + P.s1 * dy + P.s2 * dz);
-                            if (v < T(0))
-                                neg = true;
-                            else
-                                pos = true;
-                        }
-                f = neg && pos;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, f);
-            if (f) q[qn + __popc(m & lt)] = node;
-            qn += __popc(m);
-            __syncwarp();
+    if (DIM == 2) {
+        for (int fi = threadIdx.x; fi < nf; fi += kEnergyThreads) {
+            const int nd = s_list[fi];
+            const int q = nd / P.n0;
+            double s2 = 0.0;
+            ap += energy_cell_2d<T>(P, u, d, nd - q * P.n0, q, h, p, p_kind, &s2);
+            a2 += s2;
         }
-        while (qn >= 32 || (!have && qn > 0)) {
-            const int take = qn < 32 ? qn : 32;
-            const int node = lane < take ? q[lane] : -1;
-            __syncwarp();
-            if (qn > 32 && lane < qn - 32) q[lane] = q[lane + 32];  // reads [32, qn), writes [0, qn-32)
-            __syncwarp();
-            qn -= take;
-            if (node >= 0) {
-                if (DIM == 2) {
-                    long long qq = node / P.n0;
-                    double s2 = 0.0;
-                    ap += energy_cell_2d<T>(P, u, d, (int)(node - qq * P.n0), (int)qq, h, p, p_kind, &s2);
-                    a2 += s2;
-                } else {
-                    T cp = T(0), c2 = T(0);
-                    energy_cell_3d<T, INTERP, RC>(P, u, d, node, R, s_th, s_wa, thr, hp2, (T)p, p_kind, cp, c2, zs);
-                    ap += (double)cp;
-                    a2 += (double)c2;
+    } else {
+        const int items = nf * R;
+        for (int it = threadIdx.x; it < items; it += kEnergyThreads) {
+            const int fi = it / R, cz = it - fi * R;
+            const int nd = s_list[fi];
+            const int q = nd / P.n0;
+            const int i = nd - q * P.n0;
+            const int k = q / P.n1;
+            const int j = q - k * P.n1;
+            const T tz = TH(cz);
+            T dc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) dc[c] = ld(d + nd + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+            // d on the layer z = θ_z: bilinear in (x, y) from the two z-faces
+            T dz[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dz[c] = dc[c] + tz * (dc[c + 4] - dc[c]);
+            T cp = T(0), c2 = T(0);
+            if (INTERP == 1) {
+                const WenoAxis<T> wz = WA(cz);
+                int ox[4];
+                long long oy[4], oz[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    ox[a] = clampi(i - 1 + a, 0, P.n0 - 1);
+                    oy[a] = P.s1 * clampi(j - 1 + a, 0, P.n1 - 1);
+                    oz[a] = P.s2 * clampi(k - 1 + a, 0, P.n2 - 1);
+                }
+                WenoInd<T> iy[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    T zl[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const T* col = u + ox[a] + oy[b];
+                        zl[b] = weno1(ld(col + oz[0]), ld(col + oz[1]), ld(col + oz[2]), ld(col + oz[3]), wz, P.h4);
+                    }
+                    iy[a].set(zl[0], zl[1], zl[2], zl[3], P.h4);
+                }
+#pragma unroll
+                for (int by = 0; by < (RC > 0 ? RC : kMaxR); ++by) {
+                    if (RC == 0 && by >= R) break;
+                    const WenoAxis<T> wy = WA(by);
+                    const T ty = TH(by);
+                    WenoInd<T> ix;
+                    ix.set(iy[0].eval(wy), iy[1].eval(wy), iy[2].eval(wy), iy[3].eval(wy), P.h4);
+                    const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
+#pragma unroll
+                    for (int ax = 0; ax < (RC > 0 ? RC : kMaxR); ++ax) {
+                        if (RC == 0 && ax >= R) break;
+                        const T tx = TH(ax);
+                        contrib(ix.eval(WA(ax)), d0 + tx * (d1 - d0), cp, c2);
+                    }
+                }
+            } else {
+                T uc[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) uc[c] = ld(u + nd + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+                T uz[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) uz[c] = uc[c] + tz * (uc[c + 4] - uc[c]);
+                for (int by = 0; by < R; ++by) {
+                    const T ty = TH(by);
+                    const T u0 = uz[0] + ty * (uz[2] - uz[0]), u1 = uz[1] + ty * (uz[3] - uz[1]);
+                    const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
+                    for (int ax = 0; ax < R; ++ax) {
+                        const T tx = TH(ax);
+                        contrib(u0 + tx * (u1 - u0), d0 + tx * (d1 - d0), cp, c2);
+                    }
                 }
             }
+            ap += (double)cp;
+            a2 += (double)c2;
         }
-        if (!have) break;
     }
     ap = warp_sum(ap);
     a2 = warp_sum(a2);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (lane == 0) {
         s_a[wib] = ap;
         s_b[wib] = a2;
@@ -473,23 +453,17 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     Params<T> P = make_params<T>(c);
     const int* cells = c->cfg.band ? c->ecells : nullptr;
     long long ncells = c->cfg.band ? c->n_ecells : c->ncells_all;
-    size_t smem = (DIM == 3 && INTERP == 1) ? sizeof(T) * 16 * c->cfg.energy_R * kEnergyThreads : 0;
-    static bool attr_set = false;
-    if (!attr_set && smem > 0) {
-        cudaFuncSetAttribute(k_energy<T, DIM, INTERP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(T) * 16 * kMaxR * kEnergyThreads));
-        cudaFuncSetAttribute(k_energy<T, DIM, INTERP, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(T) * 16 * 5 * kEnergyThreads));
-        attr_set = true;
-    }
-    if (DIM == 3 && INTERP == 1 && c->cfg.energy_R == 5)
-        k_energy<T, DIM, INTERP, 5><<<(int)energy_blocks(c), kEnergyThreads, smem, c->stream>>>(
+    const int blocks = (int)energy_blocks(c);
+    const double hp = c->h / c->cfg.energy_R;
+    const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
+    if (DIM == 3 && c->cfg.energy_R == 5)
+        k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
-            offset, c->part_e, c->ds, check_stop);
+            thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
     else
-        k_energy<T, DIM, INTERP, 0><<<(int)energy_blocks(c), kEnergyThreads, smem, c->stream>>>(
+        k_energy<T, DIM, INTERP, 0><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
-            offset, c->part_e, c->ds, check_stop);
+            thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
     c->launches += 1;
     return cudaGetLastError();
 }

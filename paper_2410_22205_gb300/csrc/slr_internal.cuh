@@ -136,6 +136,11 @@ cudaError_t build_distance(slr_ctx* c);
 long long energy_blocks(const slr_ctx* c);
 const char* noalloc_last_error();
 long long full_step_blocks(const slr_ctx* c);
+// evolve building blocks for schedulers: capture the iteration graph if
+// needed and clear the stop flags; enqueue one iteration (no host wait)
+slr_status evolve_prepare(slr_ctx* c);
+slr_status evolve_launch(slr_ctx* c);
+cudaError_t launch_gather_status(slr_ctx* c, DevState* const* states, int n, int* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device numerics

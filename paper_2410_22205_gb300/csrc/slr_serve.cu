@@ -1,0 +1,342 @@
+// Serving form of the library: a continuous-batching request loop.
+//
+// Requests (a configuration, a host point cloud and a sphere for φ^0) are
+// queued by slr_server_submit. Two worker threads drive the device:
+//  - setup: admits queued requests in order while an active slot and enough
+//    of the HBM budget are free, creates the job's context on its own
+//    stream, copies the cloud, builds the exact distance grid and φ^0, and
+//    hands the job to the iteration thread;
+//  - iterate: round-robin over the running jobs, enqueues a few iterations
+//    of each job's captured iteration graph on the job's stream, then an
+//    asynchronous 16-byte status copy and an event; a job whose event has
+//    completed and whose device stop flag is set is retired. New jobs join
+//    the next round, so requests that arrive while others run overlap with
+//    them on the GPU.
+// A finished job's context (and its memory) stays with the server until the
+// client releases it; its budget share is returned then.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "slr_internal.cuh"
+
+struct slr_server;
+
+namespace {
+
+enum JobState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+struct Job {
+    uint64_t ticket = 0;
+    slr_config cfg;
+    std::vector<double> xyz;
+    int64_t npts = 0;
+    double sphere[4] = {0, 0, 0, 0};
+    size_t bytes = 0;
+    bool holds_budget = false;  // admitted and its share not yet returned
+    slr_ctx* ctx = nullptr;
+    std::atomic<int> state{kQueued};
+    std::string error;
+    // iteration thread bookkeeping
+    bool started = false;
+    bool outstanding = false;
+    cudaEvent_t ev = nullptr;
+    int* status = nullptr;  // pinned: n, stop, converged, error
+    std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+};
+
+// device bytes a job will hold: two φ buffers, d, argmin, band lists and
+// candidate cells (bounded by the grid), the cloud and the distance scratch
+size_t job_bytes(const slr_config& c, int64_t npts) {
+    long long N = c.n[0] * c.n[1] * (c.dim == 3 ? c.n[2] : 1);
+    size_t ts = c.precision == 32 ? 4 : 8;
+    size_t grid = (size_t)N * (3 * ts + 4) + (size_t)N / 2 * 4;
+    size_t cloud = (size_t)npts * (8 * c.dim + 4 + 16) + (size_t)(1u << 21) * 4 + (16u << 20);
+    return grid + cloud;
+}
+
+}  // namespace
+
+struct slr_server {
+    size_t budget = 0;
+    size_t used = 0;
+    int max_active = 16;
+    int device = 0;
+    int rounds_per_check = 4;
+    slr_allocator al{};
+    bool have_al = false;
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the setup thread (queue / budget changes)
+    std::condition_variable cv_iter;  // wakes the iteration thread (new running jobs)
+    std::deque<std::shared_ptr<Job>> queue;
+    std::vector<std::shared_ptr<Job>> running;  // owned by the iteration thread after handoff
+    std::vector<std::shared_ptr<Job>> incoming;
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;
+    uint64_t next_ticket = 1;
+    int active = 0;  // admitted and not yet released
+    bool stop = false;
+    std::thread setup_thread, iter_thread;
+    std::string err;
+
+    void setup_loop();
+    void iter_loop();
+};
+
+void slr_server::setup_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        std::shared_ptr<Job> j;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] {
+                if (stop) return true;
+                if (queue.empty()) return false;
+                const auto& f = queue.front();
+                return active < max_active && (used + f->bytes <= budget || active == 0);
+            });
+            if (stop) return;
+            j = queue.front();
+            queue.pop_front();
+            used += j->bytes;
+            ++active;
+            j->holds_budget = true;
+        }
+        j->t_start = std::chrono::steady_clock::now();
+        slr_ctx* c = nullptr;
+        slr_status s = slr_create(&j->cfg, have_al ? &al : nullptr, nullptr, &c);
+        if (s == SLR_OK) s = slr_load_cloud(c, j->xyz.data(), j->npts);
+        if (s == SLR_OK) s = slr_build_distance(c);
+        if (s == SLR_OK) s = slr_init_u(c, 0, j->sphere, nullptr);
+        if (s != SLR_OK) {
+            j->error = c ? slr_last_error(c) : slr_last_error(nullptr);
+            if (c) slr_destroy(c);
+            std::lock_guard<std::mutex> lk(mu);
+            j->t_done = std::chrono::steady_clock::now();
+            j->state = kFailed;
+            used -= j->bytes;
+            --active;
+            j->holds_budget = false;
+            cv.notify_all();
+            continue;
+        }
+        std::vector<double>().swap(j->xyz);  // the host copy is no longer needed
+        j->ctx = c;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            j->state = kRunning;
+            incoming.push_back(j);
+        }
+        cv_iter.notify_all();
+    }
+}
+
+namespace {
+
+// enqueue `rounds` iterations of the job's captured iteration graph and an
+// asynchronous status copy; returns false on a CUDA error
+bool enqueue_rounds(Job* j, int rounds) {
+    slr_ctx* c = j->ctx;
+    if (!j->started) {
+        if (slr::evolve_prepare(c) != SLR_OK) return false;
+        j->started = true;
+    }
+    for (int r = 0; r < rounds; ++r)
+        if (slr::evolve_launch(c) != SLR_OK) return false;
+    if (cudaMemcpyAsync(j->status, &c->ds->n, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return false;
+    if (cudaEventRecord(j->ev, c->stream) != cudaSuccess) return false;
+    j->outstanding = true;
+    return true;
+}
+
+}  // namespace
+
+void slr_server::iter_loop() {
+    cudaSetDevice(device);
+    std::vector<std::shared_ptr<Job>> run;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (run.empty()) cv_iter.wait(lk, [&] { return stop || !incoming.empty(); });
+            if (stop) break;
+            for (auto& j : incoming) run.push_back(j);
+            incoming.clear();
+        }
+        bool progressed = false;
+        for (size_t i = 0; i < run.size();) {
+            Job* j = run[i].get();
+            bool failed = false, done = false;
+            if (!j->ev) {
+                if (cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaMallocHost((void**)&j->status, 4 * sizeof(int)) != cudaSuccess) {
+                    cudaGetLastError();
+                    failed = true;
+                }
+            }
+            if (!failed && j->outstanding) {
+                cudaError_t q = cudaEventQuery(j->ev);
+                if (q == cudaSuccess) {
+                    j->outstanding = false;
+                    progressed = true;
+                    if (j->status[3] & slr::kErrLookback) {
+                        j->error = "band compaction look-back wait timed out";
+                        failed = true;
+                    } else if (j->status[1]) {
+                        done = true;
+                    }
+                } else if (q != cudaErrorNotReady) {
+                    cudaGetLastError();
+                    j->error = cudaGetErrorString(q);
+                    failed = true;
+                }
+            }
+            if (!failed && !done && !j->outstanding) {
+                if (!enqueue_rounds(j, rounds_per_check)) {
+                    j->error = slr_last_error(j->ctx);
+                    failed = true;
+                }
+                progressed = true;
+            }
+            if (failed || done) {
+                j->t_done = std::chrono::steady_clock::now();
+                if (j->ev) cudaEventDestroy(j->ev);
+                j->ev = nullptr;
+                if (j->status) cudaFreeHost(j->status);
+                j->status = nullptr;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    j->state = failed ? kFailed : kDone;
+                }
+                run.erase(run.begin() + i);
+                continue;
+            }
+            ++i;
+        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (auto& j : run) {
+        if (j->ctx) cudaStreamSynchronize(j->ctx->stream);
+        if (j->ev) cudaEventDestroy(j->ev);
+        if (j->status) cudaFreeHost(j->status);
+    }
+}
+
+extern "C" {
+
+slr_status slr_server_create(size_t hbm_budget, int max_active, const slr_allocator* alloc, slr_server** out) {
+    if (!out || max_active < 1) return SLR_E_INVALID;
+    slr_server* s = new slr_server();
+    s->budget = hbm_budget;
+    s->max_active = max_active;
+    if (alloc && alloc->alloc && alloc->free) {
+        s->al = *alloc;
+        s->have_al = true;
+    }
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return SLR_E_CUDA;
+    }
+    s->setup_thread = std::thread([s] { s->setup_loop(); });
+    s->iter_thread = std::thread([s] { s->iter_loop(); });
+    *out = s;
+    return SLR_OK;
+}
+
+slr_status slr_server_submit(slr_server* s, const slr_config* cfg, const double* xyz, int64_t n_points,
+                             const double sphere[4], uint64_t* ticket) {
+    if (!s || !cfg || !xyz || n_points < 1 || !sphere || !ticket) return SLR_E_INVALID;
+    auto j = std::make_shared<Job>();
+    j->cfg = *cfg;
+    j->npts = n_points;
+    j->xyz.assign(xyz, xyz + (size_t)n_points * cfg->dim);
+    for (int a = 0; a < 4; ++a) j->sphere[a] = sphere[a];
+    j->bytes = job_bytes(*cfg, n_points);
+    j->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        j->ticket = s->next_ticket++;
+        s->jobs[j->ticket] = j;
+        s->queue.push_back(j);
+    }
+    s->cv.notify_all();
+    *ticket = j->ticket;
+    return SLR_OK;
+}
+
+slr_status slr_server_poll(slr_server* s, uint64_t ticket, int* state, slr_ctx** result, double* latency_ms) {
+    if (!s || !state) return SLR_E_INVALID;
+    std::shared_ptr<Job> j;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return SLR_E_INVALID;
+        j = it->second;
+    }
+    int st = j->state.load();
+    *state = st;
+    if (result) *result = st == kDone ? j->ctx : nullptr;
+    if (latency_ms)
+        *latency_ms = (st == kDone || st == kFailed)
+                          ? std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count()
+                          : -1.0;
+    if (st == kFailed) {
+        s->err = j->error;
+        return SLR_E_CUDA;
+    }
+    return SLR_OK;
+}
+
+slr_status slr_server_release(slr_server* s, uint64_t ticket) {
+    if (!s) return SLR_E_INVALID;
+    std::shared_ptr<Job> j;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return SLR_E_INVALID;
+        j = it->second;
+        int st = j->state.load();
+        if (st != kDone && st != kFailed) return SLR_E_STATE;
+        s->jobs.erase(it);
+    }
+    if (j->ctx) slr_destroy(j->ctx);
+    j->ctx = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (j->holds_budget) {
+            s->used -= j->bytes;
+            --s->active;
+            j->holds_budget = false;
+        }
+    }
+    s->cv.notify_all();
+    return SLR_OK;
+}
+
+const char* slr_server_last_error(const slr_server* s) { return s ? s->err.c_str() : ""; }
+
+void slr_server_destroy(slr_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    s->cv_iter.notify_all();
+    if (s->setup_thread.joinable()) s->setup_thread.join();
+    if (s->iter_thread.joinable()) s->iter_thread.join();
+    for (auto& kv : s->jobs)
+        if (kv.second->ctx) slr_destroy(kv.second->ctx);
+    delete s;
+}
+
+}  // extern "C"

@@ -17,12 +17,14 @@
 
 namespace slr {
 
+// node index -> (i, j, k); 32-bit arithmetic (grids hold at most 2^31-1 nodes)
 template <typename T>
 __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i, int& j, int& k) {
-    long long q = idx / P.n0;
-    i = (int)(idx - q * P.n0);
-    k = (int)(q / P.n1);
-    j = (int)(q - (long long)k * P.n1);
+    const int id = (int)idx;
+    const int q = id / P.n0;
+    i = id - q * P.n0;
+    k = q / P.n1;
+    j = q - k * P.n1;
 }
 
 // fused band rebuild + SL update + cut (band mode). Work is handed out per
@@ -280,7 +282,12 @@ static cudaError_t step_t(slr_ctx* c, double ov) {
     T* u0 = (T*)c->u[0];
     T* u1 = (T*)c->u[1];
     if (c->cfg.band) {
-        k_step_band<T, DIM, INTERP><<<grid_blocks(c, 8), kStepBlock, 0, c->stream>>>(
+        // enough blocks for one round of tickets over the largest band (it only shrinks)
+        long long per_block = (long long)kStepTile * (kStepBlock / 32);
+        long long nb = (c->band_cap + per_block - 1) / per_block;
+        if (nb > grid_blocks(c, 8)) nb = grid_blocks(c, 8);
+        if (nb < 1) nb = 1;
+        k_step_band<T, DIM, INTERP><<<(int)nb, kStepBlock, 0, c->stream>>>(
             P, u0, u1, (const T*)c->d, c->band[0], c->band[1], c->tile_status, c->part_dphi, c->ds, ov);
     } else {
         long long nb = full_step_blocks(c);

@@ -65,6 +65,23 @@ __global__ void k_from_double(const double* src, T* dst, long long n) {
         dst[i] = (T)src[i];
 }
 
+// per job: stop flag, iteration count, converged flag, error bits
+__global__ void k_gather_status(DevState* const* states, int n, int* out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const DevState* s = states[j];
+    out[4 * j + 0] = s->stop;
+    out[4 * j + 1] = s->n;
+    out[4 * j + 2] = s->converged;
+    out[4 * j + 3] = s->error;
+}
+
+cudaError_t launch_gather_status(slr_ctx* c, DevState* const* states, int n, int* out, cudaStream_t st) {
+    k_gather_status<<<(n + 127) / 128, 128, 0, st>>>(states, n, out);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long n) {
     int blocks = c->num_sms * 8;
     if (c->cfg.precision == 32)

@@ -30,9 +30,11 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 # every entry point declared in include/slr.h
 EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
-    "slr_step", "slr_step_async", "slr_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
+    "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times", "slr_kernel_launches",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc",
+    "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
+    "slr_server_destroy",
 ]
 
 
@@ -96,6 +98,7 @@ def lib():
                 "slr_step": (C.c_int, [_vp, C.c_int, C.c_double]),
                 "slr_step_async": (C.c_int, [_vp, C.c_int, C.c_double]),
                 "slr_evolve": (C.c_int, [_vp, _ip, _ip]),
+                "slr_batch_evolve": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
                 "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
                 "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
                 "slr_get_band": (C.c_int, [_vp, _i64p, C.c_int64, _i64p]),
@@ -111,6 +114,14 @@ def lib():
                 "slr_distance_grid_noalloc": (C.c_int, [C.c_int, _i64p, _dp, C.c_double, C.c_int, _vp, C.c_int64,
                                                         _vp, _vp, _vp]),
             }
+            sig.update({
+                "slr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(slr_allocator), C.POINTER(_vp)]),
+                "slr_server_submit": (C.c_int, [_vp, P, _dp, C.c_int64, _dp, C.POINTER(C.c_uint64)]),
+                "slr_server_poll": (C.c_int, [_vp, C.c_uint64, _ip, C.POINTER(_vp), _dp]),
+                "slr_server_release": (C.c_int, [_vp, C.c_uint64]),
+                "slr_server_last_error": (C.c_char_p, [_vp]),
+                "slr_server_destroy": (None, [_vp]),
+            })
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
                 f.restype = res
@@ -235,6 +246,18 @@ def slr_evolve(ctx):
     return it.value, bool(conv.value)
 
 
+def slr_batch_evolve(ctxs, chunk=8, stream=None):
+    """Evolve several contexts together (one graph launch advances all of
+    them by `chunk` iterations); returns (iters, converged) per context."""
+    n = len(ctxs)
+    arr = (_vp * n)(*ctxs)
+    it = (C.c_int * n)()
+    cv = (C.c_int * n)()
+    s = lib().slr_batch_evolve(arr, n, int(chunk), C.c_void_p(stream) if stream else None, it, cv)
+    _check(ctxs[0] if n else None, s)
+    return list(it), [bool(x) for x in cv]
+
+
 def slr_extract(ctx, width):
     n = C.c_int64(0)
     _check(ctx, lib().slr_extract(ctx, float(width), None, None, 0, C.byref(n)))
@@ -317,6 +340,53 @@ def slr_distance_grid_noalloc(dim, n, lo, h, precision, pts_dev, n_points, d_dev
 def slr_destroy(ctx):
     if ctx:
         lib().slr_destroy(ctx)
+
+
+def _check_srv(srv, status):
+    if status != SLR_OK:
+        msg = lib().slr_server_last_error(srv)
+        raise SlrError(status, msg.decode() if msg else "")
+
+
+def slr_server_create(hbm_budget, max_active=16, allocator=None):
+    h = C.c_void_p()
+    al = C.byref(allocator.struct if hasattr(allocator, "struct") else allocator) if allocator is not None else None
+    s = lib().slr_server_create(int(hbm_budget), int(max_active), al, C.byref(h))
+    if s != SLR_OK:
+        raise SlrError(s, "server creation failed")
+    return h.value
+
+
+def slr_server_submit(srv, cfg, xyz, sphere):
+    xyz = _f64(xyz)
+    sp = _f64(list(sphere) + [0.0] * (4 - len(sphere)))
+    t = C.c_uint64(0)
+    _check_srv(srv, lib().slr_server_submit(srv, C.byref(cfg), _ptr(xyz), xyz.shape[0], _ptr(sp), C.byref(t)))
+    return t.value
+
+
+def slr_server_poll(srv, ticket):
+    """Returns (state, ctx or None, latency_ms or None); state 0 queued,
+    1 running, 2 done, 3 failed (raises for failed)."""
+    st = C.c_int(0)
+    res = C.c_void_p()
+    lat = C.c_double(-1.0)
+    _check_srv(srv, lib().slr_server_poll(srv, C.c_uint64(ticket), C.byref(st), C.byref(res), C.byref(lat)))
+    return st.value, res.value, (lat.value if lat.value >= 0 else None)
+
+
+def slr_server_release(srv, ticket):
+    _check_srv(srv, lib().slr_server_release(srv, C.c_uint64(ticket)))
+
+
+def slr_server_last_error(srv):
+    m = lib().slr_server_last_error(srv)
+    return m.decode() if m else ""
+
+
+def slr_server_destroy(srv):
+    if srv:
+        lib().slr_server_destroy(srv)
 
 
 # ---------------------------------------------------------------------------

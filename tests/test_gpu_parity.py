@@ -361,3 +361,88 @@ def test_profiling_times_and_async_steps():
     rec2.init_sphere(0.6)
     rec2.step(2)
     assert np.array_equal(rec2.u(), u_async)
+
+
+def _small_job(kind, seed):
+    """A small mixed job: (dim, n, prec, interp, band) by kind."""
+    dim, n, prec, interp, band = kind
+    rec, P = make(dim, n, prec, interp, band, max_iters=40)
+    pts = (synth.sphere_cloud(800, 0.5, 0.01, seed) if dim == 3 else synth.circle_noisy(300, 0.5, 0.01, seed))
+    rec.load_cloud(pts)
+    rec.build_distance()
+    rec.init_sphere(0.75)
+    return rec
+
+
+KINDS = [(2, 64, 32, 0, 1), (2, 96, 64, 1, 1), (3, 32, 32, 1, 1), (3, 40, 32, 0, 1), (3, 24, 64, 1, 0),
+         (2, 48, 32, 1, 0)]
+
+
+def test_batch_evolve_equals_solo_runs():
+    """Jobs advanced together in one graph per chunk give the same states,
+    iteration counts and energies as each job evolved alone."""
+    slr = _slr()
+    solo = []
+    for i, k in enumerate(KINDS):
+        r = _small_job(k, i)
+        it, conv = r.evolve()
+        solo.append((it, conv, r.u(), r.diagnostics()["e2"]))
+        r.close()
+    jobs = [_small_job(k, i) for i, k in enumerate(KINDS)]
+    its, convs = slr.slr_batch_evolve([j.ctx for j in jobs], chunk=4)
+    for j, (it, conv, u, e2) in zip(jobs, solo):
+        pass
+    for idx, (j, (it, conv, u, e2)) in enumerate(zip(jobs, solo)):
+        assert its[idx] == it and convs[idx] == conv
+        assert np.array_equal(j.u(), u)
+        assert np.array_equal(j.diagnostics()["e2"], e2)
+
+
+def test_server_results_equal_solo_runs():
+    """Continuous batching: jobs submitted into a running mix (at most 3
+    admitted at once, a tight memory budget) finish with exactly the state,
+    iteration count and energies of the same job run alone."""
+    import time
+
+    slr = _slr()
+    specs = []
+    for i, k in enumerate(KINDS):
+        dim, n, prec, interp, band = k
+        shape = (n,) * dim + ((1,) if dim == 2 else ())
+        cfg = slr.slr_config_default(dim=dim, n=shape, lo=(-1.0,) * dim, hi=(1.0,) * dim, precision=prec,
+                                     interp=interp, band=band, max_iters=40)
+        pts = (synth.sphere_cloud(800, 0.5, 0.01, i) if dim == 3 else synth.circle_noisy(300, 0.5, 0.01, i))
+        specs.append((cfg, pts))
+    solo = []
+    for i, k in enumerate(KINDS):
+        r = _small_job(k, i)
+        it, conv = r.evolve()
+        solo.append((it, r.u(), r.diagnostics()["e2"]))
+        r.close()
+    srv = slr.slr_server_create(64 << 20, max_active=3)
+    try:
+        tickets = []
+        for cfg, pts in specs:
+            tickets.append(slr.slr_server_submit(srv, cfg, pts, (0.0, 0.0, 0.0, 0.75)))
+            time.sleep(0.002)
+        results = {}
+        t0 = time.time()
+        while len(results) < len(tickets) and time.time() - t0 < 120:
+            for t in tickets:
+                if t in results:
+                    continue
+                st, ctx, lat = slr.slr_server_poll(srv, t)
+                if st == 2:
+                    n_nodes = int(np.prod([specs[tickets.index(t)][0].n[a] for a in range(3)]))
+                    u = slr.slr_get_field(ctx, slr.SLR_FIELD_U, n_nodes)
+                    d = slr.slr_diagnostics(ctx)
+                    results[t] = (d["iters"], u, d["e2"], lat)
+                    slr.slr_server_release(srv, t)
+            time.sleep(0.005)
+        assert len(results) == len(tickets)
+        for t, (it, u, e2) in zip(tickets, solo):
+            rit, ru, re2, lat = results[t]
+            assert rit == it and np.array_equal(ru, u) and np.array_equal(re2, e2)
+            assert lat is not None and lat > 0
+    finally:
+        slr.slr_server_destroy(srv)
