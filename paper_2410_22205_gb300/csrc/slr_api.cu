@@ -112,7 +112,7 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     return SLR_OK;
 }
 
-constexpr int kKernelsPerIteration = 3;  // step, energy, record
+constexpr int kKernelsPerIteration = 4;  // step, front cells, energy, record
 
 slr_status read_status(slr_ctx* c, int* stop, int* error, int* n) {
     int* hp = c->host_pinned_flags;
@@ -157,9 +157,13 @@ slr_status size_band_buffers(slr_ctx* c, long long count) {
 
 slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     release_t(c, c->part_e);
+    release_t(c, c->front);
     c->n_echunks = (ncells + 31) / 32;
+    long long slots = (ncells + 1023) / 1024;
+    if (slots < 1) slots = 1;
     c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2));
-    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy partials failed");
+    c->front = (int*)dev_alloc(c, sizeof(int) * (slots * 1024 + slots));
+    if (!c->part_e || !c->front) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
     return SLR_OK;
 }
 
@@ -889,6 +893,7 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->part_dphi);
     release_t(c, c->part_e);
     release_t(c, c->tile_status);
+    release_t(c, c->front);
     release_t(c, c->ds);
     if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);
     for (int i = 0; i < 4; ++i)

@@ -156,9 +156,12 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
     return neg && pos;
 }
 
-// Energy pass, one launch. Block b checks kEnergyCand consecutive candidate
-// cells for a sign change (front cells, zero counted as positive) and
-// compacts them in order into shared memory. Then:
+// Energy pass, two launches.
+//  k_front:  block b checks the kEnergyCand candidate cells [b·kEnergyCand,
+//            (b+1)·kEnergyCand) for a sign change (front cells, zero counted
+//            as positive) and writes them, in order, to slot b of the front
+//            array (fixed position b·kEnergyCand) with their count.
+//  k_energy: block b processes slot b:
 //   3-D: one thread per (front cell, subcell layer c along z): the 16 z-lines
 //        of the 4x4x4 stencil at θ_z(c), the 4 y-lines at the R θ_y, the R
 //        x-lines at the R θ_x (WENO; the data-only part of each y- and x-line
@@ -166,23 +169,60 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
 //        trilinear interpolant (Q1); d by Q1, linear along each x-line. A
 //        subcell counts when |φ(x')| < (√3/2)Δx' and adds |d(x')|^p Δx'^2.
 //   2-D: one thread per front cell (segments, FP64).
-// Many small blocks let the block scheduler even out the clustering of front
-// cells. Sums per work item in the storage type; per-thread and per-block
-// sums in FP64, in a fixed order (one partial pair per block).
-constexpr int kEnergyCand = 1024;  // candidate cells per block (4 per thread)
+// No ordering across blocks is needed, and the block scheduler evens out the
+// uneven slot sizes. Sums per work item in the storage type; per-thread and
+// per-block sums in FP64, in a fixed order (one partial pair per block).
+constexpr int kEnergyCand = 1024;  // candidate cells per slot (4 per thread)
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* ub0, const T* ub1,
+                                                          const int* __restrict__ cells, long long ncells, int offset,
+                                                          int* __restrict__ front, int* __restrict__ fcount,
+                                                          DevState* ds, int check_stop) {
+    constexpr int W = kEnergyThreads / 32;
+    constexpr int PER = kEnergyCand / kEnergyThreads;
+    __shared__ int s_warp[W + 1];
+    if (check_stop && ds->stop) return;
+    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    int* slot = front + (long long)blockIdx.x * kEnergyCand;
+    int node[PER], fl[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
+        node[r] = 0;
+        fl[r] = 0;
+        if (e < ncells) {
+            int i, j, k;
+            cell_of<T, DIM>(P, cells, e, i, j, k);
+            node[r] = (int)(i + P.s1 * j + P.s2 * k);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
+        fl[r] = e < ncells && is_front<T, DIM>(P, u, node[r]);
+    }
+    int nf = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        int tot;
+        const int off = block_exclusive_flag<kEnergyThreads>(fl[r], s_warp, &tot);
+        if (fl[r]) slot[nf + off] = node[r];
+        nf += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) fcount[blockIdx.x] = nf;
+}
 
 template <typename T, int DIM, int INTERP, int RC>
 __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T* ub0, const T* ub1,
-                                                           const T* __restrict__ d, const int* __restrict__ cells,
-                                                           long long ncells, int R_run, double h, double p,
-                                                           int p_kind, T thr, T hp2, T pT, int offset, double* part,
-                                                           DevState* ds, int check_stop) {
+                                                           const T* __restrict__ d, const int* __restrict__ front,
+                                                           const int* __restrict__ fcount, int R_run, double h,
+                                                           double p, int p_kind, T thr, T hp2, T pT, int offset,
+                                                           double* part, DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
-    constexpr int PER = kEnergyCand / kEnergyThreads;
     const int R = RC > 0 ? RC : R_run;
     constexpr double RD = RC > 0 ? (double)RC : 1.0;
-    __shared__ int s_list[kEnergyCand];
-    __shared__ int s_warp[W + 1];
     __shared__ T s_th[kMaxR];
     __shared__ WenoAxis<T> s_wa[kMaxR];
     __shared__ double s_a[W], s_b[W];
@@ -193,24 +233,9 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
         s_th[threadIdx.x] = t;
         s_wa[threadIdx.x].set(t);
     }
-    // front cells of this block's candidate range, in order (PER rounds)
-    int nf = 0;
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
-        int node = 0, f = 0;
-        if (e < ncells) {
-            int i, j, k;
-            cell_of<T, DIM>(P, cells, e, i, j, k);
-            node = (int)(i + P.s1 * j + P.s2 * k);
-            f = is_front<T, DIM>(P, u, node);
-        }
-        int tot;
-        const int off = block_exclusive_flag<kEnergyThreads>(f, s_warp, &tot);
-        if (f) s_list[nf + off] = node;
-        nf += tot;
-        __syncthreads();
-    }
+    __syncthreads();
+    const int* s_list = front + (long long)blockIdx.x * kEnergyCand;  // this block's slot
+    const int nf = fcount[blockIdx.x];
     // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
     auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
     auto WA = [&](int m) -> WenoAxis<T> {
@@ -456,15 +481,18 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const int blocks = (int)energy_blocks(c);
     const double hp = c->h / c->cfg.energy_R;
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
+    int* fcount = (int*)(c->front + (size_t)blocks * kEnergyCand);
+    k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
+                                                               offset, c->front, fcount, c->ds, check_stop);
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
-            thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
+            p_kind, thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
     else
         k_energy<T, DIM, INTERP, 0><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, c->cfg.energy_R, c->h, p, p_kind,
-            thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
-    c->launches += 1;
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
+            p_kind, thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
+    c->launches += 2;  // front cells, then energy
     return cudaGetLastError();
 }
 

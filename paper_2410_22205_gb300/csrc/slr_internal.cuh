@@ -97,6 +97,7 @@ struct slr_ctx {
     long long n_tiles_cap = 0;
     double* part_e = nullptr;      // two per energy block, plus a two-value report slot
     long long n_echunks = 0;       // candidate chunks of 32 cells (sizes part_e)
+    int* front = nullptr;          // per-block slots of front cells (1024 each) followed by the slot counts
     unsigned long long* tile_status = nullptr;  // look-back words of the step kernel
     slr::DevState* ds = nullptr;
     int* host_pinned_flags = nullptr;  // pinned host words for status readback
