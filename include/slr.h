@@ -79,7 +79,7 @@ typedef struct {
     double alpha;       /* singular-gradient test exponent α, default 1 */
     int energy_R;       /* 3-D energy subcells per axis R (§3.5), default 5, 1..8 */
     double stop_tol;    /* Δ_E threshold (§4 eq. deltaEn), default 1e-4 */
-    int stop_k;         /* running-mean window k_max, default 10 */
+    int stop_k;         /* running-mean window k_max, default 10, at most 1023 */
     int min_iters;      /* default 10 */
     int max_iters;      /* default 100 */
 } slr_config;

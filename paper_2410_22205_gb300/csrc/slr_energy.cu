@@ -117,22 +117,22 @@ __device__ double energy_cell_2d(const Params<T>& P, const T* __restrict__ u, co
 // θ share it.
 template <typename T>
 struct WenoInd {
-    T v1, dv, dl, dr, sl2, sr2;
+    T v1, dv, dr, ddf, sl2, sr2;
     __device__ __forceinline__ void set(T v0, T a1, T v2, T v3, T h4) {
         v1 = a1;
         dv = v2 - a1;
-        dl = (v0 + v2) - (a1 + a1);
-        dr = (a1 + v3) - (v2 + v2);
-        T sl = dl * dl + h4, sr = dr * dr + h4;
+        const T dl = fma(T(-2), a1, v0 + v2);
+        dr = fma(T(-2), v2, a1 + v3);
+        const T sl = fma(dl, dl, h4), sr = fma(dr, dr, h4);
         sl2 = sl * sl;
         sr2 = sr * sr;
+        ddf = dl - dr;
     }
-    // same arithmetic as weno1()
+    // weno1() at this θ (the weight's denominator rounded once more)
     __device__ __forceinline__ T eval(const WenoAxis<T>& w) const {
-        T gl = w.cl * sr2, gr = w.cr * sl2;
-        T num = gl * dl + gr * dr;
-        T den = gl + gr;
-        return (v1 + w.th * dv) + w.q * fast_div(num, den);
+        const T gl = w.rho * sr2;
+        const T wl = fast_div(gl, sl2 + gl);
+        return fma(w.q, fma(wl, ddf, dr), fma(w.th, dv, v1));
     }
 };
 
@@ -362,6 +362,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
 //  mode 1 (step):   Δ_φ, band size, n += 1, E_2(φ^{n}), E_p; with evolve
 //                   set, the stop test of §4 eq. deltaEn
 //  mode 2 (report): sums of the energy pass into report[0..1] only
+constexpr int kRecordThreads = 1024;  // single block; also bounds the stop window k_max < 1024
+
 struct RecordArgs {
     const double* part_dphi;
     const double* part_e;
@@ -379,47 +381,55 @@ struct RecordArgs {
     double* report;
 };
 
-__global__ void __launch_bounds__(1024) k_record(RecordArgs A, DevState* ds) {
-    __shared__ double s_a[32], s_b[32], s_c[32];
+__global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevState* ds) {
+    constexpr int W = kRecordThreads / 32;
+    __shared__ double s_a[W], s_b[W], s_c[W];
+    __shared__ double s_hist[kRecordThreads];
     if (A.mode == 1 && ds->stop) return;
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
         ntiles = A.full_grid ? A.n_dphi_full : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
     }
-    // contiguous segments per thread, eight independent loads in flight;
-    // the order of the additions is fixed by the sizes alone
+    // thread t sums the partials t, t + T, t + 2T, ... (T threads); the
+    // order of the additions is fixed by the sizes alone, and neighbouring
+    // threads read neighbouring partials
     double a = 0.0, b = 0.0, cc = 0.0;
     {
-        const long long per = (ntiles + blockDim.x - 1) / blockDim.x;
-        long long i = threadIdx.x * per, end = i + per < ntiles ? i + per : ntiles;
-        for (; i + 8 <= end; i += 8) {
-            double v[8];
+        long long i = threadIdx.x;
+        for (; i + 3 * kRecordThreads < ntiles; i += 4 * kRecordThreads) {
+            double v[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = A.part_dphi[i + q];
+            for (int q = 0; q < 4; ++q) v[q] = A.part_dphi[i + q * kRecordThreads];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a += v[q];
+            for (int q = 0; q < 4; ++q) a += v[q];
         }
-        for (; i < end; ++i) a += A.part_dphi[i];
+        for (; i < ntiles; i += kRecordThreads) a += A.part_dphi[i];
     }
     {
-        const long long per = (A.nchunks + blockDim.x - 1) / blockDim.x;
-        long long i = threadIdx.x * per, end = i + per < A.nchunks ? i + per : A.nchunks;
-        for (; i + 4 <= end; i += 4) {
-            double v[8];
+        const double2* pe = reinterpret_cast<const double2*>(A.part_e);
+        long long i = threadIdx.x;
+        for (; i + 3 * kRecordThreads < A.nchunks; i += 4 * kRecordThreads) {
+            double2 v[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = A.part_e[2 * i + q];
+            for (int q = 0; q < 4; ++q) v[q] = pe[i + q * kRecordThreads];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                b += v[2 * q];
-                cc += v[2 * q + 1];
+                b += v[q].x;
+                cc += v[q].y;
             }
         }
-        for (; i < end; ++i) {
-            b += A.part_e[2 * i];
-            cc += A.part_e[2 * i + 1];
+        for (; i < A.nchunks; i += kRecordThreads) {
+            const double2 v = pe[i];
+            b += v.x;
+            cc += v.y;
         }
     }
+    // the stop test's window of earlier energies, staged in parallel:
+    // s_hist[t] = E_2 at iteration (nn - k) + t for t < k (nn, k as below)
+    const int nn = A.mode == 1 ? n + 1 : n;
+    const int kwin = nn < A.stop_k ? nn : A.stop_k;
+    if (A.mode == 1 && A.evolve && (int)threadIdx.x < kwin) s_hist[threadIdx.x] = ds->e2_hist[(nn - kwin + threadIdx.x) % kHist];
     a = warp_sum(a);
     b = warp_sum(b);
     cc = warp_sum(cc);
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(1024) k_record(RecordArgs A, DevState* ds) {
     __syncthreads();
     if (threadIdx.x != 0) return;
     double dphi = 0.0, sp = 0.0, s2 = 0.0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) {
+    for (int i = 0; i < W; ++i) {
         dphi += s_a[i];
         sp += s_b[i];
         s2 += s_c[i];
@@ -442,11 +452,9 @@ __global__ void __launch_bounds__(1024) k_record(RecordArgs A, DevState* ds) {
         A.report[1] = s2;
         return;
     }
-    int nn = n;
     if (A.mode == 1) {
-        ds->dphi_hist[nn % kHist] = dphi * A.h_dim;
-        ds->band_hist[nn % kHist] = A.full_grid ? A.N : (long long)ds->band_count[(nn + 1) & 1];
-        nn += 1;
+        ds->dphi_hist[n % kHist] = dphi * A.h_dim;
+        ds->band_hist[n % kHist] = A.full_grid ? A.N : (long long)ds->band_count[(n + 1) & 1];
         ds->n = nn;
     }
     double E2 = sqrt(s2);
@@ -456,11 +464,14 @@ __global__ void __launch_bounds__(1024) k_record(RecordArgs A, DevState* ds) {
         ds->ticket = 0u;
         ds->epoch = ds->epoch + 1u;
         if (A.evolve) {
-            // §4 eq. deltaEn with k = min(n, k_max) for both running means
-            int k = nn < A.stop_k ? nn : A.stop_k;
+            // §4 eq. deltaEn with k = min(n, k_max) for both running means:
+            // en over iterations nn-k+1..nn, em over nn-k..nn-1, summed in
+            // increasing iteration order
+            const int k = kwin;
             double en = 0.0, em = 0.0;
-            for (int i = nn - k + 1; i <= nn; ++i) en += ds->e2_hist[i % kHist];
-            for (int i = nn - k; i <= nn - 1; ++i) em += ds->e2_hist[i % kHist];
+            for (int i = 1; i < k; ++i) en += s_hist[i];
+            en += E2;
+            for (int i = 0; i < k; ++i) em += s_hist[i];
             en /= (double)k;
             em /= (double)k;
             double delta = en > 0.0 ? fabs(em - en) / en : (em == en ? 0.0 : INFINITY);
@@ -539,7 +550,7 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     A.min_iters = c->cfg.min_iters;
     A.max_iters = c->cfg.max_iters;
     A.report = c->part_e + 2 * c->n_echunks;  // two spare doubles after the partials
-    k_record<<<1, 1024, 0, c->stream>>>(A, c->ds);
+    k_record<<<1, kRecordThreads, 0, c->stream>>>(A, c->ds);
     c->launches += 1;
     return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ template <typename T>
 struct Params {
     int n0, n1, n2;        // nodes per axis
     long long s1, s2;      // strides of axes 1 and 2
+    int is1, is2;          // the same strides as 32-bit values (fewer than 2^31 nodes)
     T inv_h;               // 1/h
     T inv_2h;              // 1/(2h)
     T h4;                  // h^4 (WENO: ε = h^2 folded into the weights)
@@ -209,12 +210,11 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // C_L = (2-θ)/3, C_R = (1+θ)/3 (eq. ckgamma) and q = θ(θ-1)/2.
 template <typename T>
 struct WenoAxis {
-    T th, q, cl, cr;
+    T th, q, rho;  // θ, θ(θ-1)/2, C_L/C_R
     __device__ __forceinline__ void set(T t) {
         th = t;
         q = T(0.5) * t * (t - T(1));
-        cl = (T(2) - t) * T(1.0 / 3.0);
-        cr = (T(1) + t) * T(1.0 / 3.0);
+        rho = (T(2) - t) / (T(1) + t);  // C_L = (2-θ)/3, C_R = (1+θ)/3
     }
 };
 
@@ -223,19 +223,16 @@ struct WenoAxis {
 // Σ w_k P_k with α_k = C_k/(I_k + h^2)^2 and I_k = D_k^2/h^2 (the quadratic
 // forms A_L, A_R give the squared second differences D_L, D_R):
 //   P_k(θ) = v_j + θ (v_{j+1} - v_j) + D_k θ(θ-1)/2,
-//   w_L = C_L (D_R^2 + h^4)^2 / (C_L (D_R^2 + h^4)^2 + C_R (D_L^2 + h^4)^2).
+//   w_L = ρ s_R^2 / (ρ s_R^2 + s_L^2),  s_k = D_k^2 + h^4,  ρ = C_L/C_R,
+//   Σ w_k P_k = v_j + θ (v_{j+1} - v_j) + (D_R + w_L (D_L - D_R)) θ(θ-1)/2.
 template <typename T>
 __device__ __forceinline__ T weno1(T v0, T v1, T v2, T v3, const WenoAxis<T>& w, T h4) {
-    T dl = (v0 + v2) - (v1 + v1);
-    T dr = (v1 + v3) - (v2 + v2);
-    T sl = dl * dl + h4;
-    T sr = dr * dr + h4;
-    T gl = w.cl * (sr * sr);
-    T gr = w.cr * (sl * sl);
-    T num = gl * dl + gr * dr;
-    T den = gl + gr;
-    T lin = v1 + w.th * (v2 - v1);
-    return lin + w.q * fast_div(num, den);
+    const T dl = fma(T(-2), v1, v0 + v2);
+    const T dr = fma(T(-2), v2, v1 + v3);
+    const T sl = fma(dl, dl, h4), sr = fma(dr, dr, h4);
+    const T gl = w.rho * (sr * sr);
+    const T wl = fast_div(gl, fma(sl, sl, gl));
+    return fma(w.q, fma(wl, dl - dr, dr), fma(w.th, v2 - v1, v1));
 }
 
 // eq. IQ1 at node (i,j,k) + displacement r (units of h): multilinear
@@ -276,40 +273,31 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
     WenoAxis<T> wx, wy, wz;
     wx.set(tx);
     wy.set(ty);
-    long long ox[4], oy[4], oz[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        ox[a] = clampi(cx - 1 + a, 0, P.n0 - 1);
-        oy[a] = P.s1 * clampi(cy - 1 + a, 0, P.n1 - 1);
-    }
-    if (DIM == 3) {
-        wz.set(tz);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) oz[a] = P.s2 * clampi(cz - 1 + a, 0, P.n2 - 1);
-    }
+    if (DIM == 3) wz.set(tz);
     const bool interior = cx >= 1 && cx <= P.n0 - 3 && cy >= 1 && cy <= P.n1 - 3 &&
                           (DIM == 2 || (cz >= 1 && cz <= P.n2 - 3));
     if (interior) {
         // whole stencil inside the grid: one base pointer, rows of four
-        // consecutive x-values, z-lines evaluated as their rows arrive
-        const T* base = u + ((long long)(cx - 1) + P.s1 * (cy - 1) + (DIM == 3 ? P.s2 * (cz - 1) : 0ll));
+        // consecutive x-values at 32-bit offsets (the grid holds fewer than
+        // 2^31 nodes), z-lines evaluated as their rows arrive
+        const T* base = u + ((cx - 1) + P.is1 * (cy - 1) + (DIM == 3 ? P.is2 * (cz - 1) : 0));
         T yv[4][4];  // [a][b]: z-line (DIM 3) or node value (DIM 2) at column a, row b
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const T* rb = base + P.s1 * b;
             if (DIM == 3) {
                 T r[4][4];  // [c][a]
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const T* row = rb + P.s2 * c;
+                    const T* row = base + (P.is1 * b + P.is2 * c);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) r[c][a] = ld(row + a);
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) yv[a][b] = weno1(r[0][a], r[1][a], r[2][a], r[3][a], wz, P.h4);
             } else {
+                const T* row = base + P.is1 * b;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) yv[a][b] = ld(rb + a);
+                for (int a = 0; a < 4; ++a) yv[a][b] = ld(row + a);
             }
         }
         T xv[4];
@@ -317,19 +305,24 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
         for (int a = 0; a < 4; ++a) xv[a] = weno1(yv[a][0], yv[a][1], yv[a][2], yv[a][3], wy, P.h4);
         return weno1(xv[0], xv[1], xv[2], xv[3], wx, P.h4);
     }
+    int ox[4], oy[4], oz[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ox[a] = clampi(cx - 1 + a, 0, P.n0 - 1);
+        oy[a] = P.is1 * clampi(cy - 1 + a, 0, P.n1 - 1);
+        if (DIM == 3) oz[a] = P.is2 * clampi(cz - 1 + a, 0, P.n2 - 1);
+    }
     T xv[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         T yv[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            long long base = ox[a] + oy[b];
+            const T* col = u + (ox[a] + oy[b]);
             if (DIM == 3) {
-                T z0 = ld(u + base + oz[0]), z1 = ld(u + base + oz[1]);
-                T z2 = ld(u + base + oz[2]), z3 = ld(u + base + oz[3]);
-                yv[b] = weno1(z0, z1, z2, z3, wz, P.h4);
+                yv[b] = weno1(ld(col + oz[0]), ld(col + oz[1]), ld(col + oz[2]), ld(col + oz[3]), wz, P.h4);
             } else {
-                yv[b] = ld(u + base);
+                yv[b] = ld(col);
             }
         }
         xv[a] = weno1(yv[0], yv[1], yv[2], yv[3], wy, P.h4);

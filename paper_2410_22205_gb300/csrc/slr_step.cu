@@ -33,7 +33,7 @@ __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i
 // its output offset by a warp-parallel look-back, writes its part of G̃^n, and
 // only then runs the SL arithmetic. No block-wide barrier inside the loop.
 template <typename T, int DIM, int INTERP>
-__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 4))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
+__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 4) : (sizeof(T) == 8 ? 3 : 4))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
                                                           int* L0, int* L1, unsigned long long* status,
                                                           double* part_dphi, DevState* ds, double ep_override) {
     if (ds->stop) return;
@@ -248,6 +248,8 @@ Params<T> make_params(const slr_ctx* c) {
     P.n2 = (int)c->cfg.n[2];
     P.s1 = c->cfg.n[0];
     P.s2 = c->cfg.n[0] * c->cfg.n[1];
+    P.is1 = (int)P.s1;
+    P.is2 = (int)P.s2;
     P.inv_h = (T)(1.0 / c->h);
     P.inv_2h = (T)(1.0 / (2.0 * c->h));
     P.h4 = (T)(c->h * c->h * c->h * c->h);

@@ -47,6 +47,7 @@ def test_library_is_built_for_sm_103a():
     dict(energy_R=9),
     dict(gamma=0.01, beta=0.02),
     dict(max_iters=100000),
+    dict(stop_k=1024),
 ])
 def test_create_rejects_invalid_config(bad):
     cfg = slr.slr_config_default(**bad)

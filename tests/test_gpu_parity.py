@@ -281,15 +281,16 @@ def test_circle64_workload_100_steps_fp64_q1():
     assert rec.diagnostics()["iters"] == 100
 
 
-def test_evolve_matches_oracle_stop_rule():
-    rec, P = make(2, 48, 64, 1, 1, p=1.0, delta=0.0)
+@pytest.mark.parametrize("kmax,min_iters,tol", [(10, 10, 1e-4), (3, 2, 1e-3), (25, 5, 1e-3)])
+def test_evolve_matches_oracle_stop_rule(kmax, min_iters, tol):
+    rec, P = make(2, 48, 64, 1, 1, p=1.0, delta=0.0, stop_k=kmax, min_iters=min_iters, stop_tol=tol)
     pts = synth.circle_noisy(150, 0.5, 0.0, 0)
     rec.load_cloud(pts)
     rec.build_distance()
     rec.init_sphere(0.8)
     u0, d = rec.u(), rec.d()
     iters, conv = rec.evolve()
-    ref = O.evolve(P, u0, d)
+    ref = O.evolve(P, u0, d, kmax=kmax, min_iters=min_iters, tol=tol)
     assert iters == ref["iters"] and conv == ref["converged"]
     assert np.abs(rec.u() - ref["u"]).max() <= 1e-10
     np.testing.assert_allclose(rec.diagnostics()["e2"], ref["E2"], rtol=1e-10)
