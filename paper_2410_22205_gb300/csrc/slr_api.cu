@@ -161,7 +161,7 @@ slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     c->n_echunks = (ncells + 31) / 32;
     long long slots = (ncells + 1023) / 1024;
     if (slots < 1) slots = 1;
-    c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2));
+    c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2 + 3 * 32));  // + record blocks
     c->front = (int*)dev_alloc(c, sizeof(int) * (slots * 1024 + slots));
     if (!c->part_e || !c->front) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
     return SLR_OK;
@@ -253,7 +253,7 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
     if (!(k.dt >= 0.0)) return bad("dt must be >= 0");
     if (k.band != 0 && k.band != 1) return bad("band must be 0 or 1");
     if (k.energy_R < 1 || k.energy_R > kMaxR) return bad("energy_R must be in 1..8");
-    if (k.stop_k < 1 || k.stop_k > 1023 || k.max_iters < 1 || k.min_iters < 0) return bad("bad stop parameters");
+    if (k.stop_k < 1 || k.stop_k > kMaxStopK || k.max_iters < 1 || k.min_iters < 0) return bad("bad stop parameters");
     if (k.max_iters >= kHist - 1) return bad("max_iters too large");
     if (!(k.c_sing >= 0.0)) return bad("c_sing must be >= 0");
     c->h = h;

@@ -147,7 +147,7 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                T v = ld(u + node + dx + P.s1 * dy + P.s2 * dz);
+                T v = ld(u + (node + dx + P.is1 * dy + P.is2 * dz));
                 if (v < T(0))
                     neg = true;
                 else
@@ -181,37 +181,63 @@ __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* 
                                                           DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
     constexpr int PER = kEnergyCand / kEnergyThreads;
+    static_assert(PER == 4, "four candidates per thread (one 16-byte load of the cell list)");
     __shared__ int s_warp[W + 1];
     if (check_stop && ds->stop) return;
     const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
     int* slot = front + (long long)blockIdx.x * kEnergyCand;
-    int node[PER], fl[PER];
+    // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
+    const long long e0 = (long long)blockIdx.x * kEnergyCand + PER * threadIdx.x;
+    int node[PER];
+    if (cells && e0 + PER <= ncells) {
+        const int4 c4 = *reinterpret_cast<const int4*>(cells + e0);  // slot starts are multiples of 1024
+        node[0] = c4.x;
+        node[1] = c4.y;
+        node[2] = c4.z;
+        node[3] = c4.w;
+    } else {
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
-        node[r] = 0;
-        fl[r] = 0;
-        if (e < ncells) {
-            int i, j, k;
-            cell_of<T, DIM>(P, cells, e, i, j, k);
-            node[r] = (int)(i + P.s1 * j + P.s2 * k);
+        for (int r = 0; r < PER; ++r) {
+            node[r] = 0;
+            if (e0 + r < ncells) {
+                int i, j, k;
+                cell_of<T, DIM>(P, cells, e0 + r, i, j, k);
+                node[r] = i + P.is1 * j + P.is2 * k;
+            }
         }
     }
+    bool fl[PER];
+    int cnt = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const long long e = (long long)blockIdx.x * kEnergyCand + r * kEnergyThreads + threadIdx.x;
-        fl[r] = e < ncells && is_front<T, DIM>(P, u, node[r]);
+        fl[r] = e0 + r < ncells && is_front<T, DIM>(P, u, node[r]);
+        cnt += fl[r];
     }
-    int nf = 0;
+    // block exclusive scan of the per-thread counts (candidate order kept)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        int tot;
-        const int off = block_exclusive_flag<kEnergyThreads>(fl[r], s_warp, &tot);
-        if (fl[r]) slot[nf + off] = node[r];
-        nf += tot;
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
-    if (threadIdx.x == 0) fcount[blockIdx.x] = nf;
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < W; ++w) {
+            const int c = s_warp[w];
+            s_warp[w] = run;
+            run += c;
+        }
+        s_warp[W] = run;
+    }
+    __syncthreads();
+    int off = s_warp[warp] + incl - cnt;
+#pragma unroll
+    for (int r = 0; r < PER; ++r)
+        if (fl[r]) slot[off++] = node[r];
+    if (threadIdx.x == 0) fcount[blockIdx.x] = s_warp[W];
 }
 
 template <typename T, int DIM, int INTERP, int RC>
@@ -231,7 +257,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
     if (RC == 0 && threadIdx.x < R) {
         T t = ((T)threadIdx.x + (T)0.5) / (T)R;  // subcell centre θ_m = (m + 1/2)/R
         s_th[threadIdx.x] = t;
-        s_wa[threadIdx.x].set(t);
+        s_wa[threadIdx.x].set_exact(t);
     }
     __syncthreads();
     const int* s_list = front + (long long)blockIdx.x * kEnergyCand;  // this block's slot
@@ -241,7 +267,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
     auto WA = [&](int m) -> WenoAxis<T> {
         if (RC > 0) {
             WenoAxis<T> w;
-            w.set((T)((m + 0.5) / RD));
+            w.set_exact((T)((m + 0.5) / RD));
             return w;
         }
         return s_wa[m];
@@ -263,6 +289,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
             a2 += s2;
         }
     } else {
+        // sums over this thread's items in the storage type, widened once
+        T tp = T(0), t2 = T(0);
         const int items = nf * R;
         for (int it = threadIdx.x; it < items; it += kEnergyThreads) {
             const int fi = it / R, cz = it - fi * R;
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
             const T tz = TH(cz);
             T dc[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) dc[c] = ld(d + nd + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+            for (int c = 0; c < 8; ++c) dc[c] = ld(d + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
             // d on the layer z = θ_z: bilinear in (x, y) from the two z-faces
             T dz[4];
 #pragma unroll
@@ -282,13 +310,12 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
             T cp = T(0), c2 = T(0);
             if (INTERP == 1) {
                 const WenoAxis<T> wz = WA(cz);
-                int ox[4];
-                long long oy[4], oz[4];
+                int ox[4], oy[4], oz[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     ox[a] = clampi(i - 1 + a, 0, P.n0 - 1);
-                    oy[a] = P.s1 * clampi(j - 1 + a, 0, P.n1 - 1);
-                    oz[a] = P.s2 * clampi(k - 1 + a, 0, P.n2 - 1);
+                    oy[a] = P.is1 * clampi(j - 1 + a, 0, P.n1 - 1);
+                    oz[a] = P.is2 * clampi(k - 1 + a, 0, P.n2 - 1);
                 }
                 WenoInd<T> iy[4];
 #pragma unroll
@@ -296,7 +323,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
                     T zl[4];
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const T* col = u + ox[a] + oy[b];
+                        const T* col = u + (ox[a] + oy[b]);
                         zl[b] = weno1(ld(col + oz[0]), ld(col + oz[1]), ld(col + oz[2]), ld(col + oz[3]), wz, P.h4);
                     }
                     iy[a].set(zl[0], zl[1], zl[2], zl[3], P.h4);
@@ -319,7 +346,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
             } else {
                 T uc[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) uc[c] = ld(u + nd + (c & 1) + P.s1 * ((c >> 1) & 1) + P.s2 * (c >> 2));
+                for (int c = 0; c < 8; ++c) uc[c] = ld(u + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
                 T uz[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) uz[c] = uc[c] + tz * (uc[c + 4] - uc[c]);
@@ -333,9 +360,11 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
                     }
                 }
             }
-            ap += (double)cp;
-            a2 += (double)c2;
+            tp += cp;
+            t2 += c2;
         }
+        ap = (double)tp;
+        a2 = (double)t2;
     }
     ap = warp_sum(ap);
     a2 = warp_sum(a2);
@@ -357,16 +386,22 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
 }
 
 // Reduction of the step and energy partials and the bookkeeping of one
-// iteration (single block, fixed summation order).
+// iteration. kRecordBlocks blocks each sum a fixed slice of the partials
+// (FP64, fixed order) into one triple; the last block to finish sums the
+// triples in block order and does the bookkeeping:
 //  mode 0 (init):   E_2(φ^0) into the history, E_p for the first step
 //  mode 1 (step):   Δ_φ, band size, n += 1, E_2(φ^{n}), E_p; with evolve
 //                   set, the stop test of §4 eq. deltaEn
 //  mode 2 (report): sums of the energy pass into report[0..1] only
-constexpr int kRecordThreads = 1024;  // single block; also bounds the stop window k_max < 1024
+// The slices depend on the sizes alone, so the result does not depend on
+// which block finishes last.
+constexpr int kRecordBlocks = 32;
+constexpr int kRecordThreads = 256;
 
 struct RecordArgs {
     const double* part_dphi;
     const double* part_e;
+    double* block_part;    // 3 per record block
     long long nchunks;     // number of energy partial pairs (energy blocks)
     long long n_dphi_full; // number of Δ_φ partials in whole-grid mode (step blocks)
     long long N;
@@ -384,52 +419,31 @@ struct RecordArgs {
 __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevState* ds) {
     constexpr int W = kRecordThreads / 32;
     __shared__ double s_a[W], s_b[W], s_c[W];
-    __shared__ double s_hist[kRecordThreads];
+    __shared__ double s_hist[kMaxStopK + 1];
+    __shared__ int s_last;
     if (A.mode == 1 && ds->stop) return;
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
         ntiles = A.full_grid ? A.n_dphi_full : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
     }
-    // thread t sums the partials t, t + T, t + 2T, ... (T threads); the
-    // order of the additions is fixed by the sizes alone, and neighbouring
-    // threads read neighbouring partials
+    const long long G = gridDim.x;
     double a = 0.0, b = 0.0, cc = 0.0;
     {
-        long long i = threadIdx.x;
-        for (; i + 3 * kRecordThreads < ntiles; i += 4 * kRecordThreads) {
-            double v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = A.part_dphi[i + q * kRecordThreads];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) a += v[q];
-        }
-        for (; i < ntiles; i += kRecordThreads) a += A.part_dphi[i];
+        const long long per = (ntiles + G - 1) / G;
+        const long long beg = blockIdx.x * per, end = beg + per < ntiles ? beg + per : ntiles;
+        for (long long i = beg + threadIdx.x; i < end; i += kRecordThreads) a += A.part_dphi[i];
     }
     {
         const double2* pe = reinterpret_cast<const double2*>(A.part_e);
-        long long i = threadIdx.x;
-        for (; i + 3 * kRecordThreads < A.nchunks; i += 4 * kRecordThreads) {
-            double2 v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = pe[i + q * kRecordThreads];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                b += v[q].x;
-                cc += v[q].y;
-            }
-        }
-        for (; i < A.nchunks; i += kRecordThreads) {
+        const long long per = (A.nchunks + G - 1) / G;
+        const long long beg = blockIdx.x * per, end = beg + per < A.nchunks ? beg + per : A.nchunks;
+        for (long long i = beg + threadIdx.x; i < end; i += kRecordThreads) {
             const double2 v = pe[i];
             b += v.x;
             cc += v.y;
         }
     }
-    // the stop test's window of earlier energies, staged in parallel:
-    // s_hist[t] = E_2 at iteration (nn - k) + t for t < k (nn, k as below)
-    const int nn = A.mode == 1 ? n + 1 : n;
-    const int kwin = nn < A.stop_k ? nn : A.stop_k;
-    if (A.mode == 1 && A.evolve && (int)threadIdx.x < kwin) s_hist[threadIdx.x] = ds->e2_hist[(nn - kwin + threadIdx.x) % kHist];
     a = warp_sum(a);
     b = warp_sum(b);
     cc = warp_sum(cc);
@@ -440,13 +454,50 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
         s_c[w] = cc;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double dphi = 0.0, sp = 0.0, s2 = 0.0;
-    for (int i = 0; i < W; ++i) {
-        dphi += s_a[i];
-        sp += s_b[i];
-        s2 += s_c[i];
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0, z = 0.0;
+        for (int i = 0; i < W; ++i) {
+            x += s_a[i];
+            y += s_b[i];
+            z += s_c[i];
+        }
+        A.block_part[3 * blockIdx.x + 0] = x;
+        A.block_part[3 * blockIdx.x + 1] = y;
+        A.block_part[3 * blockIdx.x + 2] = z;
+        __threadfence();
+        const unsigned prev = atomicAdd(&ds->record_done, 1u);
+        s_last = prev == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the stop test's window of earlier energies:
+    // s_hist[t] = E_2 at iteration (nn - k) + t for t < k (nn, k as below)
+    const int nn = A.mode == 1 ? n + 1 : n;
+    const int kwin = nn < A.stop_k ? nn : A.stop_k;
+    if (A.mode == 1 && A.evolve)
+        for (int t = threadIdx.x; t < kwin; t += kRecordThreads) s_hist[t] = ds->e2_hist[(nn - kwin + t) % kHist];
+    if (w == 0) {
+        // block triples in block order (a fixed shuffle tree over lanes)
+        double x = 0.0, y = 0.0, z = 0.0;
+        if (lane < (int)gridDim.x) {
+            x = __ldcg(A.block_part + 3 * lane + 0);
+            y = __ldcg(A.block_part + 3 * lane + 1);
+            z = __ldcg(A.block_part + 3 * lane + 2);
+        }
+        x = warp_sum(x);
+        y = warp_sum(y);
+        z = warp_sum(z);
+        if (lane == 0) {
+            s_a[0] = x;
+            s_b[0] = y;
+            s_c[0] = z;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ds->record_done = 0u;
+    const double dphi = s_a[0], sp = s_b[0], s2 = s_c[0];
     if (A.mode == 2) {
         A.report[0] = sp;
         A.report[1] = s2;
@@ -549,8 +600,9 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     A.stop_k = c->cfg.stop_k;
     A.min_iters = c->cfg.min_iters;
     A.max_iters = c->cfg.max_iters;
-    A.report = c->part_e + 2 * c->n_echunks;  // two spare doubles after the partials
-    k_record<<<1, kRecordThreads, 0, c->stream>>>(A, c->ds);
+    A.report = c->part_e + 2 * c->n_echunks;          // two spare doubles after the partials
+    A.block_part = c->part_e + 2 * c->n_echunks + 2;  // then three per record block
+    k_record<<<kRecordBlocks, kRecordThreads, 0, c->stream>>>(A, c->ds);
     c->launches += 1;
     return cudaGetLastError();
 }

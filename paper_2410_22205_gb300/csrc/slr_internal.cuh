@@ -22,6 +22,7 @@ constexpr int kStepBlock = 256;      // threads per block of the SL step kernels
 constexpr int kStepTile = 128;       // band entries per warp ticket / look-back tile (4 per lane)
 constexpr int kEnergyBlock = 256;    // 8 warps; one warp per chunk of 32 candidate cells
 constexpr int kMaxR = 8;             // largest supported energy subcell count per axis
+constexpr int kMaxStopK = 1023;  // bound on the stop window k_max (staged in shared memory)
 constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: ~0.3 s with 64 ns sleeps
 
 // error bits written to DevState::error by device code
@@ -38,6 +39,7 @@ struct DevState {
     int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
     unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
     unsigned epoch;      // tags the step kernel's look-back words; advanced once per step
+    unsigned record_done;  // blocks of the record kernel done (reset by its last block)
     double Ep;           // E_p(φ^n) used by step n
     double e2_hist[kHist];
     double dphi_hist[kHist];
@@ -211,10 +213,18 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 template <typename T>
 struct WenoAxis {
     T th, q, rho;  // θ, θ(θ-1)/2, C_L/C_R
+    // C_L = (2-θ)/3, C_R = (1+θ)/3; set() divides with the fast reciprocal,
+    // set_exact() with a correctly rounded division (folded at compile time
+    // for a constant θ)
     __device__ __forceinline__ void set(T t) {
         th = t;
         q = T(0.5) * t * (t - T(1));
-        rho = (T(2) - t) / (T(1) + t);  // C_L = (2-θ)/3, C_R = (1+θ)/3
+        rho = fast_div(T(2) - t, T(1) + t);
+    }
+    __device__ __forceinline__ void set_exact(T t) {
+        th = t;
+        q = T(0.5) * t * (t - T(1));
+        rho = (T(2) - t) / (T(1) + t);
     }
 };
 
