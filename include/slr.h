@@ -47,8 +47,8 @@ typedef enum {
     SLR_E_INVALID = 1,  /* bad argument or configuration */
     SLR_E_NOMEM = 2,    /* the allocator returned NULL */
     SLR_E_CUDA = 3,     /* a CUDA runtime call failed */
-    SLR_E_TIMEOUT = 4,  /* a bounded device-side wait gave up */
-    SLR_E_STATE = 5,    /* call out of order */
+    SLR_E_TIMEOUT = 4,  /* reserved (no kernel of this library waits on another) */
+    SLR_E_STATE = 5,    /* call out of order, or a device-side consistency check failed */
     SLR_E_CAPACITY = 6  /* output buffer too small; the needed count is returned */
 } slr_status;
 
@@ -124,8 +124,8 @@ slr_status slr_step(slr_ctx* ctx, int n_steps, double energy_override);
 
 /* As slr_step, but only enqueues the iterations on the context's stream and
  * returns without waiting (no host synchronisation, no status read). Errors
- * raised by the device (SLR_E_TIMEOUT) are reported by the next synchronous
- * call. For overlapping host work or other jobs with the iterations. */
+ * raised by the device's own checks (SLR_E_STATE) are reported by the next
+ * synchronous call. For overlapping host work or other jobs with the iterations. */
 slr_status slr_step_async(slr_ctx* ctx, int n_steps, double energy_override);
 
 /* Iterate until the stopping criterion of §4 (eq. deltaEn: Δ_E < stop_tol

@@ -130,7 +130,8 @@ slr_status check_device_error(slr_ctx* c) {
     int err = 0;
     slr_status s = read_status(c, nullptr, &err, nullptr);
     if (s != SLR_OK) return s;
-    if (err & kErrLookback) return fail(c, SLR_E_TIMEOUT, "band compaction look-back wait timed out");
+    if (err & kErrBandOffset) return fail(c, SLR_E_STATE, "band-list offsets inconsistent with the band");
+    if (err) return fail(c, SLR_E_STATE, "a device-side check failed");
     return SLR_OK;
 }
 
@@ -141,17 +142,16 @@ slr_status size_band_buffers(slr_ctx* c, long long count) {
     release_t(c, c->band[0]);
     release_t(c, c->band[1]);
     release_t(c, c->part_dphi);
-    release_t(c, c->tile_status);
+    release_t(c, c->tile_off);
     c->band[0] = (int*)dev_alloc(c, sizeof(int) * cap);
     c->band[1] = (int*)dev_alloc(c, sizeof(int) * cap);
     long long tiles = (cap + kStepTile - 1) / kStepTile + 1;
     c->part_dphi = (double*)dev_alloc(c, sizeof(double) * tiles);
-    c->tile_status = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * tiles);
-    if (!c->band[0] || !c->band[1] || !c->part_dphi || !c->tile_status)
+    c->tile_off = (int*)dev_alloc(c, sizeof(int) * tiles);
+    if (!c->band[0] || !c->band[1] || !c->part_dphi || !c->tile_off)
         return fail(c, SLR_E_NOMEM, "allocation of the band buffers failed");
     c->band_cap = cap;
     c->n_tiles_cap = tiles;
-    CK(cudaMemsetAsync(c->tile_status, 0, sizeof(unsigned long long) * tiles, c->stream), "memset");
     return SLR_OK;
 }
 
@@ -521,7 +521,7 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
         bool all = true, err = false;
         for (int j = 0; j < n_jobs; ++j) {
             all = all && hstop[4 * j + 0];
-            err = err || (hstop[4 * j + 3] & kErrLookback);
+            err = err || hstop[4 * j + 3];
         }
         if (err) {
             cleanup();
@@ -605,7 +605,7 @@ slr_status slr_evolve(slr_ctx* c, int* iters_out, int* converged_out) {
         }
         slr_status s = read_status(c, &stop, &err, &n);
         if (s != SLR_OK) return s;
-        if (err & kErrLookback) return fail(c, SLR_E_TIMEOUT, "band compaction look-back wait timed out");
+        if (err) return fail(c, SLR_E_STATE, "a device-side check failed (band-list offsets)");
         guard += kChunk;
         if (guard > c->cfg.max_iters + 2 * kChunk && !stop)
             return fail(c, SLR_E_STATE, "evolve: stop flag never set");
@@ -861,6 +861,9 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     CK(cudaMemcpyAsync(c->d, p, c->tsize * c->N, cudaMemcpyHostToDevice, c->stream), "import");
     p += c->tsize * c->N;
     CK(cudaMemcpyAsync(c->argmin, p, sizeof(int) * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    // an energy pass in report mode recomputes the band-tile offsets the
+    // next step reads (the history and E_p stay as imported)
+    CK(launch_energy(c, 0, c->cfg.p, 2, 0), "import energy pass");
     CK(cudaStreamSynchronize(c->stream), "import");
     c->have_d = true;
     c->have_u = true;
@@ -892,7 +895,7 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->ecells);
     release_t(c, c->part_dphi);
     release_t(c, c->part_e);
-    release_t(c, c->tile_status);
+    release_t(c, c->tile_off);
     release_t(c, c->front);
     release_t(c, c->ds);
     if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);

@@ -178,13 +178,34 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* ub0, const T* ub1,
                                                           const int* __restrict__ cells, long long ncells, int offset,
                                                           int* __restrict__ front, int* __restrict__ fcount,
+                                                          const int* L0, const int* L1, int* __restrict__ tile_cnt,
                                                           DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
     constexpr int PER = kEnergyCand / kEnergyThreads;
     static_assert(PER == 4, "four candidates per thread (one 16-byte load of the cell list)");
     __shared__ int s_warp[W + 1];
     if (check_stop && ds->stop) return;
-    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    const int sel = (ds->n + offset) & 1;
+    const T* __restrict__ u = sel ? ub1 : ub0;
+    if (tile_cnt) {
+        // band mode: members (|φ| < γ, the step kernel's test) of each tile
+        // of kStepTile entries of the band list the next step reads
+        const int nb = ds->band_count[sel];
+        const int* __restrict__ Lb = sel ? L1 : L0;
+        const int ntb = (nb + kStepTile - 1) / kStepTile;
+        const int lane = threadIdx.x & 31;
+        const int nw = gridDim.x * W;
+        for (int t = blockIdx.x * W + (threadIdx.x >> 5); t < ntb; t += nw) {
+            int c = 0;
+#pragma unroll
+            for (int h = 0; h < kStepTile / 32; ++h) {
+                const int e = t * kStepTile + h * 32 + lane;
+                const bool in = e < nb && fabs(u[Lb[e]]) < P.gamma;
+                c += __popc(__ballot_sync(0xffffffffu, in));
+            }
+            if (lane == 0) tile_cnt[t] = c;
+        }
+    }
     int* slot = front + (long long)blockIdx.x * kEnergyCand;
     // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
     const long long e0 = (long long)blockIdx.x * kEnergyCand + PER * threadIdx.x;
@@ -395,10 +416,12 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
 //  mode 2 (report): sums of the energy pass into report[0..1] only
 // The slices depend on the sizes alone, so the result does not depend on
 // which block finishes last.
-constexpr int kRecordBlocks = 32;
+static_assert(kRecordBlocks <= 32, "the last record block combines one value per lane");
 constexpr int kRecordThreads = 256;
 
 struct RecordArgs {
+    int* tile_off;         // band mode: tile counts in, offsets within the slice out
+    int offset;            // 1 after a step (the band the next step reads has parity n+1), else 0
     const double* part_dphi;
     const double* part_e;
     double* block_part;    // 3 per record block
@@ -420,6 +443,7 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     constexpr int W = kRecordThreads / 32;
     __shared__ double s_a[W], s_b[W], s_c[W];
     __shared__ double s_hist[kMaxStopK + 1];
+    __shared__ int s_scan[W];
     __shared__ int s_last;
     if (A.mode == 1 && ds->stop) return;
     const int n = ds->n;
@@ -453,6 +477,38 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
         s_b[w] = b;
         s_c[w] = cc;
     }
+    if (A.tile_off) {
+        // exclusive scan of this block's slice of tile counts (in place);
+        // the slice total goes to band_base[block] for the last block
+        const int nb = ds->band_count[(n + A.offset) & 1];
+        const int ntb = (nb + kStepTile - 1) / kStepTile;
+        const int per = (ntb + (int)G - 1) / (int)G;
+        const int beg = (int)blockIdx.x * per, end = beg + per < ntb ? beg + per : ntb;
+        const int len = end > beg ? end - beg : 0;
+        const int q = (len + kRecordThreads - 1) / kRecordThreads;  // contiguous run per thread
+        const int rb = beg + (int)threadIdx.x * q, re = rb + q < end ? rb + q : end;
+        int sum = 0;
+        for (int i = rb; i < re; ++i) sum += A.tile_off[i];
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_scan[w] = incl;
+        __syncthreads();
+        int run = incl - sum;
+        for (int i = 0; i < w; ++i) run += s_scan[i];
+        for (int i = rb; i < re; ++i) {
+            const int c = A.tile_off[i];
+            A.tile_off[i] = run;
+            run += c;
+        }
+        if (threadIdx.x == kRecordThreads - 1) {
+            ds->band_base[blockIdx.x] = run;  // slice total
+            __threadfence();
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double x = 0.0, y = 0.0, z = 0.0;
@@ -477,6 +533,18 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     const int kwin = nn < A.stop_k ? nn : A.stop_k;
     if (A.mode == 1 && A.evolve)
         for (int t = threadIdx.x; t < kwin; t += kRecordThreads) s_hist[t] = ds->e2_hist[(nn - kwin + t) % kHist];
+    if (A.tile_off && w == 1) {
+        // slice totals -> exclusive slice bases; their sum is the next band size
+        int tot = lane < (int)gridDim.x ? __ldcg(ds->band_base + lane) : 0;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < (int)gridDim.x) ds->band_base[lane] = incl - tot;
+        if (lane == 31) ds->band_next = incl;
+    }
     if (w == 0) {
         // block triples in block order (a fixed shuffle tree over lanes)
         double x = 0.0, y = 0.0, z = 0.0;
@@ -513,7 +581,6 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     ds->Ep = A.p_kind == 2 ? E2 : (A.p_kind == 1 ? 1.0 : pow(sp, 1.0 / A.p));
     if (A.mode == 1) {
         ds->ticket = 0u;
-        ds->epoch = ds->epoch + 1u;
         if (A.evolve) {
             // §4 eq. deltaEn with k = min(n, k_max) for both running means:
             // en over iterations nn-k+1..nn, em over nn-k..nn-1, summed in
@@ -545,7 +612,8 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
     int* fcount = (int*)(c->front + (size_t)blocks * kEnergyCand);
     k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
-                                                               offset, c->front, fcount, c->ds, check_stop);
+                                                               offset, c->front, fcount, c->band[0], c->band[1],
+                                                               c->cfg.band ? c->tile_off : nullptr, c->ds, check_stop);
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
@@ -600,6 +668,8 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     A.stop_k = c->cfg.stop_k;
     A.min_iters = c->cfg.min_iters;
     A.max_iters = c->cfg.max_iters;
+    A.tile_off = c->cfg.band ? c->tile_off : nullptr;
+    A.offset = record_mode == 1 ? 1 : 0;
     A.report = c->part_e + 2 * c->n_echunks;          // two spare doubles after the partials
     A.block_part = c->part_e + 2 * c->n_echunks + 2;  // then three per record block
     k_record<<<kRecordBlocks, kRecordThreads, 0, c->stream>>>(A, c->ds);

@@ -19,14 +19,11 @@ namespace slr {
 // ---------------------------------------------------------------------------
 constexpr int kHist = 4096;          // ring size of the per-iteration history
 constexpr int kStepBlock = 256;      // threads per block of the SL step kernels
-constexpr int kStepTile = 128;       // band entries per warp ticket / look-back tile (4 per lane)
-constexpr int kEnergyBlock = 256;    // 8 warps; one warp per chunk of 32 candidate cells
+constexpr int kStepTile = 128;       // band entries per warp ticket (4 per lane)
 constexpr int kMaxR = 8;             // largest supported energy subcell count per axis
-constexpr int kMaxStopK = 1023;  // bound on the stop window k_max (staged in shared memory)
-constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: ~0.3 s with 64 ns sleeps
-
-// error bits written to DevState::error by device code
-constexpr int kErrLookback = 1;      // a look-back wait gave up
+constexpr int kRecordBlocks = 32;    // blocks of the record kernel (slices of the tile counts)
+constexpr int kMaxStopK = 1023;      // bound on the stop window k_max (staged in shared memory)
+constexpr int kErrBandOffset = 1;    // DevState::error: a band-list write fell outside the list
 
 // ---------------------------------------------------------------------------
 // device-resident state of one job (one allocation)
@@ -35,11 +32,12 @@ struct DevState {
     int n;               // iterations completed since init
     int stop;            // nonzero: step kernels return at entry
     int converged;       // the Δ_E test stopped the loop
-    int error;           // kErr* bits
+    int error;           // kErr* bits set by device code
     int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
     unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
-    unsigned epoch;      // tags the step kernel's look-back words; advanced once per step
     unsigned record_done;  // blocks of the record kernel done (reset by its last block)
+    int band_next;       // size of the band the next step writes (sum of the tile counts)
+    int band_base[kRecordBlocks];  // exclusive prefix of the tile counts per record-block slice
     double Ep;           // E_p(φ^n) used by step n
     double e2_hist[kHist];
     double dphi_hist[kHist];
@@ -101,7 +99,7 @@ struct slr_ctx {
     double* part_e = nullptr;      // two per energy block, plus a two-value report slot
     long long n_echunks = 0;       // candidate chunks of 32 cells (sizes part_e)
     int* front = nullptr;          // per-block slots of front cells (1024 each) followed by the slot counts
-    unsigned long long* tile_status = nullptr;  // look-back words of the step kernel
+    int* tile_off = nullptr;       // per 128-entry tile of the step's input band: count, then offset in its slice
     slr::DevState* ds = nullptr;
     int* host_pinned_flags = nullptr;  // pinned host words for status readback
 
@@ -467,76 +465,6 @@ __device__ __forceinline__ double block_sum(double v, double* smem, bool warp_do
         for (int w = 0; w < BLOCK / 32; ++w) r += smem[w];
     __syncthreads();
     return r;
-}
-
-// ---------------------------------------------------------------------------
-// look-back status words: bits 0..31 value, 32..33 flag (1 aggregate,
-// 2 inclusive prefix), 34..63 epoch (one epoch per step launch)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, unsigned value) {
-    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)flag << 32) |
-           (unsigned long long)value;
-}
-
-// A status word carries its whole message (epoch, flag, count) in one
-// 64-bit access, and no reader depends on other memory written by the
-// publisher, so relaxed GPU-scope accesses suffice (no fences).
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Warp-parallel look-back of tile t (t > 0), run by all 32 lanes of one
-// warp: lane l inspects predecessor j - l. The walk stops at the nearest
-// predecessor that has published its inclusive prefix; aggregates in between
-// are summed. Every wait is bounded: after kSpinLimit polls the error bit is
-// set and the partial prefix returned; a partial prefix never exceeds the true
-// one, so the writes it leads to stay inside the output list.
-static __device__ unsigned lookback_warp(const unsigned long long* status, int t, unsigned epoch, int* err) {
-    const int lane = threadIdx.x & 31;
-    const unsigned ep = epoch & 0x3FFFFFFFu;
-    unsigned excl = 0;
-    int j = t - 1;
-    long long spins = 0;
-    while (j >= 0) {
-        const int idx = j - lane;
-        bool valid = true, incl = true;
-        unsigned val = 0;
-        if (idx >= 0) {
-            const unsigned long long w = ld_acquire_u64(status + idx);
-            const unsigned fl = (unsigned)(w >> 32) & 3u;
-            valid = ((unsigned)(w >> 34) == ep) && fl != 0u;
-            incl = valid && fl == 2u;
-            val = (unsigned)(w & 0xffffffffull);
-        }
-        const unsigned V = __ballot_sync(0xffffffffu, valid);
-        const unsigned I = __ballot_sync(0xffffffffu, incl);
-        if (I) {
-            const int f = __ffs(I) - 1;
-            const unsigned need = f == 31 ? 0xffffffffu : ((1u << (f + 1)) - 1u);
-            if ((V & need) == need) {
-                excl += warp_sum(lane <= f ? val : 0u);
-                excl = __shfl_sync(0xffffffffu, excl, 0);
-                return excl;
-            }
-        } else if (V == 0xffffffffu) {
-            excl += warp_sum(val);
-            excl = __shfl_sync(0xffffffffu, excl, 0);
-            j -= 32;
-            continue;
-        }
-        if (++spins > kSpinLimit) {
-            if (lane == 0) atomicOr(err, kErrLookback);
-            return __shfl_sync(0xffffffffu, excl, 0);
-        }
-        __nanosleep(32);
-    }
-    return __shfl_sync(0xffffffffu, excl, 0);
 }
 
 #endif  // __CUDACC__

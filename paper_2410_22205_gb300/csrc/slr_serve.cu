@@ -187,8 +187,8 @@ void slr_server::iter_loop() {
                 if (q == cudaSuccess) {
                     j->outstanding = false;
                     progressed = true;
-                    if (j->status[3] & slr::kErrLookback) {
-                        j->error = "band compaction look-back wait timed out";
+                    if (j->status[3]) {
+                        j->error = "a device-side check failed (band-list offsets)";
                         failed = true;
                     } else if (j->status[1]) {
                         done = true;

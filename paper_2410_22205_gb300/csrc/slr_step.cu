@@ -29,17 +29,18 @@ __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i
 
 // fused band rebuild + SL update + cut (band mode). Work is handed out per
 // warp: a ticket is a tile of kStepTile consecutive entries of L^{n-1} (four
-// per lane); the warp ballots band membership, publishes its count, resolves
-// its output offset by a warp-parallel look-back, writes its part of G̃^n, and
-// only then runs the SL arithmetic. No block-wide barrier inside the loop.
+// per lane). The count of band members of every tile and their prefix were
+// computed after the previous step (front-cell kernel and record kernel), so
+// a tile knows its output offset at once: it ballots band membership, writes
+// its part of G̃^n, and runs the SL arithmetic. No warp waits on another.
 template <typename T, int DIM, int INTERP>
 __global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 4) : (sizeof(T) == 8 ? 3 : 4))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
-                                                          int* L0, int* L1, unsigned long long* status,
-                                                          double* part_dphi, DevState* ds, double ep_override) {
+                                                          int* L0, int* L1, const int* __restrict__ tile_off,
+                                                          int band_cap, double* part_dphi, DevState* ds,
+                                                          double ep_override) {
     if (ds->stop) return;
     const int lane = threadIdx.x & 31;
     const int n = ds->n;
-    const unsigned epoch = ds->epoch;
     const int cnt_in = ds->band_count[n & 1];
     const T* __restrict__ uin = (n & 1) ? ub1 : ub0;
     T* __restrict__ uout = (n & 1) ? ub0 : ub1;
@@ -47,10 +48,9 @@ __global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2
     int* __restrict__ Lout = (n & 1) ? L0 : L1;
     const T Ep = ep_override >= 0.0 ? (T)ep_override : (T)ds->Ep;
     const int ntiles = (cnt_in + kStepTile - 1) / kStepTile;
-    if (ntiles == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ds->band_count[(n + 1) & 1] = 0;
-        return;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ds->band_count[(n + 1) & 1] = ntiles ? ds->band_next : 0;
+    if (ntiles == 0) return;
+    const int per = (ntiles + kRecordBlocks - 1) / kRecordBlocks;  // tiles per record-block slice
     const unsigned lt = (1u << lane) - 1u;
     for (;;) {
         int t = 0;
@@ -62,7 +62,6 @@ __global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2
         T v[H];
         bool inb[H], valid[H];
         unsigned m[H];
-        unsigned total = 0;
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             const int e = t * kStepTile + h * 32 + lane;
@@ -71,20 +70,18 @@ __global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2
             v[h] = valid[h] ? uin[idx[h]] : T(0);
             inb[h] = valid[h] && (fabs(v[h]) < P.gamma);
             m[h] = __ballot_sync(0xffffffffu, inb[h]);
-            total += (unsigned)__popc(m[h]);
         }
-        if (lane == 0) st_release_u64(status + t, pack_status(epoch, t == 0 ? 2u : 1u, total));
-        unsigned excl = 0;
-        if (t > 0) {
-            excl = lookback_warp(status, t, epoch, &ds->error);
-            if (lane == 0) st_release_u64(status + t, pack_status(epoch, 2u, excl + total));
-        }
-        if (lane == 0 && t == ntiles - 1) ds->band_count[(n + 1) & 1] = (int)(excl + total);
         {
-            unsigned run = excl;
+            unsigned run = (unsigned)(ds->band_base[t / per] + tile_off[t]);
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-                if (inb[h]) Lout[run + __popc(m[h] & lt)] = idx[h];
+                const unsigned pos = run + __popc(m[h] & lt);
+                if (inb[h]) {
+                    if (pos < (unsigned)band_cap)
+                        Lout[pos] = idx[h];
+                    else
+                        atomicOr(&ds->error, kErrBandOffset);  // offsets not prepared for this band
+                }
                 run += (unsigned)__popc(m[h]);
             }
         }
@@ -290,7 +287,8 @@ static cudaError_t step_t(slr_ctx* c, double ov) {
         if (nb > grid_blocks(c, 8)) nb = grid_blocks(c, 8);
         if (nb < 1) nb = 1;
         k_step_band<T, DIM, INTERP><<<(int)nb, kStepBlock, 0, c->stream>>>(
-            P, u0, u1, (const T*)c->d, c->band[0], c->band[1], c->tile_status, c->part_dphi, c->ds, ov);
+            P, u0, u1, (const T*)c->d, c->band[0], c->band[1], c->tile_off, (int)c->band_cap, c->part_dphi, c->ds,
+            ov);
     } else {
         long long nb = full_step_blocks(c);
         k_step_full<T, DIM, INTERP><<<(int)nb, kStepBlock, 0, c->stream>>>(P, u0, u1, (const T*)c->d, c->N,
