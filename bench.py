@@ -234,8 +234,9 @@ def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha):
 
 
 def measure_steps(rec, steps, warmup, flush_buf, torch):
-    """Warm-up, then `steps` timed iterations; returns per-step ms, per-kernel
-    ms (3 per step) and the band sizes of the timed steps."""
+    """Warm-up, then `steps` timed iterations; returns per-step ms, per-phase
+    ms (step kernel, front-cell + energy kernels, record kernel) and the band
+    sizes of the timed steps."""
     st = rec.stream
     for _ in range(warmup):
         rec.step_async(1)
@@ -272,6 +273,7 @@ def run_gpu(args):
         peaks.update({k: v for k, v in json.load(open(pk)).items() if isinstance(v, (int, float))})
     t_setup = time.time()
     grid, cloud = workload(args)
+    cloud_s = time.time() - t_setup
     n = args.n
     rec = slr.Reconstruction(dim=3, n=n, precision=32, interp=1, band=1, **cfg_kw())
     st = rec.stream
@@ -301,7 +303,7 @@ def run_gpu(args):
     value, tot_units, tmax = aggregate(units, secs, dist)
     ms_per_step = tmax * 1e3 / args.steps
     kern = np.array(kern_ms)
-    names = ["k_step_band<float,3,WENO>", "k_energy<float,3,WENO,R=5>", "k_record"]
+    names = ["k_step_band<float,3,WENO>", "k_front + k_energy<float,3,WENO,R=5>", "k_record"]
     kmean = kern.mean(axis=0)
     dom = int(np.argmax(kmean))
     mean_band = float(np.mean(bands))
@@ -315,6 +317,8 @@ def run_gpu(args):
     roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
     iter_lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
     rec.close()
+    phase_s = {"cloud_generation": cloud_s, "setup_and_timed_steps": time.time() - t_setup - cloud_s}
+    t_ph = time.time()
 
     variants = {}
     if not args.no_variants and dist.rank == 0:
@@ -331,21 +335,30 @@ def run_gpu(args):
             variants[label] = {"value": float(np.sum(bd)) / (float(np.sum(sm)) / 1e3), "ms_per_step": float(np.mean(sm)),
                                "nodes_per_step": float(np.mean(bd)), "kernels_ms": [float(x) for x in np.mean(km, 0)]}
             r2.close()
+    phase_s["variants"] = time.time() - t_ph
+    t_ph = time.time()
 
     e2e = None
     solve_lat = None
     if args.e2e_jobs > 0:
         e2e, solve_lat = run_e2e(args, cloud, slr, torch)
+    phase_s["e2e"] = time.time() - t_ph
+    t_ph = time.time()
 
     batched = serving = None
     if dist.rank == 0 and args.batch_jobs > 0:
         batched = run_batched(args, slr, torch)
+    phase_s["batched"] = time.time() - t_ph
+    t_ph = time.time()
     if dist.rank == 0 and args.serve_seconds > 0:
         serving = run_serving(args, slr, torch)
+    phase_s["serving"] = time.time() - t_ph
+    t_ph = time.time()
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(grid, cloud, budget_s=20.0)
+    phase_s["cpu_baseline"] = time.time() - t_ph
 
     if dist.rank == 0:
         line = {
@@ -359,7 +372,7 @@ def run_gpu(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "latency": {"iteration": iter_lat, "solve": solve_lat},
             "variants": variants, "batched": batched, "serving": serving, "gpu_launches": int(launches), "clocks": clk,
-            "setup_s": time.time() - t_setup,
+            "setup_s": time.time() - t_setup, "phase_s": phase_s,
         }
         print(json.dumps(line), flush=True)
     dist.close()

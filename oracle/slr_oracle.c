@@ -106,16 +106,23 @@ void or_distance(const or_params* g, const double* pts, long long npts,
 }
 
 /* k-d tree search with the same decisions as the scan above. Median split
- * on the widest axis, leaves of at most 8 points. A subtree on the far side
- * of a split plane is skipped only when fl(diff)^2 > best: every point there
- * has |x_a - q_a| >= |x_a - split| on that axis, rounding is monotone and the
- * squared distance is a sum of non-negative terms, so its computed value is
- * at least fl(diff)^2 and it can neither win nor tie. */
+ * on the widest axis, leaves of at most 8 points; every tree node keeps the
+ * bounding box [bmin, bmax] of its points. A subtree is skipped only when
+ *   fl(..fl(o_0^2 + o_1^2) + ..) > best,  o_a = fl(bmin_a - q_a) if q_a < bmin_a,
+ *                                          fl(q_a - bmax_a) if q_a > bmax_a, else 0,
+ * summed in the same order as a point's squared distance: for a point x of
+ * the box, |fl(q_a - x_a)| >= o_a (x_a lies beyond the box face, rounding is
+ * monotone and symmetric), squares and sums of non-negative terms keep the
+ * order, so each point there has a computed squared distance at least that
+ * bound and can neither win nor tie. The nearer child is visited first; the
+ * result (smallest squared distance, then lowest index) does not depend on
+ * the visiting order. */
 typedef struct {
     int axis;          /* -1 for a leaf */
     double split;
     int left, right;
-    long long lo, hi;  /* leaf range in the permutation */
+    long long lo, hi;  /* range in the permutation */
+    double bmin[3], bmax[3];
 } kd_node;
 
 typedef struct {
@@ -159,9 +166,12 @@ static int kd_build(kd_tree* t, long long lo, long long hi) {
     nd->lo = lo;
     nd->hi = hi;
     nd->axis = -1;
-    if (hi - lo <= 8) return id;
     int best_a = 0;
     double best_w = -1.0;
+    for (int a = 0; a < 3; ++a) {
+        nd->bmin[a] = 0.0;
+        nd->bmax[a] = 0.0;
+    }
     for (int a = 0; a < t->dim; ++a) {
         double mn = INFINITY, mx = -INFINITY;
         for (long long i = lo; i < hi; ++i) {
@@ -169,11 +179,14 @@ static int kd_build(kd_tree* t, long long lo, long long hi) {
             if (v < mn) mn = v;
             if (v > mx) mx = v;
         }
+        nd->bmin[a] = mn;
+        nd->bmax[a] = mx;
         if (mx - mn > best_w) {
             best_w = mx - mn;
             best_a = a;
         }
     }
+    if (hi - lo <= 8) return id;
     long long mid = lo + (hi - lo) / 2;
     kd_select(t, lo, hi, mid, best_a);
     double split = kd_coord(t, mid, best_a);
@@ -185,6 +198,19 @@ static int kd_build(kd_tree* t, long long lo, long long hi) {
     nd->left = left;
     nd->right = right;
     return id;
+}
+
+static double kd_box_bound(const kd_tree* t, const kd_node* nd, const double x[3]) {
+    double s = 0.0;
+    for (int a = 0; a < t->dim; ++a) {
+        double o = 0.0;
+        if (x[a] < nd->bmin[a])
+            o = nd->bmin[a] - x[a];
+        else if (x[a] > nd->bmax[a])
+            o = x[a] - nd->bmax[a];
+        s = s + o * o;
+    }
+    return s;
 }
 
 static void kd_query(const kd_tree* t, int id, const double x[3], double* best, long long* arg) {
@@ -205,11 +231,12 @@ static void kd_query(const kd_tree* t, int id, const double x[3], double* best, 
         }
         return;
     }
-    double diff = x[nd->axis] - nd->split;
-    int near = diff <= 0.0 ? nd->left : nd->right;
-    int far = diff <= 0.0 ? nd->right : nd->left;
-    kd_query(t, near, x, best, arg);
-    if (!(diff * diff > *best)) kd_query(t, far, x, best, arg);
+    const double bl = kd_box_bound(t, &t->nodes[nd->left], x);
+    const double br = kd_box_bound(t, &t->nodes[nd->right], x);
+    const int first = bl <= br ? nd->left : nd->right, second = bl <= br ? nd->right : nd->left;
+    const double b1 = bl <= br ? bl : br, b2 = bl <= br ? br : bl;
+    if (!(b1 > *best)) kd_query(t, first, x, best, arg);
+    if (!(b2 > *best)) kd_query(t, second, x, best, arg);
 }
 
 void or_distance_kd(const or_params* g, const double* pts, long long npts,

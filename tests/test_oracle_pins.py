@@ -96,6 +96,24 @@ def test_kdtree_distance_identical_to_brute_force():
     assert np.array_equal(d1, d2) and np.array_equal(a1, a2)
 
 
+def test_kdtree_box_pruning_on_surface_clouds_far_queries():
+    """Surface clouds (a superquadric union, a sphere) queried from every node
+    of a grid that extends well outside them: most queries are far from all
+    points, where the k-d tree prunes by the boxes of its nodes. d and argmin
+    stay bit-identical to the scan; exact ties from a cloud symmetric under
+    x -> -x and duplicated points included."""
+    for dim, n, pts in (
+        (3, 21, synth.superquadric_union_cloud(3000, 3, 7)),
+        (3, 17, np.concatenate([synth.sphere_cloud(1500, 0.3, 0.0, 9)] * 2)),
+        (2, 41, synth.circle_noisy(900, 0.2, 0.01, 3)),
+    ):
+        pts = np.concatenate([pts, pts * np.array([-1.0] + [1.0] * (dim - 1))])  # mirror: exact ties at x = 0
+        P = _grid_params(dim, n, lo=-2.0, hi=2.0)
+        d1, a1 = O.distance(P, pts)
+        d2, a2 = O.distance(P, pts, method="kd")
+        assert np.array_equal(d1, d2) and np.array_equal(a1, a2)
+
+
 # ---------------------------------------------------------------- gradient
 
 def test_gradient_centred_exact_on_quadratics_and_onesided_on_linear():
