@@ -285,10 +285,12 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
     const int nf = fcount[blockIdx.x];
     // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
     auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
+    // WENO constants at θ_m (storage-type arithmetic; folded at compile
+    // time where m is a constant)
     auto WA = [&](int m) -> WenoAxis<T> {
         if (RC > 0) {
             WenoAxis<T> w;
-            w.set_exact((T)((m + 0.5) / RD));
+            w.set_exact(TH(m));
             return w;
         }
         return s_wa[m];
