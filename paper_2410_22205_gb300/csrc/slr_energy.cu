@@ -169,16 +169,19 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
 //        trilinear interpolant (Q1); d by Q1, linear along each x-line. A
 //        subcell counts when |φ(x')| < (√3/2)Δx' and adds |d(x')|^p Δx'^2.
 //   2-D: one thread per front cell (segments, FP64).
+//        In band mode its warps first count, per tile of kStepTile entries of
+//        the band list the next step reads, the members |φ| < γ (the step
+//        kernel's own test); the record kernel turns the counts into offsets.
 // No ordering across blocks is needed, and the block scheduler evens out the
-// uneven slot sizes. Sums per work item in the storage type; per-thread and
-// per-block sums in FP64, in a fixed order (one partial pair per block).
+// uneven slot sizes. 3-D sums per work item, per thread and per warp in the
+// storage type, then per block in FP64 (2-D: FP64 throughout), in a fixed
+// order (one partial pair per block).
 constexpr int kEnergyCand = 1024;  // candidate cells per slot (4 per thread)
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* ub0, const T* ub1,
                                                           const int* __restrict__ cells, long long ncells, int offset,
                                                           int* __restrict__ front, int* __restrict__ fcount,
-                                                          const int* L0, const int* L1, int* __restrict__ tile_cnt,
                                                           DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
     constexpr int PER = kEnergyCand / kEnergyThreads;
@@ -187,25 +190,6 @@ __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* 
     if (check_stop && ds->stop) return;
     const int sel = (ds->n + offset) & 1;
     const T* __restrict__ u = sel ? ub1 : ub0;
-    if (tile_cnt) {
-        // band mode: members (|φ| < γ, the step kernel's test) of each tile
-        // of kStepTile entries of the band list the next step reads
-        const int nb = ds->band_count[sel];
-        const int* __restrict__ Lb = sel ? L1 : L0;
-        const int ntb = (nb + kStepTile - 1) / kStepTile;
-        const int lane = threadIdx.x & 31;
-        const int nw = gridDim.x * W;
-        for (int t = blockIdx.x * W + (threadIdx.x >> 5); t < ntb; t += nw) {
-            int c = 0;
-#pragma unroll
-            for (int h = 0; h < kStepTile / 32; ++h) {
-                const int e = t * kStepTile + h * 32 + lane;
-                const bool in = e < nb && fabs(u[Lb[e]]) < P.gamma;
-                c += __popc(__ballot_sync(0xffffffffu, in));
-            }
-            if (lane == 0) tile_cnt[t] = c;
-        }
-    }
     int* slot = front + (long long)blockIdx.x * kEnergyCand;
     // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
     const long long e0 = (long long)blockIdx.x * kEnergyCand + PER * threadIdx.x;
@@ -266,7 +250,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
                                                            const T* __restrict__ d, const int* __restrict__ front,
                                                            const int* __restrict__ fcount, int R_run, double h,
                                                            double p, int p_kind, T thr, T hp2, T pT, int offset,
-                                                           double* part, DevState* ds, int check_stop) {
+                                                           double* part, const int* L0, const int* L1,
+                                                           int* __restrict__ tile_cnt, DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
     const int R = RC > 0 ? RC : R_run;
     constexpr double RD = RC > 0 ? (double)RC : 1.0;
@@ -274,7 +259,27 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
     __shared__ WenoAxis<T> s_wa[kMaxR];
     __shared__ double s_a[W], s_b[W];
     if (check_stop && ds->stop) return;
-    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    const int sel = (ds->n + offset) & 1;
+    const T* __restrict__ u = sel ? ub1 : ub0;
+    if (tile_cnt) {
+        // band mode: members (|φ| < γ, the step kernel's test) of each tile
+        // of kStepTile entries of the band list the next step reads
+        const int nb = ds->band_count[sel];
+        const int* __restrict__ Lb = sel ? L1 : L0;
+        const int ntb = (nb + kStepTile - 1) / kStepTile;
+        const int lane = threadIdx.x & 31;
+        const int nw = gridDim.x * W;
+        for (int t = blockIdx.x * W + (threadIdx.x >> 5); t < ntb; t += nw) {
+            int c = 0;
+#pragma unroll
+            for (int h = 0; h < kStepTile / 32; ++h) {
+                const int e = t * kStepTile + h * 32 + lane;
+                const bool in = e < nb && fabs(u[Lb[e]]) < P.gamma;
+                c += __popc(__ballot_sync(0xffffffffu, in));
+            }
+            if (lane == 0) tile_cnt[t] = c;
+        }
+    }
     if (RC == 0 && threadIdx.x < R) {
         T t = ((T)threadIdx.x + (T)0.5) / (T)R;  // subcell centre θ_m = (m + 1/2)/R
         s_th[threadIdx.x] = t;
@@ -386,11 +391,16 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
             tp += cp;
             t2 += c2;
         }
+        // warp sums in the storage type, per-warp sums widened
+        tp = warp_sum(tp);
+        t2 = warp_sum(t2);
         ap = (double)tp;
         a2 = (double)t2;
     }
-    ap = warp_sum(ap);
-    a2 = warp_sum(a2);
+    if (DIM == 2) {
+        ap = warp_sum(ap);
+        a2 = warp_sum(a2);
+    }
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (lane == 0) {
         s_a[wib] = ap;
@@ -614,16 +624,16 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
     int* fcount = (int*)(c->front + (size_t)blocks * kEnergyCand);
     k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
-                                                               offset, c->front, fcount, c->band[0], c->band[1],
-                                                               c->cfg.band ? c->tile_off : nullptr, c->ds, check_stop);
+                                                               offset, c->front, fcount, c->ds, check_stop);
+    int* tile_cnt = c->cfg.band ? c->tile_off : nullptr;
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
-            p_kind, thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
+            p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds, check_stop);
     else
         k_energy<T, DIM, INTERP, 0><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
-            p_kind, thr, hp2, pT, offset, c->part_e, c->ds, check_stop);
+            p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds, check_stop);
     c->launches += 2;  // front cells, then energy
     return cudaGetLastError();
 }
