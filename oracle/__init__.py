@@ -99,6 +99,10 @@ def lib():
                 "or_stop": (C.c_int, [_dp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _dp]),
                 "or_evolve": (C.c_int, [_P, _dp, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, _dp, _dp,
                                         _ip]),
+                "or_evolve_reinit": (C.c_int, [_P, _dp, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                               C.c_int, C.c_double, _dp, _dp, _ip]),
+                "or_reinit": (C.c_longlong, [_P, _dp, _dp, C.c_int, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
+                "or_reinit_sweeps": (C.c_int, [_P]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
                 "or_set_threads": (C.c_int, [C.c_int]),
@@ -292,15 +296,34 @@ def stop(E2, n, kmax=10, tol=1e-4, min_iters=10, max_iters=100):
     return bool(s), delta.value
 
 
-def evolve(P, u0, d, R=5, tol=1e-4, kmax=10, min_iters=10, max_iters=100):
+def evolve(P, u0, d, R=5, tol=1e-4, kmax=10, min_iters=10, max_iters=100, reinit=False, sweeps=0, dtau=0.0):
+    """Algorithm 1 loop (§4 stop rule); with reinit, step 4d (§3.7) after every SL step."""
     u = np.array(u0, dtype=np.float64, copy=True)
     d, dp = _d(d)
     E2 = np.zeros(max_iters + 1)
     dphi = np.zeros(max(max_iters, 1))
     conv = C.c_int(0)
-    n = lib().or_evolve(C.byref(P), u.ctypes.data_as(_dp), dp, int(R), float(tol), int(kmax), int(min_iters),
-                        int(max_iters), E2.ctypes.data_as(_dp), dphi.ctypes.data_as(_dp), C.byref(conv))
+    n = lib().or_evolve_reinit(C.byref(P), u.ctypes.data_as(_dp), dp, int(R), float(tol), int(kmax), int(min_iters),
+                               int(max_iters), int(bool(reinit)), int(sweeps), float(dtau), E2.ctypes.data_as(_dp),
+                               dphi.ctypes.data_as(_dp), C.byref(conv))
     return dict(u=u, iters=n, converged=bool(conv.value), E2=E2[: n + 1], dphi=dphi[:n])
+
+
+def reinit(P, phi_band, phi_tilde, sweeps=0, dtau=0.0):
+    """§3.7 reinitialisation of phi_tilde on the band {|phi_band| < γ} and its
+    face neighbours, then eq. cut. Returns (out, flags, |Ḡ|); flags bit 0 =
+    node in Ḡ, bit 1 = interface node (explicit step)."""
+    pb, pbp = _d(phi_band)
+    pt, ptp = _d(phi_tilde)
+    out = np.empty_like(pt)
+    flags = np.zeros(pt.shape[0], dtype=np.uint8)
+    m = lib().or_reinit(C.byref(P), pbp, ptp, int(sweeps), float(dtau), out.ctypes.data_as(_dp),
+                        flags.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    return out, flags, int(m)
+
+
+def reinit_sweeps(P):
+    return int(lib().or_reinit_sweeps(C.byref(P)))
 
 
 def extract(P, u, width):

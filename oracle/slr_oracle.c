@@ -758,10 +758,163 @@ int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int ma
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* §3.7 reinitialisation (Algorithm 1 step 4d)                          */
+/* ------------------------------------------------------------------ */
+
+/* The paper runs the constrained reinitialisation of Hartmann, Meinke and
+ * Schröder (2008) on Ḡ = G̃ and its first neighbours: one explicit step sets
+ * the signed distance on the nodes next to the interface (a sign change of
+ * φ̃ to a face neighbour); then forward-Euler steps in pseudo-time τ of the
+ * first-order discretisation of eq. reinit, φ_τ + sign(φ̃)(|∇φ| - 1) = 0
+ * (Sussman, Smereka and Osher 1994), reinitialise the rest of Ḡ while the
+ * interface nodes stay fixed; then eq. cut. The paper gives no formulas for
+ * either part; the readings taken here:
+ *  - sign classes: φ < 0 and φ >= 0 (zero with the positive side, as in the
+ *    energy of §3.5); sign(φ̃) in eq. reinit is -1, 0, +1;
+ *  - explicit step on an interface node j, the subcell estimate of Russo
+ *    and Smereka (2000): D_j = φ̃_j / |g| with, per axis, g_a the largest of
+ *    |φ̃_{j+e} - φ̃_{j-e}|/(2h), |φ̃_{j+e} - φ̃_j|/h, |φ̃_j - φ̃_{j-e}|/h
+ *    (those that exist): exact for any plane, and the difference across the
+ *    interface, which the cut never clamps, enters it; φ̃_j if g = 0;
+ *  - first-order discretisation: Godunov's upwind Hamiltonian with the
+ *    one-sided differences a = (ψ_j - ψ_{j-e})/h, b = (ψ_{j+e} - ψ_j)/h per
+ *    axis (a missing neighbour outside the grid gives a difference of 0):
+ *    sign > 0: |∇ψ|^2 = Σ_a max(max(a,0)^2, min(b,0)^2),
+ *    sign < 0: |∇ψ|^2 = Σ_a max(min(a,0)^2, max(b,0)^2);
+ *  - Jacobi sweeps ψ^{m+1}_j = ψ^m_j - Δτ sign(φ̃_j)(|∇ψ^m|_j - 1) on
+ *    Ḡ minus the interface nodes and minus the nodes on the domain boundary
+ *    (no upwind data enters from outside the grid: they keep φ̃, which
+ *    keeps the scheme from drifting there), Δτ = h/2 (within h/sqrt(dim), the
+ *    stability limit of the scheme), for M = 4(γ/h + 1) sweeps: information
+ *    moves h/2 per sweep, so 2(γ/h + 1) sweeps reach across the band and its
+ *    first neighbours, and as many again bring the band to within about
+ *    10^-4 h of the steady state of eq. reinit ("until steady state");
+ *    nodes outside Ḡ keep their values;
+ *  - the band G̃ whose neighbours form Ḡ is the one the SL step used,
+ *    {j : |φ^n_j| < γ}, given here by phi_band.
+ * Returns |Ḡ|. out receives φ̃ outside Ḡ and the cut reinitialised values
+ * in Ḡ. flags_out (may be NULL): bit 0 node in Ḡ, bit 1 interface node. */
+static int sign_class(double v) { return v < 0.0 ? -1 : 1; }
+
+static double reinit_one_step(const or_params* g, const double* v, long long idx) {
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    long long c[3] = {idx % g->n[0], (idx / g->n[0]) % g->n[1], idx / (g->n[0] * g->n[1])};
+    double vj = v[idx], s = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+        int has_m = c[a] > 0, has_p = c[a] < g->n[a] - 1;
+        double ga = 0.0;
+        if (has_m) ga = fmax(ga, fabs(vj - v[idx - stride[a]]) / g->h);
+        if (has_p) ga = fmax(ga, fabs(v[idx + stride[a]] - vj) / g->h);
+        if (has_m && has_p) ga = fmax(ga, fabs(v[idx + stride[a]] - v[idx - stride[a]]) / (2.0 * g->h));
+        s = s + ga * ga;
+    }
+    if (!(s > 0.0)) return vj;
+    return vj / sqrt(s);
+}
+
+static int reinit_is_interface(const or_params* g, const double* v, long long idx) {
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    long long c[3] = {idx % g->n[0], (idx / g->n[0]) % g->n[1], idx / (g->n[0] * g->n[1])};
+    int cj = sign_class(v[idx]);
+    for (int a = 0; a < g->dim; ++a)
+        for (int side = -1; side <= 1; side += 2) {
+            long long q = c[a] + side;
+            if (q < 0 || q >= g->n[a]) continue;
+            if (sign_class(v[idx + side * stride[a]]) != cj) return 1;
+        }
+    return 0;
+}
+
+/* node idx is not on the domain boundary: all 2·dim face neighbours exist */
+static double godunov_norm(const or_params* g, const double* v, long long idx, int sgn) {
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    double vj = v[idx], s2 = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+        double am = (vj - v[idx - stride[a]]) / g->h;
+        double bp = (v[idx + stride[a]] - vj) / g->h;
+        double t1, t2;
+        if (sgn > 0) {
+            t1 = am > 0.0 ? am : 0.0;
+            t2 = bp < 0.0 ? bp : 0.0;
+        } else {
+            t1 = am < 0.0 ? am : 0.0;
+            t2 = bp > 0.0 ? bp : 0.0;
+        }
+        t1 = t1 * t1;
+        t2 = t2 * t2;
+        s2 = s2 + (t1 > t2 ? t1 : t2);
+    }
+    return sqrt(s2);
+}
+
+int or_reinit_sweeps(const or_params* g) { return 4 * ((int)floor(g->gamma / g->h + 0.5) + 1); }
+
+long long or_reinit(const or_params* g, const double* phi_band, const double* phi_tilde, int sweeps, double dtau,
+                    double* out, unsigned char* flags_out) {
+    long long N = or_num_nodes(g);
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    if (sweeps <= 0) sweeps = or_reinit_sweeps(g);
+    if (!(dtau > 0.0)) dtau = 0.5 * g->h;
+    unsigned char* fl = (unsigned char*)calloc((size_t)N, 1);
+    /* Ḡ: the band and its face neighbours */
+    for (long long i = 0; i < N; ++i) {
+        if (!or_in_band(g, phi_band[i])) continue;
+        fl[i] |= 1;
+        long long c[3] = {i % g->n[0], (i / g->n[0]) % g->n[1], i / (g->n[0] * g->n[1])};
+        for (int a = 0; a < g->dim; ++a) {
+            if (c[a] > 0) fl[i - stride[a]] |= 1;
+            if (c[a] < g->n[a] - 1) fl[i + stride[a]] |= 1;
+        }
+    }
+    long long m = 0;
+    for (long long i = 0; i < N; ++i) m += fl[i] & 1;
+    double* psi = (double*)malloc((size_t)N * sizeof(double));
+    double* nxt = (double*)malloc((size_t)N * sizeof(double));
+    memcpy(psi, phi_tilde, (size_t)N * sizeof(double));
+    /* explicit step on the interface nodes of Ḡ */
+    for (long long i = 0; i < N; ++i)
+        if ((fl[i] & 1) && reinit_is_interface(g, phi_tilde, i)) fl[i] |= 2;
+    for (long long i = 0; i < N; ++i)
+        if (fl[i] & 2) psi[i] = reinit_one_step(g, phi_tilde, i);
+    /* forward-Euler Jacobi sweeps on the rest of Ḡ */
+    for (int it = 0; it < sweeps; ++it) {
+        memcpy(nxt, psi, (size_t)N * sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < N; ++i) {
+            if ((fl[i] & 3) != 1) continue;
+            long long c[3] = {i % g->n[0], (i / g->n[0]) % g->n[1], i / (g->n[0] * g->n[1])};
+            int edge = 0;
+            for (int a = 0; a < g->dim; ++a) edge |= (c[a] == 0 || c[a] == g->n[a] - 1);
+            if (edge) continue;
+            double v = phi_tilde[i];
+            int sgn = v > 0.0 ? 1 : (v < 0.0 ? -1 : 0);
+            if (sgn == 0) continue;
+            nxt[i] = psi[i] - dtau * (double)sgn * (godunov_norm(g, psi, i, sgn) - 1.0);
+        }
+        double* t = psi;
+        psi = nxt;
+        nxt = t;
+    }
+    for (long long i = 0; i < N; ++i) out[i] = (fl[i] & 1) ? or_cut(g, psi[i]) : phi_tilde[i];
+    if (flags_out) memcpy(flags_out, fl, (size_t)N);
+    free(fl);
+    free(psi);
+    free(nxt);
+    return m;
+}
+
 int or_evolve(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
               int min_iters, int max_iters, double* E2_hist, double* dphi_hist, int* converged) {
+    return or_evolve_reinit(g, u, d, R, stop_tol, kmax, min_iters, max_iters, 0, 0, 0.0, E2_hist, dphi_hist, converged);
+}
+
+int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
+                     int min_iters, int max_iters, int reinit, int sweeps, double dtau, double* E2_hist,
+                     double* dphi_hist, int* converged) {
     long long N = or_num_nodes(g);
     double* next = (double*)malloc((size_t)N * sizeof(double));
+    double* re = reinit ? (double*)malloc((size_t)N * sizeof(double)) : NULL;
     double e[4];
     or_energy(g, u, d, 2.0, R, 0.0, e);
     E2_hist[0] = e[1];
@@ -774,7 +927,16 @@ int or_evolve(const or_params* g, double* u, const double* d, int R, double stop
             Ep = ep[1];
         }
         double dphi = or_sl_step(g, u, d, Ep, next, NULL);
-        memcpy(u, next, (size_t)N * sizeof(double));
+        if (reinit) {
+            /* Algorithm 1 step 4d; Δ_φ then measures the whole update */
+            or_reinit(g, u, next, sweeps, dtau, re, NULL);
+            double acc = 0.0;
+            for (long long i = 0; i < N; ++i) acc += fabs(re[i] - u[i]);
+            dphi = acc * pow(g->h, (double)g->dim);
+            memcpy(u, re, (size_t)N * sizeof(double));
+        } else {
+            memcpy(u, next, (size_t)N * sizeof(double));
+        }
         dphi_hist[n] = dphi;
         ++n;
         or_energy(g, u, d, 2.0, R, 0.0, e);
@@ -786,6 +948,7 @@ int or_evolve(const or_params* g, double* u, const double* d, int R, double stop
         }
     }
     free(next);
+    free(re);
     if (converged) *converged = conv;
     return n;
 }

@@ -15,9 +15,10 @@
  *
  * Parity pins (what fixes each function independently of this code) live in
  * tests/test_oracle_pins.py. Functions without an independent pin:
- *   or_evolve  -- parity unpinned against the paper (the paper's end-to-end
- *                 tables need reinitialisation, initial-data marking and the
- *                 scan datasets); it is checked only by its parts' pins.
+ *   or_evolve, or_evolve_reinit -- parity unpinned against the paper (its
+ *                 end-to-end tables need initial-data marking, the multi-run
+ *                 driver and the scan datasets); checked only by their parts'
+ *                 pins.
  */
 #ifndef SLR_ORACLE_H
 #define SLR_ORACLE_H
@@ -123,6 +124,20 @@ int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int ma
  * number of iterations; *converged is 1 when the Δ_E test stopped the loop. */
 int or_evolve(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
               int min_iters, int max_iters, double* E2_hist, double* dphi_hist, int* converged);
+
+/* §3.7 reinitialisation on Ḡ (the band {|phi_band| < γ} and its face
+ * neighbours) of phi_tilde, then eq. cut; see the readings in slr_oracle.c.
+ * sweeps <= 0: or_reinit_sweeps(g); dtau <= 0: h/2. out: every node.
+ * flags_out (may be NULL): bit 0 in Ḡ, bit 1 interface node. Returns |Ḡ|. */
+long long or_reinit(const or_params* g, const double* phi_band, const double* phi_tilde, int sweeps, double dtau,
+                    double* out, unsigned char* flags_out);
+int or_reinit_sweeps(const or_params* g);
+
+/* or_evolve with Algorithm 1 step 4d (reinit != 0): after each SL step and
+ * cut, or_reinit with the step's band; Δ_φ then covers the whole update. */
+int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
+                     int min_iters, int max_iters, int reinit, int sweeps, double dtau, double* E2_hist,
+                     double* dphi_hist, int* converged);
 
 /* nodes with |φ| < width, ascending index */
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out);

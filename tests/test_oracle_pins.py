@@ -518,3 +518,125 @@ def test_evolve_runs_and_moves_front_toward_cloud():
     r = O.evolve(P, u0, d, max_iters=30)
     assert 10 <= r["iters"] <= 30
     assert r["E2"][-1] < r["E2"][0]
+
+
+# ---------------------------------------------------------------- reinitialisation (§3.7)
+
+def _reinit_grid(dim, n, **kw):
+    P = _grid_params(dim, n, band=1, **kw)
+    X = O.node_coords(P)
+    return P, X
+
+
+def _dilate_face(mask, shape):
+    """Face-neighbour dilation without wrap-around (numpy, independent of the oracle)."""
+    m = mask.reshape(shape)
+    out = m.copy()
+    for ax in range(m.ndim):
+        sl_a = [slice(None)] * m.ndim
+        sl_b = [slice(None)] * m.ndim
+        sl_a[ax], sl_b[ax] = slice(1, None), slice(None, -1)
+        out[tuple(sl_a)] |= m[tuple(sl_b)]
+        out[tuple(sl_b)] |= m[tuple(sl_a)]
+    return out.reshape(-1)
+
+
+def _after_sl(P, sdf, scale):
+    """A state as the SL step leaves it: the band of φ^n = cut(SDF) holds
+    scale·SDF, every other node keeps ±γ (cut)."""
+    phi_n = O.cut(P, sdf)
+    band = np.abs(phi_n) < P.gamma
+    phi_t = np.where(band, O.cut(P, scale * sdf), phi_n)
+    return phi_n, phi_t
+
+
+@pytest.mark.parametrize("normal", [(1.0, 0.0, 0.0), (1.0, 1.0, 1.0), (0.3, -0.5, 0.8), (0.0, 0.0, -1.0)])
+def test_reinit_keeps_the_distance_to_a_plane(normal):
+    """§3.7: a signed distance is the steady state of eq. reinit. For a plane
+    the explicit step is exact on the interface nodes and the upwind sweeps
+    leave the exact distance unchanged."""
+    P, X = _reinit_grid(3, 20)
+    n = np.array(normal) / np.linalg.norm(normal)
+    phi = O.cut(P, X @ n - 0.137)
+    out, flags, m = O.reinit(P, phi, phi)
+    assert m > 0 and np.any(flags & 2)
+    np.testing.assert_allclose(out, phi, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("scale", [2.5, 0.4])
+def test_reinit_restores_the_distance_of_a_scaled_plane(scale):
+    """φ̃ = scale·SDF of an oblique plane on the band: the interface nodes get
+    the exact distance in the explicit step, and the band converges to the
+    exact distance, the steady state. Checked away from the domain faces,
+    whose nodes keep φ̃ and feed characteristics that start there; no node
+    changes sign."""
+    P, X = _reinit_grid(3, 26)
+    n = np.array([0.2, 1.0, -0.4]) / np.linalg.norm([0.2, 1.0, -0.4])
+    sdf = X @ n + 0.021
+    phi_n, phi_t = _after_sl(P, sdf, scale)
+    out, flags, _ = O.reinit(P, phi_n, phi_t, sweeps=200)
+    iface = (flags & 2) != 0
+    np.testing.assert_allclose(out[iface], sdf[iface], rtol=0, atol=1e-14)
+    band = np.abs(phi_n) < P.gamma
+    inside = np.all(np.abs(X) < 1.0 - P.gamma - 2 * P.h, axis=1)
+    sel = band & inside
+    assert sel.sum() > 100
+    # the first-order scheme's domain of dependence along a weak axis of the
+    # normal still reaches the faces: their influence decays slowly
+    np.testing.assert_allclose(out[sel], phi_n[sel], rtol=0, atol=1e-5 * P.h)
+    out2, _, _ = O.reinit(P, phi_n, phi_t)  # the default sweep count
+    assert np.abs(out2[sel] - phi_n[sel]).max() < 1e-3 * P.h
+    assert np.array_equal(out2 < 0, phi_t < 0)
+
+
+@pytest.mark.parametrize("dim,n,scale", [(2, 48, 3.0), (2, 48, 0.5), (3, 32, 3.0), (3, 32, 0.5)])
+def test_reinit_of_a_scaled_circle_or_sphere(dim, n, scale):
+    """φ̃ = scale·(|x| - R) on the band: after reinitialisation the interface
+    nodes are within h²/R of the signed distance (second-order subcell
+    estimate), the band within 0.5h (first-order sweeps on a curved front),
+    and no node changes sign."""
+    P, X = _reinit_grid(dim, n)
+    R = 0.5
+    sdf = np.linalg.norm(X, axis=1) - R
+    phi_n, phi_t = _after_sl(P, sdf, scale)
+    out, flags, _ = O.reinit(P, phi_n, phi_t)
+    iface = (flags & 2) != 0
+    assert np.abs(out[iface] - sdf[iface]).max() <= P.h ** 2 / R
+    band = np.abs(phi_n) < P.gamma
+    assert np.abs(out[band] - phi_n[band]).max() <= 0.5 * P.h
+    assert np.array_equal(out < 0, phi_t < 0)
+
+
+def test_reinit_domain_is_the_band_and_its_face_neighbours():
+    """Ḡ = G̃ ∪ first neighbours (§3.8 last paragraph), checked against a numpy
+    dilation; nodes outside Ḡ are returned unchanged; the result is cut."""
+    rng = np.random.default_rng(3)
+    for dim, n in ((2, 30), (3, 14)):
+        P, X = _reinit_grid(dim, n)
+        sdf = np.linalg.norm(X - 0.1, axis=1) - 0.45
+        phi_band = O.cut(P, sdf)
+        phi_t = O.cut(P, sdf + rng.normal(0, 0.2 * P.h, sdf.shape))
+        out, flags, m = O.reinit(P, phi_band, phi_t)
+        band = np.abs(phi_band) < P.gamma
+        shape = tuple(int(P.n[a]) for a in range(dim))[::-1]
+        gbar = _dilate_face(band, shape)
+        assert np.array_equal((flags & 1) != 0, gbar) and m == int(gbar.sum())
+        assert np.array_equal(out[~gbar], phi_t[~gbar])
+        assert np.all(np.abs(out) <= P.gamma)
+
+
+def test_evolve_with_reinit_moves_the_band_to_a_far_cloud():
+    """§3.8 last paragraph: started from a circle whose band does not reach
+    the cloud, the zero level set stays inside G̃^0 without reinitialisation
+    (φ = γ at the cloud), while with it the band moves with the front and the
+    zero level set reaches the cloud (error on the cloud, eq. errCloud, below h)."""
+    pts = synth.circle_uniform(400, 0.45)
+    # p = 1: C = 1, the front moves Δt|∇d| = h/4 per step (eq. SL2d)
+    P = _grid_params(2, 64, band=1, interp=0, p=1.0, delta=0.0)
+    X = O.node_coords(P)
+    d, _ = O.distance(P, pts)
+    u0 = O.cut(P, np.linalg.norm(X, axis=1) - 0.8)
+    plain = O.evolve(P, u0, d, max_iters=80, min_iters=80)
+    moved = O.evolve(P, u0, d, max_iters=80, min_iters=80, reinit=True)
+    assert O.err_cloud(P, plain["u"], pts) > 0.99 * P.gamma
+    assert O.err_cloud(P, moved["u"], pts) < P.h
