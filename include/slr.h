@@ -82,6 +82,10 @@ typedef struct {
     int stop_k;         /* running-mean window k_max, default 10, at most 1023 */
     int min_iters;      /* default 10 */
     int max_iters;      /* default 100 */
+    int reinit;         /* 1: Algorithm 1 step 4d, the reinitialisation of §3.7 on the band and its
+                         * first neighbours after every SL step (needs band = 1); 0: off (default) */
+    int reinit_sweeps;  /* pseudo-time sweeps of eq. reinit; 0 -> 4(γ/h + 1) */
+    double reinit_dtau; /* pseudo-time step Δτ; 0 -> h/2 (at most h/sqrt(dim)) */
 } slr_config;
 
 void slr_config_default(slr_config* cfg);
@@ -185,12 +189,16 @@ slr_status slr_export_state(slr_ctx* ctx, void* buf, int64_t cap, int64_t* n_out
 slr_status slr_import_state(slr_ctx* ctx, const void* buf, int64_t n);
 
 /* Opt-in timing of the kernels of one iteration: with on != 0 the captured
- * iteration graph also records CUDA events around its three kernels (SL step
- * with band compaction, energy quadrature, record/stop). After an iteration
- * has run, slr_last_iteration_times synchronises the stream and writes the
- * three kernel durations of the most recent iteration in milliseconds. */
+ * iteration graph also records CUDA events between its phases (SL step with
+ * band compaction, reinitialisation when on, energy quadrature, record/stop).
+ * After an iteration has run, slr_last_iteration_times synchronises the
+ * stream and writes the durations of the SL step, energy and record phases of
+ * the most recent iteration in milliseconds; slr_last_iteration_phases writes
+ * the same with the reinitialisation phase: ms[0] step, ms[1]
+ * reinitialisation (0 when off), ms[2] energy, ms[3] record. */
 slr_status slr_set_profiling(slr_ctx* ctx, int on);
 slr_status slr_last_iteration_times(slr_ctx* ctx, float ms[3]);
+slr_status slr_last_iteration_phases(slr_ctx* ctx, float ms[4]);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t slr_kernel_launches(const slr_ctx* ctx);

@@ -75,6 +75,7 @@ slr_status capture_step_graph(slr_ctx* c, double ov, int evolve, cudaGraph_t* ou
     long long l0 = c->launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     cudaError_t e1 = launch_step(c, ov, evolve);
+    if (e1 == cudaSuccess && c->cfg.reinit) e1 = launch_reinit(c);
     cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve) : e1;
     cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
     c->launches = l0;
@@ -96,9 +97,11 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     cudaError_t e1 = c->profiling ? cudaEventRecordWithFlags(c->pev[0], c->stream, cudaEventRecordExternal) : cudaSuccess;
     if (e1 == cudaSuccess) e1 = launch_step(c, ov, evolve);
     if (e1 == cudaSuccess && c->profiling) e1 = cudaEventRecordWithFlags(c->pev[1], c->stream, cudaEventRecordExternal);
-    // launch_energy enqueues the energy kernel and the record kernel
-    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve, c->profiling ? c->pev[2] : nullptr) : e1;
-    if (e2 == cudaSuccess && c->profiling) e2 = cudaEventRecordWithFlags(c->pev[3], c->stream, cudaEventRecordExternal);
+    if (e1 == cudaSuccess && c->cfg.reinit) e1 = launch_reinit(c);
+    if (e1 == cudaSuccess && c->profiling) e1 = cudaEventRecordWithFlags(c->pev[2], c->stream, cudaEventRecordExternal);
+    // launch_energy enqueues the front-cell, energy and record kernels
+    cudaError_t e2 = e1 == cudaSuccess ? launch_energy(c, 1, -1.0, 1, evolve, c->profiling ? c->pev[3] : nullptr) : e1;
+    if (e2 == cudaSuccess && c->profiling) e2 = cudaEventRecordWithFlags(c->pev[4], c->stream, cudaEventRecordExternal);
     cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
     c->launches = l0;  // captured kernels are counted per replay
     if (e2 != cudaSuccess) {
@@ -112,7 +115,11 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
     return SLR_OK;
 }
 
-constexpr int kKernelsPerIteration = 4;  // step, front cells, energy, record
+// kernels of one iteration: step, front cells, energy, record, plus the
+// reinitialisation stage (10 kernels and the sweeps) when it is on
+long long kernels_per_iteration(const slr_ctx* c) {
+    return 4 + (c->cfg.reinit ? 10 + reinit_sweeps(c) : 0);
+}
 
 slr_status read_status(slr_ctx* c, int* stop, int* error, int* n) {
     int* hp = c->host_pinned_flags;
@@ -167,6 +174,29 @@ slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     return SLR_OK;
 }
 
+// the reinitialisation stage's scratch (cfg.reinit): field W, three
+// bitmasks, compaction counts, per-node flags, Δ_φ partials
+slr_status size_reinit_buffers(slr_ctx* c) {
+    release(c, c->rw);
+    release_t(c, c->bits_band);
+    release_t(c, c->bits_gbar);
+    release_t(c, c->bits_cell);
+    release_t(c, c->rblk);
+    release_t(c, c->rflags);
+    release_t(c, c->part_dphi_r);
+    const size_t words = reinit_bit_words(c);
+    c->rw = dev_alloc(c, c->tsize * c->N);
+    c->bits_band = (unsigned*)dev_alloc(c, sizeof(unsigned) * words);
+    c->bits_gbar = (unsigned*)dev_alloc(c, sizeof(unsigned) * words);
+    c->bits_cell = (unsigned*)dev_alloc(c, sizeof(unsigned) * words);
+    c->rblk = (int*)dev_alloc(c, sizeof(int) * 2 * ((size_t)reinit_scan_blocks(c) + 1));
+    c->rflags = (unsigned char*)dev_alloc(c, (size_t)c->N);
+    c->part_dphi_r = (double*)dev_alloc(c, sizeof(double) * (size_t)reinit_grid(c));
+    if (!c->rw || !c->bits_band || !c->bits_gbar || !c->bits_cell || !c->rblk || !c->rflags || !c->part_dphi_r)
+        return fail(c, SLR_E_NOMEM, "allocation of the reinitialisation buffers failed");
+    return SLR_OK;
+}
+
 bool same_config(const slr_config& a, const slr_config& b) { return memcmp(&a, &b, sizeof(slr_config)) == 0; }
 
 }  // namespace
@@ -186,7 +216,7 @@ slr_status evolve_prepare(slr_ctx* c) {
 
 slr_status evolve_launch(slr_ctx* c) {
     CK(cudaGraphLaunch(c->g_evolve, c->stream), "cudaGraphLaunch");
-    c->launches += kKernelsPerIteration;
+    c->launches += kernels_per_iteration(c);
     return SLR_OK;
 }
 
@@ -218,6 +248,9 @@ void slr_config_default(slr_config* cfg) {
     cfg->stop_k = 10;
     cfg->min_iters = 10;
     cfg->max_iters = 100;
+    cfg->reinit = 0;
+    cfg->reinit_sweeps = 0;
+    cfg->reinit_dtau = 0.0;
 }
 
 slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out) {
@@ -256,6 +289,11 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
     if (k.stop_k < 1 || k.stop_k > kMaxStopK || k.max_iters < 1 || k.min_iters < 0) return bad("bad stop parameters");
     if (k.max_iters >= kHist - 1) return bad("max_iters too large");
     if (!(k.c_sing >= 0.0)) return bad("c_sing must be >= 0");
+    if (k.reinit != 0 && k.reinit != 1) return bad("reinit must be 0 or 1");
+    if (k.reinit && !k.band) return bad("reinit needs the narrow band (band = 1)");
+    if (k.reinit_sweeps < 0 || k.reinit_sweeps > 10000) return bad("reinit_sweeps must be in 0..10000");
+    if (!(k.reinit_dtau >= 0.0) || !(k.reinit_dtau <= h / sqrt((double)k.dim) * (1.0 + 1e-12)))
+        return bad("reinit_dtau must be in [0, h/sqrt(dim)]");
     c->h = h;
     c->dt = k.dt > 0.0 ? k.dt : h / 4.0;
     c->gamma = k.gamma > 0.0 ? k.gamma : (k.dim == 2 ? 4.0 : 6.0) * h;
@@ -305,6 +343,10 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
         cudaGetLastError();
         slr_destroy(c);
         return SLR_E_CUDA;
+    }
+    if (k.reinit && size_reinit_buffers(c) != SLR_OK) {
+        slr_destroy(c);
+        return SLR_E_NOMEM;
     }
     if (!k.band) {
         long long tiles = (N + kStepBlock - 1) / kStepBlock;
@@ -391,9 +433,13 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
     dev_free(c, tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "init_u");
     if (c->cfg.band) {
+        // with reinitialisation the band can grow: lists and cells get the
+        // capacity of the whole grid, and the candidate-cell count lives on
+        // the device
+        const bool rei = c->cfg.reinit != 0;
         long long cnt = 0;
         CK(launch_count_band(c, &cnt), "init_u band count");
-        slr_status s = size_band_buffers(c, cnt);
+        slr_status s = size_band_buffers(c, rei ? c->N : cnt);
         if (s != SLR_OK) return s;
         CK(launch_build_band(c), "init_u band list");
         int ci = (int)cnt;
@@ -401,12 +447,18 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
         long long nc = 0;
         CK(launch_build_ecells(c, &nc, false), "init_u cell count");
         release_t(c, c->ecells);
-        c->ecells = (int*)dev_alloc(c, sizeof(int) * (nc > 0 ? nc : 1));
+        const long long ecap = rei ? c->ncells_all : nc;
+        c->ecells = (int*)dev_alloc(c, sizeof(int) * (ecap > 0 ? ecap : 1));
         if (!c->ecells) return fail(c, SLR_E_NOMEM, "init_u: cell list allocation failed");
-        c->n_ecells = nc;
+        c->n_ecells = ecap;
         CK(launch_build_ecells(c, &nc, true), "init_u cell list");
         s = size_energy_buffers(c, c->n_ecells);
         if (s != SLR_OK) return s;
+        if (rei) {
+            int nci = (int)nc;
+            CK(cudaMemcpyAsync(&c->ds->n_ecells_dyn, &nci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
+            CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "init_u");
+        }
     }
     CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
     CK(cudaStreamSynchronize(c->stream), "init_u sync");
@@ -430,7 +482,7 @@ slr_status slr_step(slr_ctx* c, int n_steps, double energy_override) {
     CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "step");
     for (int i = 0; i < n_steps; ++i) {
         CK(cudaGraphLaunch(c->g_step, c->stream), "cudaGraphLaunch");
-        c->launches += kKernelsPerIteration;
+        c->launches += kernels_per_iteration(c);
     }
     CK(cudaStreamSynchronize(c->stream), "step sync");
     return check_device_error(c);
@@ -512,7 +564,7 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
     int rounds = 0;
     while (e == cudaSuccess) {
         e = cudaGraphLaunch(exec, st);
-        for (int j = 0; j < n_jobs; ++j) jobs[j]->launches += (long long)chunk * kKernelsPerIteration;
+        for (int j = 0; j < n_jobs; ++j) jobs[j]->launches += (long long)chunk * kernels_per_iteration(jobs[j]);
         if (e == cudaSuccess) e = launch_gather_status(c0, dstates, n_jobs, dstop, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hstop, dstop, sizeof(int) * 4 * n_jobs, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -561,7 +613,7 @@ slr_status slr_step_async(slr_ctx* c, int n_steps, double energy_override) {
     CK(cudaMemsetAsync(&c->ds->stop, 0, sizeof(int), c->stream), "step_async");
     for (int i = 0; i < n_steps; ++i) {
         CK(cudaGraphLaunch(c->g_step, c->stream), "cudaGraphLaunch");
-        c->launches += kKernelsPerIteration;
+        c->launches += kernels_per_iteration(c);
     }
     return SLR_OK;
 }
@@ -571,7 +623,7 @@ slr_status slr_set_profiling(slr_ctx* c, int on) {
     DeviceGuard g(c->device);
     bool want = on != 0;
     if (want && !c->pev[0])
-        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->pev[i]), "cudaEventCreate");
+        for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&c->pev[i]), "cudaEventCreate");
     if (want != c->profiling) free_graphs(c);
     c->profiling = want;
     return SLR_OK;
@@ -582,7 +634,19 @@ slr_status slr_last_iteration_times(slr_ctx* c, float ms[3]) {
     if (!c->profiling) return fail(c, SLR_E_STATE, "last_iteration_times: profiling is off");
     DeviceGuard g(c->device);
     CK(cudaStreamSynchronize(c->stream), "last_iteration_times");
-    for (int i = 0; i < 3; ++i) CK(cudaEventElapsedTime(&ms[i], c->pev[i], c->pev[i + 1]), "cudaEventElapsedTime");
+    // events: 0 before the step, 1 after it, 2 after the reinitialisation, 3 between energy and record, 4 after
+    CK(cudaEventElapsedTime(&ms[0], c->pev[0], c->pev[1]), "cudaEventElapsedTime");
+    CK(cudaEventElapsedTime(&ms[1], c->pev[2], c->pev[3]), "cudaEventElapsedTime");
+    CK(cudaEventElapsedTime(&ms[2], c->pev[3], c->pev[4]), "cudaEventElapsedTime");
+    return SLR_OK;
+}
+
+slr_status slr_last_iteration_phases(slr_ctx* c, float ms[4]) {
+    if (!c || !ms) return SLR_E_INVALID;
+    if (!c->profiling) return fail(c, SLR_E_STATE, "last_iteration_phases: profiling is off");
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->stream), "last_iteration_phases");
+    for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&ms[i], c->pev[i], c->pev[i + 1]), "cudaEventElapsedTime");
     return SLR_OK;
 }
 
@@ -601,7 +665,7 @@ slr_status slr_evolve(slr_ctx* c, int* iters_out, int* converged_out) {
     while (!stop) {
         for (int i = 0; i < kChunk; ++i) {
             CK(cudaGraphLaunch(c->g_evolve, c->stream), "cudaGraphLaunch");
-            c->launches += kKernelsPerIteration;
+            c->launches += kernels_per_iteration(c);
         }
         slr_status s = read_status(c, &stop, &err, &n);
         if (s != SLR_OK) return s;
@@ -781,7 +845,14 @@ slr_status slr_export_state(slr_ctx* c, void* buf, int64_t cap, int64_t* n_out) 
         CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream), "export");
         CK(cudaStreamSynchronize(c->stream), "export");
     }
-    StateHeader hd{kStateMagic, (uint32_t)c->tsize, c->N, cnt, c->cfg.band ? c->n_ecells : 0};
+    long long ncell = c->cfg.band ? c->n_ecells : 0;
+    if (c->cfg.reinit) {
+        int nd = 0;
+        CK(cudaMemcpyAsync(&nd, &c->ds->n_ecells_dyn, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "export");
+        CK(cudaStreamSynchronize(c->stream), "export");
+        ncell = nd;
+    }
+    StateHeader hd{kStateMagic, (uint32_t)c->tsize, c->N, cnt, ncell};
     size_t need = sizeof(hd) + sizeof(slr_config) + sizeof(DevState) + sizeof(int) * (size_t)cnt +
                   sizeof(int) * (size_t)hd.n_ecells + c->tsize * 2 * c->N + sizeof(int) * c->N;
     if (n_out) *n_out = (int64_t)need;
@@ -831,11 +902,13 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     p += sizeof(DevState);
     const int n = hds->n;
     if (c->cfg.band) {
-        slr_status s = size_band_buffers(c, hd.band_count);
+        const bool rei = c->cfg.reinit != 0;
+        slr_status s = size_band_buffers(c, rei ? c->N : hd.band_count);
         if (s == SLR_OK) {
             release_t(c, c->ecells);
-            c->ecells = (int*)dev_alloc(c, sizeof(int) * (hd.n_ecells > 0 ? hd.n_ecells : 1));
-            c->n_ecells = hd.n_ecells;
+            const long long ecap = rei ? c->ncells_all : hd.n_ecells;
+            c->ecells = (int*)dev_alloc(c, sizeof(int) * (ecap > 0 ? ecap : 1));
+            c->n_ecells = ecap;
             if (!c->ecells) s = fail(c, SLR_E_NOMEM, "import_state: allocation failed");
         }
         if (s == SLR_OK) s = size_energy_buffers(c, c->n_ecells);
@@ -861,6 +934,8 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     CK(cudaMemcpyAsync(c->d, p, c->tsize * c->N, cudaMemcpyHostToDevice, c->stream), "import");
     p += c->tsize * c->N;
     CK(cudaMemcpyAsync(c->argmin, p, sizeof(int) * c->N, cudaMemcpyHostToDevice, c->stream), "import");
+    if (c->cfg.reinit)
+        CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "import");
     // an energy pass in report mode recomputes the band-tile offsets the
     // next step reads (the history and E_p stay as imported)
     CK(launch_energy(c, 0, c->cfg.p, 2, 0), "import energy pass");
@@ -897,9 +972,16 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->part_e);
     release_t(c, c->tile_off);
     release_t(c, c->front);
+    release(c, c->rw);
+    release_t(c, c->bits_band);
+    release_t(c, c->bits_gbar);
+    release_t(c, c->bits_cell);
+    release_t(c, c->rblk);
+    release_t(c, c->rflags);
+    release_t(c, c->part_dphi_r);
     release_t(c, c->ds);
     if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c->pev[i]) cudaEventDestroy(c->pev[i]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();

@@ -180,7 +180,8 @@ constexpr int kEnergyCand = 1024;  // candidate cells per slot (4 per thread)
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* ub0, const T* ub1,
-                                                          const int* __restrict__ cells, long long ncells, int offset,
+                                                          const int* __restrict__ cells, long long ncells_host,
+                                                          const int* ncells_dev, int offset,
                                                           int* __restrict__ front, int* __restrict__ fcount,
                                                           DevState* ds, int check_stop) {
     constexpr int W = kEnergyThreads / 32;
@@ -188,8 +189,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* 
     static_assert(PER == 4, "four candidates per thread (one 16-byte load of the cell list)");
     __shared__ int s_warp[W + 1];
     if (check_stop && ds->stop) return;
-    const int sel = (ds->n + offset) & 1;
-    const T* __restrict__ u = sel ? ub1 : ub0;
+    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
+    const long long ncells = ncells_dev ? (long long)*ncells_dev : ncells_host;
     int* slot = front + (long long)blockIdx.x * kEnergyCand;
     // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
     const long long e0 = (long long)blockIdx.x * kEnergyCand + PER * threadIdx.x;
@@ -441,6 +442,7 @@ struct RecordArgs {
     long long n_dphi_full; // number of Δ_φ partials in whole-grid mode (step blocks)
     long long N;
     int full_grid;
+    int reinit;            // Δ_φ partials from the reinitialisation stage; band size from band_sl
     int mode;
     int evolve;
     double h_dim;  // h^dim
@@ -461,7 +463,8 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
-        ntiles = A.full_grid ? A.n_dphi_full : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
+        ntiles = (A.full_grid || A.reinit) ? A.n_dphi_full
+                                           : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
     }
     const long long G = gridDim.x;
     double a = 0.0, b = 0.0, cc = 0.0;
@@ -585,7 +588,8 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     }
     if (A.mode == 1) {
         ds->dphi_hist[n % kHist] = dphi * A.h_dim;
-        ds->band_hist[n % kHist] = A.full_grid ? A.N : (long long)ds->band_count[(n + 1) & 1];
+        ds->band_hist[n % kHist] =
+            A.full_grid ? A.N : (A.reinit ? (long long)ds->band_sl : (long long)ds->band_count[(n + 1) & 1]);
         ds->n = nn;
     }
     double E2 = sqrt(s2);
@@ -623,8 +627,10 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const double hp = c->h / c->cfg.energy_R;
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
     int* fcount = (int*)(c->front + (size_t)blocks * kEnergyCand);
+    const int* ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;  // the list changes every iteration
     k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
-                                                               offset, c->front, fcount, c->ds, check_stop);
+                                                               ncells_dev, offset, c->front, fcount, c->ds,
+                                                               check_stop);
     int* tile_cnt = c->cfg.band ? c->tile_off : nullptr;
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
@@ -665,12 +671,13 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
         if (e != cudaSuccess) return e;
     }
     RecordArgs A;
-    A.part_dphi = c->part_dphi;
+    A.part_dphi = c->cfg.reinit ? c->part_dphi_r : c->part_dphi;
     A.part_e = c->part_e;
     A.nchunks = energy_blocks(c);
-    A.n_dphi_full = full_step_blocks(c);
+    A.n_dphi_full = c->cfg.reinit ? reinit_grid(c) : full_step_blocks(c);
     A.N = c->N;
     A.full_grid = !c->cfg.band;
+    A.reinit = c->cfg.reinit;
     A.mode = record_mode;
     A.evolve = evolve_mode;
     A.h_dim = c->cfg.dim == 3 ? c->h * c->h * c->h : c->h * c->h;

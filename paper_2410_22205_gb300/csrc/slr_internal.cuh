@@ -37,6 +37,8 @@ struct DevState {
     unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
     unsigned record_done;  // blocks of the record kernel done (reset by its last block)
     int band_next;       // size of the band the next step writes (sum of the tile counts)
+    int band_sl;         // with reinitialisation: band nodes the SL step of this iteration updated
+    int n_ecells_dyn;    // with reinitialisation: candidate cells of the energy pass
     int band_base[kRecordBlocks];  // exclusive prefix of the tile counts per record-block slice
     double Ep;           // E_p(φ^n) used by step n
     double e2_hist[kHist];
@@ -100,6 +102,14 @@ struct slr_ctx {
     long long n_echunks = 0;       // candidate chunks of 32 cells (sizes part_e)
     int* front = nullptr;          // per-block slots of front cells (1024 each) followed by the slot counts
     int* tile_off = nullptr;       // per 128-entry tile of the step's input band: count, then offset in its slice
+    // reinitialisation (cfg.reinit): scratch field, row-padded bitmasks, flags
+    void* rw = nullptr;                  // W: sweep ping-pong partner of the output φ buffer
+    unsigned* bits_band = nullptr;       // band G̃^n
+    unsigned* bits_gbar = nullptr;       // Ḡ^n
+    unsigned* bits_cell = nullptr;       // candidate cells
+    int* rblk = nullptr;                 // per-block counts of the two compactions
+    unsigned char* rflags = nullptr;     // per Ḡ position: fixed, sign
+    double* part_dphi_r = nullptr;       // Δ_φ partials of the final reinitialisation kernel
     slr::DevState* ds = nullptr;
     int* host_pinned_flags = nullptr;  // pinned host words for status readback
 
@@ -111,7 +121,7 @@ struct slr_ctx {
     cudaGraphExec_t g_step = nullptr;
     double g_step_override = -2.0;
     bool profiling = false;
-    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace slr {
@@ -131,6 +141,13 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
                           cudaEvent_t between = nullptr);
 cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double* u_dev, long long* count_out,
                            bool write);
+// Algorithm 1 step 4d (§3.7) after launch_step; see slr_reinit.cu
+cudaError_t launch_reinit(slr_ctx* c);
+int reinit_grid(const slr_ctx* c);
+int reinit_sweeps(const slr_ctx* c);
+double reinit_dtau(const slr_ctx* c);
+size_t reinit_bit_words(const slr_ctx* c);
+int reinit_scan_blocks(const slr_ctx* c);
 cudaError_t launch_err_cloud(slr_ctx* c, double* out_dev);
 cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long n);
 cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long long n);

@@ -31,7 +31,8 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
-    "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times", "slr_kernel_launches",
+    "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
+    "slr_last_iteration_phases", "slr_kernel_launches",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
     "slr_server_destroy",
@@ -65,6 +66,9 @@ class slr_config(C.Structure):
         ("stop_k", C.c_int),
         ("min_iters", C.c_int),
         ("max_iters", C.c_int),
+        ("reinit", C.c_int),
+        ("reinit_sweeps", C.c_int),
+        ("reinit_dtau", C.c_double),
     ]
 
 
@@ -108,6 +112,7 @@ def lib():
                 "slr_import_state": (C.c_int, [_vp, _vp, C.c_int64]),
                 "slr_set_profiling": (C.c_int, [_vp, C.c_int]),
                 "slr_last_iteration_times": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+                "slr_last_iteration_phases": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_kernel_launches": (C.c_int64, [_vp]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
@@ -148,6 +153,9 @@ def _ptr(a, t=_dp):
 # entry points (same names as the C ABI)
 # ---------------------------------------------------------------------------
 
+_CFG_FIELDS = {f[0] for f in slr_config._fields_}
+
+
 def slr_config_default(**overrides) -> slr_config:
     cfg = slr_config()
     lib().slr_config_default(C.byref(cfg))
@@ -157,8 +165,10 @@ def slr_config_default(**overrides) -> slr_config:
             arr = getattr(cfg, k)
             for a in range(3):
                 arr[a] = v[a]
-        else:
+        elif k in _CFG_FIELDS:
             setattr(cfg, k, v)
+        else:
+            raise TypeError(f"slr_config has no field {k!r}")
     return cfg
 
 
@@ -237,6 +247,12 @@ def slr_set_profiling(ctx, on=True):
 def slr_last_iteration_times(ctx):
     ms = (C.c_float * 3)()
     _check(ctx, lib().slr_last_iteration_times(ctx, ms))
+    return list(ms)
+
+
+def slr_last_iteration_phases(ctx):
+    ms = (C.c_float * 4)()
+    _check(ctx, lib().slr_last_iteration_phases(ctx, ms))
     return list(ms)
 
 
@@ -450,6 +466,10 @@ class Reconstruction:
 
     def last_iteration_times(self):
         return slr_last_iteration_times(self.ctx)
+
+    def last_iteration_phases(self):
+        """[SL step, reinitialisation, energy, record] of the last iteration, in ms."""
+        return slr_last_iteration_phases(self.ctx)
 
     def evolve(self):
         return slr_evolve(self.ctx)
