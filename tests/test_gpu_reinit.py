@@ -5,8 +5,9 @@ through the C ABI against the FP64 oracle.
 Bars (each written in its test):
   - the next step's scan list Ḡ^n (the step's band and its face
     neighbours): bit-exact;
-  - φ after one iteration from identical inputs: FP64 max-abs <= 1e-11; FP32
-    <= 1e-4·h. Nodes within two cells of a node whose sign class (φ̃ < 0 versus
+  - φ after one iteration from identical inputs: FP64 max-abs <= 1e-12; FP32
+    <= 1e-5·h (the SL step's own bars: the sweeps do not expand differences
+    in the max norm, and measured errors are ~1e-14·h and ~1e-6·h). Nodes within two cells of a node whose sign class (φ̃ < 0 versus
     φ̃ >= 0) could differ between the two sides (|φ̃| within the SL step's
     tolerance of 0) or of a node the SL step flags near its singular threshold
     are excluded: the interface set of the explicit step is decided there;
@@ -77,7 +78,7 @@ def test_reinit_iteration_parity(dim, n, prec, interp):
     shape = (n,) * dim
     risky = ((flags & O.FLAG_MARGIN) != 0) | (((rfl & 1) != 0) & (np.abs(nxt) <= tol_sl))
     ok = ~dilate(risky, shape, 2)
-    tol = 1e-11 if prec == 64 else 1e-4 * P.h
+    tol = 1e-12 if prec == 64 else 1e-5 * P.h
     err = np.abs(u1 - ref)[ok]
     assert err.max() <= tol, (err.max(), tol, int((~ok).sum()))
     assert np.all(np.abs(u1) <= np.float32(P.gamma) if prec == 32 else np.abs(u1) <= P.gamma)
