@@ -24,10 +24,19 @@ Params<T> make_params(const slr_ctx* c);
 
 // grid of the energy pass: one block per 1024 candidate cells (one partial
 // pair per block)
-long long energy_blocks(const slr_ctx* c) {
+// slots of 1024 candidate cells (the capacity of the list with the
+// reinitialisation on), and the energy kernels' grid, which takes slots from
+// a ticket
+long long energy_slots(const slr_ctx* c) {
     long long ncells = c->cfg.band ? c->n_ecells : c->ncells_all;
-    long long blocks = (ncells + 1023) / 1024;
-    return blocks < 1 ? 1 : blocks;
+    return (ncells + 1023) / 1024;
+}
+
+long long energy_blocks(const slr_ctx* c) {
+    long long b = energy_slots(c);
+    const long long cap = (long long)c->num_sms * 6;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : b;
 }
 
 __device__ __forceinline__ double pow_abs(double v, double p, int p_kind) {
@@ -191,65 +200,78 @@ __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* 
     if (check_stop && ds->stop) return;
     const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
     const long long ncells = ncells_dev ? (long long)*ncells_dev : ncells_host;
-    int* slot = front + (long long)blockIdx.x * kEnergyCand;
-    // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
-    const long long e0 = (long long)blockIdx.x * kEnergyCand + PER * threadIdx.x;
-    int node[PER];
-    if (cells && e0 + PER <= ncells) {
-        const int4 c4 = *reinterpret_cast<const int4*>(cells + e0);  // slot starts are multiples of 1024
-        node[0] = c4.x;
-        node[1] = c4.y;
-        node[2] = c4.z;
-        node[3] = c4.w;
-    } else {
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            node[r] = 0;
-            if (e0 + r < ncells) {
-                int i, j, k;
-                cell_of<T, DIM>(P, cells, e0 + r, i, j, k);
-                node[r] = i + P.is1 * j + P.is2 * k;
+    // slot sb = candidates [sb·kEnergyCand, (sb+1)·kEnergyCand); blocks take
+    // slots from a ticket (reset by the record kernel)
+    __shared__ long long s_sb;
+    const long long nslots = (ncells + kEnergyCand - 1) / kEnergyCand;
+    for (;;) {
+        if (threadIdx.x == 0) s_sb = (long long)atomicAdd(&ds->eticket[0], 1u);
+        __syncthreads();
+        const long long sb = s_sb;
+        __syncthreads();
+        if (sb >= nslots) break;
+        int* slot = front + sb * kEnergyCand;
+        // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
+        const long long e0 = sb * kEnergyCand + PER * threadIdx.x;
+        int node[PER];
+        if (cells && e0 + PER <= ncells) {
+            const int4 c4 = *reinterpret_cast<const int4*>(cells + e0);  // slot starts are multiples of 1024
+            node[0] = c4.x;
+            node[1] = c4.y;
+            node[2] = c4.z;
+            node[3] = c4.w;
+        } else {
+    #pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                node[r] = 0;
+                if (e0 + r < ncells) {
+                    int i, j, k;
+                    cell_of<T, DIM>(P, cells, e0 + r, i, j, k);
+                    node[r] = i + P.is1 * j + P.is2 * k;
+                }
             }
         }
-    }
-    bool fl[PER];
-    int cnt = 0;
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        fl[r] = e0 + r < ncells && is_front<T, DIM>(P, u, node[r]);
-        cnt += fl[r];
-    }
-    // block exclusive scan of the per-thread counts (candidate order kept)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int w = 0; w < W; ++w) {
-            const int c = s_warp[w];
-            s_warp[w] = run;
-            run += c;
+        bool fl[PER];
+        int cnt = 0;
+    #pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            fl[r] = e0 + r < ncells && is_front<T, DIM>(P, u, node[r]);
+            cnt += fl[r];
         }
-        s_warp[W] = run;
+        // block exclusive scan of the per-thread counts (candidate order kept)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = cnt;
+    #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < W; ++w) {
+                const int c = s_warp[w];
+                s_warp[w] = run;
+                run += c;
+            }
+            s_warp[W] = run;
+        }
+        __syncthreads();
+        int off = s_warp[warp] + incl - cnt;
+    #pragma unroll
+        for (int r = 0; r < PER; ++r)
+            if (fl[r]) slot[off++] = node[r];
+        if (threadIdx.x == 0) fcount[sb] = s_warp[W];
+        __syncthreads();
     }
-    __syncthreads();
-    int off = s_warp[warp] + incl - cnt;
-#pragma unroll
-    for (int r = 0; r < PER; ++r)
-        if (fl[r]) slot[off++] = node[r];
-    if (threadIdx.x == 0) fcount[blockIdx.x] = s_warp[W];
 }
 
 template <typename T, int DIM, int INTERP, int RC>
 __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T* ub0, const T* ub1,
                                                            const T* __restrict__ d, const int* __restrict__ front,
-                                                           const int* __restrict__ fcount, int R_run, double h,
+                                                           const int* __restrict__ fcount, long long ncells_host,
+                                                           const int* ncells_dev, int R_run, double h,
                                                            double p, int p_kind, T thr, T hp2, T pT, int offset,
                                                            double* part, const int* L0, const int* L1,
                                                            int* __restrict__ tile_cnt, DevState* ds, int check_stop) {
@@ -287,135 +309,146 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T*
         s_wa[threadIdx.x].set_exact(t);
     }
     __syncthreads();
-    const int* s_list = front + (long long)blockIdx.x * kEnergyCand;  // this block's slot
-    const int nf = fcount[blockIdx.x];
-    // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
-    auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
-    // WENO constants at θ_m (storage-type arithmetic; folded at compile
-    // time where m is a constant)
-    auto WA = [&](int m) -> WenoAxis<T> {
-        if (RC > 0) {
-            WenoAxis<T> w;
-            w.set_exact(TH(m));
-            return w;
-        }
-        return s_wa[m];
-    };
-    auto contrib = [&](T uu, T dd, T& cp, T& c2) {
-        const T a = fabs(dd);
-        const T d2 = a * a;
-        const T keep = fabs(uu) < thr ? hp2 : T(0);
-        cp += (p_kind == 2 ? d2 : (p_kind == 1 ? a : (T)pow(a, pT))) * keep;
-        c2 += d2 * keep;
-    };
-    double ap = 0.0, a2 = 0.0;
-    if (DIM == 2) {
-        for (int fi = threadIdx.x; fi < nf; fi += kEnergyThreads) {
-            const int nd = s_list[fi];
-            const int q = nd / P.n0;
-            double s2 = 0.0;
-            ap += energy_cell_2d<T>(P, u, d, nd - q * P.n0, q, h, p, p_kind, &s2);
-            a2 += s2;
-        }
-    } else {
-        // sums over this thread's items in the storage type, widened once
-        T tp = T(0), t2 = T(0);
-        const int items = nf * R;
-        for (int it = threadIdx.x; it < items; it += kEnergyThreads) {
-            const int fi = it / R, cz = it - fi * R;
-            const int nd = s_list[fi];
-            const int q = nd / P.n0;
-            const int i = nd - q * P.n0;
-            const int k = q / P.n1;
-            const int j = q - k * P.n1;
-            const T tz = TH(cz);
-            T dc[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) dc[c] = ld(d + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
-            // d on the layer z = θ_z: bilinear in (x, y) from the two z-faces
-            T dz[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) dz[c] = dc[c] + tz * (dc[c + 4] - dc[c]);
-            T cp = T(0), c2 = T(0);
-            if (INTERP == 1) {
-                const WenoAxis<T> wz = WA(cz);
-                int ox[4], oy[4], oz[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    ox[a] = clampi(i - 1 + a, 0, P.n0 - 1);
-                    oy[a] = P.is1 * clampi(j - 1 + a, 0, P.n1 - 1);
-                    oz[a] = P.is2 * clampi(k - 1 + a, 0, P.n2 - 1);
-                }
-                WenoInd<T> iy[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    T zl[4];
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const T* col = u + (ox[a] + oy[b]);
-                        zl[b] = weno1(ld(col + oz[0]), ld(col + oz[1]), ld(col + oz[2]), ld(col + oz[3]), wz, P.h4);
-                    }
-                    iy[a].set(zl[0], zl[1], zl[2], zl[3], P.h4);
-                }
-#pragma unroll
-                for (int by = 0; by < (RC > 0 ? RC : kMaxR); ++by) {
-                    if (RC == 0 && by >= R) break;
-                    const WenoAxis<T> wy = WA(by);
-                    const T ty = TH(by);
-                    WenoInd<T> ix;
-                    ix.set(iy[0].eval(wy), iy[1].eval(wy), iy[2].eval(wy), iy[3].eval(wy), P.h4);
-                    const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
-#pragma unroll
-                    for (int ax = 0; ax < (RC > 0 ? RC : kMaxR); ++ax) {
-                        if (RC == 0 && ax >= R) break;
-                        const T tx = TH(ax);
-                        contrib(ix.eval(WA(ax)), d0 + tx * (d1 - d0), cp, c2);
-                    }
-                }
-            } else {
-                T uc[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) uc[c] = ld(u + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
-                T uz[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) uz[c] = uc[c] + tz * (uc[c + 4] - uc[c]);
-                for (int by = 0; by < R; ++by) {
-                    const T ty = TH(by);
-                    const T u0 = uz[0] + ty * (uz[2] - uz[0]), u1 = uz[1] + ty * (uz[3] - uz[1]);
-                    const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
-                    for (int ax = 0; ax < R; ++ax) {
-                        const T tx = TH(ax);
-                        contrib(u0 + tx * (u1 - u0), d0 + tx * (d1 - d0), cp, c2);
-                    }
-                }
+    const long long ncells = ncells_dev ? (long long)*ncells_dev : ncells_host;
+    const long long nslots = (ncells + kEnergyCand - 1) / kEnergyCand;
+    __shared__ long long s_sb;
+    for (;;) {
+        if (threadIdx.x == 0) s_sb = (long long)atomicAdd(&ds->eticket[1], 1u);
+        __syncthreads();
+        const long long sb = s_sb;
+        __syncthreads();
+        if (sb >= nslots) break;
+        const int* s_list = front + sb * kEnergyCand;  // this slot's front cells
+        const int nf = fcount[sb];
+        // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
+        auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
+        // WENO constants at θ_m (storage-type arithmetic; folded at compile
+        // time where m is a constant)
+        auto WA = [&](int m) -> WenoAxis<T> {
+            if (RC > 0) {
+                WenoAxis<T> w;
+                w.set_exact(TH(m));
+                return w;
             }
-            tp += cp;
-            t2 += c2;
+            return s_wa[m];
+        };
+        auto contrib = [&](T uu, T dd, T& cp, T& c2) {
+            const T a = fabs(dd);
+            const T d2 = a * a;
+            const T keep = fabs(uu) < thr ? hp2 : T(0);
+            cp += (p_kind == 2 ? d2 : (p_kind == 1 ? a : (T)pow(a, pT))) * keep;
+            c2 += d2 * keep;
+        };
+        double ap = 0.0, a2 = 0.0;
+        if (DIM == 2) {
+            for (int fi = threadIdx.x; fi < nf; fi += kEnergyThreads) {
+                const int nd = s_list[fi];
+                const int q = nd / P.n0;
+                double s2 = 0.0;
+                ap += energy_cell_2d<T>(P, u, d, nd - q * P.n0, q, h, p, p_kind, &s2);
+                a2 += s2;
+            }
+        } else {
+            // sums over this thread's items in the storage type, widened once
+            T tp = T(0), t2 = T(0);
+            const int items = nf * R;
+            for (int it = threadIdx.x; it < items; it += kEnergyThreads) {
+                const int fi = it / R, cz = it - fi * R;
+                const int nd = s_list[fi];
+                const int q = nd / P.n0;
+                const int i = nd - q * P.n0;
+                const int k = q / P.n1;
+                const int j = q - k * P.n1;
+                const T tz = TH(cz);
+                T dc[8];
+    #pragma unroll
+                for (int c = 0; c < 8; ++c) dc[c] = ld(d + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
+                // d on the layer z = θ_z: bilinear in (x, y) from the two z-faces
+                T dz[4];
+    #pragma unroll
+                for (int c = 0; c < 4; ++c) dz[c] = dc[c] + tz * (dc[c + 4] - dc[c]);
+                T cp = T(0), c2 = T(0);
+                if (INTERP == 1) {
+                    const WenoAxis<T> wz = WA(cz);
+                    int ox[4], oy[4], oz[4];
+    #pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        ox[a] = clampi(i - 1 + a, 0, P.n0 - 1);
+                        oy[a] = P.is1 * clampi(j - 1 + a, 0, P.n1 - 1);
+                        oz[a] = P.is2 * clampi(k - 1 + a, 0, P.n2 - 1);
+                    }
+                    WenoInd<T> iy[4];
+    #pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        T zl[4];
+    #pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const T* col = u + (ox[a] + oy[b]);
+                            zl[b] = weno1(ld(col + oz[0]), ld(col + oz[1]), ld(col + oz[2]), ld(col + oz[3]), wz, P.h4);
+                        }
+                        iy[a].set(zl[0], zl[1], zl[2], zl[3], P.h4);
+                    }
+    #pragma unroll
+                    for (int by = 0; by < (RC > 0 ? RC : kMaxR); ++by) {
+                        if (RC == 0 && by >= R) break;
+                        const WenoAxis<T> wy = WA(by);
+                        const T ty = TH(by);
+                        WenoInd<T> ix;
+                        ix.set(iy[0].eval(wy), iy[1].eval(wy), iy[2].eval(wy), iy[3].eval(wy), P.h4);
+                        const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
+    #pragma unroll
+                        for (int ax = 0; ax < (RC > 0 ? RC : kMaxR); ++ax) {
+                            if (RC == 0 && ax >= R) break;
+                            const T tx = TH(ax);
+                            contrib(ix.eval(WA(ax)), d0 + tx * (d1 - d0), cp, c2);
+                        }
+                    }
+                } else {
+                    T uc[8];
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) uc[c] = ld(u + (nd + (c & 1) + P.is1 * ((c >> 1) & 1) + P.is2 * (c >> 2)));
+                    T uz[4];
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c) uz[c] = uc[c] + tz * (uc[c + 4] - uc[c]);
+                    for (int by = 0; by < R; ++by) {
+                        const T ty = TH(by);
+                        const T u0 = uz[0] + ty * (uz[2] - uz[0]), u1 = uz[1] + ty * (uz[3] - uz[1]);
+                        const T d0 = dz[0] + ty * (dz[2] - dz[0]), d1 = dz[1] + ty * (dz[3] - dz[1]);
+                        for (int ax = 0; ax < R; ++ax) {
+                            const T tx = TH(ax);
+                            contrib(u0 + tx * (u1 - u0), d0 + tx * (d1 - d0), cp, c2);
+                        }
+                    }
+                }
+                tp += cp;
+                t2 += c2;
+            }
+            // warp sums in the storage type, per-warp sums widened
+            tp = warp_sum(tp);
+            t2 = warp_sum(t2);
+            ap = (double)tp;
+            a2 = (double)t2;
         }
-        // warp sums in the storage type, per-warp sums widened
-        tp = warp_sum(tp);
-        t2 = warp_sum(t2);
-        ap = (double)tp;
-        a2 = (double)t2;
-    }
-    if (DIM == 2) {
-        ap = warp_sum(ap);
-        a2 = warp_sum(a2);
-    }
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_a[wib] = ap;
-        s_b[wib] = a2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        for (int w = 0; w < W; ++w) {
-            x += s_a[w];
-            y += s_b[w];
+        if (DIM == 2) {
+            ap = warp_sum(ap);
+            a2 = warp_sum(a2);
         }
-        part[2 * blockIdx.x] = x;
-        part[2 * blockIdx.x + 1] = y;
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+        if (lane == 0) {
+            s_a[wib] = ap;
+            s_b[wib] = a2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double x = 0.0, y = 0.0;
+            for (int w = 0; w < W; ++w) {
+                x += s_a[w];
+                y += s_b[w];
+            }
+            part[2 * sb] = x;
+            part[2 * sb + 1] = y;
+        }
+        __syncthreads();
     }
 }
 
@@ -433,6 +466,7 @@ static_assert(kRecordBlocks <= 32, "the last record block combines one value per
 constexpr int kRecordThreads = 256;
 
 struct RecordArgs {
+    const int* ncells_dev; // reinitialisation: candidate cells counted on the device (energy slots of 1024)
     int* tile_off;         // band mode: tile counts in, offsets within the slice out
     int offset;            // 1 after a step (the band the next step reads has parity n+1), else 0
     const double* part_dphi;
@@ -475,8 +509,9 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     }
     {
         const double2* pe = reinterpret_cast<const double2*>(A.part_e);
-        const long long per = (A.nchunks + G - 1) / G;
-        const long long beg = blockIdx.x * per, end = beg + per < A.nchunks ? beg + per : A.nchunks;
+        const long long nch = A.ncells_dev ? ((long long)*A.ncells_dev + 1023) / 1024 : A.nchunks;
+        const long long per = (nch + G - 1) / G;
+        const long long beg = blockIdx.x * per, end = beg + per < nch ? beg + per : nch;
         for (long long i = beg + threadIdx.x; i < end; i += kRecordThreads) {
             const double2 v = pe[i];
             b += v.x;
@@ -580,6 +615,8 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     __syncthreads();
     if (threadIdx.x != 0) return;
     ds->record_done = 0u;
+    ds->eticket[0] = 0u;
+    ds->eticket[1] = 0u;
     const double dphi = s_a[0], sp = s_b[0], s2 = s_c[0];
     if (A.mode == 2) {
         A.report[0] = sp;
@@ -626,7 +663,8 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const int blocks = (int)energy_blocks(c);
     const double hp = c->h / c->cfg.energy_R;
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
-    int* fcount = (int*)(c->front + (size_t)blocks * kEnergyCand);
+    const long long slots_cap = energy_slots(c) > 0 ? energy_slots(c) : 1;  // as allocated
+    int* fcount = (int*)(c->front + (size_t)slots_cap * kEnergyCand);
     const int* ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;  // the list changes every iteration
     k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
                                                                ncells_dev, offset, c->front, fcount, c->ds,
@@ -634,12 +672,14 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     int* tile_cnt = c->cfg.band ? c->tile_off : nullptr;
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
-            p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds, check_stop);
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, ncells, ncells_dev,
+            c->cfg.energy_R, c->h, p, p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds,
+            check_stop);
     else
         k_energy<T, DIM, INTERP, 0><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, c->cfg.energy_R, c->h, p,
-            p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds, check_stop);
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, ncells, ncells_dev,
+            c->cfg.energy_R, c->h, p, p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds,
+            check_stop);
     c->launches += 2;  // front cells, then energy
     return cudaGetLastError();
 }
@@ -673,7 +713,8 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     RecordArgs A;
     A.part_dphi = c->cfg.reinit ? c->part_dphi_r : c->part_dphi;
     A.part_e = c->part_e;
-    A.nchunks = energy_blocks(c);
+    A.nchunks = energy_slots(c);
+    A.ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;
     A.n_dphi_full = c->cfg.reinit ? reinit_grid(c) : full_step_blocks(c);
     A.N = c->N;
     A.full_grid = !c->cfg.band;

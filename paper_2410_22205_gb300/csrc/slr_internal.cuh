@@ -36,6 +36,7 @@ struct DevState {
     int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
     unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
     unsigned record_done;  // blocks of the record kernel done (reset by its last block)
+    unsigned eticket[2];   // slot tickets of the front-cell and energy kernels (reset by the record kernel)
     int band_next;       // size of the band the next step writes (sum of the tile counts)
     int band_sl;         // with reinitialisation: band nodes the SL step of this iteration updated
     int n_ecells_dyn;    // with reinitialisation: candidate cells of the energy pass
