@@ -320,10 +320,12 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants and dist.rank == 0:
-        for prec, interp, band, label in ((32, 0, 1, "q1_fp32_band"), (64, 1, 1, "weno_fp64_band"),
-                                          (64, 0, 1, "q1_fp64_band"), (32, 1, 0, "weno_fp32_fullgrid"),
-                                          (32, 0, 0, "q1_fp32_fullgrid")):
-            r2 = slr.Reconstruction(dim=3, n=n, precision=prec, interp=interp, band=band, **cfg_kw())
+        for prec, interp, band, rei, label in ((32, 0, 1, 0, "q1_fp32_band"), (64, 1, 1, 0, "weno_fp64_band"),
+                                               (64, 0, 1, 0, "q1_fp64_band"), (32, 1, 0, 0, "weno_fp32_fullgrid"),
+                                               (32, 0, 0, 0, "q1_fp32_fullgrid"),
+                                               (32, 1, 1, 1, "weno_fp32_band_reinit"),
+                                               (32, 0, 1, 1, "q1_fp32_band_reinit")):
+            r2 = slr.Reconstruction(dim=3, n=n, precision=prec, interp=interp, band=band, reinit=rei, **cfg_kw())
             r2.load_cloud(cloud)
             r2.build_distance()
             r2.init_sphere(0.9)
@@ -332,14 +334,18 @@ def run_gpu(args):
             sm, km, bd, _ = measure_steps(r2, ks, 2, flush, torch)
             variants[label] = {"value": float(np.sum(bd)) / (float(np.sum(sm)) / 1e3), "ms_per_step": float(np.mean(sm)),
                                "nodes_per_step": float(np.mean(bd)), "kernels_ms": [float(x) for x in np.mean(km, 0)]}
+            if rei:
+                variants[label]["phases_ms"] = {k: float(v) for k, v in
+                                                zip(("step", "reinit", "energy", "record"), r2.last_iteration_phases())}
             r2.close()
     phase_s["variants"] = time.time() - t_ph
     t_ph = time.time()
 
-    e2e = None
+    e2e = e2e_alg1 = None
     solve_lat = None
     if args.e2e_jobs > 0:
         e2e, solve_lat = run_e2e(args, cloud, slr, torch)
+        e2e_alg1, _ = run_e2e(args, cloud, slr, torch, reinit=1)
     phase_s["e2e"] = time.time() - t_ph
     t_ph = time.time()
 
@@ -367,7 +373,7 @@ def run_gpu(args):
                        "points": args.points, "interp": "WENO", "band": "6h", "p": 2, "delta": 1,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{dist.world}",
                        "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_algorithm1_reinit": e2e_alg1,
             "latency": {"iteration": iter_lat, "solve": solve_lat},
             "variants": variants, "batched": batched, "serving": serving, "gpu_launches": int(launches), "clocks": clk,
             "setup_s": time.time() - t_setup, "phase_s": phase_s,
@@ -376,10 +382,13 @@ def run_gpu(args):
     dist.close()
 
 
-def run_e2e(args, cloud, slr, torch):
+def run_e2e(args, cloud, slr, torch, reinit=0):
     """Whole jobs through the public API with host buffers: pinned host cloud
     -> load (H2D) -> exact distance grid -> φ^0 -> evolve to the stop test ->
-    extract |φ| < 2h (D2H). Timed by the host clock around each job."""
+    extract |φ| < 2h (D2H). Timed by the host clock around each job. With
+    reinit = 1 every iteration also runs Algorithm 1 step 4d (§3.7), so the
+    band follows the front; the error on the cloud (eq. errCloud) of the
+    result is reported next to the rate."""
     pinned = torch.empty(cloud.shape, dtype=torch.float64, pin_memory=True)
     pinned.numpy()[:] = cloud
     host = pinned.numpy()
@@ -388,26 +397,28 @@ def run_e2e(args, cloud, slr, torch):
     for j in range(args.e2e_jobs + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rec = slr.Reconstruction(dim=3, n=args.n, precision=32, interp=1, band=1, **cfg_kw())
+        rec = slr.Reconstruction(dim=3, n=args.n, precision=32, interp=1, band=1, reinit=reinit, **cfg_kw())
         rec.load_cloud(host)
         rec.build_distance()
         rec.init_sphere(0.9)
         it, conv = rec.evolve()
         idx, val = rec.extract(2 * h)
         t1 = time.perf_counter()
-        diag = rec.diagnostics()
+        diag = rec.diagnostics(err_cloud=True)
         rec.close()
         if j == 0:
             continue  # first job warms the allocator and the graph instantiation path
         times.append(t1 - t0)
+        err_s = diag["err_cloud"]
         units += float(np.sum(diag["band"]))
         h2d += host.nbytes
         d2h += idx.nbytes + val.nbytes
         iters.append(it)
     jobs = len(times)
     e2e = {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d // jobs, "d2h_bytes_per_step": d2h // jobs,
-           "step": "one whole job (H2D cloud, distance grid, init, evolve to the stop test, extract, D2H)",
-           "jobs": jobs, "iterations_per_job": iters}
+           "step": "one whole job (H2D cloud, distance grid, init, evolve to the stop test, extract, D2H)"
+                   + (", Algorithm 1 with the reinitialisation of §3.7 every iteration" if reinit else ""),
+           "jobs": jobs, "iterations_per_job": iters, "err_cloud_over_h": err_s / h}
     lat = {"p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)), "jobs": jobs}
     return e2e, lat
 

@@ -328,33 +328,58 @@ __global__ void __launch_bounds__(kRB) k_reinit_sweep(Params<T> P, T* ub0, T* ub
     const T* __restrict__ X = phase ? uout : W;
     T* __restrict__ Y = phase ? W : uout;
     const int st[3] = {1, P.is1, P.is2};
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < cnt; p += stride) {
-        const int j = G[p];
-        const unsigned f = rfl[p];
-        const T x = X[j];
-        if (f & 1u) {
-            Y[j] = x;
-            continue;
-        }
-        const bool pos = (f >> 1) == 1u;
-        T s2 = T(0);
+    // four positions per thread, p, p + S, p + 2S, p + 3S (S = threads of the
+    // grid): all their loads are issued before any store
+    constexpr int K = 4;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    for (long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; p0 < cnt; p0 += K * S) {
+        int j[K];
+        unsigned f[K];
+        T x[K], nb[K][2 * DIM];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            const T am = (x - X[j - st[a]]) * P.inv_h;
-            const T bp = (X[j + st[a]] - x) * P.inv_h;
-            T t1, t2;
-            if (pos) {
-                t1 = fmax(am, T(0));
-                t2 = fmin(bp, T(0));
-            } else {
-                t1 = fmin(am, T(0));
-                t2 = fmax(bp, T(0));
-            }
-            s2 += fmax(t1 * t1, t2 * t2);
+        for (int k = 0; k < K; ++k) {
+            const long long p = p0 + k * S;
+            const bool v = p < cnt;
+            j[k] = v ? G[p] : 0;
+            f[k] = v ? (unsigned)rfl[p] : 1u;
         }
-        const T sgn_dt = pos ? dtau : -dtau;
-        Y[j] = x - sgn_dt * (sqrt(s2) - T(1));
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            x[k] = X[j[k]];
+            if (!(f[k] & 1u)) {
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    nb[k][2 * a] = X[j[k] - st[a]];
+                    nb[k][2 * a + 1] = X[j[k] + st[a]];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (p0 + k * S >= cnt) break;
+            if (f[k] & 1u) {
+                Y[j[k]] = x[k];
+                continue;
+            }
+            const bool pos = (f[k] >> 1) == 1u;
+            T s2 = T(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const T am = (x[k] - nb[k][2 * a]) * P.inv_h;
+                const T bp = (nb[k][2 * a + 1] - x[k]) * P.inv_h;
+                T t1, t2;
+                if (pos) {
+                    t1 = fmax(am, T(0));
+                    t2 = fmin(bp, T(0));
+                } else {
+                    t1 = fmin(am, T(0));
+                    t2 = fmax(bp, T(0));
+                }
+                s2 += fmax(t1 * t1, t2 * t2);
+            }
+            const T sgn_dt = pos ? dtau : -dtau;
+            Y[j[k]] = x[k] - sgn_dt * (sqrt(s2) - T(1));
+        }
     }
 }
 
@@ -373,14 +398,29 @@ __global__ void __launch_bounds__(kRB) k_reinit_final(Params<T> P, T* ub0, T* ub
     T* uout = (n & 1) ? ub0 : ub1;
     const T* R = (M & 1) ? uout : W;
     T acc = T(0);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < cnt; p += stride) {
-        const int j = G[p];
-        const T v = fmin(fmax(R[j], -P.gamma), P.gamma);  // eq. cut
-        acc += fabs(v - uin[j]);
-        uin[j] = v;
-        uout[j] = v;
-        W[j] = v;
+    // R is W or the output buffer, both written here: each thread loads its
+    // four positions' values before it stores any of them
+    constexpr int K = 4;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    for (long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; p0 < cnt; p0 += K * S) {
+        int j[K];
+        T r[K], o[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) j[k] = p0 + k * S < cnt ? G[p0 + k * S] : -1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            r[k] = j[k] >= 0 ? R[j[k]] : T(0);
+            o[k] = j[k] >= 0 ? uin[j[k]] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (j[k] < 0) break;
+            const T v = fmin(fmax(r[k], -P.gamma), P.gamma);  // eq. cut
+            acc += fabs(v - o[k]);
+            uin[j[k]] = v;
+            uout[j[k]] = v;
+            W[j[k]] = v;
+        }
     }
     const double t = (double)warp_sum(acc);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
