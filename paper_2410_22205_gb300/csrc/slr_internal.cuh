@@ -408,6 +408,12 @@ __device__ T sl_update(const Params<T>& P, const T* __restrict__ u, const T* __r
     T bx = adv * ddx, by = adv * ddy, bz = adv * ddz;
     T s = sqrt(C * P.delta * dj * P.dt * P.inv_p) * P.inv_h;
     if (DIM == 2) {
+        if (s == T(0)) {
+            // δ = 0 (or C d = 0): the feet coincide; the same sum of equal terms
+            const T r[3] = {bx, by, T(0)};
+            const T f = interp_at<T, DIM, INTERP>(P, u, i, j, k, r);
+            return (f + f) * T(0.5);
+        }
         T sx = gy / gn, sy = -gx / gn;  // eq. sigma2d
         T r0[3] = {bx - s * sx, by - s * sy, T(0)};
         T r1[3] = {bx + s * sx, by + s * sy, T(0)};
@@ -427,14 +433,19 @@ __device__ T sl_update(const Params<T>& P, const T* __restrict__ u, const T* __r
         n2y = ig * rr;
         n2z = ig * (-gy * gz / rr);
     }
-    T acc = T(0);
+    // δ = 0 (or C d = 0): the four feet coincide, so one interpolation
+    // serves all of them, summed as in the general case
+    const int nfeet = s == T(0) ? 1 : 4;
+    T acc = T(0), last = T(0);
 #pragma unroll 1
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < nfeet; ++f) {
         T l1 = (f & 2) ? T(1) : T(-1);
         T l2 = (f & 1) ? T(1) : T(-1);
         T r[3] = {bx + s * (l1 * n1x + l2 * n2x), by + s * (l1 * n1y + l2 * n2y), bz + s * (l1 * n1z + l2 * n2z)};
-        acc += interp_at<T, DIM, INTERP>(P, u, i, j, k, r);
+        last = interp_at<T, DIM, INTERP>(P, u, i, j, k, r);
+        acc += last;
     }
+    if (nfeet == 1) acc = ((last + last) + last) + last;
     return acc * T(0.25);
 }
 
