@@ -103,6 +103,8 @@ def lib():
                                                C.c_int, C.c_double, _dp, _dp, _ip]),
                 "or_reinit": (C.c_longlong, [_P, _dp, _dp, C.c_int, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
                 "or_reinit_sweeps": (C.c_int, [_P]),
+                "or_init_marking": (C.c_longlong, [_P, _dp, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
+                "or_fsm_solve": (C.c_double, [_dp, C.c_int, C.c_double]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
                 "or_set_threads": (C.c_int, [C.c_int]),
@@ -320,6 +322,21 @@ def reinit(P, phi_band, phi_tilde, sweeps=0, dtau=0.0):
     m = lib().or_reinit(C.byref(P), pbp, ptp, int(sweeps), float(dtau), out.ctypes.data_as(_dp),
                         flags.ctypes.data_as(C.POINTER(C.c_ubyte)))
     return out, flags, int(m)
+
+
+def init_marking(P, d, gamma_s):
+    """§3.6 initial data from the distance field: returns (φ0, external flags)."""
+    d, dp = _d(d)
+    out = np.empty_like(d)
+    ext = np.zeros(d.shape[0], dtype=np.uint8)
+    lib().or_init_marking(C.byref(P), dp, float(gamma_s), out.ctypes.data_as(_dp),
+                          ext.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    return out, ext
+
+
+def fsm_solve(a, h):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return float(lib().or_fsm_solve(a.ctypes.data_as(_dp), int(a.size), float(h)))
 
 
 def reinit_sweeps(P):

@@ -904,6 +904,126 @@ long long or_reinit(const or_params* g, const double* phi_band, const double* ph
     return m;
 }
 
+/* ------------------------------------------------------------------ */
+/* §3.6 initial data: external marking, then fast sweeping               */
+/* ------------------------------------------------------------------ */
+
+/* Readings (the paper describes the steps in words):
+ *  - marking: every node on the grid boundary is external; then one round of
+ *    directional sweeps along the grid lines, in the order +x, -x, +y, -y
+ *    (+z, -z): a sweep in direction +x visits each line in increasing x and
+ *    marks a node external when the node before it is external and its own
+ *    d >= γ_S ("until we find a point for which d < γ_S"). The paper
+ *    iterates the round only in parallel runs, to reproduce this serial
+ *    result;
+ *  - φ0 = d - γ_S on external nodes, 1e30 (the "artificially high value")
+ *    on the others;
+ *  - fast sweeping (Zhao 2005) on the internal nodes: Gauss-Seidel sweeps in
+ *    the 2^dim orderings (x, y, z each increasing or decreasing; the sign
+ *    patterns in binary order, bit a set = axis a decreasing, x fastest in
+ *    every ordering), two rounds; the update is the Godunov local solution
+ *    of |∇φ| = 1 with a_a = min(φ_{j-e_a}, φ_{j+e_a}) (the one that exists on
+ *    the boundary), sorted a_1 <= a_2 <= a_3:
+ *      x = a_1 + h; if x > a_2: x = (a_1 + a_2 + sqrt(2h² - (a_1 - a_2)²))/2;
+ *      if x > a_3 (3-D): x = (s + sqrt(s² - 3(a_1² + a_2² + a_3² - h²)))/3,
+ *      s = a_1 + a_2 + a_3; and φ_j = min(φ_j, x); external nodes keep theirs;
+ *  - finally φ0 = -φ on the internal nodes.
+ * out: φ0 on every node; ext_out (may be NULL): 1 on external nodes.
+ * Returns the number of external nodes. */
+/* Godunov local solution of |∇φ| = 1 from the per-axis upwind values a[0..m) */
+double or_fsm_solve(const double* a_in, int m, double h) {
+    double a[3];
+    for (int i = 0; i < m; ++i) a[i] = a_in[i];
+    /* sort ascending (insertion, at most 3 values) */
+    for (int i = 1; i < m; ++i)
+        for (int j = i; j > 0 && a[j] < a[j - 1]; --j) {
+            double t = a[j];
+            a[j] = a[j - 1];
+            a[j - 1] = t;
+        }
+    double x = a[0] + h;
+    if (m > 1 && x > a[1]) {
+        double df = a[0] - a[1];
+        x = (a[0] + a[1] + sqrt(2.0 * h * h - df * df)) / 2.0;
+        if (m > 2 && x > a[2]) {
+            double sm = a[0] + a[1] + a[2];
+            double q = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] - h * h;
+            x = (sm + sqrt(sm * sm - 3.0 * q)) / 3.0;
+        }
+    }
+    return x;
+}
+
+static double fsm_local(const or_params* g, const double* v, long long idx, const long long c[3],
+                        const long long stride[3]) {
+    double a[3];
+    int m = 0;
+    for (int ax = 0; ax < g->dim; ++ax) {
+        double lo = c[ax] > 0 ? v[idx - stride[ax]] : INFINITY;
+        double hi = c[ax] < g->n[ax] - 1 ? v[idx + stride[ax]] : INFINITY;
+        a[m++] = lo < hi ? lo : hi;
+    }
+    return or_fsm_solve(a, m, g->h);
+}
+
+long long or_init_marking(const or_params* g, const double* d, double gamma_s, double* out, unsigned char* ext_out) {
+    long long N = or_num_nodes(g);
+    long long n[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    unsigned char* ext = (unsigned char*)calloc((size_t)N, 1);
+    for (long long k = 0; k < n[2]; ++k)
+        for (long long j = 0; j < n[1]; ++j)
+            for (long long i = 0; i < n[0]; ++i) {
+                int b = i == 0 || i == n[0] - 1 || j == 0 || j == n[1] - 1;
+                if (g->dim == 3) b = b || k == 0 || k == n[2] - 1;
+                if (b) ext[i + stride[1] * j + stride[2] * k] = 1;
+            }
+    /* one round of directional sweeps */
+    for (int ax = 0; ax < g->dim; ++ax)
+        for (int dir = 0; dir < 2; ++dir) {
+            int o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
+            for (long long q2 = 0; q2 < n[o2]; ++q2)
+                for (long long q1 = 0; q1 < n[o1]; ++q1) {
+                    long long base = q1 * stride[o1] + q2 * stride[o2];
+                    for (long long t = 1; t < n[ax]; ++t) {
+                        long long cur = dir == 0 ? t : n[ax] - 1 - t;
+                        long long prev = dir == 0 ? t - 1 : n[ax] - t;
+                        long long ic = base + cur * stride[ax], ip = base + prev * stride[ax];
+                        if (!ext[ic] && ext[ip] && d[ic] >= gamma_s) ext[ic] = 1;
+                    }
+                }
+        }
+    long long next = 0;
+    for (long long i = 0; i < N; ++i) {
+        out[i] = ext[i] ? d[i] - gamma_s : 1e30;
+        next += ext[i];
+    }
+    /* fast sweeping on the internal nodes */
+    int nord = 1 << g->dim;
+    for (int round = 0; round < 2; ++round)
+        for (int o = 0; o < nord; ++o) {
+            long long c[3];
+            for (long long kk = 0; kk < n[2]; ++kk) {
+                c[2] = (o & 4) ? n[2] - 1 - kk : kk;
+                for (long long jj = 0; jj < n[1]; ++jj) {
+                    c[1] = (o & 2) ? n[1] - 1 - jj : jj;
+                    for (long long ii = 0; ii < n[0]; ++ii) {
+                        c[0] = (o & 1) ? n[0] - 1 - ii : ii;
+                        long long idx = c[0] + stride[1] * c[1] + stride[2] * c[2];
+                        if (ext[idx]) continue;
+                        double x = fsm_local(g, out, idx, c, stride);
+                        if (x < out[idx]) out[idx] = x;
+                    }
+                }
+            }
+        }
+    for (long long i = 0; i < N; ++i)
+        if (!ext[i]) out[i] = -out[i];
+    if (ext_out) memcpy(ext_out, ext, (size_t)N);
+    free(ext);
+    return next;
+}
+
 int or_evolve(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
               int min_iters, int max_iters, double* E2_hist, double* dphi_hist, int* converged) {
     return or_evolve_reinit(g, u, d, R, stop_tol, kmax, min_iters, max_iters, 0, 0, 0.0, E2_hist, dphi_hist, converged);

@@ -139,6 +139,16 @@ int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, doub
                      int min_iters, int max_iters, int reinit, int sweeps, double dtau, double* E2_hist,
                      double* dphi_hist, int* converged);
 
+/* §3.6 initial data: external marking from the grid boundary through nodes
+ * with d >= gamma_s, φ0 = d - gamma_s there, fast sweeping of |∇φ| = 1 on
+ * the other nodes, whose sign is then reversed (readings in slr_oracle.c).
+ * out: every node; ext_out (may be NULL): 1 on external nodes. Returns the
+ * number of external nodes. */
+long long or_init_marking(const or_params* g, const double* d, double gamma_s, double* out, unsigned char* ext_out);
+/* the Godunov local solution of |∇φ| = 1 used by the sweeps, from the m
+ * per-axis upwind values a[0..m) (m = 1..3) */
+double or_fsm_solve(const double* a, int m, double h);
+
 /* nodes with |φ| < width, ascending index */
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out);
 

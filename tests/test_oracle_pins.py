@@ -640,3 +640,128 @@ def test_evolve_with_reinit_moves_the_band_to_a_far_cloud():
     moved = O.evolve(P, u0, d, max_iters=80, min_iters=80, reinit=True)
     assert O.err_cloud(P, plain["u"], pts) > 0.99 * P.gamma
     assert O.err_cloud(P, moved["u"], pts) < P.h
+
+
+# ---------------------------------------------------------------- initial data (§3.6)
+
+def test_init_marking_planar_cloud_closed_form():
+    """d = |z - z0| (a plane of points): nodes with d >= γ_S reach the grid
+    boundary and are external, with φ0 = d - γ_S; every boundary node is
+    external too. Away from the side faces (where the slab's boundary nodes,
+    external with d - γ_S < 0, feed the sweeps; their influence is gone 12
+    cells in) fast sweeping is exact in the slab: the node m layers inside
+    the nearer external layer gets -(φ_e + m h), φ_e that layer's value."""
+    P = _grid_params(3, 33)
+    X = O.node_coords(P)
+    z0, gs = 0.013, 0.21
+    d = np.abs(X[:, 2] - z0)
+    phi, ext = O.init_marking(P, d, gs)
+    n = int(P.n[0])
+    ijk = np.rint((X - P.lo[0]) / P.h).astype(int)
+    side = np.any((ijk[:, :2] == 0) | (ijk[:, :2] == n - 1), axis=1) | (ijk[:, 2] == 0) | (ijk[:, 2] == n - 1)
+    assert np.array_equal(ext == 1, (d >= gs) | side)
+    np.testing.assert_allclose(phi[ext == 1], d[ext == 1] - gs, rtol=0, atol=0)
+    zs = P.lo[2] + np.arange(n) * P.h
+    lo_ext = np.max(np.where((np.abs(zs - z0) >= gs) & (zs < z0))[0])
+    hi_ext = np.min(np.where((np.abs(zs - z0) >= gs) & (zs > z0))[0])
+    expected = np.full(n, np.nan)
+    for k in range(lo_ext + 1, hi_ext):
+        a = (abs(zs[lo_ext] - z0) - gs) + (k - lo_ext) * P.h
+        b = (abs(zs[hi_ext] - z0) - gs) + (hi_ext - k) * P.h
+        expected[k] = -min(a, b)
+    central = np.all((ijk[:, :2] >= 12) & (ijk[:, :2] <= n - 13), axis=1) & (ext == 0)
+    assert central.sum() > 100
+    np.testing.assert_allclose(phi[central], expected[ijk[central, 2]], rtol=0, atol=1e-15)
+
+
+def test_init_marking_sphere_shell():
+    """d = ||x| - R| (points on a sphere): the outside with d >= γ_S is
+    external; the shell and the enclosed interior (d >= γ_S but cut off from
+    the boundary) are internal and negative; near the offset surface
+    |x| = R + γ_S, φ0 is within 2h of its signed distance."""
+    P = _grid_params(3, 33)
+    X = O.node_coords(P)
+    R, gs = 0.5, 0.1
+    r = np.linalg.norm(X, axis=1)
+    d = np.abs(r - R)
+    phi, ext = O.init_marking(P, d, gs)
+    assert np.all(ext[r >= R + gs + 1e-12] == 1)
+    assert np.all(ext[r < R + gs - 1e-12] == 0)
+    assert np.all(phi[ext == 0] < 0) and np.all(phi[ext == 1] >= 0)
+    near = np.abs(r - (R + gs)) < 4 * P.h
+    assert np.abs(phi[near] - (r[near] - R - gs)).max() <= 2 * P.h
+
+
+def _sweep_marking(d, gs):
+    """The marking rule written out in plain Python on a 2-D grid (y rows, x
+    columns): boundary external; one round of sweeps +x, -x, +y, -y."""
+    ny, nx = d.shape
+    ext = np.zeros_like(d, dtype=bool)
+    ext[0, :] = ext[-1, :] = ext[:, 0] = ext[:, -1] = True
+    for ax, step in ((1, 1), (1, -1), (0, 1), (0, -1)):
+        rng = range(1, (nx if ax == 1 else ny)) if step == 1 else range((nx if ax == 1 else ny) - 2, -1, -1)
+        for t in rng:
+            if ax == 1:
+                prev = ext[:, t - step]
+                ext[:, t] |= prev & (d[:, t] >= gs)
+            else:
+                prev = ext[t - step, :]
+                ext[t, :] |= prev & (d[t, :] >= gs)
+    return ext
+
+
+def _flood(d, gs):
+    ny, nx = d.shape
+    ext = np.zeros_like(d, dtype=bool)
+    stack = [(y, x) for y in range(ny) for x in range(nx) if y in (0, ny - 1) or x in (0, nx - 1)]
+    for y, x in stack:
+        ext[y, x] = True
+    while stack:
+        y, x = stack.pop()
+        for yy, xx in ((y + 1, x), (y - 1, x), (y, x + 1), (y, x - 1)):
+            if 0 <= yy < ny and 0 <= xx < nx and not ext[yy, xx] and d[yy, xx] >= gs:
+                ext[yy, xx] = True
+                stack.append((yy, xx))
+    return ext
+
+
+def test_init_marking_follows_the_sweep_rule_on_a_hook():
+    """A 2-D wall shaped like a hook: the marking equals the sweep rule written
+    out in Python, is contained in the flood fill of {d >= γ_S} from the
+    boundary, and misses the pocket behind the hook, which one round of
+    straight sweeps cannot reach (the paper's serial marking)."""
+    n = 40
+    P = _grid_params(2, n)
+    X = O.node_coords(P)
+    x, y = X[:, 0].reshape(n, n), X[:, 1].reshape(n, n)
+    # walls: a square ring with an opening on the right, and a hook inside
+    walls = np.zeros((n, n), dtype=bool)
+    walls[8, 8:32] = walls[31, 8:32] = walls[8:32, 8] = True
+    walls[8:20, 31] = True
+    walls[14, 14:31] = walls[14:26, 14] = True
+    pts = np.stack([x[walls], y[walls]], axis=1)
+    d, _ = O.distance(P, pts)
+    gs = 0.5 * P.h
+    phi, ext = O.init_marking(P, d, gs)
+    ref = _sweep_marking(d.reshape(n, n), gs)
+    assert np.array_equal(ext.reshape(n, n) == 1, ref)
+    flood = _flood(d.reshape(n, n), gs)
+    assert np.all(flood[ref]) and (flood & ~ref).sum() > 0
+
+
+def test_fsm_local_solution_solves_the_upwind_equation():
+    """The local solver of the fast sweeping method returns the x with
+    Σ_{a_i < x} (x - a_i)^2 = h^2 (Godunov's upwind |∇φ| = 1, Zhao 2005):
+    checked on random values in 1, 2 and 3 dimensions, and the largest
+    value left out is >= x."""
+    rng = np.random.default_rng(12)
+    h = 0.1
+    for m in (1, 2, 3):
+        for _ in range(300):
+            a = rng.uniform(0.0, 2.5 * h, m)
+            x = O.fsm_solve(a, h)
+            act = a < x
+            assert act.sum() >= 1
+            assert abs(np.sum((x - a[act]) ** 2) - h * h) <= 1e-14
+            assert np.all(a[~act] >= x)
+    assert O.fsm_solve([0.0, 0.0, 0.0], h) == pytest.approx(h / math.sqrt(3), abs=1e-16)
