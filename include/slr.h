@@ -113,7 +113,16 @@ slr_status slr_set_distance(slr_ctx* ctx, const double* d_host);
 
 /* Algorithm 1 step 3: initial level set φ^0.
  *  kind 0 (sphere): params = {cx, cy, cz, r}; φ^0 = |x - c| - r (FP64, rounded to storage);
- *  kind 1 (array):  u0_host = FP64 values of all nodes.
+ *  kind 1 (array):  u0_host = FP64 values of all nodes;
+ *  kind 2 (§3.6, from the cloud): params = {γ_S}: nodes on the grid boundary
+ *    are external, the marking spreads along the grid lines (one round of
+ *    sweeps +x, -x, +y, -y, +z, -z) through nodes with d >= γ_S; φ^0 = d - γ_S
+ *    on external nodes, and the fast sweeping method (|∇φ| = 1, Godunov
+ *    local solver, two rounds of 2^dim orderings) fills the other nodes, whose
+ *    sign is then reversed: a signed distance whose zero set encloses the
+ *    cloud at about γ_S from it. The paper takes γ_S = K_S h_S, h_S the mean
+ *    nearest-neighbour spacing of the cloud and K_S = 2. Computed in FP64
+ *    (slr_init_u holds N doubles and N bytes of scratch while it runs).
  * In band mode the cut of eq. cut is applied, so |φ^0| <= γ holds before the
  * first step; the band G̃^0 (eq. subgrid, |φ| < γ) and the list of cells the
  * energy quadrature may visit are built here. Resets the iteration count and

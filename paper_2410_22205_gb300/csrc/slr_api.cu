@@ -410,7 +410,9 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
     if (!c->have_d) return fail(c, SLR_E_STATE, "init_u: distance field not set");
     if (kind == 0 && !params) return fail(c, SLR_E_INVALID, "init_u: sphere needs {cx,cy,cz,r}");
     if (kind == 1 && !u0_host) return fail(c, SLR_E_INVALID, "init_u: array needs u0_host");
-    if (kind != 0 && kind != 1) return fail(c, SLR_E_INVALID, "init_u: kind must be 0 or 1");
+    if (kind == 2 && !(params && params[0] > 0.0))
+        return fail(c, SLR_E_INVALID, "init_u: external marking needs {gamma_s > 0}");
+    if (kind < 0 || kind > 2) return fail(c, SLR_E_INVALID, "init_u: kind must be 0, 1 or 2");
     DeviceGuard g(c->device);
     free_graphs(c);
     c->have_u = false;
@@ -427,7 +429,21 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
             return cuda_fail(c, e, "init_u copy");
         }
     }
-    cudaError_t e = launch_init_u(c, kind, prm, tmp);
+    if (kind == 2) {
+        // §3.6: φ0 from d by external marking and fast sweeping (FP64), then
+        // the array path (storage type, cut)
+        tmp = (double*)dev_alloc(c, sizeof(double) * c->N);
+        unsigned char* ext = (unsigned char*)dev_alloc(c, (size_t)c->N);
+        cudaError_t e = (tmp && ext) ? launch_init_marking(c, params[0], tmp, ext) : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, ext);
+        if (e != cudaSuccess) {
+            dev_free(c, tmp);
+            if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "init_u: marking buffers");
+            return cuda_fail(c, e, "init_u marking");
+        }
+    }
+    cudaError_t e = launch_init_u(c, kind == 2 ? 1 : kind, prm, tmp);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, tmp);

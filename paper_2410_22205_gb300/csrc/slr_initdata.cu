@@ -1,0 +1,186 @@
+// §3.6 initial data from the distance field: external marking, then the
+// fast sweeping method of Zhao (2005) on the internal nodes, whose sign is
+// then reversed. The result is an FP64 field that slr_init_u passes through
+// the array path (storage type, eq. cut in band mode).
+//
+// Readings (the paper describes the steps in words):
+//  - every node on the grid boundary is external; then one round of
+//    directional sweeps along the grid lines, +x, -x, +y, -y (+z, -z): a sweep
+//    in direction +x visits each line in increasing x and marks a node
+//    external when the node before it is external and its own d >= γ_S;
+//  - φ0 = d - γ_S on external nodes, 1e30 on the others;
+//  - fast sweeping on the internal nodes: Gauss-Seidel sweeps in the 2^dim
+//    orderings (bit a of the ordering set = axis a decreasing), two rounds,
+//    with Godunov's local solution of |∇φ| = 1 and φ_j = min(φ_j, x);
+//  - finally φ0 = -φ on the internal nodes.
+//
+// A sweep in one ordering visits the nodes plane by plane, ii + jj + kk = s
+// in the ordering's own coordinates: every upwind neighbour of a node lies on
+// an earlier plane and every downwind neighbour on a later one, as in the
+// lexicographic order, so the values (and the result) are the same; the nodes
+// of one plane are independent and run in parallel. The local solver uses
+// explicitly rounded FP64 operations in the order of its definition.
+#include "slr_internal.cuh"
+
+namespace slr {
+
+namespace {
+
+constexpr int kIB = 256;
+
+__global__ void k_mark_boundary(unsigned char* ext, int n0, int n1, int n2, int dim, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) {
+        const int i = (int)(j % n0);
+        const long long q = j / n0;
+        const int y = (int)(q % n1), z = (int)(q / n1);
+        bool b = i == 0 || i == n0 - 1 || y == 0 || y == n1 - 1;
+        if (dim == 3) b = b || z == 0 || z == n2 - 1;
+        ext[j] = b ? 1 : 0;
+    }
+}
+
+// one directional sweep along axis `ax` (dir 0 increasing, 1 decreasing):
+// one thread per grid line
+template <typename T>
+__global__ void k_mark_sweep(unsigned char* ext, const T* __restrict__ d, double gamma_s, int ax, int dir, int n0,
+                             int n1, int n2) {
+    const int n[3] = {n0, n1, n2};
+    const long long st[3] = {1, (long long)n0, (long long)n0 * n1};
+    const int o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
+    const long long lines = (long long)n[o1] * n[o2];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < lines; l += stride) {
+        const int q1 = (int)(l % n[o1]), q2 = (int)(l / n[o1]);
+        const long long base = q1 * st[o1] + q2 * st[o2];
+        unsigned char prev = ext[base + (long long)(dir == 0 ? 0 : n[ax] - 1) * st[ax]];
+        for (int t = 1; t < n[ax]; ++t) {
+            const long long ic = base + (long long)(dir == 0 ? t : n[ax] - 1 - t) * st[ax];
+            unsigned char e = ext[ic];
+            if (!e && prev && (double)d[ic] >= gamma_s) {
+                e = 1;
+                ext[ic] = 1;
+            }
+            prev = e;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_phi_start(double* phi, const unsigned char* __restrict__ ext, const T* __restrict__ d,
+                            double gamma_s, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride)
+        phi[j] = ext[j] ? __dsub_rn((double)d[j], gamma_s) : 1e30;
+}
+
+// Godunov local solution from the per-axis upwind values a[0..m)
+__device__ double fsm_solve(double a0, double a1, double a2, int m, double h) {
+    double a[3] = {a0, a1, a2};
+    for (int i = 1; i < m; ++i)
+        for (int j = i; j > 0 && a[j] < a[j - 1]; --j) {
+            const double t = a[j];
+            a[j] = a[j - 1];
+            a[j - 1] = t;
+        }
+    double x = __dadd_rn(a[0], h);
+    if (m > 1 && x > a[1]) {
+        const double df = __dsub_rn(a[0], a[1]);
+        const double r = __dsub_rn(__dmul_rn(__dmul_rn(2.0, h), h), __dmul_rn(df, df));
+        x = __ddiv_rn(__dadd_rn(__dadd_rn(a[0], a[1]), __dsqrt_rn(r)), 2.0);
+        if (m > 2 && x > a[2]) {
+            const double sm = __dadd_rn(__dadd_rn(a[0], a[1]), a[2]);
+            const double q = __dsub_rn(
+                __dadd_rn(__dadd_rn(__dmul_rn(a[0], a[0]), __dmul_rn(a[1], a[1])), __dmul_rn(a[2], a[2])),
+                __dmul_rn(h, h));
+            const double r3 = __dsub_rn(__dmul_rn(sm, sm), __dmul_rn(3.0, q));
+            x = __ddiv_rn(__dadd_rn(sm, __dsqrt_rn(r3)), 3.0);
+        }
+    }
+    return x;
+}
+
+// the nodes of plane s (ii + jj + kk = s) of ordering `ord`
+template <int DIM>
+__global__ void k_fsm_plane(double* phi, const unsigned char* __restrict__ ext, int ord, int s, int n0, int n1,
+                            int n2, double h) {
+    const long long st1 = n0, st2 = (long long)n0 * n1;
+    const long long count = DIM == 3 ? (long long)n1 * n2 : (long long)n1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+        const int jj = (int)(t % n1), kk = DIM == 3 ? (int)(t / n1) : 0;
+        const int ii = s - jj - kk;
+        if (ii < 0 || ii >= n0) continue;
+        const int c0 = (ord & 1) ? n0 - 1 - ii : ii;
+        const int c1 = (ord & 2) ? n1 - 1 - jj : jj;
+        const int c2 = (ord & 4) ? n2 - 1 - kk : kk;
+        const long long idx = c0 + st1 * c1 + st2 * c2;
+        if (ext[idx]) continue;
+        const double inf = __longlong_as_double(0x7ff0000000000000ll);
+        double a[3];
+        {
+            const double lo = c0 > 0 ? phi[idx - 1] : inf, hi = c0 < n0 - 1 ? phi[idx + 1] : inf;
+            a[0] = lo < hi ? lo : hi;
+        }
+        {
+            const double lo = c1 > 0 ? phi[idx - st1] : inf, hi = c1 < n1 - 1 ? phi[idx + st1] : inf;
+            a[1] = lo < hi ? lo : hi;
+        }
+        if (DIM == 3) {
+            const double lo = c2 > 0 ? phi[idx - st2] : inf, hi = c2 < n2 - 1 ? phi[idx + st2] : inf;
+            a[2] = lo < hi ? lo : hi;
+        } else {
+            a[2] = inf;
+        }
+        const double x = fsm_solve(a[0], a[1], a[2], DIM, h);
+        if (x < phi[idx]) phi[idx] = x;
+    }
+}
+
+__global__ void k_phi_finish(double* phi, const unsigned char* __restrict__ ext, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride)
+        if (!ext[j]) phi[j] = -phi[j];
+}
+
+template <typename T>
+cudaError_t marking_t(slr_ctx* c, double gamma_s, double* phi, unsigned char* ext) {
+    const int n0 = (int)c->cfg.n[0], n1 = (int)c->cfg.n[1], n2 = c->cfg.dim == 3 ? (int)c->cfg.n[2] : 1;
+    const int dim = c->cfg.dim;
+    const int grid = c->num_sms * 8;
+    const T* d = (const T*)c->d;
+    k_mark_boundary<<<grid, kIB, 0, c->stream>>>(ext, n0, n1, n2, dim, c->N);
+    long long launches = 1;
+    for (int ax = 0; ax < dim; ++ax)
+        for (int dir = 0; dir < 2; ++dir) {
+            k_mark_sweep<T><<<grid, kIB, 0, c->stream>>>(ext, d, gamma_s, ax, dir, n0, n1, n2);
+            ++launches;
+        }
+    k_phi_start<T><<<grid, kIB, 0, c->stream>>>(phi, ext, d, gamma_s, c->N);
+    ++launches;
+    const long long count = dim == 3 ? (long long)n1 * n2 : (long long)n1;
+    const int pgrid = (int)((count + kIB - 1) / kIB < grid ? (count + kIB - 1) / kIB : grid);
+    const int planes = n0 + n1 + (dim == 3 ? n2 : 1) - 2;
+    for (int round = 0; round < 2; ++round)
+        for (int ord = 0; ord < (1 << dim); ++ord)
+            for (int s = 0; s < planes; ++s) {
+                if (dim == 3)
+                    k_fsm_plane<3><<<pgrid, kIB, 0, c->stream>>>(phi, ext, ord, s, n0, n1, n2, c->h);
+                else
+                    k_fsm_plane<2><<<pgrid, kIB, 0, c->stream>>>(phi, ext, ord, s, n0, n1, n2, c->h);
+                ++launches;
+            }
+    k_phi_finish<<<grid, kIB, 0, c->stream>>>(phi, ext, c->N);
+    ++launches;
+    c->launches += launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init_marking(slr_ctx* c, double gamma_s, double* phi_dev, unsigned char* ext_dev) {
+    return c->cfg.precision == 32 ? marking_t<float>(c, gamma_s, phi_dev, ext_dev)
+                                  : marking_t<double>(c, gamma_s, phi_dev, ext_dev);
+}
+
+}  // namespace slr

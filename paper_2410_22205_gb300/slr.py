@@ -455,6 +455,10 @@ class Reconstruction:
     def init_array(self, u0):
         slr_init_u(self.ctx, 1, u0=u0)
 
+    def init_marking(self, gamma_s):
+        """§3.6 initial data from the cloud: external marking and fast sweeping."""
+        slr_init_u(self.ctx, 2, params=[float(gamma_s), 0.0, 0.0, 0.0])
+
     def step(self, n=1, energy_override=-1.0):
         slr_step(self.ctx, n, energy_override)
 
