@@ -111,6 +111,14 @@ slr_status slr_build_distance(slr_ctx* ctx);
  * argmin is set to -1. Rounded to the storage precision. */
 slr_status slr_set_distance(slr_ctx* ctx, const double* d_host);
 
+/* Cloud resolution h_S of §4 (eq. dxdt): the mean, over the listed sample of
+ * the cloud (0-based point indices, distinct; the paper draws 10% of the
+ * points at random), of the distance from each sampled point to its nearest
+ * other point of the cloud (a duplicate counts, at distance 0). Needs the
+ * cloud (slr_load_cloud) and at least two points; sample is a host array of
+ * m indices. Exact distances (FP64), summed in sample order. */
+slr_status slr_cloud_spacing(slr_ctx* ctx, const int64_t* sample, int64_t m, double* h_s);
+
 /* Algorithm 1 step 3: initial level set φ^0.
  *  kind 0 (sphere): params = {cx, cy, cz, r}; φ^0 = |x - c| - r (FP64, rounded to storage);
  *  kind 1 (array):  u0_host = FP64 values of all nodes;

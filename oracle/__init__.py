@@ -105,6 +105,7 @@ def lib():
                 "or_reinit_sweeps": (C.c_int, [_P]),
                 "or_init_marking": (C.c_longlong, [_P, _dp, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
                 "or_fsm_solve": (C.c_double, [_dp, C.c_int, C.c_double]),
+                "or_cloud_spacing": (C.c_double, [C.c_int, _dp, C.c_longlong, _lp, C.c_longlong]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
                 "or_set_threads": (C.c_int, [C.c_int]),
@@ -332,6 +333,14 @@ def init_marking(P, d, gamma_s):
     lib().or_init_marking(C.byref(P), dp, float(gamma_s), out.ctypes.data_as(_dp),
                           ext.ctypes.data_as(C.POINTER(C.c_ubyte)))
     return out, ext
+
+
+def cloud_spacing(pts, sample):
+    """h_S of §4: mean distance from each sampled point to its nearest other point."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    smp = np.ascontiguousarray(sample, dtype=np.int64)
+    return float(lib().or_cloud_spacing(int(pts.shape[1]), pts.ctypes.data_as(_dp), int(pts.shape[0]),
+                                        smp.ctypes.data_as(_lp), int(smp.size)))
 
 
 def fsm_solve(a, h):

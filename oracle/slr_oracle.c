@@ -213,11 +213,19 @@ static double kd_box_bound(const kd_tree* t, const kd_node* nd, const double x[3
     return s;
 }
 
+static void kd_query_ex(const kd_tree* t, int id, const double x[3], long long excl, double* best, long long* arg);
+
 static void kd_query(const kd_tree* t, int id, const double x[3], double* best, long long* arg) {
+    kd_query_ex(t, id, x, -1, best, arg);
+}
+
+/* the same search, never returning point excl */
+static void kd_query_ex(const kd_tree* t, int id, const double x[3], long long excl, double* best, long long* arg) {
     const kd_node* nd = &t->nodes[id];
     if (nd->axis < 0) {
         for (long long i = nd->lo; i < nd->hi; ++i) {
             long long q = t->perm[i];
+            if (q == excl) continue;
             const double* Q = t->pts + q * t->dim;
             double s = 0.0;
             for (int a = 0; a < t->dim; ++a) {
@@ -235,8 +243,8 @@ static void kd_query(const kd_tree* t, int id, const double x[3], double* best, 
     const double br = kd_box_bound(t, &t->nodes[nd->right], x);
     const int first = bl <= br ? nd->left : nd->right, second = bl <= br ? nd->right : nd->left;
     const double b1 = bl <= br ? bl : br, b2 = bl <= br ? br : bl;
-    if (!(b1 > *best)) kd_query(t, first, x, best, arg);
-    if (!(b2 > *best)) kd_query(t, second, x, best, arg);
+    if (!(b1 > *best)) kd_query_ex(t, first, x, excl, best, arg);
+    if (!(b2 > *best)) kd_query_ex(t, second, x, excl, best, arg);
 }
 
 void or_distance_kd(const or_params* g, const double* pts, long long npts,
@@ -263,6 +271,37 @@ void or_distance_kd(const or_params* g, const double* pts, long long npts,
     }
     free(t.perm);
     free(t.nodes);
+}
+
+/* §4 (eq. dxdt) cloud resolution h_S: mean over the sample of the distance
+ * from each sampled point to its nearest other point (a duplicate counts, at
+ * distance 0), summed in sample order */
+double or_cloud_spacing(int dim, const double* pts, long long npts, const long long* sample, long long m) {
+    kd_tree t;
+    t.pts = pts;
+    t.dim = dim;
+    t.perm = (long long*)malloc(sizeof(long long) * (size_t)npts);
+    t.nodes = (kd_node*)malloc(sizeof(kd_node) * (size_t)(2 * (npts / 4 + 2)));
+    t.count = 0;
+    for (long long i = 0; i < npts; ++i) t.perm[i] = i;
+    kd_build(&t, 0, npts);
+    double* dist = (double*)malloc(sizeof(double) * (size_t)m);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long long s = 0; s < m; ++s) {
+        const long long p = sample[s];
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < dim; ++a) x[a] = pts[p * dim + a];
+        double best = INFINITY;
+        long long arg = -1;
+        kd_query_ex(&t, 0, x, p, &best, &arg);
+        dist[s] = sqrt(best);
+    }
+    double acc = 0.0;
+    for (long long s = 0; s < m; ++s) acc += dist[s];
+    free(dist);
+    free(t.perm);
+    free(t.nodes);
+    return acc / (double)m;
 }
 
 /* ------------------------------------------------------------------ */

@@ -62,6 +62,10 @@ void or_distance(const or_params* g, const double* pts, long long npts,
 void or_distance_kd(const or_params* g, const double* pts, long long npts,
                     const long long* nodes, long long m, double* d_out, int* arg_out);
 
+/* §4 eq. dxdt: h_S, the mean over the m sampled points of the distance to
+ * their nearest other point (duplicates count, at distance 0) */
+double or_cloud_spacing(int dim, const double* pts, long long npts, const long long* sample, long long m);
+
 /* §3: centred differences; one-sided first-order on the domain boundary */
 void or_gradient(const or_params* g, const double* v, long long idx, double grad[3]);
 

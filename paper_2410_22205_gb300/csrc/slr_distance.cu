@@ -22,8 +22,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "slr_compact.cuh"
 #include "slr_internal.cuh"
@@ -384,7 +386,19 @@ static void launch_search(slr_ctx* c, const SearchArgs& A) {
     c->launches += 1;
 }
 
-cudaError_t build_distance(slr_ctx* c) {
+// the sorted cloud and its box hierarchy (scratch of one search)
+struct CloudIndex {
+    char* base = nullptr;
+    int* flag = nullptr;
+    float4* spt = nullptr;
+    float4* blo = nullptr;
+    float4* bhi = nullptr;
+    int nlevels = 0;
+    long long off[kMaxLevels], cnt[kMaxLevels];
+    double extent = 0.0;
+};
+
+static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     const int dim = c->cfg.dim;
     const long long npts = c->npts;
     cudaStream_t st = c->stream;
@@ -393,7 +407,8 @@ cudaError_t build_distance(slr_ctx* c) {
     const int L = dim == 3 ? 7 : 10;
     const long long nbins = 1ll << (dim * L);
     // box hierarchy sizes
-    long long cnt[kMaxLevels], off[kMaxLevels];
+    long long* cnt = X.cnt;
+    long long* off = X.off;
     int nlevels = 0;
     long long total_boxes = 0;
     {
@@ -408,6 +423,7 @@ cudaError_t build_distance(slr_ctx* c) {
             cc = (cc + 31) / 32;
         }
     }
+    X.nlevels = nlevels;
     const long long nscan_blocks = (nbins + 4095) / 4096;
     // scratch layout
     size_t b_bbox = 64, b_flag = 16, b_codes = sizeof(unsigned) * npts, b_counts = sizeof(int) * nbins,
@@ -417,10 +433,12 @@ cudaError_t build_distance(slr_ctx* c) {
     size_t total = al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes);
     char* base = (char*)dev_alloc(c, total);
     if (!base) return cudaErrorMemoryAllocation;
+    X.base = base;
     char* p = base;
     unsigned long long* bbox = (unsigned long long*)p;
     p += al(b_bbox);
     int* flag = (int*)p;
+    X.flag = flag;
     p += al(b_flag);
     unsigned* codes = (unsigned*)p;
     p += al(b_codes);
@@ -429,9 +447,12 @@ cudaError_t build_distance(slr_ctx* c) {
     int* tot = (int*)p;
     p += al(b_tot);
     float4* spt = (float4*)p;
+    X.spt = spt;
     p += al(b_spt);
     float4* blo = (float4*)p;
     float4* bhi = blo + total_boxes;
+    X.blo = blo;
+    X.bhi = bhi;
 
     unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
     unsigned long long hb[6];
@@ -449,14 +470,8 @@ cudaError_t build_distance(slr_ctx* c) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        dev_free(c, base);
-        return e;
-    }
-    if (hflag) {
-        dev_free(c, base);
-        return cudaErrorInvalidValue;
-    }
+    if (e != cudaSuccess) return e;
+    if (hflag) return cudaErrorInvalidValue;
     BinArgs B;
     double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0}, ext = 0.0;
     for (int a = 0; a < dim; ++a) {
@@ -477,6 +492,7 @@ cudaError_t build_distance(slr_ctx* c) {
         extent = fmax(extent, fabs(bmin[a] - lo));
         extent = fmax(extent, fabs(bmax[a] - lo));
     }
+    X.extent = extent;
     {
         int blocks = (int)((npts + 255) / 256);
         k_codes<<<blocks, 256, 0, st>>>(c->pts, npts, B, codes, counts);
@@ -494,6 +510,25 @@ cudaError_t build_distance(slr_ctx* c) {
         }
         e = cudaGetLastError();
     }
+    return e;
+}
+
+cudaError_t build_distance(slr_ctx* c) {
+    const int dim = c->cfg.dim;
+    const long long npts = c->npts;
+    cudaStream_t st = c->stream;
+    CloudIndex X;
+    cudaError_t e = build_cloud_index(c, X);
+    char* base = X.base;
+    int* flag = X.flag;
+    int hflag = 0;
+    const int nlevels = X.nlevels;
+    const long long* off = X.off;
+    const long long* cnt = X.cnt;
+    float4* spt = X.spt;
+    float4* blo = X.blo;
+    float4* bhi = X.bhi;
+    const double extent = X.extent;
     if (e == cudaSuccess) {
         SearchArgs A;
         A.n0 = (int)c->cfg.n[0];
@@ -776,5 +811,268 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
         return noalloc_fail(SLR_E_CUDA, std::string("distance_grid_noalloc: ") + cudaGetErrorString(e));
     }
     if (hflag & 4) return noalloc_fail(SLR_E_CUDA, "distance_grid_noalloc: traversal stack overflow");
+    return SLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cloud spacing h_S (§4, eq. dxdt): the mean, over a sample of the cloud, of
+// the distance from each sampled point to its nearest other point. The
+// sampled points are queried in the order of the sorted cloud, so that the
+// 32 queries of a warp are neighbours; each lane skips its own point. The
+// distances are those of the distance grid (FP32 screen, exact FP64 check of
+// (x-qx)^2 + (y-qy)^2 + (z-qz)^2); the mean is summed in sample order.
+// ---------------------------------------------------------------------------
+
+namespace slr {
+
+namespace {
+
+struct SampledPred {
+    const float4* spt;
+    const int* mark;
+    __device__ bool operator()(long long t) const { return mark[__float_as_int(spt[t].w)] != 0; }
+};
+
+struct SampledEmit {
+    const float4* spt;
+    const int* mark;
+    int* out;
+    __device__ void operator()(long long pos, long long t) const { out[pos] = mark[__float_as_int(spt[t].w)] - 1; }
+};
+
+__global__ void k_mark_sample(const long long* sample, long long m, int* mark) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (long long)gridDim.x * blockDim.x)
+        mark[sample[s]] = (int)s + 1;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_point_nn(SearchArgs A, const int* __restrict__ qpos,
+                                                  const long long* __restrict__ sample, long long m, double* dist) {
+    __shared__ int s_stack[8][kStack];
+    __shared__ float4 s_leaf[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long qb = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qb * 32 >= m) return;
+    int* stack = s_stack[wib];
+    const long long qi = qb * 32 + lane;
+    const bool valid = qi < m;
+    const long long qs = qpos[valid ? qi : m - 1];
+    const int self = (int)sample[qs];
+    const double* P0 = A.pts + (long long)self * DIM;
+    const double x = P0[0], y = P0[1], z = DIM == 3 ? P0[2] : 0.0;
+    const float xf = (float)(x - A.lo0), yf = (float)(y - A.lo1), zf = DIM == 3 ? (float)(z - A.lo2) : 0.f;
+    const float tlx = warp_minf(xf), tly = warp_minf(yf), tlz = warp_minf(zf);
+    const float thx = warp_maxf(xf), thy = warp_maxf(yf), thz = warp_maxf(zf);
+    const double mscale = 1e-6;
+    double best = INFINITY;
+    float thr = INFINITY, lbound = INFINITY, wb2 = INFINITY;
+    float4* leaf = s_leaf[wib];
+    int sp = 0;
+    {
+        const int top = A.nlevels - 1;
+        const long long c = lane;
+        const bool ex = c < A.cnt[top];
+        const float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[top] + c], A.bhi[A.off[top] + c])
+                            : INFINITY;
+        const unsigned msk = __ballot_sync(0xffffffffu, ex);
+        const int np = __popc(msk);
+        int rank = 0;
+        for (int s = 0; s < 32; ++s) {
+            const float o = __shfl_sync(0xffffffffu, d2, s);
+            if (((msk >> s) & 1u) && (o < d2 || (o == d2 && s < lane))) ++rank;
+        }
+        if (ex) stack[np - 1 - rank] = (top << 27) | (int)c;
+        sp = np;
+        __syncwarp();
+    }
+    while (sp > 0) {
+        --sp;
+        const int ent = stack[sp];
+        __syncwarp();
+        const int lvl = ent >> 27;
+        const long long id = ent & ((1 << 27) - 1);
+        const float bd2 = box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]);
+        if (bd2 > wb2) continue;
+        if (lvl == 0) {
+            {
+                const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
+                const float gx = fmaxf(0.f, fmaxf(blo_.x - xf, xf - bhi_.x));
+                const float gy = fmaxf(0.f, fmaxf(blo_.y - yf, yf - bhi_.y));
+                const float gz = fmaxf(0.f, fmaxf(blo_.z - zf, zf - bhi_.z));
+                const bool need = !(gx * gx + gy * gy + gz * gz > lbound * lbound);
+                if (!__any_sync(0xffffffffu, need)) continue;
+            }
+            const long long base = id * 32;
+            const long long rem = A.npts - base;
+            const int cnt = rem < 32 ? (int)rem : 32;
+            if (lane < cnt) leaf[lane] = A.spt[base + lane];
+            __syncwarp();
+            if (best == INFINITY) {
+                float m2 = INFINITY;
+                for (int s = 0; s < cnt; ++s) {
+                    const float4 q = leaf[s];
+                    if (__float_as_int(q.w) == self) continue;
+                    const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
+                    m2 = fminf(m2, dx * dx + dy * dy + dz * dz);
+                }
+                if (m2 < INFINITY) {
+                    const double md = sqrt((double)m2);
+                    const double lim = md + 2.0 * mscale * (A.extent + md);
+                    thr = (float)(lim * lim) * 1.00001f;
+                }
+            }
+            for (int s = 0; s < cnt; ++s) {
+                const float4 q = leaf[s];
+                const int pid = __float_as_int(q.w);
+                if (pid == self) continue;
+                const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
+                const float d2f = dx * dx + dy * dy + dz * dz;
+                if (d2f <= thr) {
+                    const double* Q = A.pts + (long long)pid * DIM;
+                    const double ex = __dsub_rn(x, Q[0]);
+                    const double ey = __dsub_rn(y, Q[1]);
+                    double s2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+                    if (DIM == 3) {
+                        const double ez = __dsub_rn(z, Q[2]);
+                        s2 = __dadd_rn(s2, __dmul_rn(ez, ez));
+                    }
+                    if (s2 < best) {
+                        best = s2;
+                        const double bdist = sqrt(s2);
+                        const double lim = bdist + mscale * (A.extent + bdist);
+                        thr = (float)(lim * lim) * 1.00001f;
+                        lbound = (float)lim * 1.00001f;
+                    }
+                }
+            }
+            __syncwarp();
+            const float wb = warp_maxf(lbound);
+            wb2 = wb * wb;
+        } else {
+            const int cl = lvl - 1;
+            const long long c = id * 32 + lane;
+            const bool ex = c < A.cnt[cl];
+            const float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[cl] + c], A.bhi[A.off[cl] + c])
+                                : INFINITY;
+            const bool pass = ex && d2 <= wb2;
+            const unsigned msk = __ballot_sync(0xffffffffu, pass);
+            const int np = __popc(msk);
+            if (sp + np > kStack) {
+                if (lane == 0) atomicOr(A.flag, 4);
+                break;
+            }
+            int rank = 0;
+            for (int s = 0; s < 32; ++s) {
+                const float o = __shfl_sync(0xffffffffu, d2, s);
+                if (((msk >> s) & 1u) && (o < d2 || (o == d2 && s < lane))) ++rank;
+            }
+            if (pass) stack[sp + np - 1 - rank] = (cl << 27) | (int)c;
+            sp += np;
+            __syncwarp();
+        }
+    }
+    if (valid) dist[qs] = sqrt(best);
+}
+
+// mean of dist[0..m) in sample order: thread t sums a contiguous run, the
+// runs are added in thread order
+__global__ void __launch_bounds__(1024) k_mean_in_order(const double* dist, long long m, double* out) {
+    __shared__ double s[1024];
+    const long long per = (m + 1023) / 1024;
+    const long long beg = threadIdx.x * per, end = beg + per < m ? beg + per : m;
+    double a = 0.0;
+    for (long long i = beg; i < end; ++i) a += dist[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 1024; ++i) t += s[i];
+        *out = t / (double)m;
+    }
+}
+
+}  // namespace
+
+}  // namespace slr
+
+extern "C" slr_status slr_cloud_spacing(slr_ctx* c, const int64_t* sample, int64_t m, double* h_s) {
+    using namespace slr;
+    if (!c) return SLR_E_INVALID;
+    auto bad = [&](slr_status st, const char* msg) {
+        c->err = msg;
+        return st;
+    };
+    if (!sample || m < 1 || !h_s) return bad(SLR_E_INVALID, "cloud_spacing: need a sample and an output");
+    if (!c->pts || c->npts < 2) return bad(SLR_E_STATE, "cloud_spacing: load a cloud of at least two points first");
+    std::vector<int64_t> chk(sample, sample + m);
+    std::sort(chk.begin(), chk.end());
+    if (chk.front() < 0 || chk.back() >= c->npts) return bad(SLR_E_INVALID, "cloud_spacing: sample index out of range");
+    for (int64_t i = 1; i < m; ++i)
+        if (chk[i] == chk[i - 1]) return bad(SLR_E_INVALID, "cloud_spacing: sample indices must be distinct");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    CloudIndex X;
+    cudaError_t e = build_cloud_index(c, X);
+    int* mark = (int*)dev_alloc(c, sizeof(int) * (size_t)c->npts);
+    long long* sdev = (long long*)dev_alloc(c, sizeof(long long) * (size_t)m);
+    int* qpos = (int*)dev_alloc(c, sizeof(int) * (size_t)m);
+    double* dist = (double*)dev_alloc(c, sizeof(double) * (size_t)(m + 1));
+    if (e == cudaSuccess && (!mark || !sdev || !qpos || !dist)) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMemsetAsync(mark, 0, sizeof(int) * (size_t)c->npts, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sdev, sample, sizeof(long long) * (size_t)m, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        k_mark_sample<<<c->num_sms * 4, 256, 0, c->stream>>>(sdev, m, mark);
+        c->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = compact_write(c, SampledPred{X.spt, mark}, SampledEmit{X.spt, mark, qpos}, c->npts);
+    if (e == cudaSuccess) {
+        SearchArgs A{};
+        A.lo0 = c->cfg.lo[0];
+        A.lo1 = c->cfg.lo[1];
+        A.lo2 = c->cfg.dim == 3 ? c->cfg.lo[2] : 0.0;
+        A.spt = X.spt;
+        A.pts = c->pts;
+        A.npts = c->npts;
+        A.blo = X.blo;
+        A.bhi = X.bhi;
+        A.nlevels = X.nlevels;
+        for (int l = 0; l < kMaxLevels; ++l) {
+            A.off[l] = l < X.nlevels ? X.off[l] : 0;
+            A.cnt[l] = l < X.nlevels ? X.cnt[l] : 0;
+        }
+        A.extent = X.extent;
+        A.flag = X.flag;
+        const long long warps = (m + 31) / 32;
+        const unsigned blocks = (unsigned)((warps + 7) / 8);
+        if (c->cfg.dim == 3)
+            k_point_nn<3><<<blocks, 256, 0, c->stream>>>(A, qpos, sdev, m, dist);
+        else
+            k_point_nn<2><<<blocks, 256, 0, c->stream>>>(A, qpos, sdev, m, dist);
+        k_mean_in_order<<<1, 1024, 0, c->stream>>>(dist, m, dist + m);
+        c->launches += 2;
+        e = cudaGetLastError();
+    }
+    double hv = 0.0;
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hv, dist + m, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, X.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, X.base);
+    dev_free(c, mark);
+    dev_free(c, sdev);
+    dev_free(c, qpos);
+    dev_free(c, dist);
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+    if (e == cudaErrorMemoryAllocation) return bad(SLR_E_NOMEM, "cloud_spacing: allocation failed");
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("cloud_spacing: ") + cudaGetErrorString(e);
+        return SLR_E_CUDA;
+    }
+    if (hflag & 4) return bad(SLR_E_CUDA, "cloud_spacing: traversal stack overflow");
+    *h_s = hv;
     return SLR_OK;
 }

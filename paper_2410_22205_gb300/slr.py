@@ -33,7 +33,7 @@ EXPORTS = [
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches",
-    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc",
+    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
     "slr_server_destroy",
 ]
@@ -114,6 +114,7 @@ def lib():
                 "slr_last_iteration_times": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_last_iteration_phases": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_kernel_launches": (C.c_int64, [_vp]),
+                "slr_cloud_spacing": (C.c_int, [_vp, _i64p, C.c_int64, _dp]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
                 "slr_distance_grid_noalloc": (C.c_int, [C.c_int, _i64p, _dp, C.c_double, C.c_int, _vp, C.c_int64,
@@ -230,6 +231,13 @@ def slr_init_u(ctx, kind, params=None, u0=None):
     u = _f64(u0) if u0 is not None else None
     _check(ctx, lib().slr_init_u(ctx, int(kind), _ptr(p) if p is not None else None,
                                  _ptr(u) if u is not None else None))
+
+
+def slr_cloud_spacing(ctx, sample):
+    s = np.ascontiguousarray(sample, dtype=np.int64)
+    out = C.c_double(0.0)
+    _check(ctx, lib().slr_cloud_spacing(ctx, _ptr(s, _i64p), int(s.size), C.byref(out)))
+    return out.value
 
 
 def slr_step(ctx, n_steps=1, energy_override=-1.0):
@@ -454,6 +462,10 @@ class Reconstruction:
 
     def init_array(self, u0):
         slr_init_u(self.ctx, 1, u0=u0)
+
+    def cloud_spacing(self, sample):
+        """h_S of §4: mean nearest-other-point distance over the sampled points."""
+        return slr_cloud_spacing(self.ctx, sample)
 
     def init_marking(self, gamma_s):
         """§3.6 initial data from the cloud: external marking and fast sweeping."""

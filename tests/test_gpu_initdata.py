@@ -93,3 +93,23 @@ def test_evolution_from_the_initial_data_stays_on_the_cloud():
     e1 = rec.diagnostics(err_cloud=True)["err_cloud"]
     assert 1.5 * h < e0 < 2.5 * h
     assert e1 < 0.5 * h
+
+
+@pytest.mark.parametrize("dim,npts", [(3, 40000), (2, 5000), (3, 3)])
+def test_cloud_spacing_parity(dim, npts):
+    """h_S of §4 on the GPU equals the oracle's (exact nearest-other-point
+    distances; only the order of the mean's additions differs), with
+    duplicated points in the cloud."""
+    slr = _slr()
+    rng = np.random.default_rng(dim + npts)
+    pts = synth.superquadric_union_cloud(npts, 3, 6) if (dim == 3 and npts > 100) else (
+        synth.circle_noisy(npts, 0.5, 0.01, 1) if dim == 2 else rng.uniform(-0.5, 0.5, (npts, 3)))
+    pts = np.concatenate([pts, pts[: max(1, npts // 50)]])
+    n = 16
+    rec = slr.Reconstruction(dim=dim, n=n, precision=32, interp=1, band=1)
+    rec.load_cloud(pts)
+    sample = rng.choice(len(pts), max(2, len(pts) // 10), replace=False)
+    h = rec.cloud_spacing(sample)
+    assert h == pytest.approx(O.cloud_spacing(pts, sample), rel=1e-12)
+    with pytest.raises(slr.SlrError):
+        rec.cloud_spacing(np.array([0, 0]))

@@ -765,3 +765,21 @@ def test_fsm_local_solution_solves_the_upwind_equation():
             assert abs(np.sum((x - a[act]) ** 2) - h * h) <= 1e-14
             assert np.all(a[~act] >= x)
     assert O.fsm_solve([0.0, 0.0, 0.0], h) == pytest.approx(h / math.sqrt(3), abs=1e-16)
+
+
+def test_cloud_spacing_against_brute_force_and_closed_forms():
+    """§4 h_S: the k-d tree search excluding the query point equals a numpy
+    brute force (duplicates at distance 0 included); N equally spaced points
+    on a circle of radius R are 2R sin(π/N) apart."""
+    rng = np.random.default_rng(9)
+    for dim in (2, 3):
+        pts = rng.uniform(-1, 1, (600, dim))
+        pts = np.concatenate([pts, pts[:7]])  # duplicates
+        sample = rng.choice(len(pts), 150, replace=False)
+        d2 = ((pts[sample][:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+        d2[np.arange(len(sample)), sample] = np.inf
+        ref = np.sqrt(d2.min(1)).mean()
+        assert O.cloud_spacing(pts, sample) == pytest.approx(ref, rel=1e-14)
+    R, N = 0.7, 360
+    circ = synth.circle_uniform(N, R)
+    assert O.cloud_spacing(circ, np.arange(N)) == pytest.approx(2 * R * math.sin(math.pi / N), rel=1e-12)
