@@ -262,6 +262,57 @@ const char* slr_last_error(const slr_ctx* ctx);
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Several runs from coarse to fine (§4: eq. dxdt and Tab. param).
+ *
+ * h_S, the cloud's resolution, comes from a sample of the points
+ * (slr_cloud_spacing); run r works on a grid of width Δx(r) = h_S / 2^(r-1)
+ * over one box (the cloud's bounding box widened by K_S h_S + 8 Δx(1) on every
+ * side) with (p, δ) = (1, 0), (2, 0), then (2, 1), and with the
+ * reinitialisation of §3.7. φ^0 of the first run is the §3.6 initial data at
+ * γ_S = K_S h_S; each later run starts from the previous run's steady state,
+ * interpolated (Q1) at its nodes and cut. A run whose grid would exceed
+ * max_nodes is coarsened until it fits (report->coarsened). The sample is a
+ * Bernoulli draw with probability sample_frac per point from the
+ * counter-based splitmix64 stream of `seed` (point i is drawn when
+ * splitmix64(seed + (i+1)·0x9E3779B97F4A7C15) < sample_frac·2^64).
+ * ------------------------------------------------------------------------- */
+#define SLR_MAX_RUNS 8
+
+typedef struct {
+    int dim;             /* 2 or 3 */
+    int precision;       /* 32 or 64 */
+    int interp;          /* 0 = Q1, 1 = WENO */
+    int runs;            /* runs of Algorithm 1, 1..SLR_MAX_RUNS, default 3 */
+    double K_s;          /* γ_S = K_S h_S for the initial data, default 2 */
+    double sample_frac;  /* fraction of the points sampled for h_S, default 0.1 */
+    uint64_t seed;       /* sample stream, default 1 */
+    int64_t max_nodes;   /* node budget of one run, default 2^27 */
+    int max_iters;       /* iterations per run (§4), default 100 */
+} slr_multirun_config;
+
+typedef struct {
+    double h_s;                        /* the cloud's resolution */
+    int64_t sample_size;               /* points in the h_S sample */
+    int runs_done;
+    int coarsened;                     /* a run was coarsened to fit max_nodes */
+    double lo[3];                      /* node (0,0,0) of every run's grid */
+    double run_dx[SLR_MAX_RUNS];       /* grid width of each run */
+    int64_t run_n[SLR_MAX_RUNS][3];    /* nodes per axis of each run */
+    int run_iters[SLR_MAX_RUNS];       /* iterations of each run */
+    int run_converged[SLR_MAX_RUNS];   /* the Δ_E test stopped the run */
+} slr_multirun_report;
+
+void slr_multirun_default(slr_multirun_config* mc);
+
+/* Reconstruct from xyz (host, n_points rows of dim FP64 coordinates) with the
+ * runs above. On success *out is the context of the last run (the caller
+ * destroys it): its field, band and diagnostics are the result. report may be
+ * NULL. alloc and cuda_stream as for slr_create. */
+slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int64_t n_points,
+                           const slr_allocator* alloc, void* cuda_stream, slr_ctx** out,
+                           slr_multirun_report* report);
+
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching request loop (the paper has no counterpart;
  * it reconstructs one cloud at a time). Requests are admitted in order while

@@ -42,6 +42,19 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class MultirunReport(C.Structure):
+    _fields_ = [
+        ("h_s", C.c_double),
+        ("sample_size", C.c_longlong),
+        ("runs_done", C.c_int),
+        ("lo", C.c_double * 3),
+        ("run_dx", C.c_double * 8),
+        ("run_n", (C.c_longlong * 3) * 8),
+        ("run_iters", C.c_int * 8),
+        ("run_converged", C.c_int * 8),
+    ]
+
+
 class Params(C.Structure):
     _fields_ = [
         ("dim", C.c_int),
@@ -106,6 +119,10 @@ def lib():
                 "or_init_marking": (C.c_longlong, [_P, _dp, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
                 "or_fsm_solve": (C.c_double, [_dp, C.c_int, C.c_double]),
                 "or_cloud_spacing": (C.c_double, [C.c_int, _dp, C.c_longlong, _lp, C.c_longlong]),
+                "or_splitmix64": (C.c_ulonglong, [C.c_ulonglong, C.c_ulonglong]),
+                "or_reconstruct": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong,
+                                             C.c_longlong, C.c_int, _dp, C.c_longlong, _dp, C.c_longlong,
+                                             C.POINTER(MultirunReport)]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
                 "or_set_threads": (C.c_int, [C.c_int]),
@@ -341,6 +358,30 @@ def cloud_spacing(pts, sample):
     smp = np.ascontiguousarray(sample, dtype=np.int64)
     return float(lib().or_cloud_spacing(int(pts.shape[1]), pts.ctypes.data_as(_dp), int(pts.shape[0]),
                                         smp.ctypes.data_as(_lp), int(smp.size)))
+
+
+def splitmix64(seed, i):
+    return int(lib().or_splitmix64(int(seed), int(i)))
+
+
+def reconstruct(pts, dim, prec=64, interp=0, runs=2, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 20,
+                max_iters=100):
+    """§4 runs from coarse to fine; returns (φ of the last run, report dict)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    out = np.empty(max_nodes)
+    rep = MultirunReport()
+    rc = lib().or_reconstruct(int(dim), int(prec), int(interp), int(runs), float(K_s), float(sample_frac), int(seed),
+                              int(max_nodes), int(max_iters), pts.ctypes.data_as(_dp), int(pts.shape[0]),
+                              out.ctypes.data_as(_dp), int(max_nodes), C.byref(rep))
+    if rc != 0:
+        raise ValueError("or_reconstruct failed")
+    k = rep.runs_done
+    n = tuple(rep.run_n[k - 1][:])
+    return out[: int(np.prod(n))].copy(), dict(h_s=rep.h_s, sample_size=rep.sample_size, runs_done=k, lo=tuple(rep.lo[:]),
+                                                run_dx=list(rep.run_dx[:k]),
+                                                run_n=[tuple(rep.run_n[r][:]) for r in range(k)],
+                                                run_iters=list(rep.run_iters[:k]),
+                                                run_converged=[bool(x) for x in rep.run_converged[:k]])
 
 
 def fsm_solve(a, h):

@@ -1112,6 +1112,154 @@ int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, doub
     return n;
 }
 
+/* ------------------------------------------------------------------ */
+/* §4 runs from coarse to fine (eq. dxdt, Tab. param)                    */
+/* ------------------------------------------------------------------ */
+
+/* splitmix64 (Steele, Lea and Flood 2014), counter form: the i-th output of
+ * the stream started at `seed` */
+unsigned long long or_splitmix64(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static long long or_grid_nodes(int dim, const double* bmin, const double* bmax, double dx, double margin,
+                               long long nn[3]) {
+    long long tot = 1;
+    for (int a = 0; a < 3; ++a) nn[a] = 1;
+    for (int a = 0; a < dim; ++a) {
+        nn[a] = (long long)ceil(((bmax[a] - bmin[a]) + 2.0 * margin) / dx) + 1;
+        if (nn[a] < 8) nn[a] = 8;
+        tot *= nn[a];
+    }
+    return tot;
+}
+
+/* Readings: the sample draws point i when splitmix64(seed, i) < frac·2^64
+ * (every point when frac >= 1; point 0 if none); the box is the cloud's
+ * bounding box widened by γ_S + 8 Δx(1), Δx(1) = h_S coarsened (×
+ * (N/max_nodes)^(1/dim)·1.0001 until it fits); run r has Δx = Δx(1)/2^(r-1),
+ * coarsened the same way, (p, δ) = (1, 0), (2, 0), then (2, 1), Δt = Δx/4,
+ * band, reinitialisation; φ0 of run 1 by or_init_marking at γ_S = K_S h_S,
+ * of later runs by Q1 (or_interp_q1) of the previous state at the new nodes;
+ * both rounded to the storage type and cut. phi_out receives the last run's
+ * field (at most phi_cap values). Returns 0, or -1 (bad input / capacity). */
+int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
+                   unsigned long long seed, long long max_nodes, int max_iters, const double* pts, long long npts,
+                   double* phi_out, long long phi_cap, or_multirun_report* rep) {
+    memset(rep, 0, sizeof(*rep));
+    if (dim != 2 && dim != 3) return -1;
+    double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+        bmin[a] = INFINITY;
+        bmax[a] = -INFINITY;
+    }
+    for (long long i = 0; i < npts; ++i)
+        for (int a = 0; a < dim; ++a) {
+            double v = pts[i * dim + a];
+            if (v < bmin[a]) bmin[a] = v;
+            if (v > bmax[a]) bmax[a] = v;
+        }
+    long long* sample = (long long*)malloc(sizeof(long long) * (size_t)npts);
+    long long m = 0;
+    double limd = sample_frac * 18446744073709551616.0;
+    if (limd > 18446744073709549568.0) limd = 18446744073709549568.0;
+    unsigned long long lim = (unsigned long long)limd;
+    for (long long i = 0; i < npts; ++i)
+        if (sample_frac >= 1.0 || or_splitmix64(seed, (unsigned long long)i) < lim) sample[m++] = i;
+    if (m == 0) sample[m++] = 0;
+    double hs = or_cloud_spacing(dim, pts, npts, sample, m);
+    free(sample);
+    rep->h_s = hs;
+    rep->sample_size = m;
+    double gamma_s = K_s * hs;
+    long long nn[3];
+    double dx1 = hs;
+    for (int it = 0; it < 200; ++it) {
+        long long tot = or_grid_nodes(dim, bmin, bmax, dx1, gamma_s + 8.0 * dx1, nn);
+        if (tot <= max_nodes) break;
+        dx1 *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
+    }
+    double margin = gamma_s + 8.0 * dx1;
+    double lo[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) lo[a] = bmin[a] - margin;
+    for (int a = 0; a < 3; ++a) rep->lo[a] = lo[a];
+    double* prev = NULL;
+    or_params pp;
+    memset(&pp, 0, sizeof(pp));
+    for (int r = 1; r <= runs; ++r) {
+        double dx = dx1 / (double)(1ll << (r - 1));
+        for (int it = 0; it < 200; ++it) {
+            long long tot = or_grid_nodes(dim, bmin, bmax, dx, margin, nn);
+            if (tot <= max_nodes) break;
+            dx *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
+        }
+        or_params P;
+        memset(&P, 0, sizeof(P));
+        P.dim = dim;
+        for (int a = 0; a < 3; ++a) {
+            P.n[a] = a < dim ? nn[a] : 1;
+            P.lo[a] = a < dim ? lo[a] : 0.0;
+        }
+        double hi0 = lo[0] + (double)(nn[0] - 1) * dx;
+        P.h = (hi0 - lo[0]) / (double)(nn[0] - 1);
+        P.interp = interp;
+        P.p = r == 1 ? 1.0 : 2.0;
+        P.delta = r <= 2 ? 0.0 : 1.0;
+        P.dt = P.h / 4.0;
+        P.band = 1;
+        P.gamma = (dim == 2 ? 4.0 : 6.0) * P.h;
+        P.beta = (dim == 2 ? 2.0 : 3.0) * P.h;
+        P.c_sing = 1e-3;
+        P.alpha = 1.0;
+        P.prec = prec;
+        long long N = or_num_nodes(&P);
+        double* d = (double*)malloc(sizeof(double) * (size_t)N);
+        double* u = (double*)malloc(sizeof(double) * (size_t)N);
+        or_distance_kd(&P, pts, npts, NULL, 0, d, NULL);
+        if (prec == 32)
+            for (long long i = 0; i < N; ++i) d[i] = (double)(float)d[i];
+        if (r == 1) {
+            or_init_marking(&P, d, gamma_s, u, NULL);
+        } else {
+            for (long long i = 0; i < N; ++i) {
+                double x[3];
+                or_node_coord(&P, i, x);
+                u[i] = or_interp_q1(&pp, prev, x);
+            }
+            free(prev);
+        }
+        for (long long i = 0; i < N; ++i) {
+            double v = prec == 32 ? (double)(float)u[i] : u[i];
+            u[i] = or_cut(&P, v);
+        }
+        double* E2 = (double*)malloc(sizeof(double) * (size_t)(max_iters + 1));
+        double* dphi = (double*)malloc(sizeof(double) * (size_t)(max_iters + 1));
+        int conv = 0;
+        int it = or_evolve_reinit(&P, u, d, 5, 1e-4, 10, 10, max_iters, 1, 0, 0.0, E2, dphi, &conv);
+        free(E2);
+        free(dphi);
+        free(d);
+        rep->runs_done = r;
+        rep->run_dx[r - 1] = dx;
+        for (int a = 0; a < 3; ++a) rep->run_n[r - 1][a] = P.n[a];
+        rep->run_iters[r - 1] = it;
+        rep->run_converged[r - 1] = conv;
+        prev = u;
+        pp = P;
+    }
+    long long N = or_num_nodes(&pp);
+    if (N > phi_cap) {
+        free(prev);
+        return -1;
+    }
+    memcpy(phi_out, prev, sizeof(double) * (size_t)N);
+    free(prev);
+    return 0;
+}
+
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out) {
     long long N = or_num_nodes(g), m = 0;
     for (long long i = 0; i < N; ++i)

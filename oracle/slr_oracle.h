@@ -153,6 +153,25 @@ long long or_init_marking(const or_params* g, const double* d, double gamma_s, d
  * per-axis upwind values a[0..m) (m = 1..3) */
 double or_fsm_solve(const double* a, int m, double h);
 
+/* splitmix64 (Steele, Lea and Flood 2014): the i-th output of the stream
+ * started at seed (the state after i+1 increments, mixed) */
+unsigned long long or_splitmix64(unsigned long long seed, unsigned long long i);
+
+/* §4 runs from coarse to fine; see the readings in slr_oracle.c */
+typedef struct {
+    double h_s;
+    long long sample_size;
+    int runs_done;
+    double lo[3];
+    double run_dx[8];
+    long long run_n[8][3];
+    int run_iters[8];
+    int run_converged[8];
+} or_multirun_report;
+int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
+                   unsigned long long seed, long long max_nodes, int max_iters, const double* pts, long long npts,
+                   double* phi_out, long long phi_cap, or_multirun_report* rep);
+
 /* nodes with |φ| < width, ascending index */
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out);
 

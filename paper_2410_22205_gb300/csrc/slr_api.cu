@@ -222,6 +222,51 @@ slr_status evolve_launch(slr_ctx* c) {
 
 }  // namespace slr
 
+namespace slr {
+
+// the rest of slr_init_u once u[0] and u[1] hold φ^0 (write status e):
+// device state, band list, candidate cells, the first energy
+slr_status init_after_u(slr_ctx* c, cudaError_t e) {
+    DeviceGuard g(c->device);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init_u");
+    if (c->cfg.band) {
+        // with reinitialisation the band can grow: lists and cells get the
+        // capacity of the whole grid, and the candidate-cell count lives on
+        // the device
+        const bool rei = c->cfg.reinit != 0;
+        long long cnt = 0;
+        CK(launch_count_band(c, &cnt), "init_u band count");
+        slr_status s = size_band_buffers(c, rei ? c->N : cnt);
+        if (s != SLR_OK) return s;
+        CK(launch_build_band(c), "init_u band list");
+        int ci = (int)cnt;
+        CK(cudaMemcpyAsync(&c->ds->band_count[0], &ci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
+        long long nc = 0;
+        CK(launch_build_ecells(c, &nc, false), "init_u cell count");
+        release_t(c, c->ecells);
+        const long long ecap = rei ? c->ncells_all : nc;
+        c->ecells = (int*)dev_alloc(c, sizeof(int) * (ecap > 0 ? ecap : 1));
+        if (!c->ecells) return fail(c, SLR_E_NOMEM, "init_u: cell list allocation failed");
+        c->n_ecells = ecap;
+        CK(launch_build_ecells(c, &nc, true), "init_u cell list");
+        s = size_energy_buffers(c, c->n_ecells);
+        if (s != SLR_OK) return s;
+        if (rei) {
+            int nci = (int)nc;
+            CK(cudaMemcpyAsync(&c->ds->n_ecells_dyn, &nci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
+            CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "init_u");
+        }
+    }
+    CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
+    CK(cudaStreamSynchronize(c->stream), "init_u sync");
+    c->have_u = true;
+    return SLR_OK;
+}
+
+}  // namespace slr
+
 extern "C" {
 
 void slr_config_default(slr_config* cfg) {
@@ -444,42 +489,9 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
         }
     }
     cudaError_t e = launch_init_u(c, kind == 2 ? 1 : kind, prm, tmp);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ds, 0, sizeof(DevState), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, tmp);
-    if (e != cudaSuccess) return cuda_fail(c, e, "init_u");
-    if (c->cfg.band) {
-        // with reinitialisation the band can grow: lists and cells get the
-        // capacity of the whole grid, and the candidate-cell count lives on
-        // the device
-        const bool rei = c->cfg.reinit != 0;
-        long long cnt = 0;
-        CK(launch_count_band(c, &cnt), "init_u band count");
-        slr_status s = size_band_buffers(c, rei ? c->N : cnt);
-        if (s != SLR_OK) return s;
-        CK(launch_build_band(c), "init_u band list");
-        int ci = (int)cnt;
-        CK(cudaMemcpyAsync(&c->ds->band_count[0], &ci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
-        long long nc = 0;
-        CK(launch_build_ecells(c, &nc, false), "init_u cell count");
-        release_t(c, c->ecells);
-        const long long ecap = rei ? c->ncells_all : nc;
-        c->ecells = (int*)dev_alloc(c, sizeof(int) * (ecap > 0 ? ecap : 1));
-        if (!c->ecells) return fail(c, SLR_E_NOMEM, "init_u: cell list allocation failed");
-        c->n_ecells = ecap;
-        CK(launch_build_ecells(c, &nc, true), "init_u cell list");
-        s = size_energy_buffers(c, c->n_ecells);
-        if (s != SLR_OK) return s;
-        if (rei) {
-            int nci = (int)nc;
-            CK(cudaMemcpyAsync(&c->ds->n_ecells_dyn, &nci, sizeof(int), cudaMemcpyHostToDevice, c->stream), "init_u");
-            CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "init_u");
-        }
-    }
-    CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
-    CK(cudaStreamSynchronize(c->stream), "init_u sync");
-    c->have_u = true;
-    return SLR_OK;
+    return slr::init_after_u(c, e);
 }
 
 slr_status slr_step(slr_ctx* c, int n_steps, double energy_override) {

@@ -142,6 +142,8 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
                           cudaEvent_t between = nullptr);
 cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double* u_dev, long long* count_out,
                            bool write);
+// the rest of slr_init_u once both φ buffers hold φ^0 (e: status of writing them)
+slr_status init_after_u(slr_ctx* c, cudaError_t e);
 // §3.6 initial data into an FP64 device field (ext: N bytes of scratch); see slr_initdata.cu
 cudaError_t launch_init_marking(slr_ctx* c, double gamma_s, double* phi_dev, unsigned char* ext_dev);
 // Algorithm 1 step 4d (§3.7) after launch_step; see slr_reinit.cu

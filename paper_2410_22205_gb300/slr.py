@@ -35,7 +35,7 @@ EXPORTS = [
     "slr_last_iteration_phases", "slr_kernel_launches",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
-    "slr_server_destroy",
+    "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
 ]
 
 
@@ -69,6 +69,37 @@ class slr_config(C.Structure):
         ("reinit", C.c_int),
         ("reinit_sweeps", C.c_int),
         ("reinit_dtau", C.c_double),
+    ]
+
+
+class slr_multirun_config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("precision", C.c_int),
+        ("interp", C.c_int),
+        ("runs", C.c_int),
+        ("K_s", C.c_double),
+        ("sample_frac", C.c_double),
+        ("seed", C.c_uint64),
+        ("max_nodes", C.c_int64),
+        ("max_iters", C.c_int),
+    ]
+
+
+SLR_MAX_RUNS = 8
+
+
+class slr_multirun_report(C.Structure):
+    _fields_ = [
+        ("h_s", C.c_double),
+        ("sample_size", C.c_int64),
+        ("runs_done", C.c_int),
+        ("coarsened", C.c_int),
+        ("lo", C.c_double * 3),
+        ("run_dx", C.c_double * SLR_MAX_RUNS),
+        ("run_n", (C.c_int64 * 3) * SLR_MAX_RUNS),
+        ("run_iters", C.c_int * SLR_MAX_RUNS),
+        ("run_converged", C.c_int * SLR_MAX_RUNS),
     ]
 
 
@@ -121,6 +152,9 @@ def lib():
                                                         _vp, _vp, _vp]),
             }
             sig.update({
+                "slr_multirun_default": (None, [C.POINTER(slr_multirun_config)]),
+                "slr_reconstruct": (C.c_int, [C.POINTER(slr_multirun_config), _dp, C.c_int64, C.POINTER(slr_allocator),
+                                              _vp, C.POINTER(_vp), C.POINTER(slr_multirun_report)]),
                 "slr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(slr_allocator), C.POINTER(_vp)]),
                 "slr_server_submit": (C.c_int, [_vp, P, _dp, C.c_int64, _dp, C.POINTER(C.c_uint64)]),
                 "slr_server_poll": (C.c_int, [_vp, C.c_uint64, _ip, C.POINTER(_vp), _dp]),
@@ -416,6 +450,61 @@ def slr_server_destroy(srv):
 # ---------------------------------------------------------------------------
 # convenience wrapper: one reconstruction job
 # ---------------------------------------------------------------------------
+
+def slr_multirun_default(**overrides) -> slr_multirun_config:
+    mc = slr_multirun_config()
+    lib().slr_multirun_default(C.byref(mc))
+    names = {f[0] for f in slr_multirun_config._fields_}
+    for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"slr_multirun_config has no field {k!r}")
+        setattr(mc, k, v)
+    return mc
+
+
+def slr_reconstruct(mc, xyz, allocator=None, stream=None):
+    """Runs from coarse to fine (§4); returns (context handle, report dict)."""
+    pts = _f64(xyz)
+    h = C.c_void_p()
+    rep = slr_multirun_report()
+    al = C.byref(allocator.struct) if allocator is not None else None
+    st = C.c_void_p(stream) if stream else None
+    status = lib().slr_reconstruct(C.byref(mc), _ptr(pts), int(pts.shape[0]), al, st, C.byref(h), C.byref(rep))
+    if status != SLR_OK:
+        msg = lib().slr_last_error(None)
+        raise SlrError(status, msg.decode() if msg else "")
+    k = rep.runs_done
+    report = dict(h_s=rep.h_s, sample_size=rep.sample_size, runs_done=k, coarsened=bool(rep.coarsened),
+                  lo=tuple(rep.lo[:]),
+                  run_dx=list(rep.run_dx[:k]), run_n=[tuple(rep.run_n[r][:]) for r in range(k)],
+                  run_iters=list(rep.run_iters[:k]), run_converged=[bool(x) for x in rep.run_converged[:k]])
+    return h.value, report
+
+
+def reconstruct(xyz, dim=3, precision=32, interp=1, runs=3, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 27,
+                max_iters=100, stream=None):
+    """The paper's pipeline from a cloud (§4): h_S, the §3.6 initial data, then
+    `runs` runs of Algorithm 1 from coarse to fine. Returns (Reconstruction of
+    the last run, report)."""
+    import torch
+
+    mc = slr_multirun_default(dim=dim, precision=precision, interp=interp, runs=runs, K_s=K_s,
+                              sample_frac=sample_frac, seed=seed, max_nodes=max_nodes, max_iters=max_iters)
+    dev = torch.cuda.current_device()
+    s = stream if stream is not None else torch.cuda.Stream(dev)
+    al = _TorchAllocator(dev, s.cuda_stream)
+    ctx, rep = slr_reconstruct(mc, xyz, al, s.cuda_stream)
+    n = rep["run_n"][-1]
+    rec = Reconstruction.__new__(Reconstruction)
+    rec.dim = dim
+    rec.shape = tuple(int(x) for x in n)
+    rec.num_nodes = int(np.prod(rec.shape))
+    rec.stream = s
+    rec._alloc = al
+    rec.ctx = ctx
+    rec.cfg = None
+    return rec, rep
+
 
 class Reconstruction:
     """One reconstruction job on the current CUDA device.

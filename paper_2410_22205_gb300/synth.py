@@ -120,6 +120,18 @@ def sphere_cloud(n: int, radius: float = 1.0, sigma: float = 0.0, seed: int = 0,
     return v * np.asarray(rr).reshape(-1, 1) + np.asarray(center)
 
 
+def sphere_even(n: int, radius: float = 1.0, center=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """n evenly spread points on a sphere (the golden-angle spiral: equal-area
+    latitude bands, longitude advancing by the golden angle), a stand-in for
+    a scan without holes."""
+    k = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    t = np.pi * (3.0 - np.sqrt(5.0)) * np.arange(n)
+    v = np.stack([r * np.cos(t), r * np.sin(t), z], axis=1)
+    return v * radius + np.asarray(center)
+
+
 def _random_rotation(rng) -> np.ndarray:
     q = rng.normal(size=4)
     q /= np.linalg.norm(q)

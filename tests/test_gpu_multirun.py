@@ -1,0 +1,87 @@
+"""GPU parity of the runs from coarse to fine of §4 (eq. dxdt, Tab. param)
+through the C ABI (slr_reconstruct) against the oracle's or_reconstruct.
+
+Bars: the sample size and every run's node counts and iteration counts
+exact; h_S, the grid widths and the grid origin relative 1e-12 (h_S is a mean
+whose additions are ordered differently); the last run's field in FP64 within
+1e-9 (the trajectory bar of the FP64 evolution tests: every decision taken on
+both sides from values equal to rounding). FP32 runs: h_S, the grids and the
+sample as in FP64; the result on the cloud (eq. errCloud) below Δx/4.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_22205_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _slr():
+    from paper_2410_22205_gb300 import slr
+
+    return slr
+
+
+def compare_reports(rep, ref, iters=True):
+    assert rep["sample_size"] == ref["sample_size"]
+    assert rep["runs_done"] == ref["runs_done"]
+    assert rep["h_s"] == pytest.approx(ref["h_s"], rel=1e-12)
+    np.testing.assert_allclose(rep["lo"], ref["lo"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(rep["run_dx"], ref["run_dx"], rtol=1e-12)
+    assert rep["run_n"] == ref["run_n"]
+    if iters:
+        assert rep["run_iters"] == ref["run_iters"]
+        assert rep["run_converged"] == ref["run_converged"]
+
+
+@pytest.mark.parametrize("dim,interp,runs,max_nodes,frac", [(2, 0, 3, 1 << 22, 1.0), (2, 1, 2, 1 << 22, 0.3),
+                                                             (3, 1, 2, 60 ** 3, 0.5), (3, 0, 2, 1 << 22, 0.5)])
+def test_multirun_fp64_matches_the_oracle(dim, interp, runs, max_nodes, frac):
+    slr = _slr()
+    pts = synth.circle_noisy(600, 0.45, 0.002, 4) if dim == 2 else synth.sphere_even(800, 0.45)
+    kw = dict(runs=runs, K_s=2.0, sample_frac=frac, seed=11, max_nodes=max_nodes, max_iters=100)
+    rec, rep = slr.reconstruct(pts, dim=dim, precision=64, interp=interp, **kw)
+    ref_phi, ref = O.reconstruct(pts, dim, prec=64, interp=interp, **kw)
+    compare_reports(rep, ref)
+    u = rec.u()
+    assert u.shape == ref_phi.shape
+    assert np.abs(u - ref_phi).max() <= 1e-9
+    assert (u < 0).any() and (u > 0).any()
+    rec.close()
+
+
+def test_multirun_fp32_reaches_the_cloud():
+    """FP32 WENO in 3-D: the grids and h_S agree with the oracle's and the
+    last run's zero level set lies on the cloud. The cloud is evenly spread
+    (no hole wider than 2 h_S): with K_S = 2, §4 assumes no fake holes."""
+    slr = _slr()
+    pts = synth.sphere_even(3000, 0.45)
+    kw = dict(runs=3, K_s=2.0, sample_frac=0.2, seed=3, max_nodes=1 << 22, max_iters=100)
+    rec, rep = slr.reconstruct(pts, dim=3, precision=32, interp=1, **kw)
+    _, ref = O.reconstruct(pts, 3, prec=64, interp=1, runs=1, K_s=2.0, sample_frac=0.2, seed=3, max_nodes=1 << 22,
+                           max_iters=1)
+    assert rep["h_s"] == pytest.approx(ref["h_s"], rel=1e-12)
+    assert rep["run_n"][0] == ref["run_n"][0] and rep["sample_size"] == ref["sample_size"]
+    # the third run (Δx = h_S/4, 344^3 nodes) is coarsened to the budget
+    assert rep["coarsened"] and all(np.prod(n) <= 1 << 22 for n in rep["run_n"])
+    assert rep["run_dx"][2] < rep["run_dx"][1] < rep["run_dx"][0]
+    e = rec.diagnostics(err_cloud=True)["err_cloud"]
+    assert e < 0.25 * rep["run_dx"][-1]
+    rec.close()
+
+
+def test_multirun_rejects_bad_configs():
+    slr = _slr()
+    pts = synth.circle_uniform(50, 0.4)
+    for bad in (dict(runs=0), dict(runs=9), dict(K_s=0.0), dict(sample_frac=0.0), dict(sample_frac=1.5),
+                dict(max_nodes=10), dict(max_iters=0)):
+        kw = dict(dim=2, precision=64, interp=0)
+        kw.update(bad)
+        with pytest.raises(slr.SlrError) as e:
+            slr.reconstruct(pts, **kw)
+        assert e.value.status == slr.SLR_E_INVALID
+    with pytest.raises(slr.SlrError):
+        slr.reconstruct(np.array([[0.0, 0.0]]), dim=2)

@@ -783,3 +783,65 @@ def test_cloud_spacing_against_brute_force_and_closed_forms():
     R, N = 0.7, 360
     circ = synth.circle_uniform(N, R)
     assert O.cloud_spacing(circ, np.arange(N)) == pytest.approx(2 * R * math.sin(math.pi / N), rel=1e-12)
+
+
+# --- §4 runs from coarse to fine -------------------------------------------------
+
+
+def test_splitmix64_published_outputs():
+    """The sample draw uses splitmix64 (Steele, Lea and Flood 2014); its first
+    three outputs from the zero seed, as published with the generator's
+    reference implementation."""
+    assert [O.splitmix64(0, i) for i in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_multirun_sample_is_a_bernoulli_draw():
+    """sample_frac = 1 takes every point; 0.1 of 20000 points takes a count
+    within 5 standard deviations of 2000."""
+    pts = synth.circle_noisy(20000, 0.5, 0.01, 3)
+    _, rep = O.reconstruct(pts, 2, runs=1, sample_frac=0.1, max_nodes=64 * 64, max_iters=1)
+    sd = np.sqrt(20000 * 0.1 * 0.9)
+    assert abs(rep["sample_size"] - 2000) < 5 * sd
+    _, rep1 = O.reconstruct(pts[:500], 2, runs=1, sample_frac=1.0, max_nodes=64 * 64, max_iters=1)
+    assert rep1["sample_size"] == 500
+
+
+def test_multirun_grids_halve_and_reach_the_cloud():
+    """§4 eq. dxdt and Tab. param on the paper's circle of equally spaced
+    points: h_S = 2R sin(π/n) (the chord to either neighbour); the grid width
+    halves from run to run over one box that holds the cloud with the margin
+    K_S h_S + 8 Δx(1); after the runs the zero level set lies on the cloud
+    (eq. errCloud well below Δx of the last run)."""
+    n, R, K = 400, 0.45, 2.0
+    pts = synth.circle_uniform(n, R)
+    phi, rep = O.reconstruct(pts, 2, runs=3, K_s=K, sample_frac=1.0, max_nodes=1 << 22, max_iters=100)
+    hs = 2 * R * np.sin(np.pi / n)
+    assert rep["h_s"] == pytest.approx(hs, rel=1e-12)
+    assert rep["sample_size"] == n and rep["runs_done"] == 3
+    dx = rep["run_dx"]
+    assert dx[0] == rep["h_s"] and dx[1] == dx[0] / 2 and dx[2] == dx[0] / 4
+    margin = K * hs + 8 * dx[0]
+    for r in range(3):
+        for a in range(2):
+            lo = rep["lo"][a]
+            assert lo == pytest.approx(pts[:, a].min() - margin, rel=0, abs=1e-15)
+            top = lo + (rep["run_n"][r][a] - 1) * dx[r]
+            assert top >= pts[:, a].max() + margin - 1e-12
+            assert top - dx[r] < pts[:, a].max() + margin
+        assert 1 <= rep["run_iters"][r] <= 100
+    nn = rep["run_n"][2]
+    P = O.params(2, nn[:2], rep["lo"][:2], h=dx[2], band=1)
+    assert O.err_cloud(P, phi, pts) < 0.25 * dx[2]
+    # a signed distance near the cloud: negative at the centre side, positive outside
+    assert phi.max() > 0 and phi.min() < 0
+
+
+def test_multirun_coarsens_to_the_node_budget():
+    """A budget below the h_S grid: every run fits max_nodes and the widths
+    still halve from the coarsened first width where the budget allows."""
+    pts = synth.circle_uniform(400, 0.45)
+    _, rep = O.reconstruct(pts, 2, runs=2, sample_frac=1.0, max_nodes=60 * 60, max_iters=5)
+    for r in range(2):
+        assert rep["run_n"][r][0] * rep["run_n"][r][1] <= 60 * 60
+    assert rep["run_dx"][0] > rep["h_s"]
+    assert rep["run_dx"][1] >= rep["run_dx"][0] / 2
