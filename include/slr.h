@@ -107,6 +107,17 @@ slr_status slr_load_cloud(slr_ctx* ctx, const double* xyz, int64_t n_points);
  * minimiser is decided in FP64; d is stored in the configured precision. */
 slr_status slr_build_distance(slr_ctx* ctx);
 
+/* §3.4 as the paper builds the distance grid: the exact d of
+ * slr_build_distance on the nodes of a box of 4 grid points per axis around
+ * each point (per axis the nodes i0-1 .. i0+2, i0 = floor((Q_a - lo_a)/h),
+ * clipped to the grid), then the fast sweeping method (Zhao 2005: Godunov
+ * upwind solution of |∇d| = 1, Gauss-Seidel sweeps in the 2^dim orderings,
+ * two rounds, box nodes kept) on every other node, started at +inf. FP64
+ * throughout, rounded to the storage precision at the end; argmin is the
+ * exact minimiser on box nodes and -1 elsewhere. Needs slr_load_cloud.
+ * SLR_E_INVALID when no point lies within a cell of the grid (no box node). */
+slr_status slr_build_distance_fsm(slr_ctx* ctx);
+
 /* Set d from a host FP64 array of all nodes (e.g. an analytic distance);
  * argmin is set to -1. Rounded to the storage precision. */
 slr_status slr_set_distance(slr_ctx* ctx, const double* d_host);
@@ -289,6 +300,8 @@ typedef struct {
     uint64_t seed;       /* sample stream, default 1 */
     int64_t max_nodes;   /* node budget of one run, default 2^27 */
     int max_iters;       /* iterations per run (§4), default 100 */
+    int distance_fsm;    /* 1: every run's d by slr_build_distance_fsm (§3.4);
+                            0 (default): exact d (slr_build_distance) */
 } slr_multirun_config;
 
 typedef struct {

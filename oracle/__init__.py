@@ -119,9 +119,10 @@ def lib():
                 "or_init_marking": (C.c_longlong, [_P, _dp, C.c_double, _dp, C.POINTER(C.c_ubyte)]),
                 "or_fsm_solve": (C.c_double, [_dp, C.c_int, C.c_double]),
                 "or_cloud_spacing": (C.c_double, [C.c_int, _dp, C.c_longlong, _lp, C.c_longlong]),
+                "or_distance_fsm": (C.c_longlong, [C.POINTER(Params), _dp, C.c_longlong, _dp, C.POINTER(C.c_ubyte)]),
                 "or_splitmix64": (C.c_ulonglong, [C.c_ulonglong, C.c_ulonglong]),
                 "or_reconstruct": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong,
-                                             C.c_longlong, C.c_int, _dp, C.c_longlong, _dp, C.c_longlong,
+                                             C.c_longlong, C.c_int, C.c_int, _dp, C.c_longlong, _dp, C.c_longlong,
                                              C.POINTER(MultirunReport)]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
@@ -360,18 +361,33 @@ def cloud_spacing(pts, sample):
                                         smp.ctypes.data_as(_lp), int(smp.size)))
 
 
+def distance_fsm(P, pts):
+    """§3.4 distance grid: exact on the box of 4^dim nodes around each point,
+    fast sweeping elsewhere. Returns (d, fixed mask)."""
+    pts, pp = _d(pts)
+    N = num_nodes(P)
+    d = np.empty(N)
+    fix = np.zeros(N, np.uint8)
+    m = lib().or_distance_fsm(C.byref(P), pp, pts.shape[0], d.ctypes.data_as(_dp),
+                              fix.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    if m == 0:
+        raise ValueError("no point of the cloud lies within one cell of the grid")
+    return d, fix
+
+
 def splitmix64(seed, i):
     return int(lib().or_splitmix64(int(seed), int(i)))
 
 
 def reconstruct(pts, dim, prec=64, interp=0, runs=2, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 20,
-                max_iters=100):
+                max_iters=100, distance="exact"):
     """§4 runs from coarse to fine; returns (φ of the last run, report dict)."""
     pts = np.ascontiguousarray(pts, dtype=np.float64)
     out = np.empty(max_nodes)
     rep = MultirunReport()
     rc = lib().or_reconstruct(int(dim), int(prec), int(interp), int(runs), float(K_s), float(sample_frac), int(seed),
-                              int(max_nodes), int(max_iters), pts.ctypes.data_as(_dp), int(pts.shape[0]),
+                              int(max_nodes), int(max_iters), int(distance == "fsm"), pts.ctypes.data_as(_dp),
+                              int(pts.shape[0]),
                               out.ctypes.data_as(_dp), int(max_nodes), C.byref(rep))
     if rc != 0:
         raise ValueError("or_reconstruct failed")

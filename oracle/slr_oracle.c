@@ -1063,6 +1063,82 @@ long long or_init_marking(const or_params* g, const double* d, double gamma_s, d
     return next;
 }
 
+/* §3.4: d exact (eq. distance, the whole cloud) on the nodes of a box of 4
+ * (2-D: 4 x 4; 3-D: 4 x 4 x 4) grid points around each point, the fast
+ * sweeping method (Zhao 2005) on every other node.
+ * Readings: the box of Q holds, per axis, the nodes i0-1 .. i0+2 with
+ * i0 = floor((Q_a - lo_a)/h), those outside the grid dropped; the other nodes
+ * start at +inf and take the Godunov local solution of |∇d| = 1 in the
+ * 2^dim orderings, two rounds, box nodes kept (the sweeps of or_init_marking).
+ * d_out: FP64 on every node; fixed_out (may be NULL): 1 on box nodes.
+ * Returns the number of box nodes (0: no point within a cell of the grid,
+ * d_out untouched). */
+long long or_distance_fsm(const or_params* g, const double* pts, long long npts, double* d_out,
+                          unsigned char* fixed_out) {
+    long long N = or_num_nodes(g);
+    long long n[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    unsigned char* fix = (unsigned char*)calloc((size_t)N, 1);
+    for (long long q = 0; q < npts; ++q) {
+        long long b0[3] = {0, 0, 0}, b1[3] = {0, 0, 0};
+        int empty = 0;
+        for (int a = 0; a < g->dim; ++a) {
+            double xi = floor((pts[q * g->dim + a] - g->lo[a]) / g->h);
+            double lo = xi - 1.0, hi = xi + 2.0;
+            if (lo < 0.0) lo = 0.0;
+            if (hi > (double)(n[a] - 1)) hi = (double)(n[a] - 1);
+            if (lo > hi) empty = 1;
+            else {
+                b0[a] = (long long)lo;
+                b1[a] = (long long)hi;
+            }
+        }
+        if (empty) continue;
+        for (long long k = b0[2]; k <= b1[2]; ++k)
+            for (long long j = b0[1]; j <= b1[1]; ++j)
+                for (long long i = b0[0]; i <= b1[0]; ++i) fix[i + stride[1] * j + stride[2] * k] = 1;
+    }
+    long long m = 0;
+    for (long long i = 0; i < N; ++i) m += fix[i];
+    if (m == 0) {
+        free(fix);
+        return 0;
+    }
+    long long* list = (long long*)malloc(sizeof(long long) * (size_t)m);
+    double* dv = (double*)malloc(sizeof(double) * (size_t)m);
+    int* arg = (int*)malloc(sizeof(int) * (size_t)m);
+    m = 0;
+    for (long long i = 0; i < N; ++i)
+        if (fix[i]) list[m++] = i;
+    or_distance_kd(g, pts, npts, list, m, dv, arg);
+    for (long long i = 0; i < N; ++i) d_out[i] = INFINITY;
+    for (long long t = 0; t < m; ++t) d_out[list[t]] = dv[t];
+    free(list);
+    free(dv);
+    free(arg);
+    int nord = 1 << g->dim;
+    for (int round = 0; round < 2; ++round)
+        for (int o = 0; o < nord; ++o) {
+            long long c[3];
+            for (long long kk = 0; kk < n[2]; ++kk) {
+                c[2] = (o & 4) ? n[2] - 1 - kk : kk;
+                for (long long jj = 0; jj < n[1]; ++jj) {
+                    c[1] = (o & 2) ? n[1] - 1 - jj : jj;
+                    for (long long ii = 0; ii < n[0]; ++ii) {
+                        c[0] = (o & 1) ? n[0] - 1 - ii : ii;
+                        long long idx = c[0] + stride[1] * c[1] + stride[2] * c[2];
+                        if (fix[idx]) continue;
+                        double x = fsm_local(g, d_out, idx, c, stride);
+                        if (x < d_out[idx]) d_out[idx] = x;
+                    }
+                }
+            }
+        }
+    if (fixed_out) memcpy(fixed_out, fix, (size_t)N);
+    free(fix);
+    return m;
+}
+
 int or_evolve(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
               int min_iters, int max_iters, double* E2_hist, double* dphi_hist, int* converged) {
     return or_evolve_reinit(g, u, d, R, stop_tol, kmax, min_iters, max_iters, 0, 0, 0.0, E2_hist, dphi_hist, converged);
@@ -1144,11 +1220,12 @@ static long long or_grid_nodes(int dim, const double* bmin, const double* bmax, 
  * coarsened the same way, (p, δ) = (1, 0), (2, 0), then (2, 1), Δt = Δx/4,
  * band, reinitialisation; φ0 of run 1 by or_init_marking at γ_S = K_S h_S,
  * of later runs by Q1 (or_interp_q1) of the previous state at the new nodes;
- * both rounded to the storage type and cut. phi_out receives the last run's
+ * both rounded to the storage type and cut; d exact, or by or_distance_fsm
+ * when distance_fsm is set. phi_out receives the last run's
  * field (at most phi_cap values). Returns 0, or -1 (bad input / capacity). */
 int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
-                   unsigned long long seed, long long max_nodes, int max_iters, const double* pts, long long npts,
-                   double* phi_out, long long phi_cap, or_multirun_report* rep) {
+                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, const double* pts,
+                   long long npts, double* phi_out, long long phi_cap, or_multirun_report* rep) {
     memset(rep, 0, sizeof(*rep));
     if (dim != 2 && dim != 3) return -1;
     double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0};
@@ -1218,7 +1295,16 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
         long long N = or_num_nodes(&P);
         double* d = (double*)malloc(sizeof(double) * (size_t)N);
         double* u = (double*)malloc(sizeof(double) * (size_t)N);
-        or_distance_kd(&P, pts, npts, NULL, 0, d, NULL);
+        if (distance_fsm) {
+            if (or_distance_fsm(&P, pts, npts, d, NULL) == 0) {
+                free(d);
+                free(u);
+                free(prev);
+                return -1;
+            }
+        } else {
+            or_distance_kd(&P, pts, npts, NULL, 0, d, NULL);
+        }
         if (prec == 32)
             for (long long i = 0; i < N; ++i) d[i] = (double)(float)d[i];
         if (r == 1) {

@@ -153,6 +153,11 @@ long long or_init_marking(const or_params* g, const double* d, double gamma_s, d
  * per-axis upwind values a[0..m) (m = 1..3) */
 double or_fsm_solve(const double* a, int m, double h);
 
+/* §3.4 distance grid as the paper builds it: exact on the 4^dim node box
+ * around each point, fast sweeping elsewhere; returns the box node count */
+long long or_distance_fsm(const or_params* g, const double* pts, long long npts, double* d_out,
+                          unsigned char* fixed_out);
+
 /* splitmix64 (Steele, Lea and Flood 2014): the i-th output of the stream
  * started at seed (the state after i+1 increments, mixed) */
 unsigned long long or_splitmix64(unsigned long long seed, unsigned long long i);
@@ -169,8 +174,8 @@ typedef struct {
     int run_converged[8];
 } or_multirun_report;
 int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
-                   unsigned long long seed, long long max_nodes, int max_iters, const double* pts, long long npts,
-                   double* phi_out, long long phi_cap, or_multirun_report* rep);
+                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, const double* pts,
+                   long long npts, double* phi_out, long long phi_cap, or_multirun_report* rep);
 
 /* nodes with |φ| < width, ascending index */
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out);

@@ -434,6 +434,19 @@ slr_status slr_build_distance(slr_ctx* c) {
     return SLR_OK;
 }
 
+slr_status slr_build_distance_fsm(slr_ctx* c) {
+    if (!c) return SLR_E_INVALID;
+    if (!c->have_cloud) return fail(c, SLR_E_STATE, "build_distance_fsm: no cloud loaded");
+    DeviceGuard g(c->device);
+    cudaError_t e = build_distance_fsm(c);
+    if (e == cudaErrorInvalidValue)
+        return fail(c, SLR_E_INVALID, "build_distance_fsm: no point within a cell of the grid, or non-finite points");
+    if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "build_distance_fsm: scratch allocation failed");
+    if (e != cudaSuccess) return cuda_fail(c, e, "build_distance_fsm");
+    c->have_d = true;
+    return SLR_OK;
+}
+
 slr_status slr_set_distance(slr_ctx* c, const double* d_host) {
     if (!c) return SLR_E_INVALID;
     if (!d_host) return fail(c, SLR_E_INVALID, "set_distance: null array");

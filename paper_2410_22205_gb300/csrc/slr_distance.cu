@@ -204,6 +204,7 @@ struct SearchArgs {
     long long cnt[kMaxLevels];
     double extent;         // coordinate extent used in the FP32 error margin
     int* flag;             // bit 2: traversal stack overflow
+    const unsigned char* mask = nullptr;  // nodes to compute (nullptr: every node)
 };
 
 __device__ __forceinline__ float box_dist2(float tlx, float tly, float tlz, float thx, float thy, float thz,
@@ -247,10 +248,15 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
         j = tj * 4 + (lane >> 3);
         k = 0;
     }
-    const bool valid = i < A.n0 && j < A.n1 && k < A.n2;
+    bool valid = i < A.n0 && j < A.n1 && k < A.n2;
     i = i < A.n0 ? i : A.n0 - 1;
     j = j < A.n1 ? j : A.n1 - 1;
     k = k < A.n2 ? k : A.n2 - 1;
+    if (A.mask) {
+        // only the listed nodes; a warp with none of them has nothing to do
+        valid = valid && A.mask[(long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k)];
+        if (!__any_sync(0xffffffffu, valid)) return;
+    }
     // exact node coordinates (lo + i*h, no contraction) and FP32 offsets from lo
     const double x = __dadd_rn(A.lo0, __dmul_rn((double)i, A.h));
     const double y = __dadd_rn(A.lo1, __dmul_rn((double)j, A.h));
@@ -513,52 +519,51 @@ static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     return e;
 }
 
+// search arguments over the context's grid and a built cloud index
+static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
+    const int dim = c->cfg.dim;
+    SearchArgs A;
+    A.n0 = (int)c->cfg.n[0];
+    A.n1 = (int)c->cfg.n[1];
+    A.n2 = (int)c->cfg.n[2];
+    if (dim == 3) {
+        A.tx = (A.n0 + 3) / 4;
+        A.ty = (A.n1 + 3) / 4;
+        A.tz = (A.n2 + 1) / 2;
+    } else {
+        A.tx = (A.n0 + 7) / 8;
+        A.ty = (A.n1 + 3) / 4;
+        A.tz = 1;
+    }
+    A.lo0 = c->cfg.lo[0];
+    A.lo1 = c->cfg.lo[1];
+    A.lo2 = dim == 3 ? c->cfg.lo[2] : 0.0;
+    A.h = c->h;
+    A.spt = X.spt;
+    A.pts = c->pts;
+    A.npts = c->npts;
+    A.blo = X.blo;
+    A.bhi = X.bhi;
+    A.nlevels = X.nlevels;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        A.off[l] = l < X.nlevels ? X.off[l] : 0;
+        A.cnt[l] = l < X.nlevels ? X.cnt[l] : 0;
+    }
+    A.extent = X.extent;
+    A.flag = X.flag;
+    return A;
+}
+
 cudaError_t build_distance(slr_ctx* c) {
     const int dim = c->cfg.dim;
-    const long long npts = c->npts;
     cudaStream_t st = c->stream;
     CloudIndex X;
     cudaError_t e = build_cloud_index(c, X);
     char* base = X.base;
     int* flag = X.flag;
     int hflag = 0;
-    const int nlevels = X.nlevels;
-    const long long* off = X.off;
-    const long long* cnt = X.cnt;
-    float4* spt = X.spt;
-    float4* blo = X.blo;
-    float4* bhi = X.bhi;
-    const double extent = X.extent;
     if (e == cudaSuccess) {
-        SearchArgs A;
-        A.n0 = (int)c->cfg.n[0];
-        A.n1 = (int)c->cfg.n[1];
-        A.n2 = (int)c->cfg.n[2];
-        if (dim == 3) {
-            A.tx = (A.n0 + 3) / 4;
-            A.ty = (A.n1 + 3) / 4;
-            A.tz = (A.n2 + 1) / 2;
-        } else {
-            A.tx = (A.n0 + 7) / 8;
-            A.ty = (A.n1 + 3) / 4;
-            A.tz = 1;
-        }
-        A.lo0 = c->cfg.lo[0];
-        A.lo1 = c->cfg.lo[1];
-        A.lo2 = dim == 3 ? c->cfg.lo[2] : 0.0;
-        A.h = c->h;
-        A.spt = spt;
-        A.pts = c->pts;
-        A.npts = npts;
-        A.blo = blo;
-        A.bhi = bhi;
-        A.nlevels = nlevels;
-        for (int l = 0; l < kMaxLevels; ++l) {
-            A.off[l] = l < nlevels ? off[l] : 0;
-            A.cnt[l] = l < nlevels ? cnt[l] : 0;
-        }
-        A.extent = extent;
-        A.flag = flag;
+        SearchArgs A = search_args(c, X);
         if (c->cfg.precision == 32) {
             if (dim == 3) launch_search<float, 3>(c, A);
             else launch_search<float, 2>(c, A);
@@ -571,6 +576,29 @@ cudaError_t build_distance(slr_ctx* c) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     dev_free(c, base);
+    if (e == cudaSuccess && (hflag & 4)) return cudaErrorLaunchOutOfResources;
+    return e;
+}
+
+cudaError_t distance_on_marked(slr_ctx* c, const unsigned char* mask, double* dout) {
+    CloudIndex X;
+    cudaError_t e = build_cloud_index(c, X);
+    int hflag = 0;
+    if (e == cudaSuccess) {
+        SearchArgs A = search_args(c, X);
+        A.mask = mask;
+        const long long ntiles = (long long)A.tx * A.ty * A.tz;
+        const unsigned blocks = (unsigned)((ntiles * 32 + 255) / 256);
+        if (c->cfg.dim == 3)
+            k_dist_search<double, 3><<<blocks, 256, 0, c->stream>>>(A, dout, c->argmin);
+        else
+            k_dist_search<double, 2><<<blocks, 256, 0, c->stream>>>(A, dout, c->argmin);
+        c->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, X.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, X.base);
     if (e == cudaSuccess && (hflag & 4)) return cudaErrorLaunchOutOfResources;
     return e;
 }

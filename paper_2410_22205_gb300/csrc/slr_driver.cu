@@ -12,7 +12,7 @@
 // (Steele, Lea and Flood 2014); the box is the cloud's bounding box widened by
 // K_S h_S + 8 Δx(1) on every side, the same for every run; a run whose grid
 // would exceed max_nodes is coarsened to fit (Δx grows by the dim-th root of
-// the excess).
+// the excess); d is exact unless distance_fsm asks for the §3.4 construction.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -124,7 +124,8 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     const int dim = mc->dim;
     if (dim != 2 && dim != 3) return SLR_E_INVALID;
     if (mc->runs < 1 || mc->runs > SLR_MAX_RUNS || !(mc->K_s > 0.0) || !(mc->sample_frac > 0.0) ||
-        !(mc->sample_frac <= 1.0) || mc->max_nodes < 64 || mc->max_iters < 1)
+        !(mc->sample_frac <= 1.0) || mc->max_nodes < 64 || mc->max_iters < 1 ||
+        (mc->distance_fsm != 0 && mc->distance_fsm != 1))
         return SLR_E_INVALID;
     slr_multirun_report rep;
     memset(&rep, 0, sizeof(rep));
@@ -231,7 +232,7 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
         slr_ctx* c = nullptr;
         status = slr_create(&k, alloc, cuda_stream, &c);
         if (status == SLR_OK) status = slr_load_cloud(c, xyz, n_points);
-        if (status == SLR_OK) status = slr_build_distance(c);
+        if (status == SLR_OK) status = mc->distance_fsm ? slr_build_distance_fsm(c) : slr_build_distance(c);
         if (status == SLR_OK) {
             if (r == 1) {
                 const double prm[4] = {gamma_s, 0, 0, 0};

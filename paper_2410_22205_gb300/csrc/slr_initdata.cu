@@ -3,6 +3,11 @@
 // then reversed. The result is an FP64 field that slr_init_u passes through
 // the array path (storage type, eq. cut in band mode).
 //
+// §3.4 distance grid as the paper builds it (build_distance_fsm): the exact
+// distance on the nodes of a box of 4 grid points per axis around each point
+// of the cloud, the same fast sweeping on every other node (started at +inf),
+// in FP64, rounded to the storage type at the end. argmin is -1 off the boxes.
+//
 // Readings (the paper describes the steps in words):
 //  - every node on the grid boundary is external; then one round of
 //    directional sweeps along the grid lines, +x, -x, +y, -y (+z, -z): a sweep
@@ -143,6 +148,32 @@ __global__ void k_phi_finish(double* phi, const unsigned char* __restrict__ ext,
         if (!ext[j]) phi[j] = -phi[j];
 }
 
+// two rounds of Gauss-Seidel sweeps in the 2^dim orderings over the nodes
+// that are not fixed, one launch per plane of an ordering
+void fsm_sweeps(slr_ctx* c, double* phi, const unsigned char* fixed) {
+    const int n0 = (int)c->cfg.n[0], n1 = (int)c->cfg.n[1], n2 = c->cfg.dim == 3 ? (int)c->cfg.n[2] : 1;
+    const int dim = c->cfg.dim;
+    const int grid = c->num_sms * 8;
+    const long long count = dim == 3 ? (long long)n1 * n2 : (long long)n1;
+    const int pgrid = (int)((count + kIB - 1) / kIB < grid ? (count + kIB - 1) / kIB : grid);
+    const int planes = n0 + n1 + (dim == 3 ? n2 : 1) - 2;
+    for (int round = 0; round < 2; ++round)
+        for (int ord = 0; ord < (1 << dim); ++ord)
+            for (int s = 0; s < planes; ++s) {
+                if (dim == 3)
+                    k_fsm_plane<3><<<pgrid, kIB, 0, c->stream>>>(phi, fixed, ord, s, n0, n1, n2, c->h);
+                else
+                    k_fsm_plane<2><<<pgrid, kIB, 0, c->stream>>>(phi, fixed, ord, s, n0, n1, n2, c->h);
+            }
+    c->launches += 2ll * (1 << dim) * planes;
+}
+
+struct GridBox {
+    double lo[3];
+    double h;
+    int n[3];
+};
+
 template <typename T>
 cudaError_t marking_t(slr_ctx* c, double gamma_s, double* phi, unsigned char* ext) {
     const int n0 = (int)c->cfg.n[0], n1 = (int)c->cfg.n[1], n2 = c->cfg.dim == 3 ? (int)c->cfg.n[2] : 1;
@@ -158,25 +189,121 @@ cudaError_t marking_t(slr_ctx* c, double gamma_s, double* phi, unsigned char* ex
         }
     k_phi_start<T><<<grid, kIB, 0, c->stream>>>(phi, ext, d, gamma_s, c->N);
     ++launches;
-    const long long count = dim == 3 ? (long long)n1 * n2 : (long long)n1;
-    const int pgrid = (int)((count + kIB - 1) / kIB < grid ? (count + kIB - 1) / kIB : grid);
-    const int planes = n0 + n1 + (dim == 3 ? n2 : 1) - 2;
-    for (int round = 0; round < 2; ++round)
-        for (int ord = 0; ord < (1 << dim); ++ord)
-            for (int s = 0; s < planes; ++s) {
-                if (dim == 3)
-                    k_fsm_plane<3><<<pgrid, kIB, 0, c->stream>>>(phi, ext, ord, s, n0, n1, n2, c->h);
-                else
-                    k_fsm_plane<2><<<pgrid, kIB, 0, c->stream>>>(phi, ext, ord, s, n0, n1, n2, c->h);
-                ++launches;
-            }
-    k_phi_finish<<<grid, kIB, 0, c->stream>>>(phi, ext, c->N);
-    ++launches;
     c->launches += launches;
+    fsm_sweeps(c, phi, ext);
+    k_phi_finish<<<grid, kIB, 0, c->stream>>>(phi, ext, c->N);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
+// --- §3.4: the distance grid as the paper builds it ---------------------------
+
+// the box of 4 nodes per axis around each point: i0-1 .. i0+2 with
+// i0 = floor((Q_a - lo_a)/h), clipped to the grid
+__global__ void k_mark_boxes(const double* __restrict__ pts, long long npts, int dim, GridBox G,
+                             unsigned char* fixed) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
+        int b0[3] = {0, 0, 0}, b1[3] = {0, 0, 0};
+        bool empty = false;
+        for (int a = 0; a < dim; ++a) {
+            const double xi = floor(__ddiv_rn(__dsub_rn(pts[q * dim + a], G.lo[a]), G.h));
+            if (!isfinite(xi)) {
+                empty = true;
+                break;
+            }
+            double l = xi - 1.0, u = xi + 2.0;
+            if (l < 0.0) l = 0.0;
+            if (u > (double)(G.n[a] - 1)) u = (double)(G.n[a] - 1);
+            if (l > u) {
+                empty = true;
+                break;
+            }
+            b0[a] = (int)l;
+            b1[a] = (int)u;
+        }
+        if (empty) continue;
+        const long long s1 = G.n[0], s2 = (long long)G.n[0] * G.n[1];
+        for (int k = b0[2]; k <= b1[2]; ++k)
+            for (int j = b0[1]; j <= b1[1]; ++j)
+                for (int i = b0[0]; i <= b1[0]; ++i) fixed[i + s1 * j + s2 * k] = 1;
+    }
+}
+
+__global__ void k_count_fixed(const unsigned char* __restrict__ fixed, long long N, unsigned long long* count) {
+    __shared__ unsigned long long s_sum[kIB / 32];
+    unsigned long long v = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) v += fixed[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kIB / 32; ++w) t += s_sum[w];
+        atomicAdd(count, t);
+    }
+}
+
+__global__ void k_fill_inf(double* v, long long N) {
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) v[j] = inf;
+}
+
+template <typename T>
+__global__ void k_store_rounded(const double* __restrict__ v, T* out, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) out[j] = (T)v[j];
+}
+
 }  // namespace
+
+cudaError_t build_distance_fsm(slr_ctx* c) {
+    const long long N = c->N;
+    const int grid = c->num_sms * 8;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    char* base = (char*)dev_alloc(c, al(sizeof(double) * N) + al(N) + 256);
+    if (!base) return cudaErrorMemoryAllocation;
+    double* dv = (double*)base;
+    unsigned char* fixed = (unsigned char*)(base + al(sizeof(double) * N));
+    unsigned long long* count = (unsigned long long*)(base + al(sizeof(double) * N) + al(N));
+    GridBox G;
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = a < c->cfg.dim ? c->cfg.lo[a] : 0.0;
+        G.n[a] = (int)c->cfg.n[a];
+    }
+    G.h = c->h;
+    unsigned long long hcount = 0;
+    cudaError_t e = cudaMemsetAsync(fixed, 0, (size_t)N, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) {
+        const long long pb = (c->npts + kIB - 1) / kIB;
+        k_mark_boxes<<<(unsigned)(pb < grid ? pb : grid), kIB, 0, c->stream>>>(c->pts, c->npts, c->cfg.dim, G, fixed);
+        k_count_fixed<<<grid, kIB, 0, c->stream>>>(fixed, N, count);
+        k_fill_inf<<<grid, kIB, 0, c->stream>>>(dv, N);
+        c->launches += 3;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->argmin, 0xff, sizeof(int) * (size_t)N, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hcount, count, sizeof(hcount), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && hcount == 0) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = distance_on_marked(c, fixed, dv);
+    if (e == cudaSuccess) {
+        fsm_sweeps(c, dv, fixed);
+        if (c->cfg.precision == 32)
+            k_store_rounded<float><<<grid, kIB, 0, c->stream>>>(dv, (float*)c->d, N);
+        else
+            k_store_rounded<double><<<grid, kIB, 0, c->stream>>>(dv, (double*)c->d, N);
+        c->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, base);
+    return e;
+}
 
 cudaError_t launch_init_marking(slr_ctx* c, double gamma_s, double* phi_dev, unsigned char* ext_dev) {
     return c->cfg.precision == 32 ? marking_t<float>(c, gamma_s, phi_dev, ext_dev)

@@ -157,6 +157,11 @@ cudaError_t launch_err_cloud(slr_ctx* c, double* out_dev);
 cudaError_t launch_to_double(slr_ctx* c, const void* src, double* dst, long long n);
 cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long long n);
 cudaError_t build_distance(slr_ctx* c);
+// exact distance (FP64) and argmin on the nodes with mask[j] != 0; others untouched
+cudaError_t distance_on_marked(slr_ctx* c, const unsigned char* mask, double* dout);
+// §3.4: exact on the 4^dim node box around each point, fast sweeping elsewhere
+// (cudaErrorInvalidValue: no point within a cell of the grid)
+cudaError_t build_distance_fsm(slr_ctx* c);
 long long energy_blocks(const slr_ctx* c);
 const char* noalloc_last_error();
 long long full_step_blocks(const slr_ctx* c);

@@ -29,7 +29,8 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 
 # every entry point declared in include/slr.h
 EXPORTS = [
-    "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_set_distance", "slr_init_u",
+    "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_build_distance_fsm",
+    "slr_set_distance", "slr_init_u",
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches",
@@ -83,6 +84,7 @@ class slr_multirun_config(C.Structure):
         ("seed", C.c_uint64),
         ("max_nodes", C.c_int64),
         ("max_iters", C.c_int),
+        ("distance_fsm", C.c_int),
     ]
 
 
@@ -128,6 +130,7 @@ def lib():
                 "slr_create": (C.c_int, [P, C.POINTER(slr_allocator), _vp, C.POINTER(_vp)]),
                 "slr_load_cloud": (C.c_int, [_vp, _dp, C.c_int64]),
                 "slr_build_distance": (C.c_int, [_vp]),
+                "slr_build_distance_fsm": (C.c_int, [_vp]),
                 "slr_set_distance": (C.c_int, [_vp, _dp]),
                 "slr_init_u": (C.c_int, [_vp, C.c_int, _dp, _dp]),
                 "slr_step": (C.c_int, [_vp, C.c_int, C.c_double]),
@@ -253,6 +256,10 @@ def slr_load_cloud(ctx, xyz):
 
 def slr_build_distance(ctx):
     _check(ctx, lib().slr_build_distance(ctx))
+
+
+def slr_build_distance_fsm(ctx):
+    _check(ctx, lib().slr_build_distance_fsm(ctx))
 
 
 def slr_set_distance(ctx, d):
@@ -482,14 +489,18 @@ def slr_reconstruct(mc, xyz, allocator=None, stream=None):
 
 
 def reconstruct(xyz, dim=3, precision=32, interp=1, runs=3, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 27,
-                max_iters=100, stream=None):
+                max_iters=100, distance="exact", stream=None):
     """The paper's pipeline from a cloud (§4): h_S, the §3.6 initial data, then
-    `runs` runs of Algorithm 1 from coarse to fine. Returns (Reconstruction of
-    the last run, report)."""
+    `runs` runs of Algorithm 1 from coarse to fine. distance: "exact" or
+    "fsm" (the §3.4 construction). Returns (Reconstruction of the last run,
+    report)."""
     import torch
 
+    if distance not in ("exact", "fsm"):
+        raise ValueError(f"unknown distance method {distance!r}")
     mc = slr_multirun_default(dim=dim, precision=precision, interp=interp, runs=runs, K_s=K_s,
-                              sample_frac=sample_frac, seed=seed, max_nodes=max_nodes, max_iters=max_iters)
+                              sample_frac=sample_frac, seed=seed, max_nodes=max_nodes, max_iters=max_iters,
+                              distance_fsm=int(distance == "fsm"))
     dev = torch.cuda.current_device()
     s = stream if stream is not None else torch.cuda.Stream(dev)
     al = _TorchAllocator(dev, s.cuda_stream)
@@ -539,8 +550,15 @@ class Reconstruction:
     def load_cloud(self, xyz):
         slr_load_cloud(self.ctx, xyz)
 
-    def build_distance(self):
-        slr_build_distance(self.ctx)
+    def build_distance(self, method="exact"):
+        """d on every node: "exact" (slr_build_distance) or "fsm", the §3.4
+        construction (exact near the cloud, fast sweeping elsewhere)."""
+        if method == "exact":
+            slr_build_distance(self.ctx)
+        elif method == "fsm":
+            slr_build_distance_fsm(self.ctx)
+        else:
+            raise ValueError(f"unknown distance method {method!r}")
 
     def set_distance(self, d):
         slr_set_distance(self.ctx, d)

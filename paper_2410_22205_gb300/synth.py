@@ -86,6 +86,14 @@ def circle_noisy(n: int = 200, radius: float = 0.5, sigma: float = 0.005, seed: 
     return np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
 
 
+def circle_even_noisy(n: int = 600, radius: float = 0.5, sigma: float = 0.002, seed: int = 0) -> np.ndarray:
+    """Equal angles, Gaussian radial noise: a scan of a circle without holes."""
+    rng = np.random.default_rng(seed)
+    t = 2.0 * np.pi * np.arange(n) / n
+    r = radius + rng.normal(0.0, sigma, n)
+    return np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
+
+
 def torus_cloud(n: int = 20000, R: float = 0.5, r: float = 0.2, sigma: float = 0.002, seed: int = 1) -> np.ndarray:
     """Area-uniform torus samples with Gaussian displacement along the normal.
 

@@ -41,7 +41,8 @@ def compare_reports(rep, ref, iters=True):
                                                              (3, 1, 2, 60 ** 3, 0.5), (3, 0, 2, 1 << 22, 0.5)])
 def test_multirun_fp64_matches_the_oracle(dim, interp, runs, max_nodes, frac):
     slr = _slr()
-    pts = synth.circle_noisy(600, 0.45, 0.002, 4) if dim == 2 else synth.sphere_even(800, 0.45)
+    # clouds without holes wider than 2 h_S, as §4 assumes for K_S = 2
+    pts = synth.circle_even_noisy(600, 0.45, 0.002, 4) if dim == 2 else synth.sphere_even(800, 0.45)
     kw = dict(runs=runs, K_s=2.0, sample_frac=frac, seed=11, max_nodes=max_nodes, max_iters=100)
     rec, rep = slr.reconstruct(pts, dim=dim, precision=64, interp=interp, **kw)
     ref_phi, ref = O.reconstruct(pts, dim, prec=64, interp=interp, **kw)
@@ -50,6 +51,7 @@ def test_multirun_fp64_matches_the_oracle(dim, interp, runs, max_nodes, frac):
     assert u.shape == ref_phi.shape
     assert np.abs(u - ref_phi).max() <= 1e-9
     assert (u < 0).any() and (u > 0).any()
+    assert rec.diagnostics(err_cloud=True)["err_cloud"] < 0.5 * rep["run_dx"][-1]
     rec.close()
 
 

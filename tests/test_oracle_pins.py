@@ -845,3 +845,87 @@ def test_multirun_coarsens_to_the_node_budget():
         assert rep["run_n"][r][0] * rep["run_n"][r][1] <= 60 * 60
     assert rep["run_dx"][0] > rep["h_s"]
     assert rep["run_dx"][1] >= rep["run_dx"][0] / 2
+
+
+# --- §3.4 distance grid: exact near the cloud, fast sweeping elsewhere --------------
+
+
+def _cheb_dist_to_cloud(P, pts):
+    X = O.node_coords(P)[:, : P.dim]
+    out = np.full(X.shape[0], np.inf)
+    for q in pts:
+        out = np.minimum(out, np.abs(X - q[None, :]).max(axis=1))
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_distance_fsm_box_of_one_point(dim):
+    """One point inside the grid: exactly 4^dim exact nodes, holding every
+    node within one cell of it (max-norm) and none two cells away; on them d
+    is the Euclidean distance; on the grid lines through a point placed on a
+    node the sweeping distance is k·h (exact along the axes)."""
+    n = 17 if dim == 3 else 33
+    P = O.params(dim, (n,) * dim, (-1.0,) * dim, (1.0,) * dim)
+    rng = np.random.default_rng(dim)
+    q = rng.uniform(-0.6, 0.6, dim)
+    d, fix = O.distance_fsm(P, q[None, :])
+    assert fix.sum() == 4 ** dim
+    cheb = _cheb_dist_to_cloud(P, q[None, :])
+    assert np.all(fix[cheb <= P.h]) and not np.any(fix[cheb >= 2 * P.h])
+    X = O.node_coords(P)[:, :dim]
+    exact = np.sqrt(((X - q) ** 2).sum(axis=1))
+    np.testing.assert_allclose(d[fix == 1], exact[fix == 1], rtol=1e-15)
+    # a point on the node (8, 8[, 8]): the axis lines
+    c = 8
+    qn = np.array([-1.0 + c * P.h] * dim)
+    d2, _ = O.distance_fsm(P, qn[None, :])
+    g = d2.reshape((n,) * dim)
+    line = g[(c,) * (dim - 1)] if dim > 1 else g
+    np.testing.assert_allclose(line, np.abs(np.arange(n) - c) * P.h, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_distance_fsm_is_exact_for_a_planar_lattice(dim):
+    """Points on every node column of the plane z = c (line y = c in 2-D):
+    the distance is |z - c| on every node, exact near the plane and propagated
+    exactly by the sweeps (the Godunov update reduces to a + h)."""
+    n = 21
+    P = O.params(dim, (n,) * dim, (-1.0,) * dim, (1.0,) * dim)
+    X = O.node_coords(P)[:, :dim]
+    c = -1.0 + 7.3 * P.h
+    cols = np.unique(X[:, : dim - 1], axis=0)
+    pts = np.concatenate([cols, np.full((cols.shape[0], 1), c)], axis=1)
+    d, fix = O.distance_fsm(P, pts)
+    np.testing.assert_allclose(d, np.abs(X[:, dim - 1] - c), rtol=0, atol=1e-13)
+    assert fix.sum() == 4 * n ** (dim - 1)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_distance_fsm_converges_to_the_cloud_distance(dim):
+    """Circle / sphere cloud: exact (the k-d tree and the brute force agree)
+    on the box nodes; elsewhere the sweeping error falls under refinement
+    (a first-order method, O(h log h) at the centre's kink)."""
+    pts = synth.circle_uniform(2000, 0.5) if dim == 2 else synth.sphere_even(6000, 0.5)
+    errs = []
+    for n in ((33, 65) if dim == 3 else (65, 129, 257)):
+        P = O.params(dim, (n,) * dim, (-1.0,) * dim, (1.0,) * dim)
+        d, fix = O.distance_fsm(P, pts)
+        nodes = np.flatnonzero(fix)
+        exact_fix, _ = O.distance(P, pts, nodes=nodes[:: max(1, nodes.size // 300)], method="brute")
+        assert np.array_equal(d[nodes[:: max(1, nodes.size // 300)]], exact_fix)
+        de, _ = O.distance(P, pts, method="kd")
+        errs.append(np.abs(d - de).max())
+        assert errs[-1] < 1.5 * P.h
+    for a, b in zip(errs, errs[1:]):
+        assert b < 0.75 * a
+
+
+def test_distance_fsm_partial_boxes_and_no_box():
+    """A point just outside the grid gives the part of its box inside; a
+    cloud more than two cells outside leaves no exact node (an error)."""
+    P = O.params(2, (16, 16), (0.0, 0.0), (1.0, 1.0))
+    q = np.array([[-0.5 * P.h, 0.5]])
+    _, fix = O.distance_fsm(P, q)
+    assert fix.sum() == 2 * 4
+    with pytest.raises(ValueError):
+        O.distance_fsm(P, np.array([[-3.0, 0.5]]))
