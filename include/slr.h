@@ -273,20 +273,34 @@ const char* slr_last_error(const slr_ctx* ctx);
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);
 
+/* §4: the L^1 norm of the error against an exact signed distance,
+ * Δx^dim Σ_j |c(φ_j) - c(φ*_j)| over every node, with c the cut of eq. cut
+ * at the band half-width γ in band mode (the identity in full-grid mode),
+ * in FP64. kind 0: φ* = |x - c| - r, params = {cx, cy, cz, r} (cz unused in
+ * 2-D), evaluated on the device in FP64; kind 1: φ* from exact_host, one FP64
+ * value per node. Needs slr_init_u. */
+slr_status slr_l1_error(slr_ctx* ctx, int kind, const double* params, const double* exact_host, double* l1_out);
+
 /* ---------------------------------------------------------------------------
  * Several runs from coarse to fine (§4: eq. dxdt and Tab. param).
  *
  * h_S, the cloud's resolution, comes from a sample of the points
- * (slr_cloud_spacing); run r works on a grid of width Δx(r) = h_S / 2^(r-1)
- * over one box (the cloud's bounding box widened by K_S h_S + 8 Δx(1) on every
- * side) with (p, δ) = (1, 0), (2, 0), then (2, 1), and with the
- * reinitialisation of §3.7. φ^0 of the first run is the §3.6 initial data at
- * γ_S = K_S h_S; each later run starts from the previous run's steady state,
- * interpolated (Q1) at its nodes and cut. A run whose grid would exceed
- * max_nodes is coarsened until it fits (report->coarsened). The sample is a
- * Bernoulli draw with probability sample_frac per point from the
- * counter-based splitmix64 stream of `seed` (point i is drawn when
- * splitmix64(seed + (i+1)·0x9E3779B97F4A7C15) < sample_frac·2^64).
+ * (slr_cloud_spacing). Run r works on a grid of width Δx(r) = h_S / 2^(r-1)
+ * over the cloud's bounding box widened by 8 Δx(r) on every side, plus
+ * γ_S = K_S h_S in the first run (this reproduces the grids of the paper's
+ * circle test, 42^2, 58^2, 99^2, 181^2 and 344^2), with (p, δ) = (1, 0),
+ * (2, 0), then (2, 1), and with the reinitialisation of §3.7. φ^0 of the
+ * first run is the §3.6 initial data at γ_S; each later run starts from the
+ * previous run's steady state, interpolated (Q1) at its nodes and cut. A run
+ * whose grid would exceed max_nodes is coarsened until it fits
+ * (report->coarsened). The sample is a Bernoulli draw with probability
+ * sample_frac per point from the counter-based splitmix64 stream of `seed`
+ * (point i is drawn when splitmix64(seed + (i+1)·0x9E3779B97F4A7C15) <
+ * sample_frac·2^64).
+ *
+ * At the end of each run the report holds the quantities of the paper's
+ * tables: the grid, E_2 of the run's final state, Err_S (eq. errCloud) and,
+ * when an exact signed distance is given, the L^1 error of slr_l1_error.
  * ------------------------------------------------------------------------- */
 #define SLR_MAX_RUNS 8
 
@@ -302,6 +316,8 @@ typedef struct {
     int max_iters;       /* iterations per run (§4), default 100 */
     int distance_fsm;    /* 1: every run's d by slr_build_distance_fsm (§3.4);
                             0 (default): exact d (slr_build_distance) */
+    int exact_sphere;    /* 1: report the L^1 error against |x - c| - r */
+    double sphere[4];    /* {cx, cy, cz, r} for exact_sphere */
 } slr_multirun_config;
 
 typedef struct {
@@ -309,11 +325,14 @@ typedef struct {
     int64_t sample_size;               /* points in the h_S sample */
     int runs_done;
     int coarsened;                     /* a run was coarsened to fit max_nodes */
-    double lo[3];                      /* node (0,0,0) of every run's grid */
     double run_dx[SLR_MAX_RUNS];       /* grid width of each run */
     int64_t run_n[SLR_MAX_RUNS][3];    /* nodes per axis of each run */
+    double run_lo[SLR_MAX_RUNS][3];    /* node (0,0,0) of each run's grid */
     int run_iters[SLR_MAX_RUNS];       /* iterations of each run */
     int run_converged[SLR_MAX_RUNS];   /* the Δ_E test stopped the run */
+    double run_energy[SLR_MAX_RUNS];   /* E_2 of the run's final state */
+    double run_err_cloud[SLR_MAX_RUNS];/* Err_S (eq. errCloud) of the final state */
+    double run_l1_err[SLR_MAX_RUNS];   /* L^1 error (exact_sphere), else NaN */
 } slr_multirun_report;
 
 void slr_multirun_default(slr_multirun_config* mc);

@@ -47,11 +47,14 @@ class MultirunReport(C.Structure):
         ("h_s", C.c_double),
         ("sample_size", C.c_longlong),
         ("runs_done", C.c_int),
-        ("lo", C.c_double * 3),
         ("run_dx", C.c_double * 8),
         ("run_n", (C.c_longlong * 3) * 8),
+        ("run_lo", (C.c_double * 3) * 8),
         ("run_iters", C.c_int * 8),
         ("run_converged", C.c_int * 8),
+        ("run_energy", C.c_double * 8),
+        ("run_err_cloud", C.c_double * 8),
+        ("run_l1_err", C.c_double * 8),
     ]
 
 
@@ -122,8 +125,10 @@ def lib():
                 "or_distance_fsm": (C.c_longlong, [C.POINTER(Params), _dp, C.c_longlong, _dp, C.POINTER(C.c_ubyte)]),
                 "or_splitmix64": (C.c_ulonglong, [C.c_ulonglong, C.c_ulonglong]),
                 "or_reconstruct": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong,
-                                             C.c_longlong, C.c_int, C.c_int, _dp, C.c_longlong, _dp, C.c_longlong,
-                                             C.POINTER(MultirunReport)]),
+                                             C.c_longlong, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_longlong, _dp,
+                                             C.c_longlong, C.POINTER(MultirunReport)]),
+                "or_l1_error": (C.c_double, [_P, _dp, _dp]),
+                "or_sdf_sphere": (None, [_P, _dp, _dp]),
                 "or_extract": (C.c_longlong, [_P, _dp, C.c_double, _lp, _dp]),
                 "or_err_cloud": (C.c_double, [_P, _dp, _dp, C.c_longlong]),
                 "or_set_threads": (C.c_int, [C.c_int]),
@@ -380,24 +385,42 @@ def splitmix64(seed, i):
 
 
 def reconstruct(pts, dim, prec=64, interp=0, runs=2, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 20,
-                max_iters=100, distance="exact"):
-    """§4 runs from coarse to fine; returns (φ of the last run, report dict)."""
+                max_iters=100, distance="exact", sphere=None):
+    """§4 runs from coarse to fine; returns (φ of the last run, report dict).
+    sphere = (cx, cy, cz, r): also report the L^1 error against its signed
+    distance."""
     pts = np.ascontiguousarray(pts, dtype=np.float64)
     out = np.empty(max_nodes)
     rep = MultirunReport()
+    sph = np.zeros(4) if sphere is None else np.asarray(sphere, dtype=np.float64)
     rc = lib().or_reconstruct(int(dim), int(prec), int(interp), int(runs), float(K_s), float(sample_frac), int(seed),
-                              int(max_nodes), int(max_iters), int(distance == "fsm"), pts.ctypes.data_as(_dp),
-                              int(pts.shape[0]),
+                              int(max_nodes), int(max_iters), int(distance == "fsm"), int(sphere is not None),
+                              sph.ctypes.data_as(_dp), pts.ctypes.data_as(_dp), int(pts.shape[0]),
                               out.ctypes.data_as(_dp), int(max_nodes), C.byref(rep))
     if rc != 0:
         raise ValueError("or_reconstruct failed")
     k = rep.runs_done
     n = tuple(rep.run_n[k - 1][:])
-    return out[: int(np.prod(n))].copy(), dict(h_s=rep.h_s, sample_size=rep.sample_size, runs_done=k, lo=tuple(rep.lo[:]),
-                                                run_dx=list(rep.run_dx[:k]),
-                                                run_n=[tuple(rep.run_n[r][:]) for r in range(k)],
-                                                run_iters=list(rep.run_iters[:k]),
-                                                run_converged=[bool(x) for x in rep.run_converged[:k]])
+    return out[: int(np.prod(n))].copy(), dict(
+        h_s=rep.h_s, sample_size=rep.sample_size, runs_done=k, run_dx=list(rep.run_dx[:k]),
+        run_n=[tuple(rep.run_n[r][:]) for r in range(k)], run_lo=[tuple(rep.run_lo[r][:]) for r in range(k)],
+        run_iters=list(rep.run_iters[:k]), run_converged=[bool(x) for x in rep.run_converged[:k]],
+        run_energy=list(rep.run_energy[:k]), run_err_cloud=list(rep.run_err_cloud[:k]),
+        run_l1_err=list(rep.run_l1_err[:k]))
+
+
+def l1_error(P, u, exact):
+    """§4 L^1 error Δx^dim Σ|c(u) - c(φ*)| (c: the cut at γ in band mode)."""
+    u, up = _d(u)
+    exact, ep = _d(exact)
+    return float(lib().or_l1_error(C.byref(P), up, ep))
+
+
+def sdf_sphere(P, sphere):
+    out = np.empty(num_nodes(P))
+    s = np.asarray(sphere, dtype=np.float64)
+    lib().or_sdf_sphere(C.byref(P), s.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
+    return out
 
 
 def fsm_solve(a, h):

@@ -1188,6 +1188,37 @@ int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, doub
     return n;
 }
 
+/* §4: the L^1 norm of the error against the exact level set, read as
+ * Δx^dim Σ_j |c(u_j) - c(φ*_j)| over every node, c the cut at γ in band mode
+ * (the identity on the whole grid) */
+double or_l1_error(const or_params* g, const double* u, const double* exact) {
+    long long N = or_num_nodes(g);
+    double s = 0.0;
+    for (long long j = 0; j < N; ++j) {
+        double a = u[j], b = exact[j];
+        if (g->band) {
+            a = fmin(fmax(a, -g->gamma), g->gamma);
+            b = fmin(fmax(b, -g->gamma), g->gamma);
+        }
+        s += fabs(a - b);
+    }
+    double vol = g->h * g->h;
+    if (g->dim == 3) vol *= g->h;
+    return s * vol;
+}
+
+/* signed distance |x - c| - r to a circle (2-D) / sphere (3-D) on every node */
+void or_sdf_sphere(const or_params* g, const double* sphere, double* out) {
+    long long N = or_num_nodes(g);
+    for (long long j = 0; j < N; ++j) {
+        double x[3];
+        or_node_coord(g, j, x);
+        double s2 = (x[0] - sphere[0]) * (x[0] - sphere[0]) + (x[1] - sphere[1]) * (x[1] - sphere[1]);
+        if (g->dim == 3) s2 += (x[2] - sphere[2]) * (x[2] - sphere[2]);
+        out[j] = sqrt(s2) - sphere[3];
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* §4 runs from coarse to fine (eq. dxdt, Tab. param)                    */
 /* ------------------------------------------------------------------ */
@@ -1217,15 +1248,18 @@ static long long or_grid_nodes(int dim, const double* bmin, const double* bmax, 
  * (every point when frac >= 1; point 0 if none); the box is the cloud's
  * bounding box widened by γ_S + 8 Δx(1), Δx(1) = h_S coarsened (×
  * (N/max_nodes)^(1/dim)·1.0001 until it fits); run r has Δx = Δx(1)/2^(r-1),
- * coarsened the same way, (p, δ) = (1, 0), (2, 0), then (2, 1), Δt = Δx/4,
+ * coarsened the same way, over the bounding box widened by 8 Δx(r), plus
+ * γ_S in run 1 (the box that gives the grids printed for the circle test,
+ * Tab. errGlobCircle), (p, δ) = (1, 0), (2, 0), then (2, 1), Δt = Δx/4,
  * band, reinitialisation; φ0 of run 1 by or_init_marking at γ_S = K_S h_S,
  * of later runs by Q1 (or_interp_q1) of the previous state at the new nodes;
  * both rounded to the storage type and cut; d exact, or by or_distance_fsm
  * when distance_fsm is set. phi_out receives the last run's
  * field (at most phi_cap values). Returns 0, or -1 (bad input / capacity). */
 int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
-                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, const double* pts,
-                   long long npts, double* phi_out, long long phi_cap, or_multirun_report* rep) {
+                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, int exact_sphere,
+                   const double* sphere, const double* pts, long long npts, double* phi_out, long long phi_cap,
+                   or_multirun_report* rep) {
     memset(rep, 0, sizeof(*rep));
     if (dim != 2 && dim != 3) return -1;
     double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0};
@@ -1259,20 +1293,19 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
         if (tot <= max_nodes) break;
         dx1 *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
     }
-    double margin = gamma_s + 8.0 * dx1;
-    double lo[3] = {0, 0, 0};
-    for (int a = 0; a < dim; ++a) lo[a] = bmin[a] - margin;
-    for (int a = 0; a < 3; ++a) rep->lo[a] = lo[a];
     double* prev = NULL;
     or_params pp;
     memset(&pp, 0, sizeof(pp));
     for (int r = 1; r <= runs; ++r) {
         double dx = dx1 / (double)(1ll << (r - 1));
         for (int it = 0; it < 200; ++it) {
-            long long tot = or_grid_nodes(dim, bmin, bmax, dx, margin, nn);
+            long long tot = or_grid_nodes(dim, bmin, bmax, dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
             if (tot <= max_nodes) break;
             dx *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
         }
+        double margin = 8.0 * dx + (r == 1 ? gamma_s : 0.0);
+        double lo[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) lo[a] = bmin[a] - margin;
         or_params P;
         memset(&P, 0, sizeof(P));
         P.dim = dim;
@@ -1325,6 +1358,16 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
         double* dphi = (double*)malloc(sizeof(double) * (size_t)(max_iters + 1));
         int conv = 0;
         int it = or_evolve_reinit(&P, u, d, 5, 1e-4, 10, 10, max_iters, 1, 0, 0.0, E2, dphi, &conv);
+        rep->run_energy[r - 1] = E2[it];
+        rep->run_err_cloud[r - 1] = or_err_cloud(&P, u, pts, npts);
+        rep->run_l1_err[r - 1] = NAN;
+        if (exact_sphere) {
+            double* ex = (double*)malloc(sizeof(double) * (size_t)N);
+            or_sdf_sphere(&P, sphere, ex);
+            rep->run_l1_err[r - 1] = or_l1_error(&P, u, ex);
+            free(ex);
+        }
+        for (int a = 0; a < 3; ++a) rep->run_lo[r - 1][a] = P.lo[a];
         free(E2);
         free(dphi);
         free(d);

@@ -167,15 +167,24 @@ typedef struct {
     double h_s;
     long long sample_size;
     int runs_done;
-    double lo[3];
     double run_dx[8];
     long long run_n[8][3];
+    double run_lo[8][3];
     int run_iters[8];
     int run_converged[8];
+    double run_energy[8];
+    double run_err_cloud[8];
+    double run_l1_err[8];
 } or_multirun_report;
 int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double sample_frac,
-                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, const double* pts,
-                   long long npts, double* phi_out, long long phi_cap, or_multirun_report* rep);
+                   unsigned long long seed, long long max_nodes, int max_iters, int distance_fsm, int exact_sphere,
+                   const double* sphere, const double* pts, long long npts, double* phi_out, long long phi_cap,
+                   or_multirun_report* rep);
+
+/* §4 L^1 error against an exact signed distance (cut at γ in band mode) */
+double or_l1_error(const or_params* g, const double* u, const double* exact);
+/* |x - c| - r on every node, sphere = {cx, cy, cz, r} */
+void or_sdf_sphere(const or_params* g, const double* sphere, double* out);
 
 /* nodes with |φ| < width, ascending index */
 long long or_extract(const or_params* g, const double* u, double width, long long* idx_out, double* u_out);

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -779,6 +780,42 @@ slr_status slr_get_field(slr_ctx* c, int which, void* host_out, int64_t cap) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_field");
+    return SLR_OK;
+}
+
+slr_status slr_l1_error(slr_ctx* c, int kind, const double* params, const double* exact_host, double* l1_out) {
+    if (!c) return SLR_E_INVALID;
+    if (!l1_out) return fail(c, SLR_E_INVALID, "l1_error: null output");
+    if (kind == 0 && !(params && params[3] >= 0.0 && std::isfinite(params[0]) && std::isfinite(params[1]) &&
+                       std::isfinite(params[2]) && std::isfinite(params[3])))
+        return fail(c, SLR_E_INVALID, "l1_error: a sphere needs finite {cx, cy, cz, r >= 0}");
+    if (kind == 1 && !exact_host) return fail(c, SLR_E_INVALID, "l1_error: null exact array");
+    if (kind < 0 || kind > 1) return fail(c, SLR_E_INVALID, "l1_error: kind must be 0 or 1");
+    if (!c->have_u) return fail(c, SLR_E_STATE, "l1_error: no level set");
+    DeviceGuard g(c->device);
+    int n = 0;
+    slr_status s = read_status(c, nullptr, nullptr, &n);
+    if (s != SLR_OK) return s;
+    const int blocks = c->num_sms * 4;
+    const size_t pbytes = (sizeof(double) * (size_t)blocks + 255) & ~size_t(255);
+    char* tmp = (char*)dev_alloc(c, pbytes + (kind == 1 ? sizeof(double) * (size_t)c->N : 0));
+    if (!tmp) return fail(c, SLR_E_NOMEM, "l1_error: scratch allocation failed");
+    double* part = (double*)tmp;
+    double* ex = kind == 1 ? (double*)(tmp + pbytes) : nullptr;
+    std::vector<double> hp((size_t)blocks);
+    cudaError_t e = cudaSuccess;
+    if (kind == 1) e = cudaMemcpyAsync(ex, exact_host, sizeof(double) * (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_l1_error(c, c->u[n & 1], kind, params, ex, part, blocks);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * (size_t)blocks, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "l1_error");
+    double sum = 0.0;
+    for (int b = 0; b < blocks; ++b) sum += hp[(size_t)b];
+    double vol = c->h * c->h;
+    if (c->cfg.dim == 3) vol *= c->h;
+    *l1_out = sum * vol;
     return SLR_OK;
 }
 

@@ -1,18 +1,22 @@
 // Several runs of Algorithm 1 from coarse to fine (§4: eq. dxdt and Tab.
 // param), every step on the device:
 //  - h_S, the cloud's resolution, from a sample of the points (slr_cloud_spacing);
-//  - run r on a grid of width Δx(r) = h_S / 2^(r-1) over one box that holds the
-//    cloud with a margin, with (p, δ) = (1, 0), (2, 0), (2, 1), (2, 1), ...;
-//  - φ^0 of the first run by external marking and fast sweeping at
-//    γ_S = K_S h_S (§3.6), of the later runs by Q1 interpolation of the
-//    previous run's steady state at the new nodes, then cut;
-//  - Algorithm 1 with the reinitialisation of §3.7 to the stop test of §4.
+//  - run r on a grid of width Δx(r) = h_S / 2^(r-1) over the cloud's bounding
+//    box widened by 8 Δx(r), plus γ_S = K_S h_S in the first run, with
+//    (p, δ) = (1, 0), (2, 0), (2, 1), (2, 1), ...;
+//  - φ^0 of the first run by external marking and fast sweeping at γ_S
+//    (§3.6), of the later runs by Q1 interpolation of the previous run's
+//    steady state at the new nodes, then cut;
+//  - Algorithm 1 with the reinitialisation of §3.7 to the stop test of §4;
+//  - at the end of each run, the quantities of the paper's tables: E_2, Err_S
+//    (eq. errCloud) and the L^1 error against an exact signed distance.
 // Readings (the paper leaves them open): the sample is a Bernoulli draw with
 // probability sample_frac per point, from a counter-based splitmix64 stream
-// (Steele, Lea and Flood 2014); the box is the cloud's bounding box widened by
-// K_S h_S + 8 Δx(1) on every side, the same for every run; a run whose grid
-// would exceed max_nodes is coarsened to fit (Δx grows by the dim-th root of
-// the excess); d is exact unless distance_fsm asks for the §3.4 construction.
+// (Steele, Lea and Flood 2014); the margin of the box is the one that gives
+// the grids printed for the circle test (42, 58, 99, 181 and 344 nodes per
+// axis); a run whose grid would exceed max_nodes is coarsened to fit (Δx
+// grows by the dim-th root of the excess); d is exact unless distance_fsm
+// asks for the §3.4 construction.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -83,6 +87,52 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
+// partial sums of |c(φ_j) - c(φ*_j)| per block (FP64); kind 0: φ* the
+// signed distance to a sphere, from correctly rounded FP64 operations
+constexpr int kL1Block = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kL1Block) k_l1_error(const T* __restrict__ u, GridGeom G, int kind, double cx,
+                                                       double cy, double cz, double r,
+                                                       const double* __restrict__ exact, int band, double gamma,
+                                                       long long N, double* __restrict__ part) {
+    __shared__ double s_sum[kL1Block / 32];
+    double acc = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) {
+        double ex;
+        if (kind == 0) {
+            const long long q = j / G.n[0];
+            const int i0 = (int)(j - q * G.n[0]);
+            const int i1 = (int)(q % G.n[1]), i2 = (int)(q / G.n[1]);
+            const double x = __dsub_rn(__dadd_rn(G.lo[0], __dmul_rn((double)i0, G.h)), cx);
+            const double y = __dsub_rn(__dadd_rn(G.lo[1], __dmul_rn((double)i1, G.h)), cy);
+            double s2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+            if (G.dim == 3) {
+                const double z = __dsub_rn(__dadd_rn(G.lo[2], __dmul_rn((double)i2, G.h)), cz);
+                s2 = __dadd_rn(s2, __dmul_rn(z, z));
+            }
+            ex = __dsub_rn(__dsqrt_rn(s2), r);
+        } else {
+            ex = exact[j];
+        }
+        double v = (double)u[j];
+        if (band) {
+            v = fmin(fmax(v, -gamma), gamma);
+            ex = fmin(fmax(ex, -gamma), gamma);
+        }
+        acc += fabs(v - ex);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kL1Block / 32; ++w) t += s_sum[w];
+        part[blockIdx.x] = t;
+    }
+}
+
 GridGeom geom_of(const slr_config& k) {
     GridGeom g;
     g.dim = k.dim;
@@ -95,6 +145,21 @@ GridGeom geom_of(const slr_config& k) {
 }
 
 }  // namespace
+
+cudaError_t launch_l1_error(slr_ctx* c, const void* u, int kind, const double* prm, const double* exact_dev,
+                            double* part, int blocks) {
+    const GridGeom G = geom_of(c->cfg);
+    const double cx = kind == 0 ? prm[0] : 0.0, cy = kind == 0 ? prm[1] : 0.0;
+    const double cz = kind == 0 && c->cfg.dim == 3 ? prm[2] : 0.0, r = kind == 0 ? prm[3] : 0.0;
+    if (c->cfg.precision == 32)
+        k_l1_error<float><<<blocks, kL1Block, 0, c->stream>>>((const float*)u, G, kind, cx, cy, cz, r, exact_dev,
+                                                              c->cfg.band, c->gamma, c->N, part);
+    else
+        k_l1_error<double><<<blocks, kL1Block, 0, c->stream>>>((const double*)u, G, kind, cx, cy, cz, r, exact_dev,
+                                                               c->cfg.band, c->gamma, c->N, part);
+    c->launches += 1;
+    return cudaGetLastError();
+}
 
 }  // namespace slr
 
@@ -114,6 +179,8 @@ void slr_multirun_default(slr_multirun_config* mc) {
     mc->seed = 1;
     mc->max_nodes = 1ll << 27;
     mc->max_iters = 100;
+    mc->distance_fsm = 0;
+    mc->exact_sphere = 0;
 }
 
 slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int64_t n_points,
@@ -125,7 +192,9 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     if (dim != 2 && dim != 3) return SLR_E_INVALID;
     if (mc->runs < 1 || mc->runs > SLR_MAX_RUNS || !(mc->K_s > 0.0) || !(mc->sample_frac > 0.0) ||
         !(mc->sample_frac <= 1.0) || mc->max_nodes < 64 || mc->max_iters < 1 ||
-        (mc->distance_fsm != 0 && mc->distance_fsm != 1))
+        (mc->distance_fsm != 0 && mc->distance_fsm != 1) || (mc->exact_sphere != 0 && mc->exact_sphere != 1) ||
+        (mc->exact_sphere && !(mc->sphere[3] >= 0.0 && isfinite(mc->sphere[0]) && isfinite(mc->sphere[1]) &&
+                               isfinite(mc->sphere[2]) && isfinite(mc->sphere[3]))))
         return SLR_E_INVALID;
     slr_multirun_report rep;
     memset(&rep, 0, sizeof(rep));
@@ -177,8 +246,8 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     rep.h_s = hs;
     rep.sample_size = (int64_t)sample.size();
     const double gamma_s = mc->K_s * hs;
-    // one box for every run: the cloud's bounding box widened by
-    // γ_S + 8 Δx(1), with Δx(1) = h_S coarsened until the first grid fits
+    // the box of run r: the cloud's bounding box widened by 8 Δx(r), plus
+    // γ_S in the first run; Δx(1) = h_S coarsened until the first grid fits
     auto nodes_for = [&](double dx, double margin, long long nn[3]) {
         long long tot = 1;
         for (int a = 0; a < 3; ++a) nn[a] = 1;
@@ -199,21 +268,21 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
         }
     }
     if (dx1 > hs * 1.000001) rep.coarsened = 1;
-    const double margin = gamma_s + 8.0 * dx1;
-    double lo[3] = {0, 0, 0};
-    for (int a = 0; a < dim; ++a) lo[a] = bmin[a] - margin;
-    for (int a = 0; a < 3; ++a) rep.lo[a] = lo[a];
+    std::vector<double> e2buf((size_t)mc->max_iters + 2);
     slr_ctx* prev = nullptr;
     slr_status status = SLR_OK;
     for (int r = 1; r <= mc->runs && status == SLR_OK; ++r) {
         double dx = dx1 / (double)(1ll << (r - 1));
         long long nn[3];
         for (int it = 0; it < 200; ++it) {
-            const long long tot = nodes_for(dx, margin, nn);
+            const long long tot = nodes_for(dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
             if (tot <= mc->max_nodes) break;
             dx *= pow((double)tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
         }
         if (dx > dx1 / (double)(1ll << (r - 1)) * 1.000001) rep.coarsened = 1;
+        const double margin = 8.0 * dx + (r == 1 ? gamma_s : 0.0);
+        double lo[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) lo[a] = bmin[a] - margin;
         slr_config k;
         slr_config_default(&k);
         k.dim = dim;
@@ -276,6 +345,16 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
             for (int a = 0; a < 3; ++a) rep.run_n[r - 1][a] = k.n[a];
             rep.run_iters[r - 1] = iters;
             rep.run_converged[r - 1] = conv;
+            for (int a = 0; a < 3; ++a) rep.run_lo[r - 1][a] = k.lo[a];
+            int nit = 0;
+            double errc = 0.0;
+            status = slr_diagnostics(c, e2buf.data(), nullptr, nullptr, (int)e2buf.size(), &nit, &errc);
+            if (status == SLR_OK) {
+                rep.run_energy[r - 1] = e2buf[nit < (int)e2buf.size() ? nit : (int)e2buf.size() - 1];
+                rep.run_err_cloud[r - 1] = errc;
+                rep.run_l1_err[r - 1] = NAN;
+                if (mc->exact_sphere) status = slr_l1_error(c, 0, mc->sphere, nullptr, &rep.run_l1_err[r - 1]);
+            }
         }
         if (prev) slr_destroy(prev);
         prev = c;

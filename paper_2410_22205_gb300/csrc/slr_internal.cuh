@@ -162,6 +162,10 @@ cudaError_t distance_on_marked(slr_ctx* c, const unsigned char* mask, double* do
 // §3.4: exact on the 4^dim node box around each point, fast sweeping elsewhere
 // (cudaErrorInvalidValue: no point within a cell of the grid)
 cudaError_t build_distance_fsm(slr_ctx* c);
+// per-block partial sums of |c(u_j) - c(φ*_j)| (kind 0: sphere prm = {cx, cy,
+// cz, r}; kind 1: exact_dev) into part[0..blocks)
+cudaError_t launch_l1_error(slr_ctx* c, const void* u, int kind, const double* prm, const double* exact_dev,
+                            double* part, int blocks);
 long long energy_blocks(const slr_ctx* c);
 const char* noalloc_last_error();
 long long full_step_blocks(const slr_ctx* c);

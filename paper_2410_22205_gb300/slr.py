@@ -34,7 +34,7 @@ EXPORTS = [
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches",
-    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing",
+    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
     "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
 ]
@@ -85,6 +85,8 @@ class slr_multirun_config(C.Structure):
         ("max_nodes", C.c_int64),
         ("max_iters", C.c_int),
         ("distance_fsm", C.c_int),
+        ("exact_sphere", C.c_int),
+        ("sphere", C.c_double * 4),
     ]
 
 
@@ -97,11 +99,14 @@ class slr_multirun_report(C.Structure):
         ("sample_size", C.c_int64),
         ("runs_done", C.c_int),
         ("coarsened", C.c_int),
-        ("lo", C.c_double * 3),
         ("run_dx", C.c_double * SLR_MAX_RUNS),
         ("run_n", (C.c_int64 * 3) * SLR_MAX_RUNS),
+        ("run_lo", (C.c_double * 3) * SLR_MAX_RUNS),
         ("run_iters", C.c_int * SLR_MAX_RUNS),
         ("run_converged", C.c_int * SLR_MAX_RUNS),
+        ("run_energy", C.c_double * SLR_MAX_RUNS),
+        ("run_err_cloud", C.c_double * SLR_MAX_RUNS),
+        ("run_l1_err", C.c_double * SLR_MAX_RUNS),
     ]
 
 
@@ -149,6 +154,7 @@ def lib():
                 "slr_last_iteration_phases": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_kernel_launches": (C.c_int64, [_vp]),
                 "slr_cloud_spacing": (C.c_int, [_vp, _i64p, C.c_int64, _dp]),
+                "slr_l1_error": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
                 "slr_distance_grid_noalloc": (C.c_int, [C.c_int, _i64p, _dp, C.c_double, C.c_int, _vp, C.c_int64,
@@ -278,6 +284,19 @@ def slr_cloud_spacing(ctx, sample):
     s = np.ascontiguousarray(sample, dtype=np.int64)
     out = C.c_double(0.0)
     _check(ctx, lib().slr_cloud_spacing(ctx, _ptr(s, _i64p), int(s.size), C.byref(out)))
+    return out.value
+
+
+def slr_l1_error(ctx, sphere=None, exact=None):
+    """§4 L^1 error against |x - c| - r (sphere = (cx, cy, cz, r)) or an
+    exact array of every node."""
+    out = C.c_double(0.0)
+    if sphere is not None:
+        prm = _f64(sphere)
+        _check(ctx, lib().slr_l1_error(ctx, 0, _ptr(prm), None, C.byref(out)))
+    else:
+        ex = _f64(exact)
+        _check(ctx, lib().slr_l1_error(ctx, 1, None, _ptr(ex), C.byref(out)))
     return out.value
 
 
@@ -482,25 +501,31 @@ def slr_reconstruct(mc, xyz, allocator=None, stream=None):
         raise SlrError(status, msg.decode() if msg else "")
     k = rep.runs_done
     report = dict(h_s=rep.h_s, sample_size=rep.sample_size, runs_done=k, coarsened=bool(rep.coarsened),
-                  lo=tuple(rep.lo[:]),
                   run_dx=list(rep.run_dx[:k]), run_n=[tuple(rep.run_n[r][:]) for r in range(k)],
-                  run_iters=list(rep.run_iters[:k]), run_converged=[bool(x) for x in rep.run_converged[:k]])
+                  run_lo=[tuple(rep.run_lo[r][:]) for r in range(k)],
+                  run_iters=list(rep.run_iters[:k]), run_converged=[bool(x) for x in rep.run_converged[:k]],
+                  run_energy=list(rep.run_energy[:k]), run_err_cloud=list(rep.run_err_cloud[:k]),
+                  run_l1_err=list(rep.run_l1_err[:k]))
     return h.value, report
 
 
 def reconstruct(xyz, dim=3, precision=32, interp=1, runs=3, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 27,
-                max_iters=100, distance="exact", stream=None):
+                max_iters=100, distance="exact", sphere=None, stream=None):
     """The paper's pipeline from a cloud (§4): h_S, the §3.6 initial data, then
     `runs` runs of Algorithm 1 from coarse to fine. distance: "exact" or
-    "fsm" (the §3.4 construction). Returns (Reconstruction of the last run,
-    report)."""
+    "fsm" (the §3.4 construction). sphere = (cx, cy, cz, r): report the L^1
+    error of every run against its signed distance. Returns (Reconstruction of
+    the last run, report)."""
     import torch
 
     if distance not in ("exact", "fsm"):
         raise ValueError(f"unknown distance method {distance!r}")
     mc = slr_multirun_default(dim=dim, precision=precision, interp=interp, runs=runs, K_s=K_s,
                               sample_frac=sample_frac, seed=seed, max_nodes=max_nodes, max_iters=max_iters,
-                              distance_fsm=int(distance == "fsm"))
+                              distance_fsm=int(distance == "fsm"), exact_sphere=int(sphere is not None))
+    if sphere is not None:
+        for i in range(4):
+            mc.sphere[i] = float(sphere[i])
     dev = torch.cuda.current_device()
     s = stream if stream is not None else torch.cuda.Stream(dev)
     al = _TorchAllocator(dev, s.cuda_stream)
@@ -573,6 +598,10 @@ class Reconstruction:
     def cloud_spacing(self, sample):
         """h_S of §4: mean nearest-other-point distance over the sampled points."""
         return slr_cloud_spacing(self.ctx, sample)
+
+    def l1_error(self, sphere=None, exact=None):
+        """§4 L^1 error of the current state against an exact signed distance."""
+        return slr_l1_error(self.ctx, sphere=sphere, exact=exact)
 
     def init_marking(self, gamma_s):
         """§3.6 initial data from the cloud: external marking and fast sweeping."""

@@ -809,9 +809,9 @@ def test_multirun_sample_is_a_bernoulli_draw():
 def test_multirun_grids_halve_and_reach_the_cloud():
     """§4 eq. dxdt and Tab. param on the paper's circle of equally spaced
     points: h_S = 2R sin(π/n) (the chord to either neighbour); the grid width
-    halves from run to run over one box that holds the cloud with the margin
-    K_S h_S + 8 Δx(1); after the runs the zero level set lies on the cloud
-    (eq. errCloud well below Δx of the last run)."""
+    halves from run to run; run r covers the cloud's box widened by 8 Δx(r)
+    (plus K_S h_S in run 1); after the runs the zero level set lies on the
+    cloud (eq. errCloud well below Δx of the last run)."""
     n, R, K = 400, 0.45, 2.0
     pts = synth.circle_uniform(n, R)
     phi, rep = O.reconstruct(pts, 2, runs=3, K_s=K, sample_frac=1.0, max_nodes=1 << 22, max_iters=100)
@@ -820,20 +820,64 @@ def test_multirun_grids_halve_and_reach_the_cloud():
     assert rep["sample_size"] == n and rep["runs_done"] == 3
     dx = rep["run_dx"]
     assert dx[0] == rep["h_s"] and dx[1] == dx[0] / 2 and dx[2] == dx[0] / 4
-    margin = K * hs + 8 * dx[0]
     for r in range(3):
+        margin = 8 * dx[r] + (K * hs if r == 0 else 0.0)
         for a in range(2):
-            lo = rep["lo"][a]
+            lo = rep["run_lo"][r][a]
             assert lo == pytest.approx(pts[:, a].min() - margin, rel=0, abs=1e-15)
             top = lo + (rep["run_n"][r][a] - 1) * dx[r]
             assert top >= pts[:, a].max() + margin - 1e-12
             assert top - dx[r] < pts[:, a].max() + margin
         assert 1 <= rep["run_iters"][r] <= 100
     nn = rep["run_n"][2]
-    P = O.params(2, nn[:2], rep["lo"][:2], h=dx[2], band=1)
+    P = O.params(2, nn[:2], rep["run_lo"][2][:2], h=dx[2], band=1)
     assert O.err_cloud(P, phi, pts) < 0.25 * dx[2]
+    assert rep["run_err_cloud"][2] == pytest.approx(O.err_cloud(P, phi, pts), rel=1e-15)
     # a signed distance near the cloud: negative at the centre side, positive outside
     assert phi.max() > 0 and phi.min() < 0
+
+
+def _circle_table():
+    path = os.path.join(os.path.dirname(__file__), "golden", "circle64_runs_table.txt")
+    rows, hs = [], None
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        f = line.split()
+        if f[0] == "h_s":
+            hs = float(f[1])
+        else:
+            rows.append([float(x) for x in f])
+    return hs, np.array(rows)
+
+
+@pytest.mark.parametrize("interp", [0, 1])
+def test_circle_test_reproduces_the_papers_grids_and_trends(interp):
+    """The circle test of §4.1 with five runs (Tab. errGlobCircle): the grids
+    are the printed ones exactly; h_S is the printed 9.81e-2; the L^1 error
+    against the exact signed distance falls from run to run and ends within
+    a factor 1.5 of the printed value; the error on the cloud stays within a
+    factor 1.6 of the printed values; E_2 of the final state is within 1% of
+    the circle's exact energy (the reference line of the E_2 panel)."""
+    hs, tab = _circle_table()
+    with open(os.path.join(os.path.dirname(__file__), "golden", "circle64_energy.txt")) as f:
+        e_exact = float([ln for ln in f if ln.strip() and not ln.startswith("#")][0])
+    pts = synth.circle_uniform(64, 1.0)
+    _, rep = O.reconstruct(pts, 2, prec=64, interp=interp, runs=5, K_s=2.0, sample_frac=0.1, seed=1,
+                           max_nodes=1 << 22, max_iters=100, sphere=(0.0, 0.0, 0.0, 1.0))
+    assert round(rep["h_s"], 4) == pytest.approx(hs, abs=1e-4)
+    assert [n[0] for n in rep["run_n"]] == [int(x) for x in tab[:, 1]]
+    assert [n[1] for n in rep["run_n"]] == [int(x) for x in tab[:, 1]]
+    col = 2 if interp == 0 else 5
+    l1, ecl = np.array(rep["run_l1_err"]), np.array(rep["run_err_cloud"])
+    assert np.all(np.diff(l1) < 0)
+    assert 1 / 1.5 < l1[-1] / tab[-1, col] < 1.5
+    assert np.all(np.abs(np.log(l1 / tab[:, col])) < np.log(4.0))
+    assert np.all(np.abs(np.log(ecl / tab[:, col + 2])) < np.log(1.6))
+    assert rep["run_energy"][-1] == pytest.approx(e_exact, rel=1e-2)
+    assert np.all(np.diff(rep["run_energy"]) < 0)
+    assert all(rep["run_converged"])
 
 
 def test_multirun_coarsens_to_the_node_budget():
