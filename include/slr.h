@@ -293,7 +293,8 @@ slr_status slr_l1_error(slr_ctx* ctx, int kind, const double* params, const doub
  * first run is the §3.6 initial data at γ_S; each later run starts from the
  * previous run's steady state, interpolated (Q1) at its nodes and cut. A run
  * whose grid would exceed max_nodes is coarsened until it fits
- * (report->coarsened). The sample is a Bernoulli draw with probability
+ * (report->coarsened); a coarsened first run takes γ_S = K_S Δx(1), so that
+ * the marked shell around the cloud stays closed on its grid. The sample is a Bernoulli draw with probability
  * sample_frac per point from the counter-based splitmix64 stream of `seed`
  * (point i is drawn when splitmix64(seed + (i+1)·0x9E3779B97F4A7C15) <
  * sample_frac·2^64).
@@ -309,7 +310,8 @@ typedef struct {
     int precision;       /* 32 or 64 */
     int interp;          /* 0 = Q1, 1 = WENO */
     int runs;            /* runs of Algorithm 1, 1..SLR_MAX_RUNS, default 3 */
-    double K_s;          /* γ_S = K_S h_S for the initial data, default 2 */
+    double K_s;          /* γ_S = K_S h_S for the initial data, default 2;
+                            K_S Δx(1) when the first grid is coarsened */
     double sample_frac;  /* fraction of the points sampled for h_S, default 0.1 */
     uint64_t seed;       /* sample stream, default 1 */
     int64_t max_nodes;   /* node budget of one run, default 2^27 */

@@ -1247,11 +1247,12 @@ static long long or_grid_nodes(int dim, const double* bmin, const double* bmax, 
 /* Readings: the sample draws point i when splitmix64(seed, i) < frac·2^64
  * (every point when frac >= 1; point 0 if none); the box is the cloud's
  * bounding box widened by γ_S + 8 Δx(1), Δx(1) = h_S coarsened (×
- * (N/max_nodes)^(1/dim)·1.0001 until it fits); run r has Δx = Δx(1)/2^(r-1),
+ * (N/max_nodes)^(1/dim)·1.0001 until it fits; γ_S = K_S Δx(1), which is
+ * K_S h_S unless coarsened); run r has Δx = Δx(1)/2^(r-1),
  * coarsened the same way, over the bounding box widened by 8 Δx(r), plus
  * γ_S in run 1 (the box that gives the grids printed for the circle test,
  * Tab. errGlobCircle), (p, δ) = (1, 0), (2, 0), then (2, 1), Δt = Δx/4,
- * band, reinitialisation; φ0 of run 1 by or_init_marking at γ_S = K_S h_S,
+ * band, reinitialisation; φ0 of run 1 by or_init_marking at γ_S,
  * of later runs by Q1 (or_interp_q1) of the previous state at the new nodes;
  * both rounded to the storage type and cut; d exact, or by or_distance_fsm
  * when distance_fsm is set. phi_out receives the last run's
@@ -1285,14 +1286,16 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
     free(sample);
     rep->h_s = hs;
     rep->sample_size = m;
-    double gamma_s = K_s * hs;
     long long nn[3];
     double dx1 = hs;
     for (int it = 0; it < 200; ++it) {
-        long long tot = or_grid_nodes(dim, bmin, bmax, dx1, gamma_s + 8.0 * dx1, nn);
+        long long tot = or_grid_nodes(dim, bmin, bmax, dx1, (K_s + 8.0) * dx1, nn);
         if (tot <= max_nodes) break;
         dx1 *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
     }
+    /* γ_S = K_S h_S, or K_S Δx(1) on a coarsened first grid (the marked
+     * shell must stay closed on the grid) */
+    double gamma_s = K_s * dx1;
     double* prev = NULL;
     or_params pp;
     memset(&pp, 0, sizeof(pp));

@@ -2,10 +2,11 @@
 // param), every step on the device:
 //  - h_S, the cloud's resolution, from a sample of the points (slr_cloud_spacing);
 //  - run r on a grid of width Δx(r) = h_S / 2^(r-1) over the cloud's bounding
-//    box widened by 8 Δx(r), plus γ_S = K_S h_S in the first run, with
+//    box widened by 8 Δx(r), plus γ_S in the first run, with
 //    (p, δ) = (1, 0), (2, 0), (2, 1), (2, 1), ...;
-//  - φ^0 of the first run by external marking and fast sweeping at γ_S
-//    (§3.6), of the later runs by Q1 interpolation of the previous run's
+//  - φ^0 of the first run by external marking and fast sweeping at
+//    γ_S = K_S Δx(1) (§3.6; K_S h_S unless the first grid was coarsened), of
+//    the later runs by Q1 interpolation of the previous run's
 //    steady state at the new nodes, then cut;
 //  - Algorithm 1 with the reinitialisation of §3.7 to the stop test of §4;
 //  - at the end of each run, the quantities of the paper's tables: E_2, Err_S
@@ -245,7 +246,6 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     }
     rep.h_s = hs;
     rep.sample_size = (int64_t)sample.size();
-    const double gamma_s = mc->K_s * hs;
     // the box of run r: the cloud's bounding box widened by 8 Δx(r), plus
     // γ_S in the first run; Δx(1) = h_S coarsened until the first grid fits
     auto nodes_for = [&](double dx, double margin, long long nn[3]) {
@@ -262,12 +262,15 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     {
         long long nn[3];
         for (int it = 0; it < 200; ++it) {
-            const long long tot = nodes_for(dx1, gamma_s + 8.0 * dx1, nn);
+            const long long tot = nodes_for(dx1, (mc->K_s + 8.0) * dx1, nn);
             if (tot <= mc->max_nodes) break;
             dx1 *= pow((double)tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
         }
     }
     if (dx1 > hs * 1.000001) rep.coarsened = 1;
+    // γ_S = K_S h_S; on a coarsened first grid K_S Δx(1), so that the nodes
+    // within γ_S of the cloud still form a closed shell for the marking
+    const double gamma_s = mc->K_s * dx1;
     std::vector<double> e2buf((size_t)mc->max_iters + 2);
     slr_ctx* prev = nullptr;
     slr_status status = SLR_OK;
