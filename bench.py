@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--reinit", action="store_true",
+                    help="time the iteration with the reinitialisation of §3.7 (Algorithm 1 step 4d) on")
     ap.add_argument("--batch-jobs", type=int, default=64, help="jobs of the batched mix (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson serving run length (0: skip)")
     return ap.parse_args()
@@ -275,7 +277,7 @@ def run_gpu(args):
     grid, cloud = workload(args)
     cloud_s = time.time() - t_setup
     n = args.n
-    rec = slr.Reconstruction(dim=3, n=n, precision=32, interp=1, band=1, **cfg_kw())
+    rec = slr.Reconstruction(dim=3, n=n, precision=32, interp=1, band=1, reinit=int(args.reinit), **cfg_kw())
     st = rec.stream
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     rec.load_cloud(cloud)
@@ -314,6 +316,9 @@ def run_gpu(args):
     roof["kernel_share_of_step"] = float(kmean[dom] / np.mean(step_ms))
     roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
     iter_lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
+    if args.reinit:
+        roof["phases_ms"] = {k: float(v) for k, v in
+                             zip(("step", "reinit", "energy", "record"), rec.last_iteration_phases())}
     rec.close()
     phase_s = {"cloud_generation": cloud_s, "setup_and_timed_steps": time.time() - t_setup - cloud_s}
     t_ph = time.time()
@@ -370,7 +375,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded superquadric-union cloud)",
-            "config": {"workload": f"sq3union{args.points // 1000}k_{n}cube_band6h_weno_fp32", "grid": f"{n}^3",
+            "config": {"workload": f"sq3union{args.points // 1000}k_{n}cube_band6h_weno_fp32"
+                                   + ("_reinit" if args.reinit else ""), "grid": f"{n}^3", "reinit": bool(args.reinit),
                        "points": args.points, "interp": "WENO", "band": "6h", "p": 2, "delta": 1,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{dist.world}",
                        "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},

@@ -443,6 +443,8 @@ slr_status slr_build_distance_fsm(slr_ctx* c) {
     if (e == cudaErrorInvalidValue)
         return fail(c, SLR_E_INVALID, "build_distance_fsm: no point within a cell of the grid, or non-finite points");
     if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "build_distance_fsm: scratch allocation failed");
+    if (e == cudaErrorLaunchTimeout)
+        return fail(c, SLR_E_STATE, "build_distance_fsm: a grid barrier of the fast sweeping waited too long");
     if (e != cudaSuccess) return cuda_fail(c, e, "build_distance_fsm");
     c->have_d = true;
     return SLR_OK;
@@ -499,6 +501,8 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
         if (e != cudaSuccess) {
             dev_free(c, tmp);
             if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "init_u: marking buffers");
+            if (e == cudaErrorLaunchTimeout)
+                return fail(c, SLR_E_STATE, "init_u: a grid barrier of the fast sweeping waited too long");
             return cuda_fail(c, e, "init_u marking");
         }
     }

@@ -142,6 +142,55 @@ __global__ void k_fsm_plane(double* phi, const unsigned char* __restrict__ ext, 
     }
 }
 
+// every plane of every ordering of both rounds in one cooperative launch:
+// the blocks cross from one plane to the next through a grid-wide barrier;
+// neighbour values come through L2 (__ldcg), where the previous plane's
+// writes of the other blocks are visible after the barrier
+template <int DIM>
+__global__ void __launch_bounds__(kIB) k_fsm_coop(double* phi, const unsigned char* __restrict__ fixed, int n0,
+                                                  int n1, int n2, double h, unsigned* bar, int* err) {
+    const long long st1 = n0, st2 = (long long)n0 * n1;
+    const long long count = DIM == 3 ? (long long)n1 * n2 : (long long)n1;
+    const int planes = n0 + n1 + (DIM == 3 ? n2 : 1) - 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    for (int round = 0; round < 2; ++round)
+        for (int ord = 0; ord < (1 << DIM); ++ord)
+            for (int s = 0; s < planes; ++s) {
+                for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+                    const int jj = (int)(t % n1), kk = DIM == 3 ? (int)(t / n1) : 0;
+                    const int ii = s - jj - kk;
+                    if (ii < 0 || ii >= n0) continue;
+                    const int c0 = (ord & 1) ? n0 - 1 - ii : ii;
+                    const int c1 = (ord & 2) ? n1 - 1 - jj : jj;
+                    const int c2 = (ord & 4) ? n2 - 1 - kk : kk;
+                    const long long idx = c0 + st1 * c1 + st2 * c2;
+                    if (fixed[idx]) continue;
+                    double a[3];
+                    {
+                        const double lo = c0 > 0 ? __ldcg(phi + idx - 1) : inf;
+                        const double hi = c0 < n0 - 1 ? __ldcg(phi + idx + 1) : inf;
+                        a[0] = lo < hi ? lo : hi;
+                    }
+                    {
+                        const double lo = c1 > 0 ? __ldcg(phi + idx - st1) : inf;
+                        const double hi = c1 < n1 - 1 ? __ldcg(phi + idx + st1) : inf;
+                        a[1] = lo < hi ? lo : hi;
+                    }
+                    if (DIM == 3) {
+                        const double lo = c2 > 0 ? __ldcg(phi + idx - st2) : inf;
+                        const double hi = c2 < n2 - 1 ? __ldcg(phi + idx + st2) : inf;
+                        a[2] = lo < hi ? lo : hi;
+                    } else {
+                        a[2] = inf;
+                    }
+                    const double x = fsm_solve(a[0], a[1], a[2], DIM, h);
+                    if (x < __ldcg(phi + idx)) __stcg(phi + idx, x);
+                }
+                if (!grid_barrier(bar, err)) return;
+            }
+}
+
 __global__ void k_phi_finish(double* phi, const unsigned char* __restrict__ ext, long long N) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride)
@@ -149,14 +198,39 @@ __global__ void k_phi_finish(double* phi, const unsigned char* __restrict__ ext,
 }
 
 // two rounds of Gauss-Seidel sweeps in the 2^dim orderings over the nodes
-// that are not fixed, one launch per plane of an ordering
-void fsm_sweeps(slr_ctx* c, double* phi, const unsigned char* fixed) {
+// that are not fixed: one cooperative launch with a grid barrier between
+// planes where the device supports it (bar: two zeroed words, err: one
+// zeroed word, both device memory), else one launch per plane
+cudaError_t fsm_sweeps(slr_ctx* c, double* phi, const unsigned char* fixed, unsigned* bar, int* err) {
     const int n0 = (int)c->cfg.n[0], n1 = (int)c->cfg.n[1], n2 = c->cfg.dim == 3 ? (int)c->cfg.n[2] : 1;
     const int dim = c->cfg.dim;
     const int grid = c->num_sms * 8;
     const long long count = dim == 3 ? (long long)n1 * n2 : (long long)n1;
     const int pgrid = (int)((count + kIB - 1) / kIB < grid ? (count + kIB - 1) / kIB : grid);
     const int planes = n0 + n1 + (dim == 3 ? n2 : 1) - 2;
+    int coop = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (coop) {
+        cudaError_t e = dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsm_coop<3>, kIB, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsm_coop<2>, kIB, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+    }
+    if (coop && per_sm > 0) {
+        const long long cap = (long long)c->num_sms * per_sm;
+        const int cgrid = (int)(cap < (count + kIB - 1) / kIB ? cap : (count + kIB - 1) / kIB);
+        double h = c->h;
+        void* args[] = {&phi, (void*)&fixed, (void*)&n0, (void*)&n1, (void*)&n2, &h, &bar, &err};
+        cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel(dim == 3 ? (const void*)k_fsm_coop<3> : (const void*)k_fsm_coop<2>,
+                                            dim3(cgrid), dim3(kIB), args, 0, c->stream);
+        c->launches += 1;
+        return e;
+    }
     for (int round = 0; round < 2; ++round)
         for (int ord = 0; ord < (1 << dim); ++ord)
             for (int s = 0; s < planes; ++s) {
@@ -166,6 +240,23 @@ void fsm_sweeps(slr_ctx* c, double* phi, const unsigned char* fixed) {
                     k_fsm_plane<2><<<pgrid, kIB, 0, c->stream>>>(phi, fixed, ord, s, n0, n1, n2, c->h);
             }
     c->launches += 2ll * (1 << dim) * planes;
+    return cudaGetLastError();
+}
+
+// the sweeps with their barrier words and error word in a small scratch;
+// a barrier that waited too long reports cudaErrorLaunchTimeout
+cudaError_t sweeps_checked(slr_ctx* c, double* phi, const unsigned char* fixed) {
+    void* base = dev_alloc(c, 256);
+    if (!base) return cudaErrorMemoryAllocation;
+    unsigned* bar = (unsigned*)base;
+    int* err = (int*)((char*)base + 64);
+    int herr = 0;
+    cudaError_t e = fsm_sweeps(c, phi, fixed, bar, err);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, base);
+    if (e == cudaSuccess && herr) e = cudaErrorLaunchTimeout;
+    return e;
 }
 
 struct GridBox {
@@ -190,7 +281,9 @@ cudaError_t marking_t(slr_ctx* c, double gamma_s, double* phi, unsigned char* ex
     k_phi_start<T><<<grid, kIB, 0, c->stream>>>(phi, ext, d, gamma_s, c->N);
     ++launches;
     c->launches += launches;
-    fsm_sweeps(c, phi, ext);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = sweeps_checked(c, phi, ext);
+    if (e != cudaSuccess) return e;
     k_phi_finish<<<grid, kIB, 0, c->stream>>>(phi, ext, c->N);
     c->launches += 1;
     return cudaGetLastError();
@@ -291,8 +384,8 @@ cudaError_t build_distance_fsm(slr_ctx* c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && hcount == 0) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = distance_on_marked(c, fixed, dv);
+    if (e == cudaSuccess) e = sweeps_checked(c, dv, fixed);
     if (e == cudaSuccess) {
-        fsm_sweeps(c, dv, fixed);
         if (c->cfg.precision == 32)
             k_store_rounded<float><<<grid, kIB, 0, c->stream>>>(dv, (float*)c->d, N);
         else

@@ -24,6 +24,44 @@ constexpr int kMaxR = 8;             // largest supported energy subcell count p
 constexpr int kRecordBlocks = 32;    // blocks of the record kernel (slices of the tile counts)
 constexpr int kMaxStopK = 1023;      // bound on the stop window k_max (staged in shared memory)
 constexpr int kErrBandOffset = 1;    // DevState::error: a band-list write fell outside the list
+constexpr int kErrBarrier = 2;       // a grid-wide barrier of a cooperative kernel waited too long
+constexpr long long kBarrierSpinLimit = 1ll << 22;  // polls of one barrier wait (~0.3 s with the sleeps)
+
+// Grid-wide barrier of a cooperative launch (every block co-resident).
+// bar[0] counts the arrivals, bar[1] is the generation; both start at 0.
+// Writes before the barrier are visible to loads after it that bypass L1
+// (__ldcg). A wait longer than the poll limit sets kErrBarrier in *err and
+// makes every block of the caller see false, so the kernel can return.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(bar, 1u) == nb - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long polls = 0;
+            while (*vgen == gen) {
+                if (++polls > kBarrierSpinLimit || (*(volatile int*)err & kErrBarrier)) {
+                    ok = 0;
+                    atomicOr(err, kErrBarrier);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 // ---------------------------------------------------------------------------
 // device-resident state of one job (one allocation)
