@@ -95,3 +95,20 @@ def test_multirun_with_the_swept_distance_matches_the_oracle():
     assert np.abs(rec.u() - ref_phi).max() <= 1e-9
     assert rec.diagnostics(err_cloud=True)["err_cloud"] < 0.5 * rep["run_dx"][-1]
     rec.close()
+
+
+@pytest.mark.parametrize("dim,shape,prec", [(3, (33, 41, 29), 32), (3, (21, 17, 26), 64), (2, (37, 29), 32)])
+def test_distance_fsm_bit_exact_on_ragged_grids(dim, shape, prec):
+    slr = _slr()
+    shape = tuple(shape) + ((1,) if dim == 2 else ())
+    los = (-1.0,) * dim
+    his = tuple(-1.0 + 2.0 * (shape[a] - 1) / (shape[0] - 1) for a in range(dim))
+    rec = slr.Reconstruction(dim=dim, n=shape, lo=los, hi=his, precision=prec, interp=1, band=1)
+    P = O.params(dim, shape[:dim], los, his, band=1, prec=prec)
+    pts = synth.sphere_even(3000, 0.45) if dim == 3 else synth.circle_even_noisy(500, 0.45, 0.003, 5)
+    rec.load_cloud(pts)
+    rec.build_distance("fsm")
+    ref, fix = O.distance_fsm(P, pts)
+    if prec == 32:
+        ref = ref.astype(np.float32).astype(np.float64)
+    assert np.array_equal(rec.d(), ref)

@@ -176,3 +176,21 @@ def test_sphere_test_of_the_paper():
         assert all(rep["run_converged"])
     assert reps[1]["run_l1_err"][-1] < reps[0]["run_l1_err"][-1]
     assert reps[1]["run_err_cloud"][-1] < reps[0]["run_err_cloud"][-1]
+
+
+def test_multirun_edge_cases():
+    """A cloud of one repeated point has h_S = 0 (invalid); a sample that
+    draws nothing falls back to point 0, as in the oracle; one run in FP32."""
+    slr = _slr()
+    with pytest.raises(slr.SlrError) as e:
+        slr.reconstruct(np.tile([[0.1, 0.2]], (10, 1)), dim=2, precision=64, interp=0, runs=1)
+    assert e.value.status == slr.SLR_E_INVALID
+    pts = synth.circle_uniform(200, 0.4)
+    kw = dict(runs=1, K_s=2.0, sample_frac=1e-12, seed=7, max_nodes=1 << 20, max_iters=40)
+    rec, rep = slr.reconstruct(pts, dim=2, precision=32, interp=1, **kw)
+    _, ref = O.reconstruct(pts, 2, prec=32, interp=1, **kw)
+    assert rep["sample_size"] == ref["sample_size"] == 1
+    assert rep["run_n"] == ref["run_n"] and rep["runs_done"] == 1
+    assert rep["h_s"] == pytest.approx(2 * 0.4 * np.sin(np.pi / 200), rel=1e-12)
+    assert rec.diagnostics(err_cloud=True)["err_cloud"] < 0.5 * rep["run_dx"][0]
+    rec.close()

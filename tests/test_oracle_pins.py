@@ -797,13 +797,16 @@ def test_splitmix64_published_outputs():
 
 def test_multirun_sample_is_a_bernoulli_draw():
     """sample_frac = 1 takes every point; 0.1 of 20000 points takes a count
-    within 5 standard deviations of 2000."""
+    within 5 standard deviations of 2000; a draw of nothing falls back to one
+    point."""
     pts = synth.circle_noisy(20000, 0.5, 0.01, 3)
     _, rep = O.reconstruct(pts, 2, runs=1, sample_frac=0.1, max_nodes=64 * 64, max_iters=1)
     sd = np.sqrt(20000 * 0.1 * 0.9)
     assert abs(rep["sample_size"] - 2000) < 5 * sd
     _, rep1 = O.reconstruct(pts[:500], 2, runs=1, sample_frac=1.0, max_nodes=64 * 64, max_iters=1)
     assert rep1["sample_size"] == 500
+    _, rep0 = O.reconstruct(pts[:500], 2, runs=1, sample_frac=1e-12, max_nodes=64 * 64, max_iters=1)
+    assert rep0["sample_size"] == 1
 
 
 def test_multirun_grids_halve_and_reach_the_cloud():
