@@ -264,7 +264,11 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
     const float xf = (float)(x - A.lo0), yf = (float)(y - A.lo1), zf = DIM == 3 ? (float)(z - A.lo2) : 0.f;
     const float tlx = warp_minf(xf), tly = warp_minf(yf), tlz = warp_minf(zf);
     const float thx = warp_maxf(xf), thy = warp_maxf(yf), thz = warp_maxf(zf);
-    const double mscale = 1e-6;
+    // the FP32 screen's margin, 1.2e-6 (extent + d): the FP32 offsets and
+    // squared distances err by ~1e-7 extent, the FP32 square roots of the
+    // bounds below by ~1e-7 d; bounds only screen, the decision is FP64
+    const float mscale = 1.2e-6f;
+    const float extf = (float)A.extent;
 
     double best = INFINITY;
     int bi = 0x7fffffff;
@@ -323,9 +327,9 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
                     const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
                     m2 = fminf(m2, dx * dx + dy * dy + dz * dz);
                 }
-                const double md = sqrt((double)m2);
-                const double lim = md + 2.0 * mscale * (A.extent + md);
-                thr = (float)(lim * lim) * 1.00001f;
+                const float md = sqrtf(m2);
+                const float lim = md + 2.0f * mscale * (extf + md);
+                thr = lim * lim * 1.00001f;
             }
             for (int s = 0; s < cnt; ++s) {
                 const float4 q = leaf[s];
@@ -344,10 +348,10 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
                     if (s2 < best || (s2 == best && pid < bi)) {
                         best = s2;
                         bi = pid;
-                        const double bdist = sqrt(s2);
-                        const double lim = bdist + mscale * (A.extent + bdist);
-                        thr = (float)(lim * lim) * 1.00001f;
-                        lbound = (float)lim * 1.00001f;
+                        const float bdist = sqrtf((float)s2);
+                        const float lim = bdist + mscale * (extf + bdist);
+                        thr = lim * lim * 1.00001f;
+                        lbound = lim * 1.00001f;
                     }
                 }
             }
@@ -891,7 +895,11 @@ __global__ void __launch_bounds__(256) k_point_nn(SearchArgs A, const int* __res
     const float xf = (float)(x - A.lo0), yf = (float)(y - A.lo1), zf = DIM == 3 ? (float)(z - A.lo2) : 0.f;
     const float tlx = warp_minf(xf), tly = warp_minf(yf), tlz = warp_minf(zf);
     const float thx = warp_maxf(xf), thy = warp_maxf(yf), thz = warp_maxf(zf);
-    const double mscale = 1e-6;
+    // the FP32 screen's margin, 1.2e-6 (extent + d): the FP32 offsets and
+    // squared distances err by ~1e-7 extent, the FP32 square roots of the
+    // bounds below by ~1e-7 d; bounds only screen, the decision is FP64
+    const float mscale = 1.2e-6f;
+    const float extf = (float)A.extent;
     double best = INFINITY;
     float thr = INFINITY, lbound = INFINITY, wb2 = INFINITY;
     float4* leaf = s_leaf[wib];
@@ -944,9 +952,9 @@ __global__ void __launch_bounds__(256) k_point_nn(SearchArgs A, const int* __res
                     m2 = fminf(m2, dx * dx + dy * dy + dz * dz);
                 }
                 if (m2 < INFINITY) {
-                    const double md = sqrt((double)m2);
-                    const double lim = md + 2.0 * mscale * (A.extent + md);
-                    thr = (float)(lim * lim) * 1.00001f;
+                    const float md = sqrtf(m2);
+                    const float lim = md + 2.0f * mscale * (extf + md);
+                    thr = lim * lim * 1.00001f;
                 }
             }
             for (int s = 0; s < cnt; ++s) {
@@ -966,10 +974,10 @@ __global__ void __launch_bounds__(256) k_point_nn(SearchArgs A, const int* __res
                     }
                     if (s2 < best) {
                         best = s2;
-                        const double bdist = sqrt(s2);
-                        const double lim = bdist + mscale * (A.extent + bdist);
-                        thr = (float)(lim * lim) * 1.00001f;
-                        lbound = (float)lim * 1.00001f;
+                        const float bdist = sqrtf((float)s2);
+                        const float lim = bdist + mscale * (extf + bdist);
+                        thr = lim * lim * 1.00001f;
+                        lbound = lim * 1.00001f;
                     }
                 }
             }
