@@ -506,8 +506,10 @@ def run_batched(args, slr, torch):
     """The 64-job mix (half 2-D, half 3-D, Q1/WENO mixed, FP32): whole jobs
     one after another versus all jobs set up on their own streams from a
     thread pool and evolved together by slr_batch_evolve (one graph launch
-    advances every job by 8 iterations). Reconstructions per second over the
-    whole job (distance grid, φ^0, evolve to the stop test, extract)."""
+    advances every job by 8 iterations; the autotuned chunk costs more in
+    graph instantiation than it saves on a batch this short). Reconstructions
+    per second over the whole job (distance grid, φ^0, evolve to the stop
+    test, extract)."""
     import concurrent.futures as cf
 
     t0 = time.time()
@@ -534,6 +536,7 @@ def run_batched(args, slr, torch):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     its, _ = slr.slr_batch_evolve([r.ctx for r in recs], chunk=8)
+    chunk = slr.slr_batch_chunk(recs[0].ctx)
     t_evolve = time.perf_counter() - t0 - t_setup
     bat_state = []
     for j, r in zip(jobs, recs):
@@ -548,7 +551,7 @@ def run_batched(args, slr, torch):
                                             "Q1/WENO mixed, FP32, band",
             "one_at_a_time": {"reconstructions_per_s": len(jobs) / t_seq, "seconds": t_seq},
             "batched": {"reconstructions_per_s": len(jobs) / t_bat, "seconds": t_bat, "setup_s": t_setup,
-                        "evolve_s": t_evolve},
+                        "evolve_s": t_evolve, "chunk": chunk},
             "speedup": t_seq / t_bat, "identical_results": bool(same), "iterations": its,
             "input_generation_s": gen_s}
 

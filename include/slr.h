@@ -168,7 +168,7 @@ slr_status slr_evolve(slr_ctx* ctx, int* iters_out, int* converged_out);
 
 /* Batched form of slr_evolve for independent jobs on one device: each
  * launch of one CUDA graph advances every job by `chunk` iterations (1..64,
- * 0 -> 8), the jobs as parallel branches, so that the iterations of many
+ * 0 -> 8; < 0: autotuned, see below), the jobs as parallel branches, so that the iterations of many
  * small and large reconstructions overlap on the GPU instead of running one
  * job after another. A job whose stop test (§4) has fired turns the rest of
  * its branch into no-ops. Returns when every job has stopped. Every job must
@@ -178,6 +178,14 @@ slr_status slr_evolve(slr_ctx* ctx, int* iters_out, int* converged_out);
  * NULL. The jobs' contexts must not be used by other threads meanwhile. */
 slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* cuda_stream, int* iters_out,
                             int* converged_out);
+
+/* The chunk of the last slr_batch_evolve whose first job was first_job. With
+ * chunk < 0 the batch autotunes it: the first launches try 32, 16, 8 and 4
+ * iterations per launch once each, timed on the device, and the rest of the
+ * batch keeps the one with the least time per iteration. The iterations do
+ * not depend on the chunk, so the results are the same as with any fixed
+ * chunk. 0 before any batch. */
+int slr_batch_chunk(const slr_ctx* first_job);
 
 /* Nodes with |φ| < width, in ascending linear index (the reconstructed zero
  * level set's neighbourhood). idx/u: caller buffers of `cap` entries (either

@@ -538,7 +538,8 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
                             int* converged_out) {
     if (!jobs || n_jobs < 1) return SLR_E_INVALID;
     if (chunk == 0) chunk = 8;
-    if (chunk < 1 || chunk > 64) return fail(jobs[0], SLR_E_INVALID, "batch_evolve: chunk must be in 1..64");
+    const bool tune = chunk < 0;
+    if (!tune && chunk > 64) return fail(jobs[0], SLR_E_INVALID, "batch_evolve: chunk must be in 1..64 (or <= 0)");
     int dev = -1;
     for (int j = 0; j < n_jobs; ++j) {
         slr_ctx* c = jobs[j];
@@ -550,39 +551,52 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
     slr_ctx* c0 = jobs[0];
     DeviceGuard g(dev);
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c0->stream;
-    // the batch graph: per job a chain of `chunk` copies of its iteration graph
-    cudaGraph_t parent = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // the batch graphs: per job a chain of `chunk` copies of its iteration
+    // graph; with autotuning one graph per candidate chunk
+    static const int kCand[] = {4, 8, 16, 32};
+    constexpr int kNCand = 4;
+    cudaGraphExec_t execs[kNCand] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaGraph_t> tmpl(n_jobs, nullptr);
     slr_status status = SLR_OK;
     DevState** dstates = nullptr;
     int* dstop = nullptr;
     int* hstop = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (parent) cudaGraphDestroy(parent);
+        for (auto& x : execs)
+            if (x) cudaGraphExecDestroy(x);
         for (auto t : tmpl)
             if (t) cudaGraphDestroy(t);
         if (dstates) dev_free(c0, dstates);
         if (dstop) dev_free(c0, dstop);
         if (hstop) cudaFreeHost(hstop);
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
     };
-    cudaError_t e = cudaGraphCreate(&parent, 0);
-    for (int j = 0; j < n_jobs && e == cudaSuccess && status == SLR_OK; ++j) {
-        status = capture_step_graph(jobs[j], -1.0, 1, &tmpl[j]);
-        if (status != SLR_OK) break;
-        cudaGraphNode_t prev = nullptr;
-        for (int r = 0; r < chunk && e == cudaSuccess; ++r) {
-            cudaGraphNode_t node;
-            e = cudaGraphAddChildGraphNode(&node, parent, prev ? &prev : nullptr, prev ? 1 : 0, tmpl[j]);
-            prev = node;
-        }
-    }
+    for (int j = 0; j < n_jobs && status == SLR_OK; ++j) status = capture_step_graph(jobs[j], -1.0, 1, &tmpl[j]);
     if (status != SLR_OK) {
         cleanup();
         return status;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
+    auto build = [&](int ch, cudaGraphExec_t* out) -> cudaError_t {
+        cudaGraph_t parent = nullptr;
+        cudaError_t e = cudaGraphCreate(&parent, 0);
+        for (int j = 0; j < n_jobs && e == cudaSuccess; ++j) {
+            cudaGraphNode_t prev = nullptr;
+            for (int r = 0; r < ch && e == cudaSuccess; ++r) {
+                cudaGraphNode_t node;
+                e = cudaGraphAddChildGraphNode(&node, parent, prev ? &prev : nullptr, prev ? 1 : 0, tmpl[j]);
+                prev = node;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, parent, 0);
+        if (parent) cudaGraphDestroy(parent);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < (tune ? kNCand : 1) && e == cudaSuccess; ++k) e = build(tune ? kCand[k] : chunk, &execs[k]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
     // stop flags of all jobs gathered by one kernel into one array
     if (e == cudaSuccess) {
         dstates = (DevState**)dev_alloc(c0, sizeof(DevState*) * n_jobs);
@@ -607,26 +621,59 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
     }
     int max_iters = 0;
     for (int j = 0; j < n_jobs; ++j) max_iters = jobs[j]->cfg.max_iters > max_iters ? jobs[j]->cfg.max_iters : max_iters;
+    // autotuning: the first launches try each candidate once (largest first)
+    // and keep the one with the least device time per iteration and per node
+    // of the jobs still running when the launch starts (jobs that stop within
+    // a chunk are charged for its no-op iterations, the cost of a large
+    // chunk); the iterations themselves do not depend on the chunk, so
+    // neither do the results
+    int cur = 0, tried = 0;
+    float best_ms = 0.f;
+    std::vector<char> running(n_jobs, 1);
+    int best = 0;
+    if (tune) cur = kNCand - 1;
+    long long advanced = 0;
     int rounds = 0;
     while (e == cudaSuccess) {
-        e = cudaGraphLaunch(exec, st);
-        for (int j = 0; j < n_jobs; ++j) jobs[j]->launches += (long long)chunk * kernels_per_iteration(jobs[j]);
+        const int ch = tune ? kCand[cur] : chunk;
+        const bool timing = tune && tried < kNCand;
+        if (timing) e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(execs[tune ? cur : 0], st);
+        if (e == cudaSuccess && timing) e = cudaEventRecord(ev[1], st);
+        for (int j = 0; j < n_jobs; ++j) jobs[j]->launches += (long long)ch * kernels_per_iteration(jobs[j]);
+        advanced += ch;
         if (e == cudaSuccess) e = launch_gather_status(c0, dstates, n_jobs, dstop, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hstop, dstop, sizeof(int) * 4 * n_jobs, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) break;
         ++rounds;
+        if (timing) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e != cudaSuccess) break;
+            double work = 0.0;
+            for (int j = 0; j < n_jobs; ++j)
+                if (running[j]) work += (double)jobs[j]->N;
+            const float per = work > 0.0 ? (float)(ms / ((double)ch * work)) : ms / (float)ch;
+            if (tried == 0 || per < best_ms) {
+                best_ms = per;
+                best = cur;
+            }
+            ++tried;
+            cur = tried < kNCand ? kNCand - 1 - tried : best;
+        }
         bool all = true, err = false;
         for (int j = 0; j < n_jobs; ++j) {
             all = all && hstop[4 * j + 0];
             err = err || hstop[4 * j + 3];
+            running[j] = !hstop[4 * j + 0];
         }
         if (err) {
             cleanup();
-            return fail(c0, SLR_E_TIMEOUT, "batch_evolve: band compaction look-back wait timed out");
+            return fail(c0, SLR_E_STATE, "batch_evolve: a device-side check failed in a job");
         }
         if (all) break;
-        if ((long long)rounds * chunk > max_iters + 2 * chunk) {
+        if (advanced > (long long)max_iters + 2 * 64) {
             cleanup();
             return fail(c0, SLR_E_STATE, "batch_evolve: stop flags never set");
         }
@@ -635,6 +682,7 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
         cleanup();
         return cuda_fail(c0, e, "batch_evolve");
     }
+    c0->batch_chunk = tune ? kCand[best] : chunk;
     for (int j = 0; j < n_jobs; ++j) {
         if (iters_out) iters_out[j] = hstop[4 * j + 1];
         if (converged_out) converged_out[j] = hstop[4 * j + 2];
@@ -642,6 +690,8 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
     cleanup();
     return SLR_OK;
 }
+
+int slr_batch_chunk(const slr_ctx* first_job) { return first_job ? first_job->batch_chunk : 0; }
 
 slr_status slr_step_async(slr_ctx* c, int n_steps, double energy_override) {
     if (!c) return SLR_E_INVALID;

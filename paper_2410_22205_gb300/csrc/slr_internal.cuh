@@ -153,6 +153,7 @@ struct slr_ctx {
     int* host_pinned_flags = nullptr;  // pinned host words for status readback
 
     bool have_cloud = false, have_d = false, have_u = false;
+    int batch_chunk = 0;  // chunk of the last slr_batch_evolve this context led (autotuned or given)
     std::string err;
     long long launches = 0;
 

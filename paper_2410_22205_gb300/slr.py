@@ -31,7 +31,7 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_build_distance_fsm",
     "slr_set_distance", "slr_init_u",
-    "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
+    "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_batch_chunk", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error",
@@ -142,6 +142,7 @@ def lib():
                 "slr_step_async": (C.c_int, [_vp, C.c_int, C.c_double]),
                 "slr_evolve": (C.c_int, [_vp, _ip, _ip]),
                 "slr_batch_evolve": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
+                "slr_batch_chunk": (C.c_int, [_vp]),
                 "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
                 "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
                 "slr_get_band": (C.c_int, [_vp, _i64p, C.c_int64, _i64p]),
@@ -332,7 +333,8 @@ def slr_evolve(ctx):
 
 def slr_batch_evolve(ctxs, chunk=8, stream=None):
     """Evolve several contexts together (one graph launch advances all of
-    them by `chunk` iterations); returns (iters, converged) per context."""
+    them by `chunk` iterations; chunk < 0: autotuned); returns (iters,
+    converged) per context."""
     n = len(ctxs)
     arr = (_vp * n)(*ctxs)
     it = (C.c_int * n)()
@@ -340,6 +342,11 @@ def slr_batch_evolve(ctxs, chunk=8, stream=None):
     s = lib().slr_batch_evolve(arr, n, int(chunk), C.c_void_p(stream) if stream else None, it, cv)
     _check(ctxs[0] if n else None, s)
     return list(it), [bool(x) for x in cv]
+
+
+def slr_batch_chunk(ctx):
+    """Chunk used by the last slr_batch_evolve that ctx led (ctx = its first job)."""
+    return int(lib().slr_batch_chunk(ctx))
 
 
 def slr_extract(ctx, width):

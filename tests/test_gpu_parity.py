@@ -379,9 +379,12 @@ KINDS = [(2, 64, 32, 0, 1), (2, 96, 64, 1, 1), (3, 32, 32, 1, 1), (3, 40, 32, 0,
          (2, 48, 32, 1, 0)]
 
 
-def test_batch_evolve_equals_solo_runs():
+@pytest.mark.parametrize("chunk", [4, -1])
+def test_batch_evolve_equals_solo_runs(chunk):
     """Jobs advanced together in one graph per chunk give the same states,
-    iteration counts and energies as each job evolved alone."""
+    iteration counts and energies as each job evolved alone; with chunk -1
+    the chunk is autotuned (one of 4, 8, 16, 32) and the results are the
+    same."""
     slr = _slr()
     solo = []
     for i, k in enumerate(KINDS):
@@ -390,9 +393,9 @@ def test_batch_evolve_equals_solo_runs():
         solo.append((it, conv, r.u(), r.diagnostics()["e2"]))
         r.close()
     jobs = [_small_job(k, i) for i, k in enumerate(KINDS)]
-    its, convs = slr.slr_batch_evolve([j.ctx for j in jobs], chunk=4)
-    for j, (it, conv, u, e2) in zip(jobs, solo):
-        pass
+    its, convs = slr.slr_batch_evolve([j.ctx for j in jobs], chunk=chunk)
+    used = slr.slr_batch_chunk(jobs[0].ctx)
+    assert used == chunk if chunk > 0 else used in (4, 8, 16, 32)
     for idx, (j, (it, conv, u, e2)) in enumerate(zip(jobs, solo)):
         assert its[idx] == it and convs[idx] == conv
         assert np.array_equal(j.u(), u)
