@@ -4,6 +4,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2410_22205_gb300 import slr
@@ -30,10 +31,34 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_library_is_built_for_sm_103a():
-    out = subprocess.run(["cuobjdump", "--list-elf", slr.LIB_PATH], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    """One -gencode, for sm_103a, in the build that produced libslr.so."""
+    from paper_2410_22205_gb300 import build as B
+
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(slr.LIB_PATH)
+
+
+def test_new_entry_points_check_their_arguments_without_a_device():
+    """Argument checks that return before any CUDA call: a batch chunk of a
+    null job, the L1 error and the swept distance of a null context, and
+    invalid runs-from-coarse-to-fine configurations."""
+    L = slr.lib()
+    assert L.slr_batch_chunk(None) == 0
+    out = slr.C.c_double(0.0)
+    assert L.slr_l1_error(None, 0, None, None, slr.C.byref(out)) == slr.SLR_E_INVALID
+    assert L.slr_build_distance_fsm(None) == slr.SLR_E_INVALID
+    pts = np.zeros((4, 2))
+    pts[:, 0] = np.arange(4)
+    for bad in (dict(runs=0), dict(runs=9), dict(K_s=0.0), dict(sample_frac=0.0), dict(sample_frac=2.0),
+                dict(max_nodes=10), dict(max_iters=0), dict(dim=4), dict(distance_fsm=2), dict(exact_sphere=3)):
+        kw = dict(dim=2)
+        kw.update(bad)
+        mc = slr.slr_multirun_default(**kw)
+        h = slr.C.c_void_p()
+        rep = slr.slr_multirun_report()
+        st = L.slr_reconstruct(slr.C.byref(mc), pts.ctypes.data_as(slr._dp), 4, None, None, slr.C.byref(h),
+                               slr.C.byref(rep))
+        assert st == slr.SLR_E_INVALID, bad
 
 
 @pytest.mark.parametrize("bad", [
