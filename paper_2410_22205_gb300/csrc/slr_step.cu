@@ -8,8 +8,9 @@
 //   decided in the storage precision); band nodes get the SL update of §3.1
 //   followed by the cut of eq. cut, the others are copied unchanged into
 //   u^{n+1} (they sit at ±γ since the initial cut); G̃^n is written as a
-//   sorted list by an ordered compaction with decoupled look-back across
-//   tiles; per-tile FP64 partial sums of |u^{n+1} - u^n| feed Δ_φ.
+//   sorted list at offsets prepared before the step (per-tile member counts
+//   from the energy kernel, their prefix from the record kernel); per-tile
+//   FP64 partial sums of |u^{n+1} - u^n| feed Δ_φ.
 // Without reinitialisation a node outside the band keeps |u| = γ and can
 // never re-enter, so G̃^n ⊆ G̃^{n-1} and scanning L^{n-1} finds the whole band.
 #include "slr_compact.cuh"
