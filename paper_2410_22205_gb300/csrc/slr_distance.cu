@@ -9,7 +9,7 @@
 //  3. a 32-ary box hierarchy over the sorted points: a leaf box per 32
 //     consecutive points, a box per 32 consecutive boxes above, up to a top
 //     level of at most 32 boxes;
-//  4. one warp per tile of 32 grid nodes (4x4x2 in 3-D, 8x4 in 2-D): a
+//  4. one warp per tile of 32 grid nodes (2x4x4 in 3-D, 8x4 in 2-D): a
 //     depth-first walk of the hierarchy, nearest child first, pruning boxes
 //     farther from the tile than the warp's worst current best. At the leaves
 //     each lane screens the 32 points in FP32 and re-checks in FP64 — with the
@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int*
     int tk = (int)(r / A.ty);
     int i, j, k;
     if (DIM == 3) {
-        i = ti * 4 + (lane & 3);
-        j = tj * 4 + ((lane >> 2) & 3);
-        k = tk * 2 + (lane >> 4);
+        i = ti * 2 + (lane & 1);
+        j = tj * 4 + ((lane >> 1) & 3);
+        k = tk * 4 + (lane >> 3);
     } else {
         i = ti * 8 + (lane & 7);
         j = tj * 4 + (lane >> 3);
@@ -531,9 +531,9 @@ static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
     A.n1 = (int)c->cfg.n[1];
     A.n2 = (int)c->cfg.n[2];
     if (dim == 3) {
-        A.tx = (A.n0 + 3) / 4;
+        A.tx = (A.n0 + 1) / 2;
         A.ty = (A.n1 + 3) / 4;
-        A.tz = (A.n2 + 1) / 2;
+        A.tz = (A.n2 + 3) / 4;
     } else {
         A.tx = (A.n0 + 7) / 8;
         A.ty = (A.n1 + 3) / 4;
@@ -798,9 +798,9 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
     A.n1 = (int)n[1];
     A.n2 = dim == 3 ? (int)n[2] : 1;
     if (dim == 3) {
-        A.tx = (A.n0 + 3) / 4;
+        A.tx = (A.n0 + 1) / 2;
         A.ty = (A.n1 + 3) / 4;
-        A.tz = (A.n2 + 1) / 2;
+        A.tz = (A.n2 + 3) / 4;
     } else {
         A.tx = (A.n0 + 7) / 8;
         A.ty = (A.n1 + 3) / 4;
