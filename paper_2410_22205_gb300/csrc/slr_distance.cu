@@ -65,11 +65,22 @@ __global__ void k_bbox(const double* pts, long long npts, int dim, unsigned long
             mn[a] = e < mn[a] ? e : mn[a];
             mx[a] = e > mx[a] ? e : mx[a];
         }
-    for (int a = 0; a < dim; ++a) {
-        atomicMin(&bbox[a], mn[a]);
-        atomicMax(&bbox[3 + a], mx[a]);
+    // warp reduction first: one atomic per warp instead of one per thread
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long m0 = __shfl_xor_sync(0xffffffffu, mn[a], o);
+            const unsigned long long m1 = __shfl_xor_sync(0xffffffffu, mx[a], o);
+            mn[a] = m0 < mn[a] ? m0 : mn[a];
+            mx[a] = m1 > mx[a] ? m1 : mx[a];
+        }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < dim; ++a) {
+            atomicMin(&bbox[a], mn[a]);
+            atomicMax(&bbox[3 + a], mx[a]);
+        }
+        if (bad) atomicOr(flag, 1);
     }
-    if (bad) atomicOr(flag, 1);
 }
 
 __device__ __forceinline__ unsigned spread3(unsigned v) {  // 10 bits -> every third bit
