@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* 
 }
 
 template <typename T, int DIM, int INTERP, int RC>
-__global__ void __launch_bounds__(kEnergyThreads) k_energy(Params<T> P, const T* ub0, const T* ub1,
+__global__ void __launch_bounds__(kEnergyThreads, (INTERP == 1 && sizeof(T) == 4) ? 4 : 1) k_energy(Params<T> P, const T* ub0, const T* ub1,
                                                            const T* __restrict__ d, const int* __restrict__ front,
                                                            const int* __restrict__ fcount, long long ncells_host,
                                                            const int* ncells_dev, int R_run, double h,

@@ -35,7 +35,7 @@ __device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i
 // a tile knows its output offset at once: it ballots band membership, writes
 // its part of G̃^n, and runs the SL arithmetic. No warp waits on another.
 template <typename T, int DIM, int INTERP>
-__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 4))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
+__global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 8))) k_step_band(Params<T> P, T* ub0, T* ub1, const T* __restrict__ d,
                                                           int* L0, int* L1, const int* __restrict__ tile_off,
                                                           int band_cap, double* part_dphi, DevState* ds,
                                                           double ep_override) {
