@@ -237,7 +237,7 @@ __device__ __forceinline__ float warp_minf(float v) {
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_dist_search(SearchArgs A, T* dout, int* aout) {
+__global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, int* aout) {
     __shared__ int s_stack[8][kStack];
     __shared__ float4 s_leaf[8][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
