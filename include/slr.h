@@ -47,7 +47,8 @@ typedef enum {
     SLR_E_INVALID = 1,  /* bad argument or configuration */
     SLR_E_NOMEM = 2,    /* the allocator returned NULL */
     SLR_E_CUDA = 3,     /* a CUDA runtime call failed */
-    SLR_E_TIMEOUT = 4,  /* reserved (no kernel of this library waits on another) */
+    SLR_E_TIMEOUT = 4,  /* a bounded wait inside a kernel gave up (the grid barrier between
+                           the planes of the cooperative fast sweeping, §3.4 / §3.6) */
     SLR_E_STATE = 5,    /* call out of order, or a device-side consistency check failed */
     SLR_E_CAPACITY = 6  /* output buffer too small; the needed count is returned */
 } slr_status;
@@ -280,6 +281,16 @@ const char* slr_last_error(const slr_ctx* ctx);
 
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);
+
+/* Failure-detection check of the bounded grid barrier that the cooperative
+ * fast-sweeping kernel uses between planes (the paper has no counterpart).
+ * Runs the barrier alone in a two-block cooperative launch on the current
+ * device. unreachable = 0: a normal barrier, SLR_OK. unreachable = 1: a
+ * barrier that no block completes; every wait gives up after its poll limit
+ * (about 0.3 s) and the call returns SLR_E_TIMEOUT, the device staying usable.
+ * SLR_E_CUDA when cooperative launch is unavailable; slr_last_error(NULL)
+ * gives the reason. */
+slr_status slr_selftest_barrier(int unreachable);
 
 /* §4: the L^1 norm of the error against an exact signed distance,
  * Δx^dim Σ_j |c(φ_j) - c(φ*_j)| over every node, with c the cut of eq. cut

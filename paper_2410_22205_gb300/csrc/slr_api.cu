@@ -444,7 +444,7 @@ slr_status slr_build_distance_fsm(slr_ctx* c) {
         return fail(c, SLR_E_INVALID, "build_distance_fsm: no point within a cell of the grid, or non-finite points");
     if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "build_distance_fsm: scratch allocation failed");
     if (e == cudaErrorLaunchTimeout)
-        return fail(c, SLR_E_STATE, "build_distance_fsm: a grid barrier of the fast sweeping waited too long");
+        return fail(c, SLR_E_TIMEOUT, "build_distance_fsm: a grid barrier of the fast sweeping waited too long");
     if (e != cudaSuccess) return cuda_fail(c, e, "build_distance_fsm");
     c->have_d = true;
     return SLR_OK;
@@ -502,7 +502,7 @@ slr_status slr_init_u(slr_ctx* c, int kind, const double* params, const double* 
             dev_free(c, tmp);
             if (e == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "init_u: marking buffers");
             if (e == cudaErrorLaunchTimeout)
-                return fail(c, SLR_E_STATE, "init_u: a grid barrier of the fast sweeping waited too long");
+                return fail(c, SLR_E_TIMEOUT, "init_u: a grid barrier of the fast sweeping waited too long");
             return cuda_fail(c, e, "init_u marking");
         }
     }
@@ -834,6 +834,26 @@ slr_status slr_get_field(slr_ctx* c, int which, void* host_out, int64_t cap) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_field");
+    return SLR_OK;
+}
+
+slr_status slr_selftest_barrier(int unreachable) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SLR_E_CUDA;
+    }
+    int err = 0;
+    cudaError_t e = barrier_selftest(dev, unreachable ? 1 : 0, &err);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = std::string("selftest_barrier: ") + cudaGetErrorString(e);
+        return SLR_E_CUDA;
+    }
+    if (err & kErrBarrier) {
+        g_create_error = "selftest_barrier: the barrier's wait ran out";
+        return SLR_E_TIMEOUT;
+    }
     return SLR_OK;
 }
 

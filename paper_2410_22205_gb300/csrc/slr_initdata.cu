@@ -398,6 +398,34 @@ cudaError_t build_distance_fsm(slr_ctx* c) {
     return e;
 }
 
+// the bounded grid barrier on its own: a barrier that one block cannot
+// complete (the arrival count starting at the grid size) makes every wait run
+// out, which the caller reads back from err
+__global__ void k_barrier_check(unsigned* bar, int* err) { grid_barrier(bar, err); }
+
+cudaError_t barrier_selftest(int device, int unreachable, int* err_out) {
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, 256);
+    if (e != cudaSuccess) return e;
+    unsigned* bar = (unsigned*)base;
+    int* err = (int*)((char*)base + 64);
+    const unsigned grid = 2;
+    unsigned init[2] = {unreachable ? grid : 0u, 0u};
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    e = coop ? cudaSuccess : cudaErrorNotSupported;
+    if (e == cudaSuccess) e = cudaMemcpy(bar, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        void* args[] = {&bar, &err};
+        e = cudaLaunchCooperativeKernel((const void*)k_barrier_check, dim3(grid), dim3(32), args, 0, 0);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(base);
+    return e;
+}
+
 cudaError_t launch_init_marking(slr_ctx* c, double gamma_s, double* phi_dev, unsigned char* ext_dev) {
     return c->cfg.precision == 32 ? marking_t<float>(c, gamma_s, phi_dev, ext_dev)
                                   : marking_t<double>(c, gamma_s, phi_dev, ext_dev);

@@ -201,6 +201,9 @@ cudaError_t distance_on_marked(slr_ctx* c, const unsigned char* mask, double* do
 // §3.4: exact on the 4^dim node box around each point, fast sweeping elsewhere
 // (cudaErrorInvalidValue: no point within a cell of the grid)
 cudaError_t build_distance_fsm(slr_ctx* c);
+// the grid barrier alone on the current device (unreachable: one that no
+// block completes); *err_out receives the kernel's error bits
+cudaError_t barrier_selftest(int device, int unreachable, int* err_out);
 // per-block partial sums of |c(u_j) - c(φ*_j)| (kind 0: sphere prm = {cx, cy,
 // cz, r}; kind 1: exact_dev) into part[0..blocks)
 cudaError_t launch_l1_error(slr_ctx* c, const void* u, int kind, const double* prm, const double* exact_dev,

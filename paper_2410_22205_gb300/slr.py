@@ -34,7 +34,7 @@ EXPORTS = [
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_batch_chunk", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches",
-    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error",
+    "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error", "slr_selftest_barrier",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
     "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
 ]
@@ -156,6 +156,7 @@ def lib():
                 "slr_kernel_launches": (C.c_int64, [_vp]),
                 "slr_cloud_spacing": (C.c_int, [_vp, _i64p, C.c_int64, _dp]),
                 "slr_l1_error": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
+                "slr_selftest_barrier": (C.c_int, [C.c_int]),
                 "slr_last_error": (C.c_char_p, [_vp]),
                 "slr_destroy": (None, [_vp]),
                 "slr_distance_grid_noalloc": (C.c_int, [C.c_int, _i64p, _dp, C.c_double, C.c_int, _vp, C.c_int64,
@@ -299,6 +300,11 @@ def slr_l1_error(ctx, sphere=None, exact=None):
         ex = _f64(exact)
         _check(ctx, lib().slr_l1_error(ctx, 1, None, _ptr(ex), C.byref(out)))
     return out.value
+
+
+def slr_selftest_barrier(unreachable):
+    """Status of the bounded grid barrier's self-test (see include/slr.h)."""
+    return int(lib().slr_selftest_barrier(int(unreachable)))
 
 
 def slr_step(ctx, n_steps=1, energy_override=-1.0):
