@@ -14,7 +14,7 @@ steps divided by their device time (CUDA events on the job's stream). The L2
 cache is flushed (a 256 MB write) between timed steps, outside the events.
 
 Also reported on the same JSON line:
-  roofline      the dominant kernel of a step against its bound (see DESIGN.md);
+  roofline      the dominant kernel of a step against its bound;
   cpu_baseline  the FP64 oracle on the host cores, a bounded sample;
   e2e           whole jobs through the public API from host buffers (copy in,
                 distance grid, init, evolve to the stop test, extract, copy out);

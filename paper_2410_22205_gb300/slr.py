@@ -127,7 +127,7 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"libslr.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+                raise RuntimeError(f"libslr.so not built ({LIB_PATH}); run paper_2410_22205_gb300/build.py first")
             L = C.CDLL(LIB_PATH)
             P = C.POINTER(slr_config)
             sig = {
