@@ -691,9 +691,79 @@ def cpu_baseline(grid, cloud, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s * 0.5 or its >= 3:
             break
     dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{its} whole oracle iterations (WENO FP64 SL step on {units // its} band nodes + energy) of the "
-                      f"{grid.n[0]}^3 workload from φ^0, {dt:.1f} s"}
+    out = {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{its} whole oracle iterations (WENO FP64 SL step on {units // its} band nodes + energy) of the "
+                     f"{grid.n[0]}^3 workload from φ^0, {dt:.1f} s"}
+    out["detail"] = oracle_detail(O, P, u, d, cloud, cores)
+    return out
+
+
+def cpu_model():
+    """The host CPU's name as /proc/cpuinfo or the platform gives it."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "hardware", "cpu model"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_detail(O, P, u, d, cloud, cores):
+    """The oracle's rates on 1 thread and on every core: the SL step (node
+    updates/s) of the bench's WENO band, of the 128^3 torus band (Q1 and WENO)
+    and of the 64^2 circle (whole grid, FP64 Q1), and the exact distance grid
+    (nodes/s, k-d tree). Each a bounded sample of a second or so."""
+    rng = np.random.default_rng(0)
+    res = {"cpu_model": cpu_model(), "affinity_cores": len(os.sched_getaffinity(0))}
+
+    def rate(fn, units, threads):
+        O.set_threads(threads)
+        t0 = time.perf_counter()
+        fn()
+        return units / (time.perf_counter() - t0)
+
+    band = np.flatnonzero(np.abs(u) < np.float32(P.gamma))
+    Ep = O.energy(P, u, d, 2.0)["E"]
+    s1, sa = rng.choice(band, 4000, replace=False), rng.choice(band, 60000, replace=False)
+    nc = int(P.n[0])
+    res[f"sl_weno_fp64_{nc}cube"] = {
+        "1_thread": rate(lambda: O.sl_nodes(P, u, d, Ep, s1), s1.size, 1),
+        "all_cores": rate(lambda: O.sl_nodes(P, u, d, Ep, sa), sa.size, cores)}
+    nodes = rng.choice(P.n[0] * P.n[1] * P.n[2], 20000, replace=False)
+    res[f"distance_grid_kd_{nc}cube_{len(cloud) // 1000}k_points"] = {
+        "1_thread": rate(lambda: O.distance(P, cloud, nodes[:2000], method="kd"), 2000, 1),
+        "all_cores": rate(lambda: O.distance(P, cloud, nodes, method="kd"), nodes.size, cores)}
+    # the 128^3 torus workload
+    g2 = synth.cube_grid(3, 128)
+    torus = synth.torus_cloud(20000, 0.5, 0.2, 0.002, 1)
+    for interp, name in ((0, "q1"), (1, "weno")):
+        P2 = O.params_for_grid(g2, interp=interp, band=1, p=2.0, delta=1.0, prec=64)
+        u2 = O.cut(P2, synth.sphere_sdf(g2, 0.9))
+        b2 = np.flatnonzero(np.abs(u2) < P2.gamma)
+        smp = rng.choice(b2, 20000, replace=False)
+        d2 = np.zeros(g2.num_nodes)
+        near = np.unique(np.concatenate([smp + o for o in (0, -1, 1, -128, 128, -128 * 128, 128 * 128)]))
+        d2[near] = O.distance(P2, torus, near, method="kd")[0]
+        res[f"sl_{name}_fp64_torus_128cube"] = {
+            "1_thread": rate(lambda: O.sl_nodes(P2, u2, d2, 0.5, smp[:4000]), 4000, 1),
+            "all_cores": rate(lambda: O.sl_nodes(P2, u2, d2, 0.5, smp), smp.size, cores)}
+    # the 64^2 circle workload, whole grid
+    g1 = synth.cube_grid(2, 64)
+    P1 = O.params_for_grid(g1, interp=0, band=0, prec=64)
+    circ = synth.circle_noisy(200, 0.5, 0.005, 0)
+    d1, _ = O.distance(P1, circ, method="kd")
+    u1 = synth.sphere_sdf(g1, 0.9)
+    res["sl_q1_fp64_circle_64sq_whole_grid"] = {
+        "1_thread": rate(lambda: [O.sl_step(P1, u1, d1, 0.5) for _ in range(20)], 20 * g1.num_nodes, 1),
+        "all_cores": rate(lambda: [O.sl_step(P1, u1, d1, 0.5) for _ in range(20)], 20 * g1.num_nodes, cores)}
+    O.set_threads(cores)
+    res["unit"] = "node-updates/s (SL step), nodes/s (distance grid)"
+    return res
 
 
 def run_reference(args):
