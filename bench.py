@@ -699,9 +699,17 @@ def cpu_baseline(grid, cloud, budget_s=20.0):
 
 
 def cpu_model():
-    """The host CPU's name as /proc/cpuinfo or the platform gives it."""
+    """The host CPU's name as lscpu, /proc/cpuinfo or the platform gives it."""
     import platform
+    import subprocess
 
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:

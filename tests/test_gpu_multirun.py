@@ -194,3 +194,24 @@ def test_multirun_edge_cases():
     assert rep["h_s"] == pytest.approx(2 * 0.4 * np.sin(np.pi / 200), rel=1e-12)
     assert rec.diagnostics(err_cloud=True)["err_cloud"] < 0.5 * rep["run_dx"][0]
     rec.close()
+
+
+@pytest.mark.parametrize("interp", [0, 1])
+def test_square_test_of_the_paper_matches_the_oracle(interp):
+    """The square test of §4.1 (24 points on a square rotated by 45
+    degrees, five runs, Tab. errGlobSquare) on the GPU in FP64: the printed
+    grids, and every run's iterations, energy and error on the cloud as the
+    oracle's."""
+    slr = _slr()
+    R = 3.0
+    V = np.array([[R, 0.0], [0.0, R], [-R, 0.0], [0.0, -R]])
+    pts = np.array([V[k] + (t / 6) * (V[(k + 1) % 4] - V[k]) for k in range(4) for t in range(6)])
+    kw = dict(runs=5, K_s=2.0, sample_frac=0.1, seed=1, max_nodes=1 << 22, max_iters=100)
+    rec, rep = slr.reconstruct(pts, dim=2, precision=64, interp=interp, **kw)
+    ref_phi, ref = O.reconstruct(pts, 2, prec=64, interp=interp, **kw)
+    assert [n[0] for n in rep["run_n"]] == [30, 34, 51, 85, 153]
+    assert rep["run_iters"] == ref["run_iters"]
+    np.testing.assert_allclose(rep["run_energy"], ref["run_energy"], rtol=1e-9)
+    np.testing.assert_allclose(rep["run_err_cloud"], ref["run_err_cloud"], rtol=1e-9)
+    assert np.abs(rec.u() - ref_phi).max() <= 1e-9
+    rec.close()
