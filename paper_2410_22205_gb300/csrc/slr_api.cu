@@ -169,7 +169,7 @@ slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     c->n_echunks = (ncells + 31) / 32;
     long long slots = (ncells + 1023) / 1024;
     if (slots < 1) slots = 1;
-    c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2 + 3 * 32));  // + record blocks
+    c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2 + 3 * kRecordBlocks));  // + record blocks
     c->front = (int*)dev_alloc(c, sizeof(int) * (slots * 1024 + slots));
     if (!c->part_e || !c->front) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
     return SLR_OK;
