@@ -37,6 +37,8 @@ Params<T> make_params(const slr_ctx* c);
 
 constexpr int kMaxLevels = 8;
 constexpr int kStack = 256;
+// widening of the exact search's FP32 screen for its expanded form (about 67 ulp)
+constexpr float kWide = 4e-6f;
 
 __device__ __forceinline__ unsigned long long enc_double(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -239,7 +241,8 @@ __device__ __forceinline__ float warp_minf(float v) {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, int* aout) {
     __shared__ int s_stack[8][kStack];
-    __shared__ float4 s_leaf[8][32];
+    __shared__ float4 s_leaf[8][32];  // a leaf's points about the leaf centre, |q'|^2 in .w
+    __shared__ int s_pid[8][32];      // their input indices
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long ntiles = (long long)A.tx * A.ty * A.tz;
@@ -287,6 +290,7 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
     float lbound = INFINITY; // this lane's best plus the error margin (FP32)
     float wb2 = INFINITY;    // squared warp bound
     float4* leaf = s_leaf[wib];
+    int* lpid = s_pid[wib];
 
     int sp = 0;
     {
@@ -312,42 +316,59 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
         __syncwarp();
         const int lvl = ent >> 27;
         const long long id = ent & ((1 << 27) - 1);
-        const float bd2 = box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]);
-        if (bd2 > wb2) continue;
         if (lvl == 0) {
+            // no tile-box test for a leaf: the per-lane test below implies it,
+            // as no lane's bound exceeds the warp bound
+            const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
             // per-lane test: skip the leaf when its box is beyond every lane's own bound
             {
-                const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
                 const float gx = fmaxf(0.f, fmaxf(blo_.x - xf, xf - bhi_.x));
                 const float gy = fmaxf(0.f, fmaxf(blo_.y - yf, yf - bhi_.y));
                 const float gz = fmaxf(0.f, fmaxf(blo_.z - zf, zf - bhi_.z));
                 const bool need = !(gx * gx + gy * gy + gz * gz > lbound * lbound);
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
+            // The screen works about the leaf centre c: with u = x - c and
+            // q' = q - c, |x - q|^2 = |u|^2 + (|q'|^2 - 2 u.q'), three FMAs per
+            // point. Rounding u, q' and the expanded form moves the squared
+            // distance by at most ~16 ulp (|x - q|^2 + e^2), e the diagonal of
+            // the leaf's box; the screens widen by 4e-6 (thr + e^2) for it.
+            const float cx = 0.5f * (blo_.x + bhi_.x), cy = 0.5f * (blo_.y + bhi_.y), cz = 0.5f * (blo_.z + bhi_.z);
+            const float ex_ = bhi_.x - blo_.x, ey_ = bhi_.y - blo_.y, ez_ = bhi_.z - blo_.z;
+            const float we2 = kWide * (ex_ * ex_ + ey_ * ey_ + ez_ * ez_);
             const long long base = id * 32;
             long long rem = A.npts - base;
             const int cnt = rem < 32 ? (int)rem : 32;
-            if (lane < cnt) leaf[lane] = A.spt[base + lane];
+            if (lane < cnt) {
+                const float4 p = A.spt[base + lane];
+                const float qx = p.x - cx, qy = p.y - cy, qz = p.z - cz;
+                leaf[lane] = make_float4(qx, qy, qz, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+                lpid[lane] = __float_as_int(p.w);
+            }
             __syncwarp();
+            const float ux = xf - cx, uy = yf - cy, uz = zf - cz;
+            const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+            const float ax = -2.f * ux, ay = -2.f * uy, az = -2.f * uz;
             if (best == INFINITY) {
                 // first leaf of this lane: an FP32 minimum bounds the exact best,
                 // so only points within the margin of it need the FP64 check
                 float m2 = INFINITY;
                 for (int s = 0; s < cnt; ++s) {
                     const float4 q = leaf[s];
-                    const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
-                    m2 = fminf(m2, dx * dx + dy * dy + dz * dz);
+                    m2 = fminf(m2, fmaf(ax, q.x, fmaf(ay, q.y, fmaf(az, q.z, q.w))));
                 }
+                m2 = fmaf(fmaxf(0.f, m2 + uu), 1.f + kWide, we2);
                 const float md = sqrtf(m2);
                 const float lim = md + 2.0f * mscale * (extf + md);
                 thr = lim * lim * 1.00001f;
             }
+            // this leaf's screen, moved to the side of the expanded form
+            float tl = fmaf(thr, 1.f + kWide, we2) - uu;
             for (int s = 0; s < cnt; ++s) {
                 const float4 q = leaf[s];
-                const float dx = xf - q.x, dy = yf - q.y, dz = zf - q.z;
-                const float d2f = dx * dx + dy * dy + dz * dz;
-                if (d2f <= thr) {
-                    const int pid = __float_as_int(q.w);
+                const float sc = fmaf(ax, q.x, fmaf(ay, q.y, fmaf(az, q.z, q.w)));
+                if (sc <= tl) {
+                    const int pid = lpid[s];
                     const double* Q = A.pts + (long long)pid * DIM;
                     const double ex = __dsub_rn(x, Q[0]);
                     const double ey = __dsub_rn(y, Q[1]);
@@ -363,6 +384,7 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
                         const float lim = bdist + mscale * (extf + bdist);
                         thr = lim * lim * 1.00001f;
                         lbound = lim * 1.00001f;
+                        tl = fmaf(thr, 1.f + kWide, we2) - uu;
                     }
                 }
             }
@@ -370,6 +392,7 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
             const float wb = warp_maxf(lbound);
             wb2 = wb * wb;
         } else {
+            if (box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]) > wb2) continue;
             const int cl = lvl - 1;
             const long long c = id * 32 + lane;
             const bool ex = c < A.cnt[cl];
