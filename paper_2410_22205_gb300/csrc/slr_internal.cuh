@@ -316,6 +316,57 @@ __device__ __forceinline__ T weno1(T v0, T v1, T v2, T v3, const WenoAxis<T>& w,
     return fma(w.q, fma(wl, dl - dr, dr), fma(w.th, v2 - v1, v1));
 }
 
+// Two-wide values for evaluating two interpolation lines at once. FP32 pairs
+// use the packed two-wide add, multiply and FMA of sm_100 and later (each lane
+// rounded to nearest, as the scalar operation), which halves the issued
+// arithmetic; FP64 pairs are two scalar operations. a - b is written
+// fma(-1, b, a), which rounds identically.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <typename T>
+using V2 = typename Vec2<T>::type;
+__device__ __forceinline__ float2 v2_make(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 v2_make(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 v2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 v2_add(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 v2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 v2_mul(double2 a, double2 b) { return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 v2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 v2_fma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T>
+__device__ __forceinline__ V2<T> v2_div(V2<T> a, V2<T> b) {
+    return v2_make(fast_div(a.x, b.x), fast_div(a.y, b.y));
+}
+
+// Two lines at once (same axis, same θ): each result equals weno1 of its own
+// data bit for bit.
+template <typename T>
+__device__ __forceinline__ void weno_pair(T a0, T a1, T a2, T a3, T b0, T b1, T b2, T b3, const WenoAxis<T>& w,
+                                          T h4, T& ra, T& rb) {
+    const V2<T> v0 = v2_make(a0, b0), v1 = v2_make(a1, b1), v2 = v2_make(a2, b2), v3 = v2_make(a3, b3);
+    const V2<T> m2 = v2_make(T(-2), T(-2)), m1 = v2_make(T(-1), T(-1)), hh = v2_make(h4, h4);
+    const V2<T> dl = v2_fma(m2, v1, v2_add(v0, v2));
+    const V2<T> dr = v2_fma(m2, v2, v2_add(v1, v3));
+    const V2<T> sl = v2_fma(dl, dl, hh), sr = v2_fma(dr, dr, hh);
+    const V2<T> gl = v2_mul(v2_make(w.rho, w.rho), v2_mul(sr, sr));
+    const V2<T> wl = v2_div<T>(gl, v2_fma(sl, sl, gl));
+    const V2<T> t1 = v2_fma(wl, v2_fma(m1, dr, dl), dr);
+    const V2<T> t2 = v2_fma(v2_make(w.th, w.th), v2_fma(m1, v1, v2), v1);
+    const V2<T> res = v2_fma(v2_make(w.q, w.q), t1, t2);
+    ra = res.x;
+    rb = res.y;
+}
+
 // eq. IQ1 at node (i,j,k) + displacement r (units of h): multilinear
 // interpolation in the cell holding the foot, along x, then y, then z.
 template <typename T, int DIM>
@@ -360,7 +411,7 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
     if (interior) {
         // whole stencil inside the grid: one base pointer, rows of four
         // consecutive x-values at 32-bit offsets (the grid holds fewer than
-        // 2^31 nodes), z-lines evaluated as their rows arrive
+        // 2^31 nodes), z-lines evaluated in pairs as their rows arrive
         const T* base = u + ((cx - 1) + P.is1 * (cy - 1) + (DIM == 3 ? P.is2 * (cz - 1) : 0));
         T yv[4][4];  // [a][b]: z-line (DIM 3) or node value (DIM 2) at column a, row b
 #pragma unroll
@@ -373,8 +424,10 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
 #pragma unroll
                     for (int a = 0; a < 4; ++a) r[c][a] = ld(row + a);
                 }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) yv[a][b] = weno1(r[0][a], r[1][a], r[2][a], r[3][a], wz, P.h4);
+                weno_pair(r[0][0], r[1][0], r[2][0], r[3][0], r[0][1], r[1][1], r[2][1], r[3][1], wz, P.h4, yv[0][b],
+                          yv[1][b]);
+                weno_pair(r[0][2], r[1][2], r[2][2], r[3][2], r[0][3], r[1][3], r[2][3], r[3][3], wz, P.h4, yv[2][b],
+                          yv[3][b]);
             } else {
                 const T* row = base + P.is1 * b;
 #pragma unroll
@@ -382,8 +435,8 @@ __device__ __forceinline__ T interp_weno(const Params<T>& P, const T* __restrict
             }
         }
         T xv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) xv[a] = weno1(yv[a][0], yv[a][1], yv[a][2], yv[a][3], wy, P.h4);
+        weno_pair(yv[0][0], yv[0][1], yv[0][2], yv[0][3], yv[1][0], yv[1][1], yv[1][2], yv[1][3], wy, P.h4, xv[0], xv[1]);
+        weno_pair(yv[2][0], yv[2][1], yv[2][2], yv[2][3], yv[3][0], yv[3][1], yv[3][2], yv[3][3], wy, P.h4, xv[2], xv[3]);
         return weno1(xv[0], xv[1], xv[2], xv[3], wx, P.h4);
     }
     int ox[4], oy[4], oz[4] = {0, 0, 0, 0};
