@@ -317,8 +317,13 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
     }
     for (int a = 0; a < k.dim; ++a)
         if (k.n[a] < 4) return bad("need at least 4 nodes per axis");
-    long long N = k.n[0] * k.n[1] * k.n[2];
-    if (N <= 0 || N > 2147483647ll) return bad("at most 2^31-1 nodes");
+    // every factor is positive here; bound each one before multiplying, so
+    // the product cannot overflow
+    long long N = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (k.n[a] > 2147483647ll / N) return bad("at most 2^31-1 nodes");
+        N *= k.n[a];
+    }
     double h = (k.hi[0] - k.lo[0]) / (double)(k.n[0] - 1);
     if (!(h > 0.0) || !isfinite(h)) return bad("hi must exceed lo");
     for (int a = 1; a < k.dim; ++a) {

@@ -713,8 +713,9 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
     long long N = 1;
     for (int a = 0; a < dim; ++a) {
         if (n[a] < 2) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: need at least 2 nodes per axis");
+        // bounded before the product, which therefore cannot overflow
+        if (n[a] > 2147483647ll / N) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: at most 2^31-1 nodes");
         N *= n[a];
-        if (N > 2147483647ll) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: at most 2^31-1 nodes");
     }
     if (dim == 3 ? false : (n[2] != 1))
         return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: n[2] must be 1 in 2-D");

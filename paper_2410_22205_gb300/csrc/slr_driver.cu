@@ -249,12 +249,14 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     // the box of run r: the cloud's bounding box widened by 8 Δx(r), plus
     // γ_S in the first run; Δx(1) = h_S coarsened until the first grid fits
     auto nodes_for = [&](double dx, double margin, long long nn[3]) {
-        long long tot = 1;
+        double tot = 1.0;
         for (int a = 0; a < 3; ++a) nn[a] = 1;
         for (int a = 0; a < dim; ++a) {
-            nn[a] = (long long)ceil(((bmax[a] - bmin[a]) + 2.0 * margin) / dx) + 1;
-            if (nn[a] < 8) nn[a] = 8;
-            tot *= nn[a];
+            // clamped far above any grid slr_create accepts, so that the
+            // conversion and the product stay finite for any cloud extent
+            const double q = fmin(ceil(((bmax[a] - bmin[a]) + 2.0 * margin) / dx) + 1.0, 4e9);
+            nn[a] = q < 8.0 ? 8 : (long long)q;
+            tot *= (double)nn[a];
         }
         return tot;
     };
@@ -262,9 +264,9 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
     {
         long long nn[3];
         for (int it = 0; it < 200; ++it) {
-            const long long tot = nodes_for(dx1, (mc->K_s + 8.0) * dx1, nn);
-            if (tot <= mc->max_nodes) break;
-            dx1 *= pow((double)tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
+            const double tot = nodes_for(dx1, (mc->K_s + 8.0) * dx1, nn);
+            if (tot <= (double)mc->max_nodes) break;
+            dx1 *= pow(tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
         }
     }
     if (dx1 > hs * 1.000001) rep.coarsened = 1;
@@ -278,9 +280,9 @@ slr_status slr_reconstruct(const slr_multirun_config* mc, const double* xyz, int
         double dx = dx1 / (double)(1ll << (r - 1));
         long long nn[3];
         for (int it = 0; it < 200; ++it) {
-            const long long tot = nodes_for(dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
-            if (tot <= mc->max_nodes) break;
-            dx *= pow((double)tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
+            const double tot = nodes_for(dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
+            if (tot <= (double)mc->max_nodes) break;
+            dx *= pow(tot / (double)mc->max_nodes, 1.0 / dim) * 1.0001;
         }
         if (dx > dx1 / (double)(1ll << (r - 1)) * 1.000001) rep.coarsened = 1;
         const double margin = 8.0 * dx + (r == 1 ? gamma_s : 0.0);

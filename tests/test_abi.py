@@ -82,6 +82,31 @@ def test_create_rejects_invalid_config(bad):
     assert slr.slr_last_error(None)
 
 
+def test_create_rejects_grids_of_2_31_nodes_or_more():
+    """The node-count limit holds before any device call, including sizes
+    whose 64-bit product would wrap around to a small number."""
+    big = 2 ** 62 + 1
+    for kw in (dict(n=(1300, 1300, 1300)),
+               dict(n=(46341, 46341, 4), lo=(0.0, 0.0, 0.0), hi=(46340.0, 46340.0, 3.0)),
+               dict(n=(big, 4, 4), lo=(0.0, 0.0, 0.0), hi=(float(big - 1), 3.0, 3.0))):
+        cfg = slr.slr_config_default(**kw)
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_create(cfg)
+        assert e.value.status == slr.SLR_E_INVALID
+        assert "2^31" in slr.slr_last_error(None)
+
+
+def test_noalloc_rejects_grids_of_2_31_nodes_or_more():
+    """The allocation-free distance grid checks its sizes before any device
+    call (the buffer addresses are never touched), including a wrapping
+    product."""
+    for n in ((1300, 1300, 1300), (2 ** 62 + 1, 4, 4), (4, 2 ** 62 + 1, 2 ** 62 + 1)):
+        with pytest.raises(slr.SlrError) as e:
+            slr.slr_distance_grid_noalloc(3, n, (0.0, 0.0, 0.0), 1.0, 32, 256, 10, 512, 768)
+        assert e.value.status == slr.SLR_E_INVALID
+        assert "2^31" in slr.slr_last_error(None)
+
+
 def test_default_config_is_the_papers():
     cfg = slr.slr_config_default()
     assert (cfg.p, cfg.delta, cfg.c_sing, cfg.alpha, cfg.energy_R) == (2.0, 1.0, 1e-3, 1.0, 5)
