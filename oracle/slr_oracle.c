@@ -1232,14 +1232,16 @@ unsigned long long or_splitmix64(unsigned long long seed, unsigned long long i) 
     return z ^ (z >> 31);
 }
 
-static long long or_grid_nodes(int dim, const double* bmin, const double* bmax, double dx, double margin,
+static double or_grid_nodes(int dim, const double* bmin, const double* bmax, double dx, double margin,
                                long long nn[3]) {
-    long long tot = 1;
+    double tot = 1.0;
     for (int a = 0; a < 3; ++a) nn[a] = 1;
     for (int a = 0; a < dim; ++a) {
-        nn[a] = (long long)ceil(((bmax[a] - bmin[a]) + 2.0 * margin) / dx) + 1;
-        if (nn[a] < 8) nn[a] = 8;
-        tot *= nn[a];
+        /* clamped (far above any grid the budget admits) so that the
+         * conversion and the product stay finite for any cloud extent */
+        double q = fmin(ceil(((bmax[a] - bmin[a]) + 2.0 * margin) / dx) + 1.0, 4e9);
+        nn[a] = q < 8.0 ? 8 : (long long)q;
+        tot *= (double)nn[a];
     }
     return tot;
 }
@@ -1289,9 +1291,9 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
     long long nn[3];
     double dx1 = hs;
     for (int it = 0; it < 200; ++it) {
-        long long tot = or_grid_nodes(dim, bmin, bmax, dx1, (K_s + 8.0) * dx1, nn);
-        if (tot <= max_nodes) break;
-        dx1 *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
+        double tot = or_grid_nodes(dim, bmin, bmax, dx1, (K_s + 8.0) * dx1, nn);
+        if (tot <= (double)max_nodes) break;
+        dx1 *= pow(tot / (double)max_nodes, 1.0 / dim) * 1.0001;
     }
     /* γ_S = K_S h_S, or K_S Δx(1) on a coarsened first grid (the marked
      * shell must stay closed on the grid) */
@@ -1302,9 +1304,9 @@ int or_reconstruct(int dim, int prec, int interp, int runs, double K_s, double s
     for (int r = 1; r <= runs; ++r) {
         double dx = dx1 / (double)(1ll << (r - 1));
         for (int it = 0; it < 200; ++it) {
-            long long tot = or_grid_nodes(dim, bmin, bmax, dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
-            if (tot <= max_nodes) break;
-            dx *= pow((double)tot / (double)max_nodes, 1.0 / dim) * 1.0001;
+            double tot = or_grid_nodes(dim, bmin, bmax, dx, 8.0 * dx + (r == 1 ? gamma_s : 0.0), nn);
+            if (tot <= (double)max_nodes) break;
+            dx *= pow(tot / (double)max_nodes, 1.0 / dim) * 1.0001;
         }
         double margin = 8.0 * dx + (r == 1 ? gamma_s : 0.0);
         double lo[3] = {0, 0, 0};
