@@ -22,7 +22,9 @@
  *                 through the exact pins of their parts.
  *   or_evolve  -- the paper prints no end-to-end result without the
  *                 reinitialisation; pinned through its parts (the SL step,
- *                 the band, the cut, the energy and the stop test).
+ *                 the band, the cut, the energy and the stop test) and a
+ *                 closed form of the loop (a plane front moving toward a
+ *                 line cloud by Δt per iteration).
  */
 #ifndef SLR_ORACLE_H
 #define SLR_ORACLE_H

@@ -520,6 +520,43 @@ def test_evolve_runs_and_moves_front_toward_cloud():
     assert r["E2"][-1] < r["E2"][0]
 
 
+@pytest.mark.parametrize("interp", [0, 1])
+def test_evolve_moves_a_plane_front_at_unit_speed_toward_a_line_cloud(interp):
+    """Closed form of Algorithm 1's loop (p = 1, δ = 0, whole grid): with one
+    point of the cloud above every node column on the line y = c, d = |y - c|
+    on the nodes and the centred ∇d is (0, 1) more than a cell above the line;
+    with C = 1 (p = 1, §4) each step of eq. SL2d samples φ at y + Δt, and both
+    interpolators reproduce linear data. So the front y = y0 moves toward the
+    cloud by exactly Δt per step: after n steps φ = y - (y0 - nΔt) on every row
+    that neither the line nor the grid edge can influence (Δt = Δx/4: one row
+    per step for Q1, two for WENO, whose stencil reaches two rows up). A wrong
+    sign, Δt or scale factor fails it."""
+    n, steps = 64, 8
+    P = O.params(2, (n, n), (-1.0, -1.0), hi=(1.0, 1.0), interp=interp, p=1.0, delta=0.0, band=0)
+    h, dt = P.h, P.dt
+    x = -1.0 + h * np.arange(n)
+    c = -1.0 + 10.5 * h
+    pts = np.stack([x, np.full(n, c)], 1)
+    d, _ = O.distance(P, pts)
+    X, Y = np.meshgrid(x, x)  # rows: y
+    assert np.allclose(d.reshape(n, n), np.abs(Y - c), rtol=0, atol=1e-15)
+    y0 = -1.0 + 40.3 * h
+    u0 = (Y - y0).reshape(-1)
+    r = O.evolve(P, u0, d, min_iters=steps, max_iters=steps)
+    assert r["iters"] == steps
+    u = r["u"].reshape(n, n)
+    rows = np.arange(n)
+    reach = (1 if interp == 0 else 2) * (steps + 1)
+    clean = (rows > 10.5 + reach) & (rows < n - 1 - reach)
+    assert clean[38] and clean[39] and clean.sum() >= 10
+    expect = Y - (y0 - steps * dt)
+    assert np.max(np.abs(u[clean] - expect[clean])) < 1e-12
+    # the zero level moved from row 40.3 to row 38.3
+    col = u[:, n // 2]
+    j = np.flatnonzero((col[:-1] < 0) & (col[1:] >= 0))[0]
+    assert abs((j - col[j] / (col[j + 1] - col[j])) - 38.3) < 1e-9
+
+
 # ---------------------------------------------------------------- reinitialisation (§3.7)
 
 def _reinit_grid(dim, n, **kw):
