@@ -281,6 +281,36 @@ def test_circle64_workload_100_steps_fp64_q1():
     assert rec.diagnostics()["iters"] == 100
 
 
+@pytest.mark.parametrize("interp", [0, 1])
+def test_plane_front_moves_at_unit_speed_toward_a_line_cloud(interp):
+    """The closed form the oracle is pinned to, through the C ABI: FP64, whole
+    grid, p = 1, δ = 0, a line cloud y = c with one point above every node
+    column, the plane front y = y0; 8 steps. Every node equals the oracle's
+    loop (<= 1e-12), and the rows beyond the reach of the line and the grid
+    edge equal y - (y0 - 8Δt) (<= 1e-12)."""
+    n, steps = 64, 8
+    rec, P = make(2, n, 64, interp, 0, p=1.0, delta=0.0)
+    h, dt = P.h, P.dt
+    x = -1.0 + h * np.arange(n)
+    c = -1.0 + 10.5 * h
+    rec.load_cloud(np.stack([x, np.full(n, c)], 1))
+    rec.build_distance()
+    X, Y = np.meshgrid(x, x)
+    y0 = -1.0 + 40.3 * h
+    u0 = (Y - y0).reshape(-1)
+    rec.init_array(u0)
+    rec.step(steps)
+    u = rec.u()
+    ref = O.evolve(P, u0, rec.d(), min_iters=steps, max_iters=steps)
+    assert ref["iters"] == steps
+    assert np.abs(u - ref["u"]).max() <= 1e-12
+    reach = (1 if interp == 0 else 2) * (steps + 1)
+    rows = np.arange(n)
+    clean = (rows > 10.5 + reach) & (rows < n - 1 - reach)
+    err = np.abs(u.reshape(n, n) - (Y - (y0 - steps * dt)))[clean]
+    assert err.max() <= 1e-12
+
+
 @pytest.mark.parametrize("kmax,min_iters,tol", [(10, 10, 1e-4), (3, 2, 1e-3), (25, 5, 1e-3)])
 def test_evolve_matches_oracle_stop_rule(kmax, min_iters, tol):
     rec, P = make(2, 48, 64, 1, 1, p=1.0, delta=0.0, stop_k=kmax, min_iters=min_iters, stop_tol=tol)
