@@ -315,7 +315,7 @@ def run_gpu(args):
     value, tot_units, tmax = aggregate(units, secs, dist)
     ms_per_step = tmax * 1e3 / args.steps
     kern = np.array(kern_ms)
-    names = ["k_step_band<float,3,WENO>", "k_front + k_energy<float,3,WENO,R=5>", "k_record"]
+    names = ["k_step_band<float,3,WENO>", "k_energy<float,3,WENO,R=5> (front cells + quadrature)", "k_record"]
     kmean = kern.mean(axis=0)
     dom = int(np.argmax(kmean[:2]))  # the step or the energy pass (the record kernel is a small reduction)
     mean_band = float(np.mean(bands))

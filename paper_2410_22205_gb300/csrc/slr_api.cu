@@ -119,7 +119,7 @@ slr_status capture_step(slr_ctx* c, double ov, int evolve, cudaGraphExec_t* out)
 // kernels of one iteration: step, front cells, energy, record, plus the
 // reinitialisation stage (10 kernels and the sweeps) when it is on
 long long kernels_per_iteration(const slr_ctx* c) {
-    return 4 + (c->cfg.reinit ? 10 + reinit_sweeps(c) : 0);
+    return 3 + (c->cfg.reinit ? 10 + reinit_sweeps(c) : 0);
 }
 
 slr_status read_status(slr_ctx* c, int* stop, int* error, int* n) {
@@ -165,13 +165,9 @@ slr_status size_band_buffers(slr_ctx* c, long long count) {
 
 slr_status size_energy_buffers(slr_ctx* c, long long ncells) {
     release_t(c, c->part_e);
-    release_t(c, c->front);
     c->n_echunks = (ncells + 31) / 32;
-    long long slots = (ncells + 1023) / 1024;
-    if (slots < 1) slots = 1;
     c->part_e = (double*)dev_alloc(c, sizeof(double) * (2 * c->n_echunks + 2 + 3 * kRecordBlocks));  // + record blocks
-    c->front = (int*)dev_alloc(c, sizeof(int) * (slots * 1024 + slots));
-    if (!c->part_e || !c->front) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
+    if (!c->part_e) return fail(c, SLR_E_NOMEM, "allocation of the energy buffers failed");
     return SLR_OK;
 }
 
@@ -1128,7 +1124,6 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->part_dphi);
     release_t(c, c->part_e);
     release_t(c, c->tile_off);
-    release_t(c, c->front);
     release(c, c->rw);
     release_t(c, c->bits_band);
     release_t(c, c->bits_gbar);

@@ -3,8 +3,8 @@
 //
 // Energy: the candidate cells (every cell in whole-grid mode; in band mode
 // the cells touching the initial band or crossing the front at init) are
-// checked 256 per block for a sign change (front cells, vertices of both
-// signs, zero counted as positive), which the block then processes:
+// checked 1024 per block slot for a sign change (front cells, vertices of
+// both signs, zero counted as positive), which the block then processes:
 //   2-D: edge crossings by linear interpolation of φ, d interpolated along
 //        the edge, trapezoid rule on the segment(s) (eq. energyApprox);
 //   3-D: R^3 subcells (eq. energyApproxFiner); φ at the subcell centres by
@@ -165,12 +165,11 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
     return neg && pos;
 }
 
-// Energy pass, two launches.
-//  k_front:  block b checks the kEnergyCand candidate cells [b·kEnergyCand,
-//            (b+1)·kEnergyCand) for a sign change (front cells, zero counted
-//            as positive) and writes them, in order, to slot b of the front
-//            array (fixed position b·kEnergyCand) with their count.
-//  k_energy: block b processes slot b:
+// Energy pass, one launch (k_energy). Blocks take slots of kEnergyCand
+// candidate cells from a ticket; for slot b a block first collects, in
+// candidate order and in shared memory, the front cells among candidates
+// [b·kEnergyCand, (b+1)·kEnergyCand) (sign change, zero counted as
+// positive), then processes them:
 //   3-D: one thread per (front cell, subcell layer c along z): the 16 z-lines
 //        of the 4x4x4 stencil at θ_z(c), the 4 y-lines at the R θ_y, the R
 //        x-lines at the R θ_x (WENO; the data-only part of each y- and x-line
@@ -187,90 +186,76 @@ __device__ __forceinline__ bool is_front(const Params<T>& P, const T* __restrict
 // order (one partial pair per block).
 constexpr int kEnergyCand = 1024;  // candidate cells per slot (4 per thread)
 
+// The front cells of slot sb: the candidate cells [sb·kEnergyCand,
+// (sb+1)·kEnergyCand) with vertices of both signs (zero counted as
+// positive), in candidate order, into out[] (block-wide: every thread of the
+// block calls it). Returns their count.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kEnergyThreads) k_front(Params<T> P, const T* ub0, const T* ub1,
-                                                          const int* __restrict__ cells, long long ncells_host,
-                                                          const int* ncells_dev, int offset,
-                                                          int* __restrict__ front, int* __restrict__ fcount,
-                                                          DevState* ds, int check_stop) {
+__device__ __forceinline__ int front_of_slot(const Params<T>& P, const T* __restrict__ u, const int* __restrict__ cells,
+                                             long long ncells, long long sb, int* out, int* s_warp) {
     constexpr int W = kEnergyThreads / 32;
     constexpr int PER = kEnergyCand / kEnergyThreads;
     static_assert(PER == 4, "four candidates per thread (one 16-byte load of the cell list)");
-    __shared__ int s_warp[W + 1];
-    if (check_stop && ds->stop) return;
-    const T* __restrict__ u = ((ds->n + offset) & 1) ? ub1 : ub0;
-    const long long ncells = ncells_dev ? (long long)*ncells_dev : ncells_host;
-    // slot sb = candidates [sb·kEnergyCand, (sb+1)·kEnergyCand); blocks take
-    // slots from a ticket (reset by the record kernel)
-    __shared__ long long s_sb;
-    const long long nslots = (ncells + kEnergyCand - 1) / kEnergyCand;
-    for (;;) {
-        if (threadIdx.x == 0) s_sb = (long long)atomicAdd(&ds->eticket[0], 1u);
-        __syncthreads();
-        const long long sb = s_sb;
-        __syncthreads();
-        if (sb >= nslots) break;
-        int* slot = front + sb * kEnergyCand;
-        // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
-        const long long e0 = sb * kEnergyCand + PER * threadIdx.x;
-        int node[PER];
-        if (cells && e0 + PER <= ncells) {
-            const int4 c4 = *reinterpret_cast<const int4*>(cells + e0);  // slot starts are multiples of 1024
-            node[0] = c4.x;
-            node[1] = c4.y;
-            node[2] = c4.z;
-            node[3] = c4.w;
-        } else {
-    #pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                node[r] = 0;
-                if (e0 + r < ncells) {
-                    int i, j, k;
-                    cell_of<T, DIM>(P, cells, e0 + r, i, j, k);
-                    node[r] = i + P.is1 * j + P.is2 * k;
-                }
-            }
-        }
-        bool fl[PER];
-        int cnt = 0;
-    #pragma unroll
+    // thread t checks the candidates e0 .. e0+3, e0 = slot start + 4t
+    const long long e0 = sb * kEnergyCand + PER * threadIdx.x;
+    int node[PER];
+    if (cells && e0 + PER <= ncells) {
+        const int4 c4 = *reinterpret_cast<const int4*>(cells + e0);  // slot starts are multiples of 1024
+        node[0] = c4.x;
+        node[1] = c4.y;
+        node[2] = c4.z;
+        node[3] = c4.w;
+    } else {
+#pragma unroll
         for (int r = 0; r < PER; ++r) {
-            fl[r] = e0 + r < ncells && is_front<T, DIM>(P, u, node[r]);
-            cnt += fl[r];
-        }
-        // block exclusive scan of the per-thread counts (candidate order kept)
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int incl = cnt;
-    #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int w = 0; w < W; ++w) {
-                const int c = s_warp[w];
-                s_warp[w] = run;
-                run += c;
+            node[r] = 0;
+            if (e0 + r < ncells) {
+                int i, j, k;
+                cell_of<T, DIM>(P, cells, e0 + r, i, j, k);
+                node[r] = i + P.is1 * j + P.is2 * k;
             }
-            s_warp[W] = run;
         }
-        __syncthreads();
-        int off = s_warp[warp] + incl - cnt;
-    #pragma unroll
-        for (int r = 0; r < PER; ++r)
-            if (fl[r]) slot[off++] = node[r];
-        if (threadIdx.x == 0) fcount[sb] = s_warp[W];
-        __syncthreads();
     }
+    bool fl[PER];
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        fl[r] = e0 + r < ncells && is_front<T, DIM>(P, u, node[r]);
+        cnt += fl[r];
+    }
+    // block exclusive scan of the per-thread counts (candidate order kept)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < W; ++w) {
+            const int c = s_warp[w];
+            s_warp[w] = run;
+            run += c;
+        }
+        s_warp[W] = run;
+    }
+    __syncthreads();
+    int off = s_warp[warp] + incl - cnt;
+#pragma unroll
+    for (int r = 0; r < PER; ++r)
+        if (fl[r]) out[off++] = node[r];
+    const int nf = s_warp[W];
+    __syncthreads();
+    return nf;
 }
 
 template <typename T, int DIM, int INTERP, int RC>
 __global__ void __launch_bounds__(kEnergyThreads, (INTERP == 1 && sizeof(T) == 4) ? 4 : 1) k_energy(Params<T> P, const T* ub0, const T* ub1,
-                                                           const T* __restrict__ d, const int* __restrict__ front,
-                                                           const int* __restrict__ fcount, long long ncells_host,
+                                                           const T* __restrict__ d, const int* __restrict__ cells,
+                                                           long long ncells_host,
                                                            const int* ncells_dev, int R_run, double h,
                                                            double p, int p_kind, T thr, T hp2, T pT, int offset,
                                                            double* part, const int* L0, const int* L1,
@@ -281,6 +266,8 @@ __global__ void __launch_bounds__(kEnergyThreads, (INTERP == 1 && sizeof(T) == 4
     __shared__ T s_th[kMaxR];
     __shared__ WenoAxis<T> s_wa[kMaxR];
     __shared__ double s_a[W], s_b[W];
+    __shared__ int s_front[kEnergyCand];  // this slot's front cells
+    __shared__ int s_warp[W + 1];
     if (check_stop && ds->stop) return;
     const int sel = (ds->n + offset) & 1;
     const T* __restrict__ u = sel ? ub1 : ub0;
@@ -318,8 +305,8 @@ __global__ void __launch_bounds__(kEnergyThreads, (INTERP == 1 && sizeof(T) == 4
         const long long sb = s_sb;
         __syncthreads();
         if (sb >= nslots) break;
-        const int* s_list = front + sb * kEnergyCand;  // this slot's front cells
-        const int nf = fcount[sb];
+        const int nf = front_of_slot<T, DIM>(P, u, cells, ncells, sb, s_front, s_warp);
+        const int* s_list = s_front;
         // thr = (√3/2) Δx', hp2 = Δx'^2, pT = p: computed on the host
         auto TH = [&](int m) -> T { return RC > 0 ? (T)m * (T)(1.0 / RD) + (T)(0.5 / RD) : s_th[m]; };
         // WENO constants at θ_m (storage-type arithmetic; folded at compile
@@ -663,24 +650,19 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const int blocks = (int)energy_blocks(c);
     const double hp = c->h / c->cfg.energy_R;
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
-    const long long slots_cap = energy_slots(c) > 0 ? energy_slots(c) : 1;  // as allocated
-    int* fcount = (int*)(c->front + (size_t)slots_cap * kEnergyCand);
     const int* ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;  // the list changes every iteration
-    k_front<T, DIM><<<blocks, kEnergyThreads, 0, c->stream>>>(P, (const T*)c->u[0], (const T*)c->u[1], cells, ncells,
-                                                               ncells_dev, offset, c->front, fcount, c->ds,
-                                                               check_stop);
     int* tile_cnt = c->cfg.band ? c->tile_off : nullptr;
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, ncells, ncells_dev,
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, ncells_dev,
             c->cfg.energy_R, c->h, p, p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds,
             check_stop);
     else
         k_energy<T, DIM, INTERP, 0><<<blocks, kEnergyThreads, 0, c->stream>>>(
-            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, c->front, fcount, ncells, ncells_dev,
+            P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, ncells_dev,
             c->cfg.energy_R, c->h, p, p_kind, thr, hp2, pT, offset, c->part_e, c->band[0], c->band[1], tile_cnt, c->ds,
             check_stop);
-    c->launches += 2;  // front cells, then energy
+    c->launches += 1;
     return cudaGetLastError();
 }
 

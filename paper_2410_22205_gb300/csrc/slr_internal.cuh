@@ -74,7 +74,7 @@ struct DevState {
     int band_count[2];   // [n & 1]: scan domain L^{n-1}; [(n+1) & 1]: band L^n written by step n
     unsigned ticket;     // tile ticket of the fused step kernel (reset by the record kernel)
     unsigned record_done;  // blocks of the record kernel done (reset by its last block)
-    unsigned eticket[2];   // slot tickets of the front-cell and energy kernels (reset by the record kernel)
+    unsigned eticket[2];   // [1]: slot ticket of the energy kernel; [0] unused (both reset by the record kernel)
     int band_next;       // size of the band the next step writes (sum of the tile counts)
     int band_sl;         // with reinitialisation: band nodes the SL step of this iteration updated
     int n_ecells_dyn;    // with reinitialisation: candidate cells of the energy pass
@@ -139,7 +139,6 @@ struct slr_ctx {
     long long n_tiles_cap = 0;
     double* part_e = nullptr;      // two per energy block, plus a two-value report slot
     long long n_echunks = 0;       // candidate chunks of 32 cells (sizes part_e)
-    int* front = nullptr;          // per-block slots of front cells (1024 each) followed by the slot counts
     int* tile_off = nullptr;       // per 128-entry tile of the step's input band: count, then offset in its slice
     // reinitialisation (cfg.reinit): scratch field, row-padded bitmasks, flags
     void* rw = nullptr;                  // W: sweep ping-pong partner of the output φ buffer
