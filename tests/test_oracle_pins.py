@@ -557,6 +557,35 @@ def test_evolve_moves_a_plane_front_at_unit_speed_toward_a_line_cloud(interp):
     assert abs((j - col[j] / (col[j + 1] - col[j])) - 38.3) < 1e-9
 
 
+@pytest.mark.parametrize("interp", [0, 1])
+def test_evolve_moves_a_plane_front_at_unit_speed_toward_a_plane_cloud_3d(interp):
+    """The same closed form in 3-D (eq. SL3d, p = 1, δ = 0, whole grid): one
+    point above every (x, y) node column on the plane z = c gives d = |z - c|
+    on the nodes, and the front z = z0 moves toward the cloud by exactly Δt
+    per iteration wherever the plane and the grid edge cannot reach."""
+    n, steps = 40, 6
+    P = O.params(3, (n, n, n), (-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), interp=interp, p=1.0, delta=0.0, band=0)
+    h, dt = P.h, P.dt
+    x = -1.0 + h * np.arange(n)
+    c = -1.0 + 6.5 * h
+    Xp, Yp = np.meshgrid(x, x, indexing="ij")
+    pts = np.stack([Xp.ravel(), Yp.ravel(), np.full(n * n, c)], 1)
+    d, _ = O.distance(P, pts, method="kd")
+    Z = np.broadcast_to(x[:, None, None], (n, n, n))  # array index [k, j, i]: z along the slowest axis
+    assert np.allclose(d.reshape(n, n, n), np.abs(Z - c), rtol=0, atol=1e-15)
+    z0 = -1.0 + 24.3 * h
+    u0 = np.ascontiguousarray(Z - z0).reshape(-1)
+    r = O.evolve(P, u0, d, min_iters=steps, max_iters=steps)
+    assert r["iters"] == steps
+    u = r["u"].reshape(n, n, n)
+    reach = (1 if interp == 0 else 2) * (steps + 1)
+    planes = np.arange(n)
+    clean = (planes > 6.5 + reach) & (planes < n - 1 - reach)
+    assert clean[22] and clean[23]
+    expect = Z - (z0 - steps * dt)
+    assert np.max(np.abs(u[clean] - expect[clean])) < 1e-12
+
+
 # ---------------------------------------------------------------- reinitialisation (§3.7)
 
 def _reinit_grid(dim, n, **kw):
