@@ -311,6 +311,37 @@ def test_plane_front_moves_at_unit_speed_toward_a_line_cloud(interp):
     assert err.max() <= 1e-12
 
 
+@pytest.mark.parametrize("interp", [0, 1])
+def test_plane_front_moves_at_unit_speed_toward_a_plane_cloud_3d(interp):
+    """The 3-D closed form through the C ABI: FP64, whole grid, p = 1, δ = 0,
+    a plane cloud z = c with one point above every (x, y) node column, the
+    front z = z0; 6 steps. Every node equals the oracle's loop (<= 1e-12); the
+    planes beyond the reach of the cloud and the grid edge equal
+    z - (z0 - 6Δt) (<= 1e-12)."""
+    n, steps = 40, 6
+    rec, P = make(3, n, 64, interp, 0, p=1.0, delta=0.0)
+    h, dt = P.h, P.dt
+    x = -1.0 + h * np.arange(n)
+    c = -1.0 + 6.5 * h
+    Xp, Yp = np.meshgrid(x, x, indexing="ij")
+    rec.load_cloud(np.stack([Xp.ravel(), Yp.ravel(), np.full(n * n, c)], 1))
+    rec.build_distance()
+    Z = np.broadcast_to(x[:, None, None], (n, n, n))
+    z0 = -1.0 + 24.3 * h
+    u0 = np.ascontiguousarray(Z - z0).reshape(-1)
+    rec.init_array(u0)
+    rec.step(steps)
+    u = rec.u()
+    ref = O.evolve(P, u0, rec.d(), min_iters=steps, max_iters=steps)
+    assert ref["iters"] == steps
+    assert np.abs(u - ref["u"]).max() <= 1e-12
+    reach = (1 if interp == 0 else 2) * (steps + 1)
+    planes = np.arange(n)
+    clean = (planes > 6.5 + reach) & (planes < n - 1 - reach)
+    err = np.abs(u.reshape(n, n, n) - (Z - (z0 - steps * dt)))[clean]
+    assert err.max() <= 1e-12
+
+
 @pytest.mark.parametrize("kmax,min_iters,tol", [(10, 10, 1e-4), (3, 2, 1e-3), (25, 5, 1e-3)])
 def test_evolve_matches_oracle_stop_rule(kmax, min_iters, tol):
     rec, P = make(2, 48, 64, 1, 1, p=1.0, delta=0.0, stop_k=kmax, min_iters=min_iters, stop_tol=tol)
