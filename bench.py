@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--interp", choices=["weno", "q1"], default="weno",
+                    help="interpolator of the timed workload (the headline is WENO)")
+    ap.add_argument("--precision", type=int, choices=[32, 64], default=32,
+                    help="storage and arithmetic precision of the timed workload (the headline is FP32)")
+    ap.add_argument("--fullgrid", action="store_true",
+                    help="time the whole-grid step (band off) instead of the narrow band")
     ap.add_argument("--reinit", action="store_true",
                     help="time the iteration with the reinitialisation of §3.7 (Algorithm 1 step 4d) on")
     ap.add_argument("--batch-jobs", type=int, default=64, help="jobs of the batched mix (0: skip)")
@@ -219,7 +225,7 @@ def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha):
                 "hbm_view": {"achieved_gbs": 20.0 * band_nodes / (ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
                              "frac": 20.0 * band_nodes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
     elif kernel["kind"] == "step_q1":
-        bytes_ = 20.0 * band_nodes
+        bytes_ = kernel.get("bytes_per_node", 20.0) * band_nodes
         achieved = bytes_ / (ms * 1e-3) / 1e9
         info = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS)"}
@@ -282,7 +288,11 @@ def run_gpu(args):
     grid, cloud = workload(args)
     cloud_s = time.time() - t_setup
     n = args.n
-    rec = slr.Reconstruction(dim=3, n=n, precision=32, interp=1, band=1, reinit=int(args.reinit), **cfg_kw())
+    interp = 1 if args.interp == "weno" else 0
+    band = 0 if args.fullgrid else 1
+    prec = args.precision
+    rec = slr.Reconstruction(dim=3, n=n, precision=prec, interp=interp, band=band, reinit=int(args.reinit),
+                             **cfg_kw())
     st = rec.stream
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     rec.load_cloud(cloud)
@@ -315,12 +325,16 @@ def run_gpu(args):
     value, tot_units, tmax = aggregate(units, secs, dist)
     ms_per_step = tmax * 1e3 / args.steps
     kern = np.array(kern_ms)
-    names = ["k_step_band<float,3,WENO>", "k_energy<float,3,WENO,R=5> (front cells + quadrature)", "k_record"]
+    tname = "float" if prec == 32 else "double"
+    iname = "WENO" if interp else "Q1"
+    names = [f"k_step_brick<{tname},{iname},{'band' if band else 'whole grid'}>",
+             f"k_energy<{tname},3,{iname},R=5> (front cells + quadrature)", "k_record"]
     kmean = kern.mean(axis=0)
     dom = int(np.argmax(kmean[:2]))  # the step or the energy pass (the record kernel is a small reduction)
     mean_band = float(np.mean(bands))
     front = 1.5 * 4 * math.pi * 0.81 / ((2.0 / (n - 1)) ** 2)
-    kernel = {"name": names[dom], "kind": ["step_weno", "energy"][dom], "front_cells": front}
+    kernel = {"name": names[dom], "kind": [("step_weno" if interp else "step_q1"), "energy"][dom],
+              "front_cells": front, "bytes_per_node": 20.0 if band else 12.0}
     sha = sha_of_kernels()
     roof = roofline_for(kernel, float(kmean[dom]), mean_band, peaks, sha)
     roof["kernel_share_of_step"] = float(kmean[dom] / np.mean(pstep_ms))
@@ -386,10 +400,12 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded superquadric-union cloud)",
-            "config": {"workload": f"sq3union{args.points // 1000}k_{n}cube_band6h_weno_fp32"
-                                   + ("_reinit" if args.reinit else ""), "grid": f"{n}^3", "reinit": bool(args.reinit),
-                       "points": args.points, "interp": "WENO", "band": "6h", "p": 2, "delta": 1,
+            "vs_baseline": None, "dtype": f"f{prec}", "data": "synthetic (seeded superquadric-union cloud)",
+            "config": {"workload": f"sq3union{args.points // 1000}k_{n}cube_{'band6h' if band else 'fullgrid'}"
+                                   f"_{args.interp}_fp{prec}" + ("_reinit" if args.reinit else ""),
+                       "grid": f"{n}^3", "reinit": bool(args.reinit),
+                       "points": args.points, "interp": iname, "band": "6h" if band else "off (whole grid)",
+                       "p": 2, "delta": 1,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{dist.world}",
                        "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_algorithm1_reinit": e2e_alg1,

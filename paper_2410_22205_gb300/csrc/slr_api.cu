@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kChunk = 8;  // graph replays between status reads in slr_evolve
 constexpr uint32_t kStateMagic = 0x534c5231u;  // "SLR1"
-thread_local std::string g_create_error;  // reason of the last failed slr_create on this thread
+thread_local std::string g_ctxless_error;  // see ctxless_error_clear()
 
 slr_status fail(slr_ctx* c, slr_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -139,6 +139,7 @@ slr_status check_device_error(slr_ctx* c) {
     slr_status s = read_status(c, nullptr, &err, nullptr);
     if (s != SLR_OK) return s;
     if (err & kErrBandOffset) return fail(c, SLR_E_STATE, "band-list offsets inconsistent with the band");
+    if (err & kErrStage) return fail(c, SLR_E_TIMEOUT, "a shared-memory staging wait of the step gave up");
     if (err) return fail(c, SLR_E_STATE, "a device-side check failed");
     return SLR_OK;
 }
@@ -256,12 +257,26 @@ slr_status init_after_u(slr_ctx* c, cudaError_t e) {
             CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "init_u");
         }
     }
+    if (brick_mode(c)) {
+        cudaError_t eb = bricks_init(c, c->u[0]);
+        if (eb == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "init_u: brick lists allocation failed");
+        CK(eb, "init_u bricks");
+    }
     CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
     CK(cudaStreamSynchronize(c->stream), "init_u sync");
     c->have_u = true;
     return SLR_OK;
 }
 
+}  // namespace slr
+
+namespace slr {
+void ctxless_error_clear() { g_ctxless_error.clear(); }
+slr_status ctxless_error_set(slr_status s, const std::string& msg) {
+    g_ctxless_error = msg;
+    return s;
+}
+const char* ctxless_error() { return g_ctxless_error.c_str(); }
 }  // namespace slr
 
 extern "C" {
@@ -296,13 +311,14 @@ void slr_config_default(slr_config* cfg) {
 }
 
 slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out) {
-    if (!cfg || !out) return SLR_E_INVALID;
+    ctxless_error_clear();
+    if (!cfg || !out) return ctxless_error_set(SLR_E_INVALID, "create: null argument");
     *out = nullptr;
     slr_ctx* c = new slr_ctx();
     c->cfg = *cfg;
     slr_config& k = c->cfg;
     auto bad = [&](const char* m) {
-        g_create_error = m;
+        ctxless_error_set(SLR_E_INVALID, m);
         delete c;
         return SLR_E_INVALID;
     };
@@ -839,22 +855,19 @@ slr_status slr_get_field(slr_ctx* c, int which, void* host_out, int64_t cap) {
 }
 
 slr_status slr_selftest_barrier(int unreachable) {
+    ctxless_error_clear();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        return SLR_E_CUDA;
+        return ctxless_error_set(SLR_E_CUDA, "selftest_barrier: no usable current device");
     }
     int err = 0;
     cudaError_t e = barrier_selftest(dev, unreachable ? 1 : 0, &err);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        g_create_error = std::string("selftest_barrier: ") + cudaGetErrorString(e);
-        return SLR_E_CUDA;
+        return ctxless_error_set(SLR_E_CUDA, std::string("selftest_barrier: ") + cudaGetErrorString(e));
     }
-    if (err & kErrBarrier) {
-        g_create_error = "selftest_barrier: the barrier's wait ran out";
-        return SLR_E_TIMEOUT;
-    }
+    if (err & kErrBarrier) return ctxless_error_set(SLR_E_TIMEOUT, "selftest_barrier: the barrier's wait ran out");
     return SLR_OK;
 }
 
@@ -909,14 +922,26 @@ slr_status slr_get_band(slr_ctx* c, int64_t* idx, int64_t cap, int64_t* n_out) {
     slr_status s = read_status(c, nullptr, nullptr, &n);
     if (s != SLR_OK) return s;
     int cnt = 0;
-    CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream), "get_band");
-    CK(cudaStreamSynchronize(c->stream), "get_band");
+    int* list = c->band[n & 1];
+    if (brick_mode(c) && c->brick.list_iter != n) {
+        // the brick step keeps no list: the band the last step updated is
+        // {|u| < γ} of that step's input (φ^0 before any step)
+        long long lc = 0;
+        list = c->band[0];
+        CK(band_of_field(c, c->u[n >= 1 ? ((n - 1) & 1) : 0], list, &lc), "get_band");
+        cnt = (int)lc;
+    } else {
+        if (brick_mode(c)) list = c->band[0];
+        CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "get_band");
+        CK(cudaStreamSynchronize(c->stream), "get_band");
+    }
     if (n_out) *n_out = cnt;
     if (!idx) return SLR_OK;
     if (cnt > cap) return fail(c, SLR_E_CAPACITY, "get_band: buffer too small");
     int* tmp = (int*)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
     if (!tmp) return fail(c, SLR_E_NOMEM, "get_band: host allocation failed");
-    cudaError_t e = cudaMemcpyAsync(tmp, c->band[n & 1], sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaMemcpyAsync(tmp, list, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess)
         for (int i = 0; i < cnt; ++i) idx[i] = tmp[i];
@@ -994,7 +1019,22 @@ slr_status slr_export_state(slr_ctx* c, void* buf, int64_t cap, int64_t* n_out) 
     slr_status s = read_status(c, nullptr, nullptr, &n);
     if (s != SLR_OK) return s;
     int cnt = 0;
-    if (c->cfg.band) {
+    int* list = c->band[n & 1];
+    const bool bricked = brick_mode(c);
+    if (c->cfg.band && bricked) {
+        // the band the last step updated (see slr_get_band), rebuilt into band[0]
+        long long lc = 0;
+        list = c->band[0];
+        if (c->brick.list_iter != n)
+            CK(band_of_field(c, c->u[n >= 1 ? ((n - 1) & 1) : 0], list, &lc), "export");
+        else {
+            CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+               "export");
+            CK(cudaStreamSynchronize(c->stream), "export");
+            lc = cnt;
+        }
+        cnt = (int)lc;
+    } else if (c->cfg.band) {
         CK(cudaMemcpyAsync(&cnt, &c->ds->band_count[n & 1], sizeof(int), cudaMemcpyDeviceToHost, c->stream), "export");
         CK(cudaStreamSynchronize(c->stream), "export");
     }
@@ -1017,7 +1057,7 @@ slr_status slr_export_state(slr_ctx* c, void* buf, int64_t cap, int64_t* n_out) 
     p += sizeof(slr_config);
     CK(cudaMemcpyAsync(p, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "export");
     p += sizeof(DevState);
-    if (cnt) CK(cudaMemcpyAsync(p, c->band[n & 1], sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream), "export");
+    if (cnt) CK(cudaMemcpyAsync(p, list, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream), "export");
     p += sizeof(int) * cnt;
     if (hd.n_ecells)
         CK(cudaMemcpyAsync(p, c->ecells, sizeof(int) * hd.n_ecells, cudaMemcpyDeviceToHost, c->stream), "export");
@@ -1074,9 +1114,16 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     free(hds);
     if (e != cudaSuccess) return cuda_fail(c, e, "import_state");
+    const bool bricked = brick_mode(c);
     if (hd.band_count)
-        CK(cudaMemcpyAsync(c->band[n & 1], p, sizeof(int) * hd.band_count, cudaMemcpyHostToDevice, c->stream),
+        CK(cudaMemcpyAsync(c->band[bricked ? 0 : (n & 1)], p, sizeof(int) * hd.band_count, cudaMemcpyHostToDevice,
+                           c->stream),
            "import");
+    if (bricked) {
+        // the band count sits where slr_get_band reads it until the next step
+        int bc = (int)hd.band_count;
+        CK(cudaMemcpyAsync(&c->ds->band_count[n & 1], &bc, sizeof(int), cudaMemcpyHostToDevice, c->stream), "import");
+    }
     p += sizeof(int) * hd.band_count;
     if (hd.n_ecells)
         CK(cudaMemcpyAsync(c->ecells, p, sizeof(int) * hd.n_ecells, cudaMemcpyHostToDevice, c->stream), "import");
@@ -1089,6 +1136,15 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     CK(cudaMemcpyAsync(c->argmin, p, sizeof(int) * c->N, cudaMemcpyHostToDevice, c->stream), "import");
     if (c->cfg.reinit)
         CK(cudaMemcpyAsync(c->rw, c->u[0], c->tsize * c->N, cudaMemcpyDeviceToDevice, c->stream), "import");
+    if (bricked) {
+        // active bricks of the imported state; both buffers hold it, and the
+        // Δ_φ partials are keyed by brick id, so an uninterrupted run and the
+        // resumed one sum the same partials in the same order
+        cudaError_t eb = bricks_init(c, c->u[0]);
+        if (eb == cudaErrorMemoryAllocation) return fail(c, SLR_E_NOMEM, "import_state: brick lists allocation failed");
+        CK(eb, "import bricks");
+        c->brick.list_iter = c->cfg.band ? n : -1;
+    }
     // an energy pass in report mode recomputes the band-tile offsets the
     // next step reads (the history and E_p stay as imported)
     CK(launch_energy(c, 0, c->cfg.p, 2, 0), "import energy pass");
@@ -1102,8 +1158,7 @@ int64_t slr_kernel_launches(const slr_ctx* c) { return c ? c->launches : 0; }
 
 const char* slr_last_error(const slr_ctx* c) {
     if (c) return c->err.c_str();
-    const char* m = slr::noalloc_last_error();
-    return (m && m[0]) ? m : g_create_error.c_str();
+    return g_ctxless_error.c_str();
 }
 
 void slr_destroy(slr_ctx* c) {
@@ -1131,6 +1186,7 @@ void slr_destroy(slr_ctx* c) {
     release_t(c, c->rblk);
     release_t(c, c->rflags);
     release_t(c, c->part_dphi_r);
+    bricks_free(c);
     release_t(c, c->ds);
     if (c->host_pinned_flags) cudaFreeHost(c->host_pinned_flags);
     for (int i = 0; i < 5; ++i)

@@ -432,7 +432,7 @@ static void launch_search(slr_ctx* c, const SearchArgs& A) {
 
 // the sorted cloud and its box hierarchy (scratch of one search)
 struct CloudIndex {
-    char* base = nullptr;
+    char* base = nullptr;  // the context path's allocation (nullptr for fixed scratch)
     int* flag = nullptr;
     float4* spt = nullptr;
     float4* blo = nullptr;
@@ -442,77 +442,70 @@ struct CloudIndex {
     double extent = 0.0;
 };
 
-static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
-    const int dim = c->cfg.dim;
-    const long long npts = c->npts;
-    cudaStream_t st = c->stream;
-    cudaError_t e = cudaSuccess;
-    // bit-grid resolution: 2^L bins per axis
-    const int L = dim == 3 ? 7 : 10;
-    const long long nbins = 1ll << (dim * L);
-    // box hierarchy sizes
-    long long* cnt = X.cnt;
-    long long* off = X.off;
-    int nlevels = 0;
-    long long total_boxes = 0;
-    {
-        long long cc = (npts + 31) / 32;
-        for (;;) {
-            if (nlevels >= kMaxLevels) return cudaErrorInvalidValue;
-            cnt[nlevels] = cc;
-            off[nlevels] = total_boxes;
-            total_boxes += cc;
-            ++nlevels;
-            if (cc <= 32) break;
-            cc = (cc + 31) / 32;
-        }
+// device buffers of one index build
+struct IndexScratch {
+    unsigned long long* bbox;  // 6 words: encoded minima, then maxima
+    int* flag;                 // error bits (non-finite point: k_bbox; stack overflow: the search)
+    unsigned* codes;           // one bin code per point
+    int* counts;               // one counter per bin (2^(dim L))
+    int* tot;                  // scan partials
+    float4* spt;               // sorted points (FP32 offsets from lo, index in w)
+    float4* blo;               // box hierarchy: lower corners, then upper corners
+};
+
+// Level sizes of the 32-ary box hierarchy over npts points. False when the
+// hierarchy would be deeper than kMaxLevels.
+static bool hierarchy_sizes(long long npts, long long* cnt, long long* off, int* nlevels, long long* total_boxes) {
+    int nl = 0;
+    long long tot = 0;
+    long long cc = (npts + 31) / 32;
+    for (;;) {
+        if (nl >= kMaxLevels) return false;
+        cnt[nl] = cc;
+        off[nl] = tot;
+        tot += cc;
+        ++nl;
+        if (cc <= 32) break;
+        cc = (cc + 31) / 32;
     }
-    X.nlevels = nlevels;
+    *nlevels = nl;
+    *total_boxes = tot;
+    return true;
+}
+
+// Builds the bin-sorted cloud and its box hierarchy in S, with 2^L bins per
+// axis over the cloud's bounding box. X.nlevels/off/cnt must hold the sizes
+// from hierarchy_sizes. lo, hi: the grid's corners (they bound the FP32
+// offsets the search screens with). Waits on st for the bounding box;
+// cudaErrorInvalidValue when a coordinate is not finite. *launches counts the
+// kernels launched.
+static cudaError_t build_index(const double* pts, long long npts, int dim, int L, const double lo[3],
+                               const double hi[3], int num_sms, cudaStream_t st, const IndexScratch& S, CloudIndex& X,
+                               long long* launches) {
+    const long long nbins = 1ll << (dim * L);
     const long long nscan_blocks = (nbins + 4095) / 4096;
-    // scratch layout
-    size_t b_bbox = 64, b_flag = 16, b_codes = sizeof(unsigned) * npts, b_counts = sizeof(int) * nbins,
-           b_tot = sizeof(int) * (nscan_blocks + 2) + 16, b_spt = sizeof(float4) * npts,
-           b_boxes = sizeof(float4) * 2 * total_boxes;
-    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-    size_t total = al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes);
-    char* base = (char*)dev_alloc(c, total);
-    if (!base) return cudaErrorMemoryAllocation;
-    X.base = base;
-    char* p = base;
-    unsigned long long* bbox = (unsigned long long*)p;
-    p += al(b_bbox);
-    int* flag = (int*)p;
-    X.flag = flag;
-    p += al(b_flag);
-    unsigned* codes = (unsigned*)p;
-    p += al(b_codes);
-    int* counts = (int*)p;
-    p += al(b_counts);
-    int* tot = (int*)p;
-    p += al(b_tot);
-    float4* spt = (float4*)p;
-    X.spt = spt;
-    p += al(b_spt);
-    float4* blo = (float4*)p;
-    float4* bhi = blo + total_boxes;
-    X.blo = blo;
-    X.bhi = bhi;
+    long long total_boxes = 0;
+    for (int l = 0; l < X.nlevels; ++l) total_boxes += X.cnt[l];
+    X.flag = S.flag;
+    X.spt = S.spt;
+    X.blo = S.blo;
+    X.bhi = S.blo + total_boxes;
 
     unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
     unsigned long long hb[6];
     int hflag = 0;
-    e = cudaMemcpyAsync(bbox, init_bbox, sizeof(init_bbox), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, b_counts, st);
+    cudaError_t e = cudaMemcpyAsync(S.bbox, init_bbox, sizeof(init_bbox), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int) * nbins, st);
     if (e == cudaSuccess) {
         int blocks = (int)((npts + 255) / 256);
-        if (blocks > c->num_sms * 8) blocks = c->num_sms * 8;
-        k_bbox<<<blocks, 256, 0, st>>>(c->pts, npts, dim, bbox, flag);
-        c->launches += 1;
+        if (blocks > num_sms * 8) blocks = num_sms * 8;
+        k_bbox<<<blocks, 256, 0, st>>>(pts, npts, dim, S.bbox, S.flag);
+        *launches += 1;
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, S.bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, S.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     if (hflag) return cudaErrorInvalidValue;
@@ -528,42 +521,76 @@ static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     B.inv_bin = 1.0 / bin;
     B.L = L;
     B.dim = dim;
-    const double o0 = c->cfg.lo[0], o1 = c->cfg.lo[1], o2 = dim == 3 ? c->cfg.lo[2] : 0.0;
+    const double o0 = lo[0], o1 = lo[1], o2 = dim == 3 ? lo[2] : 0.0;
     double extent = 0.0;
     for (int a = 0; a < dim; ++a) {
-        double lo = c->cfg.lo[a];
-        extent = fmax(extent, fabs(c->cfg.hi[a] - lo));
-        extent = fmax(extent, fabs(bmin[a] - lo));
-        extent = fmax(extent, fabs(bmax[a] - lo));
+        extent = fmax(extent, fabs(hi[a] - lo[a]));
+        extent = fmax(extent, fabs(bmin[a] - lo[a]));
+        extent = fmax(extent, fabs(bmax[a] - lo[a]));
     }
     X.extent = extent;
-    {
-        int blocks = (int)((npts + 255) / 256);
-        k_codes<<<blocks, 256, 0, st>>>(c->pts, npts, B, codes, counts);
-        k_scan_blocks<<<(unsigned)nscan_blocks, 1024, 0, st>>>(counts, nbins, tot);
-        k_scan_counts<<<1, 1024, 0, st>>>(tot, (int)nscan_blocks, (long long*)(tot + ((nscan_blocks + 2) & ~1ll)));
-        k_scan_add<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, nbins, tot);
-        k_scatter<<<blocks, 256, 0, st>>>(c->pts, npts, dim, codes, counts, o0, o1, o2, spt);
-        c->launches += 5;
-        for (int l = 0; l < nlevels; ++l) {
-            long long own = cnt[l];
-            long long threads = own * 32;
-            k_boxes<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-                spt, npts, blo, bhi, l == 0 ? 0 : off[l - 1], l == 0 ? npts : cnt[l - 1], off[l], own, l);
-            c->launches += 1;
-        }
-        e = cudaGetLastError();
+    int blocks = (int)((npts + 255) / 256);
+    k_codes<<<blocks, 256, 0, st>>>(pts, npts, B, S.codes, S.counts);
+    k_scan_blocks<<<(unsigned)nscan_blocks, 1024, 0, st>>>(S.counts, nbins, S.tot);
+    k_scan_counts<<<1, 1024, 0, st>>>(S.tot, (int)nscan_blocks, (long long*)(S.tot + ((nscan_blocks + 2) & ~1ll)));
+    k_scan_add<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(S.counts, nbins, S.tot);
+    k_scatter<<<blocks, 256, 0, st>>>(pts, npts, dim, S.codes, S.counts, o0, o1, o2, S.spt);
+    *launches += 5;
+    for (int l = 0; l < X.nlevels; ++l) {
+        long long own = X.cnt[l];
+        long long threads = own * 32;
+        k_boxes<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            S.spt, npts, X.blo, X.bhi, l == 0 ? 0 : X.off[l - 1], l == 0 ? npts : X.cnt[l - 1], X.off[l], own, l);
+        *launches += 1;
     }
-    return e;
+    return cudaGetLastError();
 }
 
-// search arguments over the context's grid and a built cloud index
-static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
+// bytes of the scan partials for 2^(dim L) bins (the second-level sums go
+// after them, 8-byte aligned)
+static size_t scan_tot_bytes(long long nbins) { return sizeof(int) * ((nbins + 4095) / 4096 + 2) + 16; }
+
+static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     const int dim = c->cfg.dim;
+    const long long npts = c->npts;
+    // bit-grid resolution: 2^L bins per axis
+    const int L = dim == 3 ? 7 : 10;
+    const long long nbins = 1ll << (dim * L);
+    long long total_boxes = 0;
+    if (!hierarchy_sizes(npts, X.cnt, X.off, &X.nlevels, &total_boxes)) return cudaErrorInvalidValue;
+    // scratch layout
+    size_t b_bbox = 64, b_flag = 16, b_codes = sizeof(unsigned) * npts, b_counts = sizeof(int) * nbins,
+           b_tot = scan_tot_bytes(nbins), b_spt = sizeof(float4) * npts, b_boxes = sizeof(float4) * 2 * total_boxes;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t total = al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes);
+    char* base = (char*)dev_alloc(c, total);
+    if (!base) return cudaErrorMemoryAllocation;
+    X.base = base;
+    IndexScratch S;
+    char* p = base;
+    S.bbox = (unsigned long long*)p;
+    p += al(b_bbox);
+    S.flag = (int*)p;
+    p += al(b_flag);
+    S.codes = (unsigned*)p;
+    p += al(b_codes);
+    S.counts = (int*)p;
+    p += al(b_counts);
+    S.tot = (int*)p;
+    p += al(b_tot);
+    S.spt = (float4*)p;
+    p += al(b_spt);
+    S.blo = (float4*)p;
+    return build_index(c->pts, npts, dim, L, c->cfg.lo, c->cfg.hi, c->num_sms, c->stream, S, X, &c->launches);
+}
+
+// search arguments over a grid (n[2] = 1 in 2-D) and a built cloud index
+static SearchArgs search_args(int dim, const int64_t n[3], const double lo[3], double h, const double* pts,
+                              long long npts, const CloudIndex& X) {
     SearchArgs A;
-    A.n0 = (int)c->cfg.n[0];
-    A.n1 = (int)c->cfg.n[1];
-    A.n2 = (int)c->cfg.n[2];
+    A.n0 = (int)n[0];
+    A.n1 = (int)n[1];
+    A.n2 = dim == 3 ? (int)n[2] : 1;
     if (dim == 3) {
         A.tx = (A.n0 + 1) / 2;
         A.ty = (A.n1 + 3) / 4;
@@ -573,13 +600,13 @@ static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
         A.ty = (A.n1 + 3) / 4;
         A.tz = 1;
     }
-    A.lo0 = c->cfg.lo[0];
-    A.lo1 = c->cfg.lo[1];
-    A.lo2 = dim == 3 ? c->cfg.lo[2] : 0.0;
-    A.h = c->h;
+    A.lo0 = lo[0];
+    A.lo1 = lo[1];
+    A.lo2 = dim == 3 ? lo[2] : 0.0;
+    A.h = h;
     A.spt = X.spt;
-    A.pts = c->pts;
-    A.npts = c->npts;
+    A.pts = pts;
+    A.npts = npts;
     A.blo = X.blo;
     A.bhi = X.bhi;
     A.nlevels = X.nlevels;
@@ -590,6 +617,10 @@ static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
     A.extent = X.extent;
     A.flag = X.flag;
     return A;
+}
+
+static SearchArgs search_args(slr_ctx* c, const CloudIndex& X) {
+    return search_args(c->cfg.dim, c->cfg.n, c->cfg.lo, c->h, c->pts, c->npts, X);
 }
 
 cudaError_t build_distance(slr_ctx* c) {
@@ -684,16 +715,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
-thread_local std::string g_noalloc_error;
-
-slr_status noalloc_fail(slr_status s, const std::string& m) {
-    g_noalloc_error = m;
-    return s;
-}
+slr_status noalloc_fail(slr_status s, const std::string& m) { return ctxless_error_set(s, m); }
 
 }  // namespace
-
-const char* noalloc_last_error() { return g_noalloc_error.c_str(); }
 
 }  // namespace slr
 
@@ -701,7 +725,7 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
                                                 const double* pts_dev, int64_t n_points, void* d_dev,
                                                 int32_t* argmin_dev, void* cuda_stream) {
     using namespace slr;
-    g_noalloc_error.clear();
+    ctxless_error_clear();
     if (dim != 2 && dim != 3) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: dim must be 2 or 3");
     if (!n || !lo || !pts_dev || !d_dev || !argmin_dev)
         return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: null argument");
@@ -745,118 +769,39 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
         }
         base = (unsigned char*)g_noalloc_ptr[dev];
     }
-    unsigned long long* bbox = (unsigned long long*)(base + kOffBbox);
-    int* flag = (int*)(base + kOffFlag);
-    unsigned* codes = (unsigned*)(base + kOffCodes);
-    int* counts = (int*)(base + kOffCounts);
-    int* tot = (int*)(base + kOffTot);
-    float4* spt = (float4*)(base + kOffSpt);
-    float4* blo = (float4*)(base + kOffBoxes);
+    IndexScratch S;
+    S.bbox = (unsigned long long*)(base + kOffBbox);
+    S.flag = (int*)(base + kOffFlag);
+    S.codes = (unsigned*)(base + kOffCodes);
+    S.counts = (int*)(base + kOffCounts);
+    S.tot = (int*)(base + kOffTot);
+    S.spt = (float4*)(base + kOffSpt);
+    S.blo = (float4*)(base + kOffBoxes);
 
     const long long npts = n_points;
     const int L = dim == 3 ? kNoAllocL3 : kNoAllocL2;
-    const long long nbins = 1ll << (dim * L);
-    long long cnt[kMaxLevels], off[kMaxLevels];
-    int nlevels = 0;
+    CloudIndex X;
     long long total_boxes = 0;
-    {
-        long long cc = (npts + 31) / 32;
-        for (;;) {
-            cnt[nlevels] = cc;
-            off[nlevels] = total_boxes;
-            total_boxes += cc;
-            ++nlevels;
-            if (cc <= 32) break;
-            cc = (cc + 31) / 32;
-        }
-    }
-    float4* bhi = blo + total_boxes;
+    if (!hierarchy_sizes(npts, X.cnt, X.off, &X.nlevels, &total_boxes) || total_boxes > kNoAllocBoxes)
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: box hierarchy larger than the fixed scratch");
     int num_sms = 0;
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (num_sms <= 0) num_sms = 1;
-
-    // the array keeps the previous call's contents: reset what must start at zero
-    unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
-    unsigned long long hb[6];
-    int hflag = 0;
-    e = cudaMemcpyAsync(bbox, init_bbox, sizeof(init_bbox), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int) * nbins, st);
-    if (e == cudaSuccess) {
-        int blocks = (int)((npts + 255) / 256);
-        if (blocks > num_sms * 8) blocks = num_sms * 8;
-        k_bbox<<<blocks, 256, 0, st>>>(pts_dev, npts, dim, bbox, flag);
-        e = cudaGetLastError();
+    double hi[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) hi[a] = lo[a] + (double)(n[a] - 1) * h;
+    long long launches = 0;
+    // the array keeps the previous call's contents: build_index resets what
+    // must start at zero (bounding box, flag, bin counters)
+    e = build_index(pts_dev, npts, dim, L, lo, hi, num_sms, st, S, X, &launches);
+    if (e == cudaErrorInvalidValue) {
+        cudaGetLastError();
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: non-finite point coordinates");
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return noalloc_fail(SLR_E_CUDA, std::string("distance_grid_noalloc: ") + cudaGetErrorString(e));
     }
-    if (hflag) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: non-finite point coordinates");
-    BinArgs B;
-    double bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0}, ext = 0.0;
-    for (int a = 0; a < dim; ++a) {
-        bmin[a] = dec_double(hb[a]);
-        bmax[a] = dec_double(hb[3 + a]);
-        ext = fmax(ext, bmax[a] - bmin[a]);
-    }
-    double bin = ext > 0 ? ext / (double)(1 << L) * (1.0 + 1e-9) : 1.0;
-    for (int a = 0; a < 3; ++a) B.bmin[a] = bmin[a];
-    B.inv_bin = 1.0 / bin;
-    B.L = L;
-    B.dim = dim;
-    const double o0 = lo[0], o1 = lo[1], o2 = dim == 3 ? lo[2] : 0.0;
-    double extent = 0.0;
-    for (int a = 0; a < dim; ++a) {
-        double hi_a = lo[a] + (double)(n[a] - 1) * h;
-        extent = fmax(extent, fabs(hi_a - lo[a]));
-        extent = fmax(extent, fabs(bmin[a] - lo[a]));
-        extent = fmax(extent, fabs(bmax[a] - lo[a]));
-    }
-    const long long nscan = (nbins + 4095) / 4096;
-    int blocks = (int)((npts + 255) / 256);
-    k_codes<<<blocks, 256, 0, st>>>(pts_dev, npts, B, codes, counts);
-    k_scan_blocks<<<(unsigned)nscan, 1024, 0, st>>>(counts, nbins, tot);
-    k_scan_counts<<<1, 1024, 0, st>>>(tot, (int)nscan, (long long*)(tot + ((nscan + 2) & ~1ll)));
-    k_scan_add<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, nbins, tot);
-    k_scatter<<<blocks, 256, 0, st>>>(pts_dev, npts, dim, codes, counts, o0, o1, o2, spt);
-    for (int l = 0; l < nlevels; ++l) {
-        long long threads = cnt[l] * 32;
-        k_boxes<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-            spt, npts, blo, bhi, l == 0 ? 0 : off[l - 1], l == 0 ? npts : cnt[l - 1], off[l], cnt[l], l);
-    }
-    SearchArgs A;
-    A.n0 = (int)n[0];
-    A.n1 = (int)n[1];
-    A.n2 = dim == 3 ? (int)n[2] : 1;
-    if (dim == 3) {
-        A.tx = (A.n0 + 1) / 2;
-        A.ty = (A.n1 + 3) / 4;
-        A.tz = (A.n2 + 3) / 4;
-    } else {
-        A.tx = (A.n0 + 7) / 8;
-        A.ty = (A.n1 + 3) / 4;
-        A.tz = 1;
-    }
-    A.lo0 = lo[0];
-    A.lo1 = lo[1];
-    A.lo2 = dim == 3 ? lo[2] : 0.0;
-    A.h = h;
-    A.spt = spt;
-    A.pts = pts_dev;
-    A.npts = npts;
-    A.blo = blo;
-    A.bhi = bhi;
-    A.nlevels = nlevels;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        A.off[l] = l < nlevels ? off[l] : 0;
-        A.cnt[l] = l < nlevels ? cnt[l] : 0;
-    }
-    A.extent = extent;
-    A.flag = flag;
+    SearchArgs A = search_args(dim, n, lo, h, pts_dev, npts, X);
     long long ntiles = (long long)A.tx * A.ty * A.tz;
     unsigned sblocks = (unsigned)((ntiles * 32 + 255) / 256);
     if (precision == 32) {
@@ -870,6 +815,8 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
         else
             k_dist_search<double, 2><<<sblocks, 256, 0, st>>>(A, (double*)d_dev, argmin_dev);
     }
+    int hflag = 0;
+    int* flag = S.flag;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

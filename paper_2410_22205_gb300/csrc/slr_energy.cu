@@ -464,6 +464,7 @@ struct RecordArgs {
     long long N;
     int full_grid;
     int reinit;            // Δ_φ partials from the reinitialisation stage; band size from band_sl
+    int bricked;           // brick step: n_dphi_full partials, one per brick; band size from band_brick
     int mode;
     int evolve;
     double h_dim;  // h^dim
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
-        ntiles = (A.full_grid || A.reinit) ? A.n_dphi_full
+        ntiles = (A.full_grid || A.reinit || A.bricked) ? A.n_dphi_full
                                            : ((long long)ds->band_count[n & 1] + kStepTile - 1) / kStepTile;
     }
     const long long G = gridDim.x;
@@ -613,9 +614,12 @@ __global__ void __launch_bounds__(kRecordThreads) k_record(RecordArgs A, DevStat
     if (A.mode == 1) {
         ds->dphi_hist[n % kHist] = dphi * A.h_dim;
         ds->band_hist[n % kHist] =
-            A.full_grid ? A.N : (A.reinit ? (long long)ds->band_sl : (long long)ds->band_count[(n + 1) & 1]);
+            A.full_grid ? A.N
+                        : (A.bricked ? (long long)ds->band_brick
+                                     : (A.reinit ? (long long)ds->band_sl : (long long)ds->band_count[(n + 1) & 1]));
         ds->n = nn;
     }
+    if (A.mode != 2) ds->band_brick = 0;
     double E2 = sqrt(s2);
     ds->e2_hist[nn % kHist] = E2;
     ds->Ep = A.p_kind == 2 ? E2 : (A.p_kind == 1 ? 1.0 : pow(sp, 1.0 / A.p));
@@ -651,7 +655,8 @@ static cudaError_t energy_t(slr_ctx* c, int offset, double p, int p_kind, int ch
     const double hp = c->h / c->cfg.energy_R;
     const T thr = (T)(0.8660254037844386 * hp), hp2 = (T)(hp * hp), pT = (T)p;
     const int* ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;  // the list changes every iteration
-    int* tile_cnt = c->cfg.band ? c->tile_off : nullptr;
+    // the list step reads per-tile counts of the band list; the brick step does not
+    int* tile_cnt = (c->cfg.band && !brick_mode(c)) ? c->tile_off : nullptr;
     if (DIM == 3 && c->cfg.energy_R == 5)
         k_energy<T, DIM, INTERP, 5><<<blocks, kEnergyThreads, 0, c->stream>>>(
             P, (const T*)c->u[0], (const T*)c->u[1], (const T*)c->d, cells, ncells, ncells_dev,
@@ -693,11 +698,13 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
         if (e != cudaSuccess) return e;
     }
     RecordArgs A;
-    A.part_dphi = c->cfg.reinit ? c->part_dphi_r : c->part_dphi;
+    const bool bricked = brick_mode(c);
+    A.part_dphi = bricked ? c->brick.part : (c->cfg.reinit ? c->part_dphi_r : c->part_dphi);
+    A.bricked = bricked;
     A.part_e = c->part_e;
     A.nchunks = energy_slots(c);
     A.ncells_dev = c->cfg.reinit ? &c->ds->n_ecells_dyn : nullptr;
-    A.n_dphi_full = c->cfg.reinit ? reinit_grid(c) : full_step_blocks(c);
+    A.n_dphi_full = bricked ? c->brick.ntotal : (c->cfg.reinit ? reinit_grid(c) : full_step_blocks(c));
     A.N = c->N;
     A.full_grid = !c->cfg.band;
     A.reinit = c->cfg.reinit;
@@ -710,7 +717,7 @@ cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_
     A.stop_k = c->cfg.stop_k;
     A.min_iters = c->cfg.min_iters;
     A.max_iters = c->cfg.max_iters;
-    A.tile_off = c->cfg.band ? c->tile_off : nullptr;
+    A.tile_off = (c->cfg.band && !bricked) ? c->tile_off : nullptr;
     A.offset = record_mode == 1 ? 1 : 0;
     A.report = c->part_e + 2 * c->n_echunks;          // two spare doubles after the partials
     A.block_part = c->part_e + 2 * c->n_echunks + 2;  // then three per record block

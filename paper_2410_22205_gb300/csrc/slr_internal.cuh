@@ -5,6 +5,7 @@
 // Method: Preda & Semplice, arXiv 2410.22205 (§3 numerical scheme).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +26,7 @@ constexpr int kRecordBlocks = 32;    // blocks of the record kernel (slices of t
 constexpr int kMaxStopK = 1023;      // bound on the stop window k_max (staged in shared memory)
 constexpr int kErrBandOffset = 1;    // DevState::error: a band-list write fell outside the list
 constexpr int kErrBarrier = 2;       // a grid-wide barrier of a cooperative kernel waited too long
+constexpr int kErrStage = 4;         // a shared-memory staging wait of the brick step gave up
 constexpr long long kBarrierSpinLimit = 1ll << 22;  // polls of one barrier wait (~0.3 s with the sleeps)
 
 // Grid-wide barrier of a cooperative launch (every block co-resident).
@@ -78,6 +80,7 @@ struct DevState {
     int band_next;       // size of the band the next step writes (sum of the tile counts)
     int band_sl;         // with reinitialisation: band nodes the SL step of this iteration updated
     int n_ecells_dyn;    // with reinitialisation: candidate cells of the energy pass
+    int band_brick;      // brick step: band nodes of this iteration (summed by the bricks, reset by the record kernel)
     int band_base[kRecordBlocks];  // exclusive prefix of the tile counts per record-block slice
     double Ep;           // E_p(φ^n) used by step n
     double e2_hist[kHist];
@@ -108,6 +111,21 @@ struct Params {
 struct Buffer {
     void* ptr = nullptr;
     size_t bytes = 0;
+};
+
+// the brick-staged 3-D step (slr_brick.cu): bricks of 8^3 nodes
+struct BrickState {
+    int nb[3] = {0, 0, 0};      // bricks per axis
+    long long ntotal = 0;       // bricks of the grid
+    long long nbricks = 0;      // active bricks (listed at init)
+    int* list = nullptr;        // active brick ids, ascending
+    int* cnt = nullptr;         // per brick id: band count of the previous iteration
+    double* part = nullptr;     // per brick id: Δ_φ partial
+    int tma = 0;                // stage by TMA tile loads (else cp.async copies)
+    int occ[2][2] = {{0, 0}, {0, 0}};  // resident blocks per SM by [interp][band]
+    long long list_iter = -1;   // iteration whose band the band list holds (after import), else -1
+    CUtensorMap tm_u[2];        // u buffers, 16^3 boxes
+    CUtensorMap tm_d;           // d, 16x10x10 boxes
 };
 
 }  // namespace slr
@@ -161,6 +179,7 @@ struct slr_ctx {
     double g_step_override = -2.0;
     bool profiling = false;
     cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    slr::BrickState brick;
 };
 
 namespace slr {
@@ -176,6 +195,12 @@ cudaError_t launch_count_band(slr_ctx* c, long long* count_out);
 cudaError_t launch_build_band(slr_ctx* c);
 cudaError_t launch_build_ecells(slr_ctx* c, long long* count_out, bool write);
 cudaError_t launch_step(slr_ctx* c, double energy_override, int evolve_mode);
+// brick-staged 3-D step (every 3-D run without reinitialisation); see slr_brick.cu
+bool brick_mode(const slr_ctx* c);
+cudaError_t bricks_init(slr_ctx* c, const void* u);
+void bricks_free(slr_ctx* c);
+cudaError_t launch_step_brick(slr_ctx* c, double energy_override);
+cudaError_t band_of_field(slr_ctx* c, const void* u, int* out, long long* count);
 cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode,
                           cudaEvent_t between = nullptr);
 cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double* u_dev, long long* count_out,
@@ -208,7 +233,13 @@ cudaError_t barrier_selftest(int device, int unreachable, int* err_out);
 cudaError_t launch_l1_error(slr_ctx* c, const void* u, int kind, const double* prm, const double* exact_dev,
                             double* part, int blocks);
 long long energy_blocks(const slr_ctx* c);
-const char* noalloc_last_error();
+// Message of the last failed call without a context on this thread
+// (slr_create, slr_selftest_barrier, slr_distance_grid_noalloc,
+// slr_reconstruct before its first context exists): each of these clears it
+// on entry and sets it on failure; slr_last_error(NULL) returns it.
+void ctxless_error_clear();
+slr_status ctxless_error_set(slr_status s, const std::string& msg);
+const char* ctxless_error();
 long long full_step_blocks(const slr_ctx* c);
 // evolve building blocks for schedulers: capture the iteration graph if
 // needed and clear the stop flags; enqueue one iteration (no host wait)

@@ -300,6 +300,7 @@ static cudaError_t step_t(slr_ctx* c, double ov) {
 }
 
 cudaError_t launch_step(slr_ctx* c, double ov, int /*evolve_mode*/) {
+    if (brick_mode(c)) return launch_step_brick(c, ov);
     const bool f32 = c->cfg.precision == 32;
     const int dim = c->cfg.dim, ip = c->cfg.interp;
     if (f32) {
