@@ -195,17 +195,42 @@ def sha_of_kernels():
     return h.hexdigest()[:16]
 
 
-def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha):
+# WENO flops per band node and step as the survey counts the paper's
+# algorithm (§3.2: 4 feet x 21 one-dimensional WENO evaluations of about 40
+# operations with the quadratic forms A_L, A_R and the weights alpha_k =
+# C_k / (I_k + eps)^2; 3.4-4.0 kflop): the lower end is the roofline's count
+WENO_FLOPS_SURVEY = 3400.0
+# the kernel's own count: 4 feet x 21 evaluations of the closed form (24 flops
+# with FMA = 2) plus ~140 for gradients, tangents and feet
+WENO_FLOPS_EXECUTED = 2156.0
+
+
+def alu_peaks(peaks, probe):
+    """FP32 ALU peaks: derived from the unit counts (SMs x 128 FP32 lanes x 2
+    flops per FMA x the maximum SM clock, both read from the device) and
+    measured by slr_probe_fma on the device in this run."""
+    derived = peaks["sms"] * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    return {"derived_tflops": derived, "derived_from": f"{peaks['sms']} SMs x 128 FP32 lanes x 2 x "
+                                                     f"{peaks['sm_max_mhz']:.0f} MHz",
+            "measured_tflops": probe.get("fp32_tflops"), "measured_fp64_tflops": probe.get("fp64_tflops")}
+
+
+def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha, probe):
     """Algorithmic work per launch of the dominant kernel over its measured
     duration. Per band node and step (FP32):
       bytes: read u_j, d_j, the band-list entry, write u_j and the new band
-             entry = 4 + 4 + 4 + 4 + 4 = 20 B (HBM bound for Q1);
-      flops: WENO needs 4 feet x 21 one-dimensional WENO evaluations of 24
-             flops (FMA = 2) plus ~140 for gradients, tangents and feet =
-             2156 flops (ALU bound); Q1: 4 feet x 7 lerps x 3 + 140 = 224.
+             entry = 20 B (SURVEY's 19-22 B); 12 B on the whole grid (read u_j,
+             d_j, write u_j). HBM bound for Q1.
+      flops: WENO_FLOPS_SURVEY per node (ALU bound), the kernel's own
+             WENO_FLOPS_EXECUTED beside it.
     Energy kernel: per front cell 305 WENO evaluations + 125 trilinear
-    d-lookups... reported when it dominates (flops, ALU bound)."""
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+    d-lookups, reported when it dominates (flops, ALU bound).
+    The ALU peak is the measured FP32 FMA rate (slr_probe_fma) when the probe
+    ran, else the derived one."""
+    ap = alu_peaks(peaks, probe)
+    fp32_peak = ap["measured_tflops"] or ap["derived_tflops"]
+    peak_src = ("measured: slr_probe_fma (8 FMA chains x 256 threads x 8 blocks per SM)" if ap["measured_tflops"]
+                else "derived: " + ap["derived_from"])
     info = {}
     traffic = None
     side = os.path.join(ROOT, "profiles", "traffic.json")
@@ -216,29 +241,60 @@ def roofline_for(kernel, ms, band_nodes, peaks, kernel_sha):
                 traffic = tr.get("dram_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    bpn = kernel.get("bytes_per_node", 20.0)
+    hbm = bpn * band_nodes / (ms * 1e-3) / 1e9
     if kernel["kind"] == "step_weno":
-        flops = 2156.0 * band_nodes
-        achieved = flops / (ms * 1e-3) / 1e12
+        achieved = WENO_FLOPS_SURVEY * band_nodes / (ms * 1e-3) / 1e12
+        executed = WENO_FLOPS_EXECUTED * band_nodes / (ms * 1e-3) / 1e12
         info = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "hbm_view": {"achieved_gbs": 20.0 * band_nodes / (ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                             "frac": 20.0 * band_nodes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+                "frac": achieved / fp32_peak, "traffic": traffic, "peak_source": peak_src,
+                "flops_per_node": WENO_FLOPS_SURVEY,
+                "executed_view": {"flops_per_node": WENO_FLOPS_EXECUTED, "achieved_tflops": executed,
+                                  "frac": executed / fp32_peak},
+                "alu_peaks": ap,
+                "hbm_view": {"bytes_per_node": bpn, "achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"],
+                             "frac": hbm / peaks["hbm_gbs"]}}
     elif kernel["kind"] == "step_q1":
-        bytes_ = kernel.get("bytes_per_node", 20.0) * band_nodes
-        achieved = bytes_ / (ms * 1e-3) / 1e9
-        info = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS)"}
+        info = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes_per_node": bpn,
+                "frac": hbm / peaks["hbm_gbs"], "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS)"}
     else:
         fc = kernel.get("front_cells", 0)
         flops = (305 * 24 + 125 * 20) * fc
         achieved = flops / (ms * 1e-3) / 1e12
         info = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "frac": achieved / fp32_peak, "traffic": traffic, "peak_source": peak_src, "alu_peaks": ap}
     info["kernel"] = kernel["name"]
     info["ms_per_launch"] = ms
     return info
+
+
+def device_peaks(torch):
+    """HBM and bf16 peaks from MEASURED_PEAKS.json, the SM count from the
+    device and its maximum SM clock (MEASURED_PEAKS, else nvidia-smi)."""
+    peaks = {"hbm_gbs": 6794.5, "bf16_tflops": 1921.5, "sm_max_mhz": None}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks.update({k: v for k, v in json.load(open(pk)).items() if isinstance(v, (int, float))})
+    peaks["sms"] = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    if not peaks.get("sm_max_mhz"):
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20).stdout
+            peaks["sm_max_mhz"] = float(out.strip().splitlines()[0])
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            peaks["sm_max_mhz"] = 2070.0
+    return peaks
+
+
+def fma_probe(slr):
+    """FP32 and FP64 FMA rates of this device (slr_probe_fma); None on failure."""
+    out = {}
+    for prec, key in ((32, "fp32_tflops"), (64, "fp64_tflops")):
+        try:
+            out[key], out[key.replace("tflops", "ms")] = slr.slr_probe_fma(prec)
+        except slr.SlrError:
+            out[key] = None
+    return out
 
 
 def measure_steps(rec, steps, warmup, flush_buf, torch, profiled=False):
@@ -273,6 +329,25 @@ def measure_steps(rec, steps, warmup, flush_buf, torch, profiled=False):
     return step_ms, kern_ms, bands, launches
 
 
+def record_step(rec, label, n, prec, interp, band, seed=11, nodes=2000):
+    """The inputs and outputs of one GPU step for the per-result error against
+    the FP64 oracle: φ^n and d as stored, E_p of φ^n (given to both sides),
+    and φ^{n+1} on a seeded sample of band nodes (any nodes on the whole
+    grid). The comparison itself runs in the cpu_baseline leg."""
+    u0 = rec.u()
+    d = rec.d()
+    Ep = float(rec.energy(2.0)[0])
+    rec.step(1, energy_override=Ep)
+    u1 = rec.u()
+    dt = np.float32 if prec == 32 else np.float64
+    g = np.float32(6.0 * 2.0 / (n - 1)) if prec == 32 else 6.0 * 2.0 / (n - 1)
+    pool = np.flatnonzero(np.abs(u0.astype(dt)) < g) if band else np.arange(u0.size)
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(pool, min(nodes, pool.size), replace=False))
+    return {"label": label, "n": n, "prec": prec, "interp": interp, "band": band, "u0": u0.astype(dt),
+            "d": d.astype(dt), "Ep": Ep, "sample": sample, "u1": u1[sample]}
+
+
 def run_gpu(args):
     import torch
 
@@ -280,10 +355,8 @@ def run_gpu(args):
 
     dist = Dist("nccl")
     torch.cuda.set_device(dist.local_rank)
-    peaks = {"hbm_gbs": 6794.5, "bf16_tflops": 1921.5}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks.update({k: v for k, v in json.load(open(pk)).items() if isinstance(v, (int, float))})
+    peaks = device_peaks(torch)
+    probe = fma_probe(slr)
     t_setup = time.time()
     grid, cloud = workload(args)
     cloud_s = time.time() - t_setup
@@ -336,15 +409,25 @@ def run_gpu(args):
     kernel = {"name": names[dom], "kind": [("step_weno" if interp else "step_q1"), "energy"][dom],
               "front_cells": front, "bytes_per_node": 20.0 if band else 12.0}
     sha = sha_of_kernels()
-    roof = roofline_for(kernel, float(kmean[dom]), mean_band, peaks, sha)
+    roof = roofline_for(kernel, float(kmean[dom]), mean_band, peaks, sha, probe)
     roof["kernel_share_of_step"] = float(kmean[dom] / np.mean(pstep_ms))
     roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
     roof["kernels_timed"] = (f"{kprof} further steps with an event between the kernels captured in the graph "
                              f"({float(np.mean(pstep_ms)):.4f} ms per step with the events)")
+    try:
+        bt, bs, bms = rec.brick_shape()
+        roof["launch_shape"] = {"threads_per_block": bt, "stages": bs, "autotune_trial_ms": bms,
+                                "chosen_by": "the brick step's autotuner at init (fastest of 4 shapes on φ^0)"}
+    except slr.SlrError:
+        pass
     iter_lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
     if args.reinit:
         roof["phases_ms"] = {k: float(v) for k, v in
                              zip(("step", "reinit", "energy", "record"), rec.last_iteration_phases())}
+    records = []
+    want_err = not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1 and not args.reinit
+    if want_err:
+        records.append(record_step(rec, "headline", n, prec, interp, band))
     rec.close()
     phase_s = {"cloud_generation": cloud_s, "setup_and_timed_steps": time.time() - t_setup - cloud_s}
     t_ph = time.time()
@@ -368,6 +451,13 @@ def run_gpu(args):
             if rei:
                 variants[label]["phases_ms"] = {k: float(v) for k, v in
                                                 zip(("step", "reinit", "energy", "record"), r2.last_iteration_phases())}
+            try:
+                bt, bs, bms = r2.brick_shape()
+                variants[label]["launch_shape"] = {"threads_per_block": bt, "stages": bs}
+            except slr.SlrError:
+                pass
+            if want_err and not rei:
+                records.append(record_step(r2, label, n, prec, interp, band))
             r2.close()
     phase_s["variants"] = time.time() - t_ph
     t_ph = time.time()
@@ -392,8 +482,13 @@ def run_gpu(args):
     t_ph = time.time()
 
     cpu = None
+    errors = {}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(grid, cloud, budget_s=20.0)
+        cpu = cpu_baseline(grid, cloud, budget_s=20.0, records=records)
+        errors = cpu.get("error_vs_oracle", {})
+        for lab, e in errors.items():
+            if lab in variants:
+                variants[lab]["error_vs_oracle"] = e
     phase_s["cpu_baseline"] = time.time() - t_ph
 
     if dist.rank == 0:
@@ -408,6 +503,7 @@ def run_gpu(args):
                        "p": 2, "delta": 1,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{dist.world}",
                        "units_all_ranks": tot_units, "distance_grid_ms": dist_ms},
+            "error_vs_oracle": errors.get("headline"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_algorithm1_reinit": e2e_alg1,
             "e2e_paper_pipeline": e2e_runs,
             "latency": {"iteration": iter_lat, "solve": solve_lat},
@@ -476,6 +572,7 @@ def run_multirun(args, cloud, slr, torch):
     pinned.numpy()[:] = cloud
     host = pinned.numpy()
     out = {}
+    u_last = None
     for distance in ("exact", "fsm"):
         times, reps, d2h = [], [], 0
         jobs = max(1, min(2, args.e2e_jobs)) if distance == "exact" else 1
@@ -486,6 +583,8 @@ def run_multirun(args, cloud, slr, torch):
                                        max_nodes=args.n ** 3, max_iters=100, distance=distance)
             idx, val = rec.extract(2 * rep["run_dx"][-1])
             t1 = time.perf_counter()
+            if distance == "exact":
+                u_last = rec.u()
             rec.close()
             if distance == "exact" and j == 0:
                 continue
@@ -504,6 +603,24 @@ def run_multirun(args, cloud, slr, torch):
         }
     out["step"] = ("one whole reconstruction from the host cloud: sample and h_S, three runs (distance grid, φ^0, "
                    "Algorithm 1 with §3.7 to the stop test), extract |φ| < 2Δx, D2H")
+    # the same reconstruction in FP64 on the GPU: how far the FP32 result is
+    # from it near the front (the measurement behind keeping d in FP32)
+    rec64, rep64 = slr.reconstruct(host, dim=3, precision=64, interp=1, runs=3, K_s=2.0, sample_frac=0.1, seed=1,
+                                   max_nodes=args.n ** 3, max_iters=100, distance="exact")
+    u64 = rec64.u()
+    rec64.close()
+    rep32 = out["exact"]
+    dx = rep64["run_dx"][-1]
+    same_grid = u_last is not None and u_last.size == u64.size
+    near = np.abs(u64) < 2 * dx
+    out["fp32_vs_fp64"] = {
+        "same_iterations": [int(x) for x in rep64["run_iters"]] == [r["iters"] for r in rep32["runs"]],
+        "iterations_fp64": [int(x) for x in rep64["run_iters"]],
+        "max_abs_diff_within_2dx_over_dx": float(np.abs(u_last - u64)[near].max() / dx) if same_grid else None,
+        "nodes_within_2dx": int(near.sum()),
+        "err_cloud_over_dx_fp64": rep64["run_err_cloud"][-1] / dx,
+        "err_cloud_over_dx_fp32": rep32["runs"][-1]["err_cloud_over_dx"],
+        "how": "the exact-distance pipeline run again in FP64 on the GPU; φ compared where |φ_64| < 2Δx"}
     return out
 
 
@@ -691,10 +808,41 @@ def oracle_iteration(O, P, u, d, Ep):
     return out, E, nb
 
 
-def cpu_baseline(grid, cloud, budget_s=20.0):
+def oracle_errors(O, records):
+    """Per result: max |u_gpu - u_oracle| over the recorded sample of one step
+    from identical inputs (φ^n and d as the GPU stores them, the same E_p),
+    in units of h, beside the bar of the parity tests (1e-5 h in FP32, with 4
+    units in the last place where the FP32 value is large enough for that to
+    exceed it; 1e-12 in FP64). Nodes the oracle flags within 1e-6 of the
+    singular-gradient threshold are excluded and counted."""
+    out = {}
+    for r in records:
+        n = r["n"]
+        P = O.params(3, (n,) * 3, (-1.0,) * 3, (1.0,) * 3, interp=r["interp"], band=r["band"], prec=r["prec"],
+                     p=2.0, delta=1.0)
+        ref, flags = O.sl_nodes(P, r["u0"], r["d"], r["Ep"], r["sample"])
+        if r["band"]:
+            g = np.float32(P.gamma) if r["prec"] == 32 else P.gamma
+            ref = np.clip(ref, -g, g)
+        ok = (flags & O.FLAG_MARGIN) == 0
+        err = np.abs(r["u1"] - ref)[ok]
+        if r["prec"] == 32:
+            bar = np.maximum(1e-5 * P.h, 4.0 * np.spacing(np.abs(ref[ok]).astype(np.float32)).astype(np.float64))
+        else:
+            bar = np.full(err.size, 1e-12)
+        out[r["label"]] = {"max_abs_over_h": float(err.max() / P.h) if err.size else 0.0,
+                           "bar_over_h": (1e-5 if r["prec"] == 32 else 1e-12 / P.h),
+                           "within_bar": bool((err <= bar).all()), "nodes": int(err.size),
+                           "excluded_near_singular_threshold": int((~ok).sum()),
+                           "how": "one GPU step from identical inputs vs the FP64 oracle on seeded sampled nodes"}
+    return out
+
+
+def cpu_baseline(grid, cloud, budget_s=20.0, records=()):
     """The oracle as it stands on the host cores: whole iterations (band scan,
     WENO SL step in FP64 on every band node, cut, energy) from φ^0 until about
-    budget_s seconds of work."""
+    budget_s seconds of work. It also compares the recorded GPU steps with the
+    oracle (oracle_errors)."""
     O, P, u, d = oracle_setup(grid, cloud)
     cores = O.set_threads(len(os.sched_getaffinity(0)))
     Ep = O.energy(P, u, d, 2.0)["E"]
@@ -711,6 +859,8 @@ def cpu_baseline(grid, cloud, budget_s=20.0):
            "sample": f"{its} whole oracle iterations (WENO FP64 SL step on {units // its} band nodes + energy) of the "
                      f"{grid.n[0]}^3 workload from φ^0, {dt:.1f} s"}
     out["detail"] = oracle_detail(O, P, u, d, cloud, cores)
+    if records:
+        out["error_vs_oracle"] = oracle_errors(O, records)
     return out
 
 

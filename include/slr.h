@@ -240,6 +240,22 @@ slr_status slr_last_iteration_phases(slr_ctx* ctx, float ms[4]);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t slr_kernel_launches(const slr_ctx* ctx);
 
+/* Launch shape of the brick-staged 3-D step (every 3-D context without the
+ * reinitialisation runs its SL step, §3.1 eq. SL3d, on 8x8x8-node bricks
+ * whose u and d are staged in shared memory). slr_init_u times each candidate
+ * shape on φ^0 and keeps the fastest; every shape gives identical results.
+ * *threads: threads per block; *stages: 2 when the next brick is prefetched
+ * by TMA while one is computed, else 1; *trial_ms: the chosen shape's trial
+ * time. Any output may be NULL. SLR_E_STATE for 2-D contexts, contexts with
+ * the reinitialisation, or before slr_init_u. */
+slr_status slr_brick_shape(const slr_ctx* ctx, int* threads, int* stages, float* trial_ms);
+
+/* Force the brick step's launch shape (threads 128 or 256, stages 1 or 2;
+ * where TMA does not stage the boxes, stages 2 runs as 1) in place of the
+ * autotuner's choice, until the next slr_init_u. Results do not change.
+ * SLR_E_INVALID for another shape, SLR_E_STATE as slr_brick_shape. */
+slr_status slr_brick_shape_set(slr_ctx* ctx, int threads, int stages);
+
 /* Distance grid for callers that cannot allocate device memory.
  *
  * The paper has no counterpart to this call; it exists for users of this
@@ -278,6 +294,15 @@ slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], const double l
  * ctx == NULL: the reason of the last failed slr_create or
  * slr_distance_grid_noalloc on this thread. */
 const char* slr_last_error(const slr_ctx* ctx);
+
+/* FMA throughput of the current device (the paper has no counterpart: the
+ * benchmark's ALU roofline divides by it). Launches 8 blocks of 256 threads
+ * per SM, each thread running 8 independent chains of `trips` x 8 FMAs in
+ * `precision` (32 or 64), twice, and times the second launch with CUDA events
+ * on the legacy default stream. *tflops_out = 2 flops x FMAs / time;
+ * *ms_out = that launch's time. Allocates a few bytes of device memory.
+ * SLR_E_INVALID for another precision, trips < 1 or a NULL output. */
+slr_status slr_probe_fma(int precision, int64_t trips, double* tflops_out, double* ms_out);
 
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);

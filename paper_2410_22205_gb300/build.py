@@ -23,6 +23,10 @@ LIB = os.path.join(PKG, "libslr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# The brick step instantiates one kernel per launch shape; without implicit
+# FMA contraction every instance rounds each operation as written, so the
+# autotuner's choice cannot change a result.
+FILE_FLAGS = {"slr_brick.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -59,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nv, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
+            cmd = [nv, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(s), []), "-c", s, "-o", o]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)

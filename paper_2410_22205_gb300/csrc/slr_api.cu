@@ -263,6 +263,7 @@ slr_status init_after_u(slr_ctx* c, cudaError_t e) {
         CK(eb, "init_u bricks");
     }
     CK(launch_energy(c, 0, -1.0, 0, 0), "init_u energy");
+    if (brick_mode(c)) CK(bricks_autotune(c), "init_u brick autotune");
     CK(cudaStreamSynchronize(c->stream), "init_u sync");
     c->have_u = true;
     return SLR_OK;
@@ -1148,6 +1149,7 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
     // an energy pass in report mode recomputes the band-tile offsets the
     // next step reads (the history and E_p stay as imported)
     CK(launch_energy(c, 0, c->cfg.p, 2, 0), "import energy pass");
+    if (bricked) CK(bricks_autotune(c), "import brick autotune");
     CK(cudaStreamSynchronize(c->stream), "import");
     c->have_d = true;
     c->have_u = true;
@@ -1155,6 +1157,23 @@ slr_status slr_import_state(slr_ctx* c, const void* buf, int64_t nbytes) {
 }
 
 int64_t slr_kernel_launches(const slr_ctx* c) { return c ? c->launches : 0; }
+
+slr_status slr_brick_shape_set(slr_ctx* c, int threads, int stages) {
+    if (!c) return SLR_E_INVALID;
+    if (!brick_mode(c) || !c->have_u) return fail(c, SLR_E_STATE, "brick_shape_set: no brick-staged step");
+    const int sh = brick_shape_index(threads, stages);
+    if (sh < 0) return fail(c, SLR_E_INVALID, "brick_shape_set: threads must be 128 or 256 and stages 1 or 2");
+    free_graphs(c);  // the captured iteration holds the old launch
+    c->brick.shape = sh;
+    return SLR_OK;
+}
+
+slr_status slr_brick_shape(const slr_ctx* c, int* threads, int* stages, float* trial_ms) {
+    if (!c) return SLR_E_INVALID;
+    if (!brick_mode(c) || !c->have_u) return SLR_E_STATE;
+    brick_shape_of(c, threads, stages, trial_ms);
+    return SLR_OK;
+}
 
 const char* slr_last_error(const slr_ctx* c) {
     if (c) return c->err.c_str();

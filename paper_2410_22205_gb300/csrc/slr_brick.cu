@@ -6,10 +6,12 @@
 // node of the band G̃^0 (every brick on the whole grid) form a fixed list.
 // Per iteration, one persistent launch hands the bricks out by ticket; for
 // each brick a block
-//   1. stages u^n on the brick plus a halo of 4 nodes (a 16^3 box) and d on
-//      the brick plus 1 node in y and z (16x10x10) into shared memory: one
-//      TMA tile load per box when rows are 16-byte aligned, 4- or 8-byte
-//      cp.async copies with zero fill otherwise;
+//   1. stages u^n on the brick plus a halo of 4 nodes in y and z and of 4
+//      (left) and 12 (right) in x (a 24x16x16 box), and d on the brick plus
+//      4 and 12 nodes in x and 1 in y and z (24x10x10), into shared memory:
+//      one TMA tile load per box when rows are 16-byte aligned, 4- or 8-byte
+//      cp.async copies with zero fill otherwise (with two stages the next
+//      brick's boxes load while this one is computed);
 //   2. compacts the brick's band nodes (|u^n_j| < γ in the storage
 //      precision: every node outside the band sits at ±γ since the initial
 //      cut, so this is G̃^n) into a shared list, in node order;
@@ -21,9 +23,16 @@
 //      silent cases are read;
 //   4. writes u^{n+1} on the band nodes (after the cut) and copies u^n into
 //      u^{n+1} on the brick's other nodes, so both buffers agree outside the
-//      band; writes the brick's Δ_φ partial (FP64) and its band count.
+//      band; writes the brick's Δ_φ partial (FP64, summed in list order)
+//      and its band count.
 // A brick whose band count was zero in the previous iteration has both
-// buffers equal on all its nodes and is skipped.
+// buffers equal on all its nodes and is skipped. The launch shape (threads per
+// block, stages) is chosen at init by timing each candidate.
+//
+// This file is compiled with -fmad=false: each launch shape is its own
+// template instance, and an implicit a*b + c that the compiler fused in one
+// instance and not in another would make results depend on the autotuner's
+// choice. Every FMA here is written explicitly.
 #include <cuda.h>
 
 #include "slr_compact.cuh"
@@ -36,29 +45,50 @@ Params<T> make_params(const slr_ctx* c);
 
 namespace {
 
-constexpr int kBr = 8;                            // nodes per axis of a brick
-constexpr int kBrN = kBr * kBr * kBr;             // nodes per brick
+constexpr int kBX = 8, kBY = 8, kBZ = 8;          // nodes of a brick per axis
+constexpr int kBrN = kBX * kBY * kBZ;             // nodes per brick (512)
 constexpr int kHalo = 4;                          // staged halo of u per side
-constexpr int kBox = kBr + 2 * kHalo;             // u box per axis (16)
-constexpr int kBoxN = kBox * kBox * kBox;         // 4096
-constexpr int kDY = kBr + 2;                      // d box along y and z (10); 16 along x (16-byte TMA rows)
-constexpr int kDBoxN = kBox * kDY * kDY;          // 1600
-constexpr int kBrickThreads = 256;
+constexpr int kBox = kBY + 2 * kHalo;             // u box along y and z (16)
+constexpr int kDY = kBY + 2;                      // d box along y and z (10)
 constexpr long long kStageWaitLimit = 1ll << 22;  // polls of one staging wait before it gives up
 
-// dynamic shared memory of one block (bytes): u box, d box, member list,
-// per-warp counts, the staging barrier and the ticket words
-template <typename T>
-struct BrickSmem {
-    static constexpr int kU = 0;
-    static constexpr int kD = kU + kBoxN * (int)sizeof(T);
-    static constexpr int kList = kD + ((kDBoxN * (int)sizeof(T) + 127) & ~127);
-    static constexpr int kCnt = kList + kBrN * 2;
-    static constexpr int kRed = kCnt + 128;
-    static constexpr int kBar = kRed + 64;
-    static constexpr int kTicket = kBar + 16;
-    static constexpr int kBytes = kTicket + 16;
+// Box geometry: both boxes are 24 nodes wide along x (kHalo = 4 on the left,
+// the brick's 8, and 12 on the right), the row pitch in shared memory. The
+// compacted node order puts a warp's 32 nodes in 4 rows of 8 at one z; with a
+// pitch of 24 words those rows (and the feet, which move with their nodes)
+// fall in 32 distinct banks, where a pitch of 16 would alias rows y and y+2.
+// The 16-byte TMA rows need a width that is a multiple of 4 nodes.
+struct BoxGeom {
+    static constexpr int X = 24;                     // row pitch
+    static constexpr int PY = X * kBox;              // u plane pitch
+    static constexpr int BoxN = X * kBox * kBox;     // u box
+    static constexpr int DPZ = X * kDY;              // d plane pitch
+    static constexpr int DBoxN = X * kDY * kDY;      // d box
+    static_assert((BoxN * 4) % 128 == 0 && (DBoxN * 4) % 128 == 0, "boxes keep 128-byte alignment");
 };
+
+// dynamic shared memory of one block (bytes): ST stages of (u box, d box),
+// then the member list, the per-member |Δu|, per-warp counts, the staging
+// barriers and the ticket words
+template <typename T, int ST>
+struct BrickSmem {
+    using G = BoxGeom;
+    static constexpr int kStage = (G::BoxN + G::DBoxN) * (int)sizeof(T);  // multiple of 128
+    static constexpr int kList = ST * kStage;
+    static constexpr int kAbs = kList + kBrN * 2;
+    static constexpr int kCnt = kAbs + kBrN * (int)sizeof(T);
+    static constexpr int kBar = kCnt + 256;
+    static constexpr int kTicket = kBar + 16;
+    static constexpr int kBytes = kTicket + 32;
+};
+
+// node l of a brick: x fastest, then y, then z
+__device__ __forceinline__ void brick_local(int l, int& lx, int& ly, int& lz) {
+    lx = l & 7;
+    ly = (l >> 3) & 7;
+    lz = l >> 6;
+}
+static_assert(kBX == 8 && kBY == 8 && kBZ == 8, "brick_local decodes 8x8x8 bricks");
 
 // ---- staging primitives (inline PTX: mbarrier, TMA tile load, cp.async) ----
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -121,6 +151,7 @@ struct Norm<double> {
 template <typename T>
 __device__ __forceinline__ T weno_box(const T* __restrict__ base, const WenoAxis<T>& wx, const WenoAxis<T>& wy,
                                       const WenoAxis<T>& wz, T h4) {
+    using G = BoxGeom;
     T yv[4][4];  // [column a][row b]: the z-line at (a, b)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -128,7 +159,7 @@ __device__ __forceinline__ T weno_box(const T* __restrict__ base, const WenoAxis
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) r[c][a] = base[a + kBox * b + kBox * kBox * c];
+            for (int a = 0; a < 4; ++a) r[c][a] = base[a + G::X * b + G::PY * c];
         weno_pair(r[0][0], r[1][0], r[2][0], r[3][0], r[0][1], r[1][1], r[2][1], r[3][1], wz, h4, yv[0][b], yv[1][b]);
         weno_pair(r[0][2], r[1][2], r[2][2], r[3][2], r[0][3], r[1][3], r[2][3], r[3][3], wz, h4, yv[2][b], yv[3][b]);
     }
@@ -142,16 +173,16 @@ __device__ __forceinline__ T weno_box(const T* __restrict__ base, const WenoAxis
 // then y, then z
 template <typename T>
 __device__ __forceinline__ T q1_box(const T* __restrict__ base, T tx, T ty, T tz) {
-    const T v00 = base[0], v10 = base[1], v01 = base[kBox], v11 = base[kBox + 1];
-    const T w00 = base[kBox * kBox], w10 = base[kBox * kBox + 1], w01 = base[kBox * kBox + kBox],
-            w11 = base[kBox * kBox + kBox + 1];
-    const T a0 = v00 + tx * (v10 - v00);
-    const T a1 = v01 + tx * (v11 - v01);
-    const T s0 = a0 + ty * (a1 - a0);
-    const T c0 = w00 + tx * (w10 - w00);
-    const T c1 = w01 + tx * (w11 - w01);
-    const T s1 = c0 + ty * (c1 - c0);
-    return s0 + tz * (s1 - s0);
+    using G = BoxGeom;
+    const T v00 = base[0], v10 = base[1], v01 = base[G::X], v11 = base[G::X + 1];
+    const T w00 = base[G::PY], w10 = base[G::PY + 1], w01 = base[G::PY + G::X], w11 = base[G::PY + G::X + 1];
+    const T a0 = fma(tx, v10 - v00, v00);
+    const T a1 = fma(tx, v11 - v01, v01);
+    const T s0 = fma(ty, a1 - a0, a0);
+    const T c0 = fma(tx, w10 - w00, w00);
+    const T c1 = fma(tx, w11 - w01, w01);
+    const T s1 = fma(ty, c1 - c0, c0);
+    return fma(tz, s1 - s0, s0);
 }
 
 // centred difference along one axis from a staged box; one-sided first
@@ -186,20 +217,29 @@ __device__ __forceinline__ T brick_node(const Params<T>& P, const BrickArgs<T>& 
                                         const T* __restrict__ sd, const T* __restrict__ uin,
                                         const T* __restrict__ d, T Ep, T invEp, int i, int j, int k, int su_i,
                                         int sd_i, const T flo[3], const T fhi[3], T uc) {
-    const T gx = diff_box(su, su_i, 1, i, P.n0, uc, P.inv_2h, P.inv_h);
-    const T gy = diff_box(su, su_i, kBox, j, P.n1, uc, P.inv_2h, P.inv_h);
-    const T gz = diff_box(su, su_i, kBox * kBox, k, P.n2, uc, P.inv_2h, P.inv_h);
-    const T g2 = gx * gx + gy * gy + gz * gz;
+    using G = BoxGeom;
+    const bool inner = i > 0 && i < P.n0 - 1 && j > 0 && j < P.n1 - 1 && k > 0 && k < P.n2 - 1;
+    T gx, gy, gz;
+    if (inner) {
+        gx = (su[su_i + 1] - su[su_i - 1]) * P.inv_2h;
+        gy = (su[su_i + G::X] - su[su_i - G::X]) * P.inv_2h;
+        gz = (su[su_i + G::PY] - su[su_i - G::PY]) * P.inv_2h;
+    } else {
+        gx = diff_box(su, su_i, 1, i, P.n0, uc, P.inv_2h, P.inv_h);
+        gy = diff_box(su, su_i, G::X, j, P.n1, uc, P.inv_2h, P.inv_h);
+        gz = diff_box(su, su_i, G::PY, k, P.n2, uc, P.inv_2h, P.inv_h);
+    }
+    const T g2 = fma(gx, gx, fma(gy, gy, gz * gz));
     if (g2 < A.thr2) {
         // eq. SL:2: mean of the face neighbours inside the grid (-x,+x,-y,+y,-z,+z)
         T s = T(0);
         int cnt = 0;
         if (i > 0) { s += su[su_i - 1]; ++cnt; }
         if (i < P.n0 - 1) { s += su[su_i + 1]; ++cnt; }
-        if (j > 0) { s += su[su_i - kBox]; ++cnt; }
-        if (j < P.n1 - 1) { s += su[su_i + kBox]; ++cnt; }
-        if (k > 0) { s += su[su_i - kBox * kBox]; ++cnt; }
-        if (k < P.n2 - 1) { s += su[su_i + kBox * kBox]; ++cnt; }
+        if (j > 0) { s += su[su_i - G::X]; ++cnt; }
+        if (j < P.n1 - 1) { s += su[su_i + G::X]; ++cnt; }
+        if (k > 0) { s += su[su_i - G::PY]; ++cnt; }
+        if (k < P.n2 - 1) { s += su[su_i + G::PY]; ++cnt; }
         return s / T(cnt);
     }
     const T dj = sd[sd_i];
@@ -213,9 +253,16 @@ __device__ __forceinline__ T brick_node(const Params<T>& P, const BrickArgs<T>& 
     else
         C = pow(dj / Ep, P.p - T(1));
     if (BAND) C *= cutoff(P, uc);
-    const T ddx = diff_box(sd, sd_i, 1, i, P.n0, dj, P.inv_2h, P.inv_h);
-    const T ddy = diff_box(sd, sd_i, kBox, j, P.n1, dj, P.inv_2h, P.inv_h);
-    const T ddz = diff_box(sd, sd_i, kBox * kDY, k, P.n2, dj, P.inv_2h, P.inv_h);
+    T ddx, ddy, ddz;
+    if (inner) {
+        ddx = (sd[sd_i + 1] - sd[sd_i - 1]) * P.inv_2h;
+        ddy = (sd[sd_i + G::X] - sd[sd_i - G::X]) * P.inv_2h;
+        ddz = (sd[sd_i + G::DPZ] - sd[sd_i - G::DPZ]) * P.inv_2h;
+    } else {
+        ddx = diff_box(sd, sd_i, 1, i, P.n0, dj, P.inv_2h, P.inv_h);
+        ddy = diff_box(sd, sd_i, G::X, j, P.n1, dj, P.inv_2h, P.inv_h);
+        ddz = diff_box(sd, sd_i, G::DPZ, k, P.n2, dj, P.inv_2h, P.inv_h);
+    }
     // displacements in cells: advective C Δt ∇d / h, diffusive sqrt(C δ d Δt / p) / h
     const T adv = C * A.dt_h;
     const T bx = adv * ddx, by = adv * ddy, bz = adv * ddz;
@@ -223,7 +270,7 @@ __device__ __forceinline__ T brick_node(const Params<T>& P, const BrickArgs<T>& 
     // eq. sigma3d: ν1 = (-φz, 0, φx)/r, ν2 = (-φx φy, r^2, -φy φz)/(r |∇φ|),
     // r = sqrt(φx^2 + φz^2); (1,0,0), (0,0,1) when φx = φz = 0
     T n1x, n1z, n2x, n2y, n2z;
-    const T w = gx * gx + gz * gz;
+    const T w = fma(gx, gx, gz * gz);
     if (gx == T(0) && gz == T(0)) {
         n1x = T(1); n1z = T(0);
         n2x = T(0); n2y = T(0); n2z = T(1);
@@ -253,16 +300,16 @@ __device__ __forceinline__ T brick_node(const Params<T>& P, const BrickArgs<T>& 
         const bool fast = fx >= flo[0] && fx <= fhi[0] && fy >= flo[1] && fy <= fhi[1] && fz >= flo[2] &&
                           fz <= fhi[2];
         if (fast) {
-            const int off = su_i + (int)fx + kBox * (int)fy + kBox * kBox * (int)fz;
+            const int off = su_i + (int)fx + G::X * (int)fy + G::PY * (int)fz;
             const T tx = r[0] - fx, ty = r[1] - fy, tz = r[2] - fz;
             if (INTERP == 1) {
                 WenoAxis<T> wx, wy, wz;
                 wx.set(tx);
                 wy.set(ty);
                 wz.set(tz);
-                last = weno_box(su + (off - 1 - kBox - kBox * kBox), wx, wy, wz, P.h4);
+                last = weno_box<T>(su + (off - 1 - G::X - G::PY), wx, wy, wz, P.h4);
             } else {
-                last = q1_box(su + off, tx, ty, tz);
+                last = q1_box<T>(su + off, tx, ty, tz);
             }
         } else {
             last = interp_at<T, 3, INTERP>(P, uin, i, j, k, r);
@@ -273,76 +320,114 @@ __device__ __forceinline__ T brick_node(const Params<T>& P, const BrickArgs<T>& 
     return acc * T(0.25);
 }
 
-template <typename T, int INTERP, int BAND>
-__global__ void __launch_bounds__(kBrickThreads, (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 6)))
+// blocks per SM the launch bounds ask for: register budget of the scalar
+// type and interpolator, scaled by the block size
+template <typename T, int INTERP, int NT>
+struct BrickOcc {
+    static constexpr int v = (INTERP == 1 ? (sizeof(T) == 8 ? 2 : 3) : (sizeof(T) == 8 ? 3 : 4)) * (256 / NT);
+};
+
+// One persistent launch over the active bricks. NT threads per block; ST = 2
+// prefetches the next brick's boxes by TMA while the current brick is
+// computed (the cp.async path stages one brick at a time).
+template <typename T, int INTERP, int BAND, int NT, int ST>
+__global__ void __launch_bounds__(NT, BrickOcc<T, INTERP, NT>::v)
     k_step_brick(const __grid_constant__ CUtensorMap tm_u0, const __grid_constant__ CUtensorMap tm_u1,
                  const __grid_constant__ CUtensorMap tm_d, Params<T> P, BrickArgs<T> A, T* ub0, T* ub1,
                  const T* __restrict__ d, DevState* ds, double ep_override) {
-    using S = BrickSmem<T>;
+    using S = BrickSmem<T, ST>;
+    using G = BoxGeom;
+    constexpr int W = NT / 32;    // warps per block
+    constexpr int PER = kBrN / NT;  // nodes per thread in the compaction
     extern __shared__ __align__(1024) unsigned char smem[];
-    T* su = reinterpret_cast<T*>(smem + S::kU);
-    T* sd = reinterpret_cast<T*>(smem + S::kD);
     unsigned short* s_list = reinterpret_cast<unsigned short*>(smem + S::kList);
+    T* s_abs = reinterpret_cast<T*>(smem + S::kAbs);
     int* s_cnt = reinterpret_cast<int*>(smem + S::kCnt);
-    int* s_tk = reinterpret_cast<int*>(smem + S::kTicket);
-    const unsigned bar = smem_addr(smem + S::kBar);
+    int* s_tk = reinterpret_cast<int*>(smem + S::kTicket);  // per stage: ticket, brick id, skip
     if (ds->stop) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = ds->n;
     const T* __restrict__ uin = (n & 1) ? ub1 : ub0;
     T* __restrict__ uout = (n & 1) ? ub0 : ub1;
     const CUtensorMap* tmu = (n & 1) ? &tm_u1 : &tm_u0;
+    const CUtensorMap* tmd = &tm_d;
     const T Ep = ep_override >= 0.0 ? (T)ep_override : (T)ds->Ep;
     const T invEp = Ep > T(0) ? T(1) / Ep : T(0);
-    if (A.tma && tid == 0) {
-        mbar_init(bar, 1);
+    const bool tma = A.tma != 0;
+    const bool pipe = ST == 2 && tma;
+    auto stage_u = [&](int st) { return reinterpret_cast<T*>(smem + st * S::kStage); };
+    auto stage_d = [&](int st) { return reinterpret_cast<T*>(smem + st * S::kStage + G::BoxN * (int)sizeof(T)); };
+    auto bar_of = [&](int st) { return smem_addr(smem + S::kBar + 8 * st); };
+    // thread 0: take a ticket into stage st and, by TMA, start its copies
+    auto take = [&](int st) {
+        const int t = (int)atomicAdd(&ds->ticket, 1u);
+        const int b = t < A.nbricks ? A.bricks[t] : 0;
+        const int skip = (BAND && t < A.nbricks) ? (A.bcnt[b] == 0) : 0;
+        s_tk[4 * st + 0] = t;
+        s_tk[4 * st + 1] = b;
+        s_tk[4 * st + 2] = skip;
+        if (tma && t < A.nbricks && !skip) {
+            const int bxi = b % A.nbx, q = b / A.nbx;
+            const int ox = bxi * kBX - kHalo, oy = (q % A.nby) * kBY - kHalo, oz = (q / A.nby) * kBZ - kHalo;
+            const unsigned bar = bar_of(st);
+            fence_proxy_async();
+            mbar_expect_tx(bar, (unsigned)((G::BoxN + G::DBoxN) * sizeof(T)));
+            tma_load_3d(smem_addr(stage_u(st)), tmu, bar, ox, oy, oz);
+            tma_load_3d(smem_addr(stage_d(st)), tmd, bar, ox, oy + kHalo - 1, oz + kHalo - 1);
+        }
+    };
+    if (tma && tid == 0) {
+        mbar_init(bar_of(0), 1);
+        if (ST == 2) mbar_init(bar_of(1), 1);
         fence_mbar_init();
     }
-    unsigned phase = 0;
+    unsigned phases = 0u;  // bit s: parity of the next completion of stage s's barrier
+    int st = 0;
+    if (tid == 0) take(0);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            const int t = (int)atomicAdd(&ds->ticket, 1u);
-            s_tk[0] = t;
-            s_tk[1] = t < A.nbricks ? A.bricks[t] : 0;
-            s_tk[2] = (BAND && t < A.nbricks) ? (A.bcnt[s_tk[1]] == 0) : 0;
-        }
-        __syncthreads();
-        const int t = s_tk[0];
+        const int t = s_tk[4 * st + 0];
         if (t >= A.nbricks) break;
-        if (!s_tk[2]) {
-            const int b = s_tk[1];
+        const int b = s_tk[4 * st + 1];
+        const int skip = s_tk[4 * st + 2];
+        // the other stage was released by the barrier that ended the previous brick
+        if (pipe && tid == 0) take(st ^ 1);
+        if (!skip) {
+            T* su = stage_u(st);
+            T* sd = stage_d(st);
             const int bxi = b % A.nbx, q = b / A.nbx;
-            const int byi = q % A.nby, bzi = q / A.nby;
-            const int ox = bxi * kBr - kHalo, oy = byi * kBr - kHalo, oz = bzi * kBr - kHalo;
-            // ---- 1. stage u (16^3 box) and d (16x10x10 box) ----
+            const int ox = bxi * kBX - kHalo, oy = (q % A.nby) * kBY - kHalo, oz = (q / A.nby) * kBZ - kHalo;
+            // ---- 1. stage u (24x16x16 box) and d (24x10x10 box) ----
             bool staged = true;
-            if (A.tma) {
+            if (tma) {
+                // one thread polls the barrier; the others wait at the block
+                // barrier below without issuing
                 if (tid == 0) {
-                    fence_proxy_async();
-                    mbar_expect_tx(bar, (unsigned)((kBoxN + kDBoxN) * sizeof(T)));
-                    tma_load_3d(smem_addr(su), tmu, bar, ox, oy, oz);
-                    tma_load_3d(smem_addr(sd), &tm_d, bar, ox, oy + kHalo - 1, oz + kHalo - 1);
-                }
-                long long it = 0;
-                while (!mbar_try_wait(bar, phase) && ++it < kStageWaitLimit) {
-                }
-                staged = it < kStageWaitLimit;
-                if (!staged) {
-                    // give the copies in flight a second bounded wait before leaving
-                    long long it2 = 0;
-                    while (!mbar_try_wait(bar, phase) && ++it2 < kStageWaitLimit) {
+                    const unsigned bar = bar_of(st);
+                    long long it = 0;
+                    const unsigned par = (phases >> st) & 1u;
+                    while (!mbar_try_wait(bar, par) && ++it < kStageWaitLimit) {
+                    }
+                    staged = it < kStageWaitLimit;
+                    if (!staged) {
+                        // give the copies in flight a second bounded wait before leaving
+                        long long it2 = 0;
+                        while (!mbar_try_wait(bar, par) && ++it2 < kStageWaitLimit) {
+                        }
                     }
                 }
-                phase ^= 1u;
+                phases ^= 1u << st;
             } else {
-                for (int e = tid; e < kBoxN; e += kBrickThreads) {
-                    const int x = ox + (e & 15), y = oy + ((e >> 4) & 15), z = oz + (e >> 8);
+                for (int e = tid; e < G::BoxN; e += NT) {
+                    const int r = e / G::X;
+                    const int x = ox + (e - r * G::X), y = oy + (r & 15), z = oz + (r >> 4);
                     const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
                     const T* src = in ? uin + (x + P.is1 * y + P.is2 * z) : uin;
                     cp_async_zfill<(int)sizeof(T)>(smem_addr(su + e), src, in);
                 }
-                for (int e = tid; e < kDBoxN; e += kBrickThreads) {
-                    const int x = ox + (e & 15), r = e >> 4;
+                for (int e = tid; e < G::DBoxN; e += NT) {
+                    const int r = e / G::X;
+                    const int x = ox + (e - r * G::X);
                     const int y = oy + kHalo - 1 + r % kDY, z = oz + kHalo - 1 + r / kDY;
                     const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
                     const T* src = in ? d + (x + P.is1 * y + P.is2 * z) : d;
@@ -352,83 +437,100 @@ __global__ void __launch_bounds__(kBrickThreads, (INTERP == 1 ? (sizeof(T) == 8 
             }
             if (__syncthreads_or(!staged)) {
                 if (tid == 0) atomicOr(&ds->error, kErrStage);
+                if (pipe && tid == 0) {
+                    // the prefetch of the other stage: a bounded wait, then leave
+                    long long it3 = 0;
+                    while (!mbar_try_wait(bar_of(st ^ 1), (phases >> (st ^ 1)) & 1u) && ++it3 < kStageWaitLimit) {
+                    }
+                }
                 return;
             }
             // ---- 2. band nodes of the brick, in node order ----
-            bool mem[2];
-            T val[2];
-            int gidx[2];
+            bool mem[PER];
+            T val[PER];
+            int gidx[PER];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int l = tid + h * kBrickThreads;
-                const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            for (int h = 0; h < PER; ++h) {
+                const int l = tid + h * NT;
+                int lx, ly, lz;
+                brick_local(l, lx, ly, lz);
                 const int i = ox + kHalo + lx, j = oy + kHalo + ly, k = oz + kHalo + lz;
                 const bool in = i < P.n0 && j < P.n1 && k < P.n2;
-                val[h] = su[(lx + kHalo) + kBox * (ly + kHalo) + kBox * kBox * (lz + kHalo)];
+                val[h] = su[(lx + kHalo) + G::X * (ly + kHalo) + G::PY * (lz + kHalo)];
                 gidx[h] = in ? i + P.is1 * j + P.is2 * k : -1;
                 mem[h] = in && (!BAND || fabs(val[h]) < P.gamma);
                 const unsigned m = __ballot_sync(0xffffffffu, mem[h]);
-                if (lane == 0) s_cnt[h * 8 + warp] = __popc(m);
+                if (lane == 0) s_cnt[h * W + warp] = __popc(m);
             }
             __syncthreads();
             if (tid == 0) {
                 int run = 0;
-                for (int w = 0; w < 16; ++w) {
+                for (int w = 0; w < kBrN / 32; ++w) {
                     const int c = s_cnt[w];
                     s_cnt[w] = run;
                     run += c;
                 }
-                s_cnt[16] = run;
+                s_cnt[kBrN / 32] = run;
             }
             __syncthreads();
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < PER; ++h) {
                 const unsigned m = __ballot_sync(0xffffffffu, mem[h]);
-                if (mem[h]) s_list[s_cnt[h * 8 + warp] + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(tid + h * kBrickThreads);
+                if (mem[h]) s_list[s_cnt[h * W + warp] + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(tid + h * NT);
                 // nodes of the brick outside the band: u^{n+1} = u^n (both buffers agree there)
                 if (BAND && gidx[h] >= 0 && !mem[h]) uout[gidx[h]] = val[h];
             }
             __syncthreads();
-            const int count = s_cnt[16];
-            // fast-path ranges of floor(displacement), relative to the node:
+            const int count = s_cnt[kBrN / 32];
+            // fast-path ranges of floor(displacement) in box coordinates:
             // Q1 needs the cell c, c+1 in the box and c in [0, n-2];
             // WENO needs c-1 .. c+2 in the box and inside the grid
-            const int lo_b = INTERP == 1 ? 1 : 0, hi_b = INTERP == 1 ? kBox - 3 : kBox - 2;
-            const int lo_g = INTERP == 1 ? 1 : 0;
-            const int bx_lo = max(lo_b, lo_g - ox), by_lo = max(lo_b, lo_g - oy), bz_lo = max(lo_b, lo_g - oz);
-            const int hx = min(hi_b, (INTERP == 1 ? P.n0 - 3 : P.n0 - 2) - ox);
-            const int hy = min(hi_b, (INTERP == 1 ? P.n1 - 3 : P.n1 - 2) - oy);
-            const int hz = min(hi_b, (INTERP == 1 ? P.n2 - 3 : P.n2 - 2) - oz);
+            constexpr int lo_b = INTERP == 1 ? 1 : 0;
+            constexpr int hx_b = INTERP == 1 ? G::X - 3 : G::X - 2, hb = INTERP == 1 ? kBox - 3 : kBox - 2;
+            const int bx_lo = max(lo_b, lo_b - ox), by_lo = max(lo_b, lo_b - oy), bz_lo = max(lo_b, lo_b - oz);
+            const int hx = min(hx_b, (INTERP == 1 ? P.n0 - 3 : P.n0 - 2) - ox);
+            const int hy = min(hb, (INTERP == 1 ? P.n1 - 3 : P.n1 - 2) - oy);
+            const int hz = min(hb, (INTERP == 1 ? P.n2 - 3 : P.n2 - 2) - oz);
             // ---- 3. the SL update of the band nodes ----
-            T dabs = T(0);
-            for (int e = tid; e < count; e += kBrickThreads) {
+            for (int e = tid; e < count; e += NT) {
                 const int l = s_list[e];
-                const int lx = (l & 7) + kHalo, ly = ((l >> 3) & 7) + kHalo, lz = (l >> 6) + kHalo;
+                int lx, ly, lz;
+                brick_local(l, lx, ly, lz);
+                lx += kHalo;
+                ly += kHalo;
+                lz += kHalo;
                 const int i = ox + lx, j = oy + ly, k = oz + lz;
-                const int su_i = lx + kBox * ly + kBox * kBox * lz;
-                const int sd_i = lx + kBox * (ly - kHalo + 1) + kBox * kDY * (lz - kHalo + 1);
+                const int su_i = lx + G::X * ly + G::PY * lz;
+                const int sd_i = lx + G::X * (ly - kHalo + 1) + G::DPZ * (lz - kHalo + 1);
                 const T uc = su[su_i];
                 const T flo[3] = {(T)(bx_lo - lx), (T)(by_lo - ly), (T)(bz_lo - lz)};
                 const T fhi[3] = {(T)(hx - lx), (T)(hy - ly), (T)(hz - lz)};
                 T out = brick_node<T, INTERP, BAND>(P, A, su, sd, uin, d, Ep, invEp, i, j, k, su_i, sd_i, flo, fhi, uc);
                 if (BAND) out = fmin(fmax(out, -P.gamma), P.gamma);  // eq. cut
                 uout[i + P.is1 * j + P.is2 * k] = out;
-                dabs += fabs(out - uc);
+                s_abs[e] = fabs(out - uc);
             }
-            // ---- 4. Δ_φ partial and band count of the brick ----
-            dabs = warp_sum(dabs);
-            double* s_red = reinterpret_cast<double*>(smem + S::kRed);
-            if (lane == 0) s_red[warp] = (double)dabs;
             __syncthreads();
-            if (tid == 0) {
+            // ---- 4. Δ_φ partial (FP64, in list order: independent of NT) and band count ----
+            if (warp == 0) {
                 double sum = 0.0;
-                for (int w = 0; w < kBrickThreads / 32; ++w) sum += s_red[w];
-                A.part_dphi[b] = sum;
-                A.bcnt[b] = count;
-                if (BAND && count) atomicAdd(&ds->band_brick, count);
+                for (int e = lane; e < count; e += 32) sum += (double)s_abs[e];
+                sum = warp_sum(sum);
+                if (lane == 0) {
+                    A.part_dphi[b] = sum;
+                    A.bcnt[b] = count;
+                    if (BAND && count) atomicAdd(&ds->band_brick, count);
+                }
             }
         }
         __syncthreads();
+        if (!pipe) {
+            // one stage: the next ticket (and its copies) once every thread is done with this brick
+            if (tid == 0) take(st);
+            __syncthreads();
+        } else {
+            st ^= 1;
+        }
     }
 }
 
@@ -443,15 +545,15 @@ struct BrickPred {
         if (!band) return true;
         const int bx = (int)(b % nbx), q = (int)(b / nbx);
         const int by = q % nby, bz = q / nby;
-        for (int lz = 0; lz < kBr; ++lz) {
-            const int k = bz * kBr + lz;
+        for (int lz = 0; lz < kBZ; ++lz) {
+            const int k = bz * kBZ + lz;
             if (k >= n2) break;
-            for (int ly = 0; ly < kBr; ++ly) {
-                const int j = by * kBr + ly;
+            for (int ly = 0; ly < kBY; ++ly) {
+                const int j = by * kBY + ly;
                 if (j >= n1) break;
                 const long long row = (long long)n0 * (j + (long long)n1 * k);
-                for (int lx = 0; lx < kBr; ++lx) {
-                    const int i = bx * kBr + lx;
+                for (int lx = 0; lx < kBX; ++lx) {
+                    const int i = bx * kBX + lx;
                     if (i >= n0) break;
                     if (fabs(u[row + i]) < gamma) return true;
                 }
@@ -459,6 +561,11 @@ struct BrickPred {
         }
         return false;
     }
+};
+
+struct EmitIdx {
+    int* out;
+    __device__ void operator()(long long pos, long long i) const { out[pos] = (int)i; }
 };
 
 __global__ void k_fill_int(int* p, long long n, int v) {
@@ -501,18 +608,24 @@ bool encode_field(CUtensorMap* m, void* base, const slr_ctx* c, unsigned bx, uns
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <typename T, int INTERP, int BAND>
-cudaError_t brick_launch_t(slr_ctx* c, double ov) {
-    using S = BrickSmem<T>;
-    auto kern = k_step_brick<T, INTERP, BAND>;
+// the launch shapes the autotuner chooses between: threads per block and
+// pipeline stages (2: the next brick's boxes prefetched by TMA)
+constexpr int kShapes = 4;
+constexpr int kShapeNT[kShapes] = {256, 128, 256, 128};
+constexpr int kShapeST[kShapes] = {1, 1, 2, 2};
+
+template <typename T, int INTERP, int BAND, int NT, int ST>
+cudaError_t brick_launch_t(slr_ctx* c, double ov, int shape) {
+    using S = BrickSmem<T, ST>;
+    auto kern = k_step_brick<T, INTERP, BAND, NT, ST>;
     BrickState& B = c->brick;
-    if (B.occ[INTERP][BAND] == 0) {
+    if (B.occ[shape] == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
         if (e != cudaSuccess) return e;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBrickThreads, S::kBytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, S::kBytes);
         if (e != cudaSuccess) return e;
-        B.occ[INTERP][BAND] = occ > 0 ? occ : 1;
+        B.occ[shape] = occ > 0 ? occ : 1;
     }
     Params<T> P = make_params<T>(c);
     BrickArgs<T> A;
@@ -527,26 +640,35 @@ cudaError_t brick_launch_t(slr_ctx* c, double ov) {
     A.kdiff = (T)(c->cfg.delta * c->dt / (c->cfg.p * c->h * c->h));
     const double thr = c->cfg.c_sing * pow(c->dt, c->cfg.alpha);
     A.thr2 = (T)thr * (T)thr;
-    long long grid = (long long)c->num_sms * B.occ[INTERP][BAND];
+    long long grid = (long long)c->num_sms * B.occ[shape];
     if (grid > B.nbricks) grid = B.nbricks;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kBrickThreads, S::kBytes, c->stream>>>(B.tm_u[0], B.tm_u[1], B.tm_d, P, A, (T*)c->u[0],
-                                                                   (T*)c->u[1], (const T*)c->d, c->ds, ov);
+    kern<<<(unsigned)grid, NT, S::kBytes, c->stream>>>(B.tm_u[0], B.tm_u[1], B.tm_d, P, A, (T*)c->u[0], (T*)c->u[1],
+                                                        (const T*)c->d, c->ds, ov);
     c->launches += 1;
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t brick_launch_p(slr_ctx* c, double ov) {
-    const bool band = c->cfg.band != 0;
-    if (c->cfg.interp) return band ? brick_launch_t<T, 1, 1>(c, ov) : brick_launch_t<T, 1, 0>(c, ov);
-    return band ? brick_launch_t<T, 0, 1>(c, ov) : brick_launch_t<T, 0, 0>(c, ov);
+template <typename T, int INTERP, int BAND>
+cudaError_t brick_launch_s(slr_ctx* c, double ov, int shape) {
+    switch (shape) {
+        case 1: return brick_launch_t<T, INTERP, BAND, 128, 1>(c, ov, 1);
+        case 2: return brick_launch_t<T, INTERP, BAND, 256, 2>(c, ov, 2);
+        case 3: return brick_launch_t<T, INTERP, BAND, 128, 2>(c, ov, 3);
+        default: return brick_launch_t<T, INTERP, BAND, 256, 1>(c, ov, 0);
+    }
 }
 
-struct EmitIdx {
-    int* out;
-    __device__ void operator()(long long pos, long long i) const { out[pos] = (int)i; }
-};
+template <typename T>
+cudaError_t brick_launch_p(slr_ctx* c, double ov, int shape) {
+    const bool band = c->cfg.band != 0;
+    if (c->cfg.interp) return band ? brick_launch_s<T, 1, 1>(c, ov, shape) : brick_launch_s<T, 1, 0>(c, ov, shape);
+    return band ? brick_launch_s<T, 0, 1>(c, ov, shape) : brick_launch_s<T, 0, 0>(c, ov, shape);
+}
+
+cudaError_t brick_launch(slr_ctx* c, double ov, int shape) {
+    return c->tsize == 4 ? brick_launch_p<float>(c, ov, shape) : brick_launch_p<double>(c, ov, shape);
+}
 
 // the active-brick list from field u (bricks with a node |u| < γ; every
 // brick on the whole grid)
@@ -578,7 +700,8 @@ cudaError_t bricks_init(slr_ctx* c, const void* u) {
     BrickState& B = c->brick;
     B.ntotal = 1;
     for (int a = 0; a < 3; ++a) {
-        B.nb[a] = (int)((c->cfg.n[a] + kBr - 1) / kBr);
+        const int bs = a == 0 ? kBX : (a == 1 ? kBY : kBZ);
+        B.nb[a] = (int)((c->cfg.n[a] + bs - 1) / bs);
         B.ntotal *= B.nb[a];
     }
     bricks_free(c);
@@ -603,17 +726,32 @@ cudaError_t bricks_init(slr_ctx* c, const void* u) {
     const bool rows = (c->cfg.n[0] * (long long)c->tsize) % 16 == 0;
     const bool al = ((uintptr_t)c->u[0] % 16 == 0) && ((uintptr_t)c->u[1] % 16 == 0) && ((uintptr_t)c->d % 16 == 0);
     B.tma = 0;
-    memset(&B.tm_u[0], 0, sizeof(CUtensorMap));
-    memset(&B.tm_u[1], 0, sizeof(CUtensorMap));
-    memset(&B.tm_d, 0, sizeof(CUtensorMap));
+    memset(B.tm_u, 0, sizeof(B.tm_u));
+    memset(&B.tm_d, 0, sizeof(B.tm_d));
     if (rows && al) {
-        bool ok = encode_field(&B.tm_u[0], c->u[0], c, kBox, kBox, kBox) &&
-                  encode_field(&B.tm_u[1], c->u[1], c, kBox, kBox, kBox) &&
-                  encode_field(&B.tm_d, c->d, c, kBox, kDY, kDY);
+        const unsigned px = (unsigned)BoxGeom::X;
+        bool ok = encode_field(&B.tm_u[0], c->u[0], c, px, kBox, kBox) &&
+                  encode_field(&B.tm_u[1], c->u[1], c, px, kBox, kBox) && encode_field(&B.tm_d, c->d, c, px, kDY, kDY);
         B.tma = ok ? 1 : 0;
     }
     B.list_iter = -1;
+    for (int i = 0; i < kShapes; ++i) B.occ[i] = 0;
+    static_assert(kShapes <= (int)(sizeof(B.occ) / sizeof(B.occ[0])), "occupancy slot per shape");
     return cudaGetLastError();
+}
+
+// the launch shape with these threads per block and stages; -1 if none
+int brick_shape_index(int threads, int stages) {
+    for (int i = 0; i < kShapes; ++i)
+        if (kShapeNT[i] == threads && kShapeST[i] == stages) return i;
+    return -1;
+}
+
+void brick_shape_of(const slr_ctx* c, int* threads, int* stages, float* trial_ms) {
+    const int sh = c->brick.shape;
+    if (threads) *threads = kShapeNT[sh];
+    if (stages) *stages = (kShapeST[sh] == 2 && c->brick.tma) ? 2 : 1;
+    if (trial_ms) *trial_ms = c->brick.tuned_ms;
 }
 
 void bricks_free(slr_ctx* c) {
@@ -629,7 +767,60 @@ void bricks_free(slr_ctx* c) {
 
 cudaError_t launch_step_brick(slr_ctx* c, double ov) {
     if (c->brick.nbricks <= 0) return cudaSuccess;
-    return c->tsize == 4 ? brick_launch_p<float>(c, ov) : brick_launch_p<double>(c, ov);
+    return brick_launch(c, ov, c->brick.shape);
+}
+
+// The brick step's autotuner: times each launch shape (threads per block x
+// pipeline stages; two stages only where TMA stages the boxes)
+// on the current state and keeps the fastest.
+// Every shape computes the same u^{n+1}, band count and Δ_φ partials (each
+// node's arithmetic does not depend on the shape, and the partials are
+// summed in list order), so the choice changes timing only. The trial
+// launches write only the output buffer of the next step, which that step
+// overwrites on every node they touched; the counters are reset after.
+cudaError_t bricks_autotune(slr_ctx* c) {
+    BrickState& B = c->brick;
+    B.shape = 0;
+    if (B.nbricks <= 0) return cudaSuccess;
+    // without TMA the two-stage shapes run as one stage: the one-stage shapes only
+    static const int kCand[] = {0, 1, 2, 3};
+    const int* cand = kCand;
+    const int nshapes = B.tma ? 4 : 2;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int ci = 0; ci < nshapes && e == cudaSuccess; ++ci) {
+        const int sh = cand[ci];
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned), c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess) e = brick_launch(c, -1.0, sh);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            B.shape = sh;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    c->launches -= 2 * nshapes;  // trial launches are not steps
+    // back to the state after init: no ticket taken, every listed brick due, no
+    // partials, no band count
+    e = cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->ds->band_brick, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.part, 0, sizeof(double) * B.ntotal, c->stream);
+    if (e == cudaSuccess) {
+        k_fill_int<<<(unsigned)((B.ntotal + 255) / 256), 256, 0, c->stream>>>(B.cnt, B.ntotal, 1);
+        e = cudaGetLastError();
+    }
+    B.tuned_ms = best;
+    return e;
 }
 
 // {j : |u_j| < γ} of field u, ascending, into out (capacity band_cap); the

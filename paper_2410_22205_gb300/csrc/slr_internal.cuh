@@ -113,7 +113,7 @@ struct Buffer {
     size_t bytes = 0;
 };
 
-// the brick-staged 3-D step (slr_brick.cu): bricks of 8^3 nodes
+// the brick-staged 3-D step (slr_brick.cu): bricks of 8x8x8 nodes
 struct BrickState {
     int nb[3] = {0, 0, 0};      // bricks per axis
     long long ntotal = 0;       // bricks of the grid
@@ -122,10 +122,12 @@ struct BrickState {
     int* cnt = nullptr;         // per brick id: band count of the previous iteration
     double* part = nullptr;     // per brick id: Δ_φ partial
     int tma = 0;                // stage by TMA tile loads (else cp.async copies)
-    int occ[2][2] = {{0, 0}, {0, 0}};  // resident blocks per SM by [interp][band]
+    int occ[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // resident blocks per SM of each launch shape
+    int shape = 0;              // launch shape chosen by the autotuner
+    float tuned_ms = 0.f;       // its trial time
     long long list_iter = -1;   // iteration whose band the band list holds (after import), else -1
-    CUtensorMap tm_u[2];        // u buffers, 16^3 boxes
-    CUtensorMap tm_d;           // d, 16x10x10 boxes
+    CUtensorMap tm_u[2];        // u buffers, 24x16x16 boxes
+    CUtensorMap tm_d;           // d, 24x10x10 boxes
 };
 
 }  // namespace slr
@@ -200,6 +202,9 @@ bool brick_mode(const slr_ctx* c);
 cudaError_t bricks_init(slr_ctx* c, const void* u);
 void bricks_free(slr_ctx* c);
 cudaError_t launch_step_brick(slr_ctx* c, double energy_override);
+cudaError_t bricks_autotune(slr_ctx* c);
+void brick_shape_of(const slr_ctx* c, int* threads, int* stages, float* trial_ms);
+int brick_shape_index(int threads, int stages);
 cudaError_t band_of_field(slr_ctx* c, const void* u, int* out, long long* count);
 cudaError_t launch_energy(slr_ctx* c, int offset, double p_override, int record_mode, int evolve_mode,
                           cudaEvent_t between = nullptr);
@@ -409,16 +414,17 @@ __device__ __forceinline__ T interp_q1(const Params<T>& P, const T* __restrict__
     if (DIM == 3) locate_rel(k, r[2], P.n2, cz, tz);
     long long b = (long long)cx + P.s1 * cy + P.s2 * cz;
     T v00 = ld(u + b), v10 = ld(u + b + 1), v01 = ld(u + b + P.s1), v11 = ld(u + b + P.s1 + 1);
-    T a0 = v00 + tx * (v10 - v00);
-    T a1 = v01 + tx * (v11 - v01);
-    T s0 = a0 + ty * (a1 - a0);
+    // lerps written as explicit FMAs, so that every kernel rounds them alike
+    T a0 = fma(tx, v10 - v00, v00);
+    T a1 = fma(tx, v11 - v01, v01);
+    T s0 = fma(ty, a1 - a0, a0);
     if (DIM == 2) return s0;
     long long b2 = b + P.s2;
     T w00 = ld(u + b2), w10 = ld(u + b2 + 1), w01 = ld(u + b2 + P.s1), w11 = ld(u + b2 + P.s1 + 1);
-    T c0 = w00 + tx * (w10 - w00);
-    T c1 = w01 + tx * (w11 - w01);
-    T s1 = c0 + ty * (c1 - c0);
-    return s0 + tz * (s1 - s0);
+    T c0 = fma(tx, w10 - w00, w00);
+    T c1 = fma(tx, w11 - w01, w01);
+    T s1 = fma(ty, c1 - c0, c0);
+    return fma(tz, s1 - s0, s0);
 }
 
 // §3.2 WENO by dimension splitting: 16 lines along z, then 4 along y, then

@@ -103,3 +103,80 @@ cudaError_t launch_from_double(slr_ctx* c, const double* src, void* dst, long lo
 }
 
 }  // namespace slr
+
+// ---------------------------------------------------------------------------
+// FMA throughput probe (the paper has no counterpart): the ALU roofline of the
+// WENO step divides by the device's measured FP32 FMA rate. Every thread runs
+// 8 independent FMA chains (enough to cover the FMA latency with 8 warps per
+// scheduler), 64 FMAs per loop trip; the result is stored only when it takes
+// a value it never takes, so the work cannot be removed.
+// ---------------------------------------------------------------------------
+namespace slr {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, long long trips, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x & 31) * T(1e-3) + (T)i;
+    for (long long t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == T(-1.25e30)) out[blockIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t probe_t(long long trips, double* tflops, double* ms_out) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8;
+    T* out = nullptr;
+    e = cudaMalloc(&out, sizeof(T) * blocks);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    const T a = T(0.9999999), b = T(1e-7);
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+        e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess) {
+            k_fma_probe<T><<<blocks, 256>>>(out, trips, a, b);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * 64.0 * (double)trips * 256.0 * (double)blocks;
+    *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    *ms_out = ms;
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace slr
+
+extern "C" slr_status slr_probe_fma(int precision, int64_t trips, double* tflops_out, double* ms_out) {
+    using namespace slr;
+    if ((precision != 32 && precision != 64) || trips < 1 || !tflops_out || !ms_out) return SLR_E_INVALID;
+    cudaError_t e = precision == 32 ? probe_t<float>(trips, tflops_out, ms_out)
+                                    : probe_t<double>(trips, tflops_out, ms_out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SLR_E_NOMEM : SLR_E_CUDA;
+    }
+    return SLR_OK;
+}

@@ -33,7 +33,7 @@ EXPORTS = [
     "slr_set_distance", "slr_init_u",
     "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_batch_chunk", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
-    "slr_last_iteration_phases", "slr_kernel_launches",
+    "slr_last_iteration_phases", "slr_kernel_launches", "slr_brick_shape", "slr_brick_shape_set", "slr_probe_fma",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error", "slr_selftest_barrier",
     "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
     "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
@@ -154,6 +154,9 @@ def lib():
                 "slr_last_iteration_times": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_last_iteration_phases": (C.c_int, [_vp, C.POINTER(C.c_float)]),
                 "slr_kernel_launches": (C.c_int64, [_vp]),
+                "slr_brick_shape": (C.c_int, [_vp, _ip, _ip, C.POINTER(C.c_float)]),
+                "slr_brick_shape_set": (C.c_int, [_vp, C.c_int, C.c_int]),
+                "slr_probe_fma": (C.c_int, [C.c_int, C.c_int64, _dp, _dp]),
                 "slr_cloud_spacing": (C.c_int, [_vp, _i64p, C.c_int64, _dp]),
                 "slr_l1_error": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
                 "slr_selftest_barrier": (C.c_int, [C.c_int]),
@@ -417,6 +420,29 @@ def slr_kernel_launches(ctx) -> int:
     return int(lib().slr_kernel_launches(ctx))
 
 
+def slr_brick_shape(ctx):
+    """(threads per block, stages, trial ms) of the brick-staged 3-D step."""
+    t, s = C.c_int(0), C.c_int(0)
+    ms = C.c_float(0.0)
+    _check(ctx, lib().slr_brick_shape(ctx, C.byref(t), C.byref(s), C.byref(ms)))
+    return t.value, s.value, ms.value
+
+
+def slr_brick_shape_set(ctx, threads, stages):
+    _check(ctx, lib().slr_brick_shape_set(ctx, int(threads), int(stages)))
+
+
+def slr_probe_fma(precision=32, trips=None):
+    """Measured FMA throughput of the current device: (TFLOP/s, ms of the timed launch)."""
+    if trips is None:
+        trips = 50_000 if precision == 32 else 2_000
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    st = lib().slr_probe_fma(int(precision), int(trips), C.byref(tf), C.byref(ms))
+    if st != SLR_OK:
+        raise SlrError(st, "probe_fma failed")
+    return tf.value, ms.value
+
+
 def slr_last_error(ctx) -> str:
     m = lib().slr_last_error(ctx)
     return m.decode() if m else ""
@@ -669,6 +695,12 @@ class Reconstruction:
     @property
     def kernel_launches(self):
         return slr_kernel_launches(self.ctx)
+
+    def brick_shape(self):
+        return slr_brick_shape(self.ctx)
+
+    def set_brick_shape(self, threads, stages):
+        slr_brick_shape_set(self.ctx, threads, stages)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -111,3 +111,28 @@ def test_default_config_is_the_papers():
     cfg = slr.slr_config_default()
     assert (cfg.p, cfg.delta, cfg.c_sing, cfg.alpha, cfg.energy_R) == (2.0, 1.0, 1e-3, 1.0, 5)
     assert (cfg.stop_tol, cfg.stop_k, cfg.min_iters, cfg.max_iters) == (1e-4, 10, 10, 100)
+
+
+def test_last_error_without_a_context_is_that_of_the_last_failed_call():
+    """slr_last_error(NULL) reports the most recent failed call without a
+    context on this thread: a failed allocation-free distance grid followed
+    by a failed slr_create reports the create's reason, and the other way
+    round. Both fail in their argument checks, before any device call."""
+    with pytest.raises(slr.SlrError):
+        slr.slr_distance_grid_noalloc(5, (8, 8, 8), (0.0, 0.0, 0.0), 1.0, 32, 256, 10, 512, 768)
+    assert "distance_grid_noalloc" in slr.slr_last_error(None)
+    with pytest.raises(slr.SlrError):
+        slr.slr_create(slr.slr_config_default(dim=4))
+    msg = slr.slr_last_error(None)
+    assert "dim must be 2 or 3" in msg and "noalloc" not in msg
+    with pytest.raises(slr.SlrError):
+        slr.slr_distance_grid_noalloc(3, (8, 8, 8), (0.0, 0.0, 0.0), 1.0, 16, 256, 10, 512, 768)
+    assert "precision" in slr.slr_last_error(None)
+
+
+def test_fma_probe_checks_its_arguments_without_a_device():
+    L = slr.lib()
+    a, b = slr.C.c_double(0.0), slr.C.c_double(0.0)
+    assert L.slr_probe_fma(16, 10, slr.C.byref(a), slr.C.byref(b)) == slr.SLR_E_INVALID
+    assert L.slr_probe_fma(32, 0, slr.C.byref(a), slr.C.byref(b)) == slr.SLR_E_INVALID
+    assert L.slr_probe_fma(32, 10, None, slr.C.byref(b)) == slr.SLR_E_INVALID

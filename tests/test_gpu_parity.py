@@ -144,9 +144,7 @@ def test_empty_band_steps_are_no_ops():
 @pytest.mark.parametrize("dim,n", [(2, 64), (3, 40), (3, (33, 41, 29))])
 def test_sl_step_band_parity(dim, n, prec, interp):
     rec, P = make(dim, n, prec, interp, 1)
-    rng = np.random.default_rng(1)
     pts = (synth.sphere_cloud(800, 0.5, 0.01, 2) if dim == 3 else synth.circle_noisy(300, 0.5, 0.01, 2))
-    pts = pts + rng.normal(0, 0.02, pts.shape) * 0
     rec.load_cloud(pts)
     rec.build_distance()
     rec.init_sphere(0.62)
