@@ -811,11 +811,20 @@ int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int ma
  * either part; the readings taken here:
  *  - sign classes: φ < 0 and φ >= 0 (zero with the positive side, as in the
  *    energy of §3.5); sign(φ̃) in eq. reinit is -1, 0, +1;
- *  - explicit step on an interface node j, the subcell estimate of Russo
- *    and Smereka (2000): D_j = φ̃_j / |g| with, per axis, g_a the largest of
- *    |φ̃_{j+e} - φ̃_{j-e}|/(2h), |φ̃_{j+e} - φ̃_j|/h, |φ̃_j - φ̃_{j-e}|/h
- *    (those that exist): exact for any plane, and the difference across the
- *    interface, which the cut never clamps, enters it; φ̃_j if g = 0;
+ *  - explicit step on an interface node j ("one step", keeping the
+ *    interface where φ̃ puts it), in two parts:
+ *    (a) the subcell estimate of Russo and Smereka (2000) on every interface
+ *        node k: D_k = φ̃_k / Δ_k with Δ_k the largest of the norm of the
+ *        gradient (centred components (φ̃_{k+e} - φ̃_{k-e})/(2h), one-sided
+ *        on the domain boundary) and the one-sided differences
+ *        |φ̃_{k±e} - φ̃_k|/h (those that exist); D_k = φ̃_k if Δ_k = 0.
+ *        Exact for any plane, scaled or not;
+ *    (b) the constraint of the constrained reinitialisation: with S_j the
+ *        face neighbours of j of the other sign class, φ_j = φ̃_j Σ_{k∈S_j}
+ *        D_k / Σ_{k∈S_j} φ̃_k, so that j keeps against its neighbours across
+ *        the interface the ratio it has in φ̃ (the zero crossings of the
+ *        linear interpolant do not move, on average over S_j); D_j if the
+ *        sum of φ̃ over S_j is 0;
  *  - first-order discretisation: Godunov's upwind Hamiltonian with the
  *    one-sided differences a = (ψ_j - ψ_{j-e})/h, b = (ψ_{j+e} - ψ_j)/h per
  *    axis (a missing neighbour outside the grid gives a difference of 0):
@@ -836,20 +845,47 @@ int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int ma
  * in Ḡ. flags_out (may be NULL): bit 0 node in Ḡ, bit 1 interface node. */
 static int sign_class(double v) { return v < 0.0 ? -1 : 1; }
 
+/* (a) the Russo-Smereka estimate at node idx (of v = φ̃) */
+static double reinit_rs_estimate(const or_params* g, const double* v, long long idx) {
+    long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
+    long long c[3] = {idx % g->n[0], (idx / g->n[0]) % g->n[1], idx / (g->n[0] * g->n[1])};
+    double vj = v[idx], cn = 0.0, mx = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+        int has_m = c[a] > 0, has_p = c[a] < g->n[a] - 1;
+        if (has_m) mx = fmax(mx, fabs(vj - v[idx - stride[a]]) / g->h);
+        if (has_p) mx = fmax(mx, fabs(v[idx + stride[a]] - vj) / g->h);
+        /* the gradient component: centred, one-sided on the domain boundary (reading of §3) */
+        double ce = 0.0;
+        if (has_m && has_p)
+            ce = (v[idx + stride[a]] - v[idx - stride[a]]) / (2.0 * g->h);
+        else if (has_p)
+            ce = (v[idx + stride[a]] - vj) / g->h;
+        else if (has_m)
+            ce = (vj - v[idx - stride[a]]) / g->h;
+        cn = cn + ce * ce;
+    }
+    double den = fmax(sqrt(cn), mx);
+    if (!(den > 0.0)) return vj;
+    return vj / den;
+}
+
+/* the explicit value of interface node idx: (a), then the constraint (b) */
 static double reinit_one_step(const or_params* g, const double* v, long long idx) {
     long long stride[3] = {1, g->n[0], g->n[0] * g->n[1]};
     long long c[3] = {idx % g->n[0], (idx / g->n[0]) % g->n[1], idx / (g->n[0] * g->n[1])};
-    double vj = v[idx], s = 0.0;
-    for (int a = 0; a < g->dim; ++a) {
-        int has_m = c[a] > 0, has_p = c[a] < g->n[a] - 1;
-        double ga = 0.0;
-        if (has_m) ga = fmax(ga, fabs(vj - v[idx - stride[a]]) / g->h);
-        if (has_p) ga = fmax(ga, fabs(v[idx + stride[a]] - vj) / g->h);
-        if (has_m && has_p) ga = fmax(ga, fabs(v[idx + stride[a]] - v[idx - stride[a]]) / (2.0 * g->h));
-        s = s + ga * ga;
-    }
-    if (!(s > 0.0)) return vj;
-    return vj / sqrt(s);
+    int cj = v[idx] < 0.0 ? -1 : 1;
+    double sd = 0.0, sp = 0.0;
+    for (int a = 0; a < g->dim; ++a)
+        for (int side = -1; side <= 1; side += 2) {
+            long long q = c[a] + side;
+            if (q < 0 || q >= g->n[a]) continue;
+            long long k = idx + side * stride[a];
+            if ((v[k] < 0.0 ? -1 : 1) == cj) continue;
+            sd = sd + reinit_rs_estimate(g, v, k);
+            sp = sp + v[k];
+        }
+    if (sp == 0.0) return reinit_rs_estimate(g, v, idx);
+    return v[idx] * sd / sp;
 }
 
 static int reinit_is_interface(const or_params* g, const double* v, long long idx) {

@@ -94,6 +94,7 @@ struct Params {
     int n0, n1, n2;        // nodes per axis
     long long s1, s2;      // strides of axes 1 and 2
     int is1, is2;          // the same strides as 32-bit values (fewer than 2^31 nodes)
+    T h;                   // mesh width
     T inv_h;               // 1/h
     T inv_2h;              // 1/(2h)
     T h4;                  // h^4 (WENO: ε = h^2 folded into the weights)

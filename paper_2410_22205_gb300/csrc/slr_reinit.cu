@@ -15,9 +15,13 @@
 // Readings (the paper cites Hartmann et al. 2008 and Sussman et al. 1994
 // without formulas; these match the oracle):
 //  - explicit step on an interface node j (a face neighbour of the other
-//    sign class, φ < 0 versus φ >= 0): D_j = φ̃_j / |g| with g_a the largest
-//    of |φ̃_{j+e} - φ̃_{j-e}|/(2h), |φ̃_{j+e} - φ̃_j|/h, |φ̃_j - φ̃_{j-e}|/h
-//    (Russo and Smereka 2000);
+//    sign class, φ < 0 versus φ >= 0), keeping the interface where φ̃ puts
+//    it: (a) the estimate of Russo and Smereka (2000) on every interface node
+//    k, D_k = φ̃_k / Δ_k with Δ_k the largest of the gradient norm (centred,
+//    one-sided on the domain boundary) and the one-sided differences; then
+//    (b) the constraint of the constrained reinitialisation: φ_j = φ̃_j
+//    Σ_{k∈S_j} D_k / Σ_{k∈S_j} φ̃_k over the face neighbours S_j of the
+//    other sign class, which keeps j's ratio to them as in φ̃;
 //  - Jacobi sweeps ψ ← ψ - Δτ sign(φ̃)(|∇ψ|_G - 1) with Godunov's upwind
 //    |∇ψ|_G on the other nodes of Ḡ; interface nodes, nodes on the domain
 //    boundary and nodes with φ̃ = 0 keep their value;
@@ -294,16 +298,46 @@ __global__ void __launch_bounds__(kRB) k_reinit_prep(Params<T> P, const T* ub0, 
         }
         T out = vj;
         if (iface) {
-            T s = T(0);
+            // (a) the Russo-Smereka estimate of node k at coordinates ck
+            auto rs = [&](int k, const int* ck) -> T {
+                const T vk = view(k);
+                T cn = T(0), mx = T(0);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    const bool m = ck[a] > 0, pp = ck[a] < nn[a] - 1;
+                    const T wm = m ? view(k - st[a]) : T(0), wp = pp ? view(k + st[a]) : T(0);
+                    if (m) mx = fmax(mx, fabs(vk - wm) / P.h);
+                    if (pp) mx = fmax(mx, fabs(wp - vk) / P.h);
+                    T ce = T(0);  // centred; one-sided on the domain boundary
+                    if (m && pp)
+                        ce = (wp - wm) / (T(2) * P.h);
+                    else if (pp)
+                        ce = (wp - vk) / P.h;
+                    else if (m)
+                        ce = (vk - wm) / P.h;
+                    cn = cn + ce * ce;
+                }
+                const T den = fmax(sqrt(cn), mx);
+                return den > T(0) ? vk / den : vk;
+            };
+            // (b) the constraint over the face neighbours of the other sign class
+            T sd = T(0), sp = T(0);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
-                T ga = T(0);
-                if (hm[a]) ga = fmax(ga, fabs(vj - vm[a]) * P.inv_h);
-                if (hp[a]) ga = fmax(ga, fabs(vp[a] - vj) * P.inv_h);
-                if (hm[a] && hp[a]) ga = fmax(ga, fabs(vp[a] - vm[a]) * P.inv_2h);
-                s += ga * ga;
+                if (hm[a] && ((vm[a] < T(0)) != neg)) {
+                    int ck[3] = {c[0], c[1], c[2]};
+                    ck[a] -= 1;
+                    sd = sd + rs(j - st[a], ck);
+                    sp = sp + vm[a];
+                }
+                if (hp[a] && ((vp[a] < T(0)) != neg)) {
+                    int ck[3] = {c[0], c[1], c[2]};
+                    ck[a] += 1;
+                    sd = sd + rs(j + st[a], ck);
+                    sp = sp + vp[a];
+                }
             }
-            if (s > T(0)) out = vj / sqrt(s);
+            out = sp != T(0) ? vj * sd / sp : rs(j, c);
         }
         const unsigned sg = vj > T(0) ? 1u : (vj < T(0) ? 2u : 0u);
         const bool fixed = iface || edge || sg == 0u;

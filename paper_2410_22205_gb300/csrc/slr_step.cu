@@ -248,6 +248,7 @@ Params<T> make_params(const slr_ctx* c) {
     P.s2 = c->cfg.n[0] * c->cfg.n[1];
     P.is1 = (int)P.s1;
     P.is2 = (int)P.s2;
+    P.h = (T)c->h;
     P.inv_h = (T)(1.0 / c->h);
     P.inv_2h = (T)(1.0 / (2.0 * c->h));
     P.h4 = (T)(c->h * c->h * c->h * c->h);
