@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--reinit", action="store_true",
                     help="time the iteration with the reinitialisation of §3.7 (Algorithm 1 step 4d) on")
     ap.add_argument("--batch-jobs", type=int, default=64, help="jobs of the batched mix (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson serving run length (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=15.0,
+                    help="length of each Poisson serving stream (0: skip)")
     return ap.parse_args()
 
 
@@ -705,75 +706,85 @@ def run_serving(args, slr, torch):
     """Continuous batching: requests of 3-D WENO FP32 reconstructions (grids
     log-uniform 64^3-256^3, clouds log-uniform 5k-2M points on superquadric
     unions, drawn from a pool of pre-generated clouds) are submitted to the
-    server. A burst first measures its capacity; then a Poisson stream at
-    0.8 x capacity runs for --serve-seconds; p50/p99 submit-to-finish
-    latency and reconstructions per second are reported."""
-    rng = np.random.default_rng(4)
+    server. A burst first measures its capacity (one setup thread); then the
+    same Poisson stream at 0.8 x that capacity (same seed, same arrivals) runs
+    for --serve-seconds with one, two and four setup threads, whose set-ups
+    (context, distance grid, φ^0) overlap each other and the iterations. Per
+    stream: p50/p99 submit-to-finish latency, its split into queue, setup and
+    iteration time, and reconstructions per second."""
     pool_sizes = [int(round(math.exp(x))) for x in np.linspace(math.log(5000), math.log(2_000_000), 6)]
     t0 = time.time()
     pool = [synth.superquadric_union_cloud(nn, 3, 100 + i) for i, nn in enumerate(pool_sizes)]
     gen_s = time.time() - t0
 
-    def draw():
-        n = int(round(math.exp(rng.uniform(math.log(64), math.log(256)))))
-        ci = int(rng.integers(0, len(pool)))
-        cfg = slr.slr_config_default(dim=3, n=(n, n, n), lo=(-1.0,) * 3, hi=(1.0,) * 3, precision=32, interp=1, band=1)
-        return cfg, pool[ci], n
+    def draws(seed, count):
+        rng = np.random.default_rng(seed)
+        out = []
+        for _ in range(count):
+            n = int(round(math.exp(rng.uniform(math.log(64), math.log(256)))))
+            out.append((n, int(rng.integers(0, len(pool))), float(rng.exponential(1.0))))
+        return out
 
-    srv = slr.slr_server_create(96 << 30, max_active=16)
-    done_lat = []
+    def cfg_of(n):
+        return slr.slr_config_default(dim=3, n=(n, n, n), lo=(-1.0,) * 3, hi=(1.0,) * 3, precision=32, interp=1,
+                                      band=1)
 
-    def drain(tickets, deadline):
-        pending = set(tickets)
-        while pending and time.time() < deadline:
-            for t in list(pending):
-                st, ctx, lat = slr.slr_server_poll(srv, t)
-                if st == 2:
-                    done_lat.append(lat)
-                    slr.slr_server_release(srv, t)
-                    pending.discard(t)
-            time.sleep(0.002)
-        return pending
+    def serve(setup_threads, reqs, lam):
+        """Submit reqs (lam None: all at once) and wait for all; returns the
+        finished jobs' (latency, queue, setup, iterate) in ms and the span."""
+        srv = slr.slr_server_create(96 << 30, max_active=16, setup_threads=setup_threads)
+        done, pending = [], {}
+        try:
+            t_start = time.perf_counter()
+            t_next = t_start
+            k = 0
+            deadline = t_start + (args.serve_seconds if lam else 600.0)
+            while (k < len(reqs) and time.perf_counter() < deadline) or pending:
+                now = time.perf_counter()
+                while k < len(reqs) and now < deadline and (lam is None or now >= t_next):
+                    n, ci, ex = reqs[k]
+                    pending[slr.slr_server_submit(srv, cfg_of(n), pool[ci], (0.0, 0.0, 0.0, 0.9))] = k
+                    k += 1
+                    if lam:
+                        t_next += ex / lam
+                    now = time.perf_counter()
+                for t in list(pending):
+                    st, _, lat = slr.slr_server_poll(srv, t)
+                    if st == 2:
+                        q, su, it = slr.slr_server_timing(srv, t)
+                        done.append((lat, q, su, it))
+                        slr.slr_server_release(srv, t)
+                        del pending[t]
+                if time.perf_counter() > deadline + 300:
+                    break
+                time.sleep(0.001)
+            span = (time.perf_counter() - t_start) if lam is None else args.serve_seconds
+        finally:
+            slr.slr_server_destroy(srv)
+        return np.array(done).reshape(-1, 4), span, k
 
-    try:
-        # capacity: a burst of requests submitted at once
-        burst = 24
-        t0 = time.perf_counter()
-        tickets = [slr.slr_server_submit(srv, *draw()[:2], (0.0, 0.0, 0.0, 0.9)) for _ in range(burst)]
-        left = drain(tickets, time.time() + 300)
-        cap = burst / (time.perf_counter() - t0)
-        done_lat.clear()
-        # Poisson stream at 0.8 x capacity
-        lam = 0.8 * cap
-        t_end = time.perf_counter() + args.serve_seconds
-        tickets, t_next = [], time.perf_counter()
-        pending = set()
-        while time.perf_counter() < t_end:
-            now = time.perf_counter()
-            if now >= t_next:
-                t = slr.slr_server_submit(srv, *draw()[:2], (0.0, 0.0, 0.0, 0.9))
-                tickets.append(t)
-                pending.add(t)
-                t_next += rng.exponential(1.0 / lam)
-            for t in list(pending):
-                st, ctx, lat = slr.slr_server_poll(srv, t)
-                if st == 2:
-                    done_lat.append(lat)
-                    slr.slr_server_release(srv, t)
-                    pending.discard(t)
-            time.sleep(0.001)
-        t_stream = args.serve_seconds
-        left = drain(pending, time.time() + 300)
-        n_done = len(done_lat)
-        lat = np.array(done_lat)
-        return {"workload": "3-D WENO FP32, grids 64^3-256^3, clouds 5k-2M points (superquadric unions)",
-                "capacity_burst_per_s": cap, "lambda_per_s": lam, "submitted": len(tickets), "completed": n_done,
-                "reconstructions_per_s": n_done / (t_stream + 1e-9),
-                "latency_ms": {"p50": float(np.percentile(lat, 50)) if n_done else None,
-                               "p99": float(np.percentile(lat, 99)) if n_done else None},
-                "unfinished_after_drain": len(left), "max_active": 16, "cloud_pool_generation_s": gen_s}
-    finally:
-        slr.slr_server_destroy(srv)
+    def pct(x):
+        return {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99))} if len(x) else None
+
+    burst = draws(4, 24)
+    res_b, span_b, _ = serve(1, burst, None)
+    cap = len(res_b) / span_b
+    lam = 0.8 * cap
+    stream = draws(5, int(lam * args.serve_seconds * 2) + 16)
+    out = {"workload": "3-D WENO FP32, grids 64^3-256^3, clouds 5k-2M points (superquadric unions)",
+           "capacity_burst_per_s": cap, "capacity_setup_threads": 1, "lambda_per_s": lam, "max_active": 16,
+           "cloud_pool_generation_s": gen_s}
+    for th in (1, 2, 4):
+        res, span, submitted = serve(th, stream, lam)
+        out[f"setup_threads_{th}"] = {
+            "submitted": submitted, "completed": int(len(res)), "reconstructions_per_s": len(res) / span,
+            "latency_ms": pct(res[:, 0]), "queue_ms": pct(res[:, 1]), "setup_ms": pct(res[:, 2]),
+            "iterate_ms": pct(res[:, 3])}
+    best = min((1, 2, 4), key=lambda th: out[f"setup_threads_{th}"]["latency_ms"]["p99"])
+    out["best_setup_threads_by_p99"] = best
+    out["reconstructions_per_s"] = out[f"setup_threads_{best}"]["reconstructions_per_s"]
+    out["latency_ms"] = out[f"setup_threads_{best}"]["latency_ms"]
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -406,9 +406,12 @@ typedef struct slr_server slr_server;
 
 /* hbm_budget: device bytes the server may hold for admitted jobs (a job is
  * admitted alone even if its estimate exceeds the budget); max_active: jobs
- * admitted at once; alloc: allocator for the jobs' contexts (NULL: cudaMalloc).
- * Binds to the current device; starts the setup and iteration threads. */
-slr_status slr_server_create(size_t hbm_budget, int max_active, const slr_allocator* alloc, slr_server** out);
+ * admitted at once; setup_threads (1..64): threads that set admitted jobs up
+ * (context, distance grid, φ^0) at the same time, each on its job's stream;
+ * alloc: allocator for the jobs' contexts (NULL: cudaMalloc). Binds to the
+ * current device; starts the setup and iteration threads. */
+slr_status slr_server_create(size_t hbm_budget, int max_active, int setup_threads, const slr_allocator* alloc,
+                             slr_server** out);
 
 /* Queue one reconstruction: cfg as for slr_create, the cloud (host, copied),
  * φ^0 = |x - c| - r with sphere = {cx, cy, cz, r}; the job then runs to the
@@ -421,6 +424,14 @@ slr_status slr_server_submit(slr_server* s, const slr_config* cfg, const double*
  * owned by the server. latency_ms (may be NULL): submit-to-finish time once
  * done or failed, else -1. */
 slr_status slr_server_poll(slr_server* s, uint64_t ticket, int* state, slr_ctx** result, double* latency_ms);
+
+/* Where a finished (done or failed) job's latency went, in milliseconds:
+ * queue_ms from submission to admission, setup_ms from admission to its first
+ * iteration (context, cloud copy, distance grid, φ^0), iterate_ms from then to
+ * the stop test's end. Any output may be NULL. SLR_E_STATE while the job is
+ * queued or running; SLR_E_INVALID for an unknown or released ticket. */
+slr_status slr_server_timing(slr_server* s, uint64_t ticket, double* queue_ms, double* setup_ms,
+                             double* iterate_ms);
 
 /* Destroy a finished (done or failed) job's context and return its budget
  * share; SLR_E_STATE while it is queued or running. */

@@ -35,6 +35,8 @@
 // choice. Every FMA here is written explicitly.
 #include <cuda.h>
 
+#include <mutex>
+
 #include "slr_compact.cuh"
 #include "slr_internal.cuh"
 
@@ -577,11 +579,12 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// the driver's tensor-map encoder, looked up once (contexts may be set up
+// from several threads at a time, as the server does)
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
@@ -590,7 +593,7 @@ EncodeTiledFn encode_fn() {
             fn = (EncodeTiledFn)p;
         else
             cudaGetLastError();
-    }
+    });
     return fn;
 }
 

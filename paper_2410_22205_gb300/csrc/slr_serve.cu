@@ -1,13 +1,17 @@
 // Serving form of the library: a continuous-batching request loop.
 //
 // Requests (a configuration, a host point cloud and a sphere for φ^0) are
-// queued by slr_server_submit. Two worker threads drive the device:
-//  - setup: admits queued requests in order while an active slot and enough
-//    of the HBM budget are free, creates the job's context on its own
-//    stream, copies the cloud, builds the exact distance grid and φ^0, and
-//    hands the job to the iteration thread;
+// queued by slr_server_submit. Worker threads drive the device:
+//  - setup (setup_threads of them): each admits the next queued request, in
+//    order, while an active slot and enough of the HBM budget are free,
+//    creates the job's context on its own stream, copies the cloud, builds
+//    the exact distance grid and φ^0, and hands the job to the iteration
+//    thread. Several set-ups run at once, so a large request's distance grid
+//    does not hold back the admission of the requests queued behind it;
 //  - iterate: round-robin over the running jobs, enqueues a few iterations
-//    of each job's captured iteration graph on the job's stream, then an
+//    of each job's captured iteration graph on a stream of the greatest
+//    priority (so that set-ups running beside them take only the SMs that
+//    iterations leave idle), then an
 //    asynchronous 16-byte status copy and an event; a job whose event has
 //    completed and whose device stop flag is set is retired. New jobs join
 //    the next round, so requests that arrive while others run overlap with
@@ -51,7 +55,9 @@ struct Job {
     bool outstanding = false;
     cudaEvent_t ev = nullptr;
     int* status = nullptr;  // pinned: n, stop, converged, error
-    std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+    cudaStream_t run_stream = nullptr;    // iterations, greatest priority
+    cudaStream_t setup_stream = nullptr;  // the context's own stream, restored when the job finishes
+    std::chrono::steady_clock::time_point t_submit, t_start, t_ready, t_done;
 };
 
 // device bytes a job will hold: two φ buffers, d, argmin, band lists and
@@ -84,7 +90,8 @@ struct slr_server {
     uint64_t next_ticket = 1;
     int active = 0;  // admitted and not yet released
     bool stop = false;
-    std::thread setup_thread, iter_thread;
+    std::vector<std::thread> setup_threads;
+    std::thread iter_thread;
     std::string err;
 
     void setup_loop();
@@ -121,6 +128,7 @@ void slr_server::setup_loop() {
             if (c) slr_destroy(c);
             std::lock_guard<std::mutex> lk(mu);
             j->t_done = std::chrono::steady_clock::now();
+            j->t_ready = j->t_done;
             j->state = kFailed;
             used -= j->bytes;
             --active;
@@ -130,6 +138,7 @@ void slr_server::setup_loop() {
         }
         std::vector<double>().swap(j->xyz);  // the host copy is no longer needed
         j->ctx = c;
+        j->t_ready = std::chrono::steady_clock::now();
         {
             std::lock_guard<std::mutex> lk(mu);
             j->state = kRunning;
@@ -176,10 +185,17 @@ void slr_server::iter_loop() {
             Job* j = run[i].get();
             bool failed = false, done = false;
             if (!j->ev) {
+                int least = 0, greatest = 0;
+                cudaDeviceGetStreamPriorityRange(&least, &greatest);
                 if (cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess ||
-                    cudaMallocHost((void**)&j->status, 4 * sizeof(int)) != cudaSuccess) {
+                    cudaMallocHost((void**)&j->status, 4 * sizeof(int)) != cudaSuccess ||
+                    cudaStreamCreateWithPriority(&j->run_stream, cudaStreamNonBlocking, greatest) != cudaSuccess) {
                     cudaGetLastError();
                     failed = true;
+                } else {
+                    // the set-up is complete (slr_init_u returned); later work goes to the run stream
+                    j->setup_stream = j->ctx->stream;
+                    j->ctx->stream = j->run_stream;
                 }
             }
             if (!failed && j->outstanding) {
@@ -208,6 +224,12 @@ void slr_server::iter_loop() {
             }
             if (failed || done) {
                 j->t_done = std::chrono::steady_clock::now();
+                if (j->run_stream) {
+                    cudaStreamSynchronize(j->run_stream);
+                    j->ctx->stream = j->setup_stream;  // the client reads results on the context's own stream
+                    cudaStreamDestroy(j->run_stream);
+                    j->run_stream = nullptr;
+                }
                 if (j->ev) cudaEventDestroy(j->ev);
                 j->ev = nullptr;
                 if (j->status) cudaFreeHost(j->status);
@@ -225,6 +247,10 @@ void slr_server::iter_loop() {
     }
     for (auto& j : run) {
         if (j->ctx) cudaStreamSynchronize(j->ctx->stream);
+        if (j->run_stream) {
+            j->ctx->stream = j->setup_stream;
+            cudaStreamDestroy(j->run_stream);
+        }
         if (j->ev) cudaEventDestroy(j->ev);
         if (j->status) cudaFreeHost(j->status);
     }
@@ -232,8 +258,9 @@ void slr_server::iter_loop() {
 
 extern "C" {
 
-slr_status slr_server_create(size_t hbm_budget, int max_active, const slr_allocator* alloc, slr_server** out) {
-    if (!out || max_active < 1) return SLR_E_INVALID;
+slr_status slr_server_create(size_t hbm_budget, int max_active, int setup_threads, const slr_allocator* alloc,
+                             slr_server** out) {
+    if (!out || max_active < 1 || setup_threads < 1 || setup_threads > 64) return SLR_E_INVALID;
     slr_server* s = new slr_server();
     s->budget = hbm_budget;
     s->max_active = max_active;
@@ -246,7 +273,7 @@ slr_status slr_server_create(size_t hbm_budget, int max_active, const slr_alloca
         delete s;
         return SLR_E_CUDA;
     }
-    s->setup_thread = std::thread([s] { s->setup_loop(); });
+    for (int i = 0; i < setup_threads; ++i) s->setup_threads.emplace_back([s] { s->setup_loop(); });
     s->iter_thread = std::thread([s] { s->iter_loop(); });
     *out = s;
     return SLR_OK;
@@ -296,6 +323,24 @@ slr_status slr_server_poll(slr_server* s, uint64_t ticket, int* state, slr_ctx**
     return SLR_OK;
 }
 
+slr_status slr_server_timing(slr_server* s, uint64_t ticket, double* queue_ms, double* setup_ms, double* iterate_ms) {
+    if (!s) return SLR_E_INVALID;
+    std::shared_ptr<Job> j;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return SLR_E_INVALID;
+        j = it->second;
+    }
+    const int st = j->state.load();
+    if (st != kDone && st != kFailed) return SLR_E_STATE;
+    using ms = std::chrono::duration<double, std::milli>;
+    if (queue_ms) *queue_ms = ms(j->t_start - j->t_submit).count();
+    if (setup_ms) *setup_ms = ms(j->t_ready - j->t_start).count();
+    if (iterate_ms) *iterate_ms = ms(j->t_done - j->t_ready).count();
+    return SLR_OK;
+}
+
 slr_status slr_server_release(slr_server* s, uint64_t ticket) {
     if (!s) return SLR_E_INVALID;
     std::shared_ptr<Job> j;
@@ -332,7 +377,8 @@ void slr_server_destroy(slr_server* s) {
     }
     s->cv.notify_all();
     s->cv_iter.notify_all();
-    if (s->setup_thread.joinable()) s->setup_thread.join();
+    for (auto& t : s->setup_threads)
+        if (t.joinable()) t.join();
     if (s->iter_thread.joinable()) s->iter_thread.join();
     for (auto& kv : s->jobs)
         if (kv.second->ctx) slr_destroy(kv.second->ctx);

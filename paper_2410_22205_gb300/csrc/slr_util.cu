@@ -1,15 +1,58 @@
 // Small utility kernels: exclusive scan of block counts, type conversions,
 // and allocation through the context's allocator.
+#include <mutex>
+
 #include "slr_compact.cuh"
 #include "slr_internal.cuh"
 
 namespace slr {
 
+// Without an injected allocator, memory comes from the library's own
+// stream-ordered pool on the context's stream (cudaMallocFromPoolAsync /
+// cudaFreeAsync): neither call waits for the device, so contexts set up from
+// several threads (the server) do not stall behind each other's work the way
+// cudaFree does. One pool per device, created on first use, keeps freed
+// memory for reuse (release threshold: unlimited), as a caching allocator
+// would; the process's default pool is left as it is. Everything a context
+// allocates is used on its own stream, or after that stream was
+// synchronised. Devices without memory pools use cudaMalloc / cudaFree.
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+bool g_pool_tried[kPoolDevices] = {};
+
+cudaMemPool_t pool_of(int device) {
+    if (device < 0 || device >= kPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (!g_pool_tried[device]) {
+        g_pool_tried[device] = true;
+        int ok = 0;
+        if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, device) == cudaSuccess && ok) {
+            cudaMemPoolProps pr = {};
+            pr.allocType = cudaMemAllocationTypePinned;
+            pr.location.type = cudaMemLocationTypeDevice;
+            pr.location.id = device;
+            cudaMemPool_t mp = nullptr;
+            if (cudaMemPoolCreate(&mp, &pr) == cudaSuccess) {
+                unsigned long long thr = ~0ull;
+                cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+                g_pool[device] = mp;
+            }
+        }
+        cudaGetLastError();
+    }
+    return g_pool[device];
+}
+}  // namespace
+
 void* dev_alloc(slr_ctx* c, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (c->default_alloc) {
         void* p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaMemPool_t mp = pool_of(c->device);
+        const cudaError_t e = mp ? cudaMallocFromPoolAsync(&p, bytes, mp, c->stream) : cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -20,10 +63,14 @@ void* dev_alloc(slr_ctx* c, size_t bytes) {
 
 void dev_free(slr_ctx* c, void* p) {
     if (!p) return;
-    if (c->default_alloc)
-        cudaFree(p);
-    else
+    if (c->default_alloc) {
+        if (pool_of(c->device))
+            cudaFreeAsync(p, c->stream);
+        else
+            cudaFree(p);
+    } else {
         c->al.free(p, c->al.user);
+    }
 }
 
 // single block of 1024 threads; nb <= 4 * 1024

@@ -35,7 +35,8 @@ EXPORTS = [
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches", "slr_brick_shape", "slr_brick_shape_set", "slr_probe_fma",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error", "slr_selftest_barrier",
-    "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_release", "slr_server_last_error",
+    "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_timing", "slr_server_release",
+    "slr_server_last_error",
     "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
 ]
 
@@ -169,7 +170,9 @@ def lib():
                 "slr_multirun_default": (None, [C.POINTER(slr_multirun_config)]),
                 "slr_reconstruct": (C.c_int, [C.POINTER(slr_multirun_config), _dp, C.c_int64, C.POINTER(slr_allocator),
                                               _vp, C.POINTER(_vp), C.POINTER(slr_multirun_report)]),
-                "slr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(slr_allocator), C.POINTER(_vp)]),
+                "slr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(slr_allocator),
+                                                C.POINTER(_vp)]),
+                "slr_server_timing": (C.c_int, [_vp, C.c_uint64, _dp, _dp, _dp]),
                 "slr_server_submit": (C.c_int, [_vp, P, _dp, C.c_int64, _dp, C.POINTER(C.c_uint64)]),
                 "slr_server_poll": (C.c_int, [_vp, C.c_uint64, _ip, C.POINTER(_vp), _dp]),
                 "slr_server_release": (C.c_int, [_vp, C.c_uint64]),
@@ -471,10 +474,10 @@ def _check_srv(srv, status):
         raise SlrError(status, msg.decode() if msg else "")
 
 
-def slr_server_create(hbm_budget, max_active=16, allocator=None):
+def slr_server_create(hbm_budget, max_active=16, allocator=None, setup_threads=1):
     h = C.c_void_p()
     al = C.byref(allocator.struct if hasattr(allocator, "struct") else allocator) if allocator is not None else None
-    s = lib().slr_server_create(int(hbm_budget), int(max_active), al, C.byref(h))
+    s = lib().slr_server_create(int(hbm_budget), int(max_active), int(setup_threads), al, C.byref(h))
     if s != SLR_OK:
         raise SlrError(s, "server creation failed")
     return h.value
@@ -496,6 +499,13 @@ def slr_server_poll(srv, ticket):
     lat = C.c_double(-1.0)
     _check_srv(srv, lib().slr_server_poll(srv, C.c_uint64(ticket), C.byref(st), C.byref(res), C.byref(lat)))
     return st.value, res.value, (lat.value if lat.value >= 0 else None)
+
+
+def slr_server_timing(srv, ticket):
+    """(queue_ms, setup_ms, iterate_ms) of a finished job."""
+    q, su, it = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check_srv(srv, lib().slr_server_timing(srv, C.c_uint64(ticket), C.byref(q), C.byref(su), C.byref(it)))
+    return q.value, su.value, it.value
 
 
 def slr_server_release(srv, ticket):

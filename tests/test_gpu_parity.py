@@ -482,7 +482,7 @@ def test_server_results_equal_solo_runs():
         it, conv = r.evolve()
         solo.append((it, r.u(), r.diagnostics()["e2"]))
         r.close()
-    srv = slr.slr_server_create(64 << 20, max_active=3)
+    srv = slr.slr_server_create(64 << 20, max_active=3, setup_threads=2)
     try:
         tickets = []
         for cfg, pts in specs:
@@ -499,8 +499,13 @@ def test_server_results_equal_solo_runs():
                     n_nodes = int(np.prod([specs[tickets.index(t)][0].n[a] for a in range(3)]))
                     u = slr.slr_get_field(ctx, slr.SLR_FIELD_U, n_nodes)
                     d = slr.slr_diagnostics(ctx)
+                    q, su, itm = slr.slr_server_timing(srv, t)
+                    # the three parts of the latency: queue, set-up, iterations
+                    assert min(q, su, itm) >= 0.0 and abs(q + su + itm - lat) <= 1e-6 * max(lat, 1.0)
                     results[t] = (d["iters"], u, d["e2"], lat)
                     slr.slr_server_release(srv, t)
+                    with pytest.raises(slr.SlrError):
+                        slr.slr_server_timing(srv, t)  # released
             time.sleep(0.005)
         assert len(results) == len(tickets)
         for t, (it, u, e2) in zip(tickets, solo):
