@@ -438,7 +438,7 @@ def slr_brick_shape_set(ctx, threads, stages):
 def slr_probe_fma(precision=32, trips=None):
     """Measured FMA throughput of the current device: (TFLOP/s, ms of the timed launch)."""
     if trips is None:
-        trips = 50_000 if precision == 32 else 2_000
+        trips = 50_000 if precision == 32 else 1_000
     tf, ms = C.c_double(0.0), C.c_double(0.0)
     st = lib().slr_probe_fma(int(precision), int(trips), C.byref(tf), C.byref(ms))
     if st != SLR_OK:
