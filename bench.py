@@ -401,7 +401,10 @@ def run_gpu(args):
     kern = np.array(kern_ms)
     tname = "float" if prec == 32 else "double"
     iname = "WENO" if interp else "Q1"
-    names = [f"k_step_brick<{tname},{iname},{'band' if band else 'whole grid'}>",
+    # the list step runs with the reinitialisation (its band can leave the bricks of the initial band)
+    step_name = (f"k_step_band<{tname},3,{iname}>" if args.reinit else
+                 f"k_step_brick<{tname},{iname},{'band' if band else 'whole grid'}>")
+    names = [step_name,
              f"k_energy<{tname},3,{iname},R=5> (front cells + quadrature)", "k_record"]
     kmean = kern.mean(axis=0)
     dom = int(np.argmax(kmean[:2]))  # the step or the energy pass (the record kernel is a small reduction)

@@ -280,9 +280,12 @@ slr_status slr_brick_shape_set(slr_ctx* ctx, int threads, int stages);
  *  cuda_stream:   stream for the work (NULL: the legacy default stream). The
  *                 call returns after the stream has finished the work.
  *
- * The first call on each device looks up that device's address of the
- * scratch array (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture. All calls share the one array and it
+ * The call is synchronous: it reads the cloud's bounding box and a status
+ * word back to the host and waits on cuda_stream, so it cannot be recorded
+ * into a CUDA graph; call it on a stream that is not capturing (a capturing
+ * stream gives SLR_E_INVALID, with nothing enqueued). The first call on each device also looks up that
+ * device's address of the scratch array (cudaGetSymbolAddress, with that
+ * device current). All calls share the one array and it
  * keeps the last call's contents (what must start at zero is cleared at the
  * start of each call): calls that overlap on the GPU, from different threads
  * or streams, race. Errors are described by slr_last_error(NULL). */

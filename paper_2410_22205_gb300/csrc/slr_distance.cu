@@ -745,6 +745,15 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
         return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: n[2] must be 1 in 2-D");
     if (!(h > 0.0)) return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: h must be > 0");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the call reads results back to the host and waits on the stream, which
+    // a stream capture cannot record
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(SLR_E_CUDA, "distance_grid_noalloc: invalid stream");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return noalloc_fail(SLR_E_INVALID, "distance_grid_noalloc: the call is synchronous and cannot be captured");
 
     // per-device set-up: the host-side name of the array is not a device
     // address; ask the runtime for this device's address once

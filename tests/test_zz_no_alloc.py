@@ -69,3 +69,30 @@ def test_noalloc_rejects_clouds_beyond_its_scratch():
                                       d_dev.data_ptr(), a_dev.data_ptr())
     assert e.value.status == slr.SLR_E_INVALID
     assert "65536" in str(e.value)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call reads results back to the host and waits on its stream, so it
+    cannot be recorded into a CUDA graph: on a capturing stream it returns
+    SLR_E_INVALID with nothing enqueued, and the capture stays valid."""
+    from paper_2410_22205_gb300 import slr
+
+    pts_dev = torch.zeros((16, 3), dtype=torch.float64, device="cuda")
+    d_dev = torch.empty(8 ** 3, dtype=torch.float32, device="cuda")
+    a_dev = torch.empty(8 ** 3, dtype=torch.int32, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(g):
+        x.add_(1.0)
+        try:
+            slr.slr_distance_grid_noalloc(3, (8, 8, 8), (-1.0,) * 3, 2.0 / 7, 32, pts_dev.data_ptr(), 16,
+                                          d_dev.data_ptr(), a_dev.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        except slr.SlrError as e:
+            err = e
+    g.replay()
+    torch.cuda.synchronize()
+    assert err is not None and err.status == slr.SLR_E_INVALID
+    assert "captured" in str(err)
+    assert float(x[0].item()) == 1.0
