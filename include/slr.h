@@ -266,9 +266,10 @@ slr_status slr_brick_shape_set(slr_ctx* ctx, int threads, int stages);
  * the lowest point index on ties, d rounded to `precision`), but from
  * caller-owned device buffers and without a context, and it allocates
  * nothing: no cudaMalloc, cudaFree or allocating library routine. Its
- * scratch (point codes, bin counts, sorted points, box hierarchy) is one
- * fixed array of about 2.4 MB in the library's device memory, present on
- * every GPU that loads the library until the process exits.
+ * scratch (point codes, bin counts, sorted points, box hierarchy, leaf
+ * cylinders) is one fixed array of about 2.5 MB in the library's device
+ * memory, present on every GPU that loads the library until the process
+ * exits.
  *
  *  dim, n, lo, h: the grid (as in slr_config; node coordinates lo + i*h;
  *                 n[2] = 1 in 2-D); at most 2^31-1 nodes.

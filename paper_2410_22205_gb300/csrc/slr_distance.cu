@@ -8,10 +8,15 @@
 //     consecutive points are spatially close;
 //  3. a 32-ary box hierarchy over the sorted points: a leaf box per 32
 //     consecutive points, a box per 32 consecutive boxes above, up to a top
-//     level of at most 32 boxes;
+//     level of at most 32 boxes; each leaf also gets a bounding cylinder
+//     (centre, unit axis along the leaf's least-variance direction,
+//     half-height, radius): on a surface cloud a leaf is a thin patch, and
+//     the cylinder bounds the distance to it far more tightly than its box;
 //  4. one warp per tile of 32 grid nodes (2x4x4 in 3-D, 8x4 in 2-D): a
 //     depth-first walk of the hierarchy, nearest child first, pruning boxes
-//     farther from the tile than the warp's worst current best. At the leaves
+//     farther from the tile than the warp's worst current best. A leaf is
+//     screened only if, for some lane, both its box and its cylinder lie
+//     within that lane's bound. At the leaves
 //     each lane screens the 32 points in FP32 and re-checks in FP64 — with the
 //     oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 + (z-qz)^2 without
 //     contraction — every point whose FP32 distance is within a safety
@@ -203,6 +208,107 @@ __global__ void k_boxes(const float4* spt, long long npts, float4* blo, float4* 
     }
 }
 
+// One warp per leaf: its bounding cylinder, cyl[2 l] = (centre, half-height),
+// cyl[2 l + 1] = (unit axis, radius). The axis is the least-variance
+// direction of the leaf's points (any unit vector gives a valid bound; this
+// one makes the cylinder thin on a surface patch). Half-height and radius are
+// widened by 1e-5 relative plus `slack`, which covers the FP32 rounding of the
+// point offsets and of the search's evaluation of the bound.
+__global__ void k_leaf_cyl(const float4* spt, long long npts, int dim, long long nleaves, float slack, float4* cyl) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaves) return;
+    const long long q = w * 32 + lane;
+    const long long rem = npts - w * 32;
+    const int cnt = rem < 32 ? (int)rem : 32;
+    const bool have = lane < cnt;
+    float4 p = have ? spt[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float sx = p.x, sy = p.y, sz = p.z;
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    const float cx = sx / (float)cnt, cy = sy / (float)cnt, cz = dim == 3 ? sz / (float)cnt : 0.f;
+    const float wx = have ? p.x - cx : 0.f, wy = have ? p.y - cy : 0.f, wz = have && dim == 3 ? p.z - cz : 0.f;
+    float m[6] = {wx * wx, wx * wy, wx * wz, wy * wy, wy * wz, wz * wz};
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+    double ax = 0.0, ay = 0.0, az = 1.0;
+    if (lane == 0) {
+        const double xx = m[0], xy = m[1], xz = m[2], yy = m[3], yz = m[4], zz = m[5];
+        if (dim == 2) {
+            // the normal of the 2-D patch: the eigenvector of the smaller
+            // eigenvalue of [[xx, xy], [xy, yy]]
+            const double hm = 0.5 * (xx + yy), hd = 0.5 * (xx - yy);
+            const double lmin = hm - sqrt(hd * hd + xy * xy);
+            double ux = xy, uy = lmin - xx, vx = lmin - yy, vy = xy;
+            if (ux * ux + uy * uy < vx * vx + vy * vy) {
+                ux = vx;
+                uy = vy;
+            }
+            ax = ux;
+            ay = uy;
+            az = 0.0;
+            if (ax * ax + ay * ay == 0.0) {
+                ax = 1.0;
+                ay = 0.0;
+            }
+        } else {
+            // adj(M) = sum_i (product of the other two eigenvalues) v_i v_i^T:
+            // its dominant direction is the least-variance one; its largest
+            // column, refined by two products with adj(M)
+            const double a00 = yy * zz - yz * yz, a01 = xz * yz - xy * zz, a02 = xy * yz - xz * yy;
+            const double a11 = xx * zz - xz * xz, a12 = xy * xz - xx * yz, a22 = xx * yy - xy * xy;
+            const double n0 = a00 * a00 + a01 * a01 + a02 * a02, n1 = a01 * a01 + a11 * a11 + a12 * a12,
+                         n2 = a02 * a02 + a12 * a12 + a22 * a22;
+            if (n0 >= n1 && n0 >= n2) {
+                ax = a00; ay = a01; az = a02;
+            } else if (n1 >= n2) {
+                ax = a01; ay = a11; az = a12;
+            } else {
+                ax = a02; ay = a12; az = a22;
+            }
+            for (int it = 0; it < 2; ++it) {
+                const double bx = a00 * ax + a01 * ay + a02 * az, by = a01 * ax + a11 * ay + a12 * az,
+                             bz = a02 * ax + a12 * ay + a22 * az;
+                const double nb = sqrt(bx * bx + by * by + bz * bz);
+                if (!(nb > 0.0) || !isfinite(nb)) break;
+                ax = bx / nb;
+                ay = by / nb;
+                az = bz / nb;
+            }
+            if (!(ax * ax + ay * ay + az * az > 0.0) || !isfinite(ax + ay + az)) {
+                // a rank-1 or empty spread: the axis of least extent
+                ax = (xx <= yy && xx <= zz) ? 1.0 : 0.0;
+                ay = (ax == 0.0 && yy <= zz) ? 1.0 : 0.0;
+                az = (ax == 0.0 && ay == 0.0) ? 1.0 : 0.0;
+            }
+        }
+        const double na = sqrt(ax * ax + ay * ay + az * az);
+        ax /= na;
+        ay /= na;
+        az /= na;
+    }
+    const float nx = (float)__shfl_sync(0xffffffffu, ax, 0), ny = (float)__shfl_sync(0xffffffffu, ay, 0),
+                nz = (float)__shfl_sync(0xffffffffu, az, 0);
+    float hh = 0.f, rr = 0.f;
+    if (have) {
+        const float an = fmaf(wx, nx, fmaf(wy, ny, wz * nz));
+        const float px = fmaf(-an, nx, wx), py = fmaf(-an, ny, wy), pz = fmaf(-an, nz, wz);
+        hh = fabsf(an);
+        rr = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        hh = fmaxf(hh, __shfl_xor_sync(0xffffffffu, hh, o));
+        rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    }
+    if (lane == 0) {
+        cyl[2 * w] = make_float4(cx, cy, cz, fmaf(hh, 1.00001f, slack));
+        cyl[2 * w + 1] = make_float4(nx, ny, nz, fmaf(rr, 1.00001f, slack));
+    }
+}
+
 struct SearchArgs {
     int n0, n1, n2;
     int tx, ty, tz;        // tiles per axis
@@ -212,6 +318,7 @@ struct SearchArgs {
     long long npts;
     const float4* blo;
     const float4* bhi;
+    const float4* cyl;     // leaf cylinders (k_leaf_cyl)
     int nlevels;
     long long off[kMaxLevels];
     long long cnt[kMaxLevels];
@@ -320,12 +427,25 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
             // no tile-box test for a leaf: the per-lane test below implies it,
             // as no lane's bound exceeds the warp bound
             const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
-            // per-lane test: skip the leaf when its box is beyond every lane's own bound
+            // per-lane test: skip the leaf when its box, or else its cylinder,
+            // is beyond every lane's own bound
             {
                 const float gx = fmaxf(0.f, fmaxf(blo_.x - xf, xf - bhi_.x));
                 const float gy = fmaxf(0.f, fmaxf(blo_.y - yf, yf - bhi_.y));
                 const float gz = fmaxf(0.f, fmaxf(blo_.z - zf, zf - bhi_.z));
-                const bool need = !(gx * gx + gy * gy + gz * gz > lbound * lbound);
+                const float lb2 = lbound * lbound;
+                bool need = !(gx * gx + gy * gy + gz * gz > lb2);
+                if (!__any_sync(0xffffffffu, need)) continue;
+                // the distance to a point of the leaf is at least that to the
+                // cylinder: its axial excess over the half-height and its
+                // radial excess over the radius, orthogonal components
+                const float4 cc = A.cyl[2 * id], cn = A.cyl[2 * id + 1];
+                const float wx = xf - cc.x, wy = yf - cc.y, wz = zf - cc.z;
+                const float an = fmaf(wx, cn.x, fmaf(wy, cn.y, wz * cn.z));
+                const float px = fmaf(-an, cn.x, wx), py = fmaf(-an, cn.y, wy), pz = fmaf(-an, cn.z, wz);
+                const float ga = fmaxf(0.f, fabsf(an) - cc.w);
+                const float gb = fmaxf(0.f, sqrtf(fmaf(px, px, fmaf(py, py, pz * pz))) - cn.w);
+                need = need && !(fmaf(ga, ga, gb * gb) > lb2);
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
             // The screen works about the leaf centre c: with u = x - c and
@@ -437,6 +557,7 @@ struct CloudIndex {
     float4* spt = nullptr;
     float4* blo = nullptr;
     float4* bhi = nullptr;
+    float4* cyl = nullptr;
     int nlevels = 0;
     long long off[kMaxLevels], cnt[kMaxLevels];
     double extent = 0.0;
@@ -451,6 +572,7 @@ struct IndexScratch {
     int* tot;                  // scan partials
     float4* spt;               // sorted points (FP32 offsets from lo, index in w)
     float4* blo;               // box hierarchy: lower corners, then upper corners
+    float4* cyl;               // leaf cylinders, two per leaf
 };
 
 // Level sizes of the 32-ary box hierarchy over npts points. False when the
@@ -490,6 +612,7 @@ static cudaError_t build_index(const double* pts, long long npts, int dim, int L
     X.spt = S.spt;
     X.blo = S.blo;
     X.bhi = S.blo + total_boxes;
+    X.cyl = S.cyl;
 
     unsigned long long init_bbox[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
     unsigned long long hb[6];
@@ -543,6 +666,12 @@ static cudaError_t build_index(const double* pts, long long npts, int dim, int L
             S.spt, npts, X.blo, X.bhi, l == 0 ? 0 : X.off[l - 1], l == 0 ? npts : X.cnt[l - 1], X.off[l], own, l);
         *launches += 1;
     }
+    // cylinder slack: the FP32 offsets of points and nodes err by ~1.2e-7
+    // extent per coordinate, the search's evaluation of the axial and radial
+    // components by ~1.5e-6 extent; 8e-6 extent covers both with room
+    const float slack = (float)(8e-6 * (extent > 0.0 ? extent : 1.0));
+    k_leaf_cyl<<<(unsigned)((X.cnt[0] * 32 + 255) / 256), 256, 0, st>>>(S.spt, npts, dim, X.cnt[0], slack, S.cyl);
+    *launches += 1;
     return cudaGetLastError();
 }
 
@@ -560,9 +689,11 @@ static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     if (!hierarchy_sizes(npts, X.cnt, X.off, &X.nlevels, &total_boxes)) return cudaErrorInvalidValue;
     // scratch layout
     size_t b_bbox = 64, b_flag = 16, b_codes = sizeof(unsigned) * npts, b_counts = sizeof(int) * nbins,
-           b_tot = scan_tot_bytes(nbins), b_spt = sizeof(float4) * npts, b_boxes = sizeof(float4) * 2 * total_boxes;
+           b_tot = scan_tot_bytes(nbins), b_spt = sizeof(float4) * npts, b_boxes = sizeof(float4) * 2 * total_boxes,
+           b_cyl = sizeof(float4) * 2 * X.cnt[0];
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-    size_t total = al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes);
+    size_t total =
+        al(b_bbox) + al(b_flag) + al(b_codes) + al(b_counts) + al(b_tot) + al(b_spt) + al(b_boxes) + al(b_cyl);
     char* base = (char*)dev_alloc(c, total);
     if (!base) return cudaErrorMemoryAllocation;
     X.base = base;
@@ -581,6 +712,8 @@ static cudaError_t build_cloud_index(slr_ctx* c, CloudIndex& X) {
     S.spt = (float4*)p;
     p += al(b_spt);
     S.blo = (float4*)p;
+    p += al(b_boxes);
+    S.cyl = (float4*)p;
     return build_index(c->pts, npts, dim, L, c->cfg.lo, c->cfg.hi, c->num_sms, c->stream, S, X, &c->launches);
 }
 
@@ -609,6 +742,7 @@ static SearchArgs search_args(int dim, const int64_t n[3], const double lo[3], d
     A.npts = npts;
     A.blo = X.blo;
     A.bhi = X.bhi;
+    A.cyl = X.cyl;
     A.nlevels = X.nlevels;
     for (int l = 0; l < kMaxLevels; ++l) {
         A.off[l] = l < X.nlevels ? X.off[l] : 0;
@@ -703,7 +837,8 @@ constexpr size_t kOffCounts = kOffCodes + al256(sizeof(unsigned) * kNoAllocMaxPo
 constexpr size_t kOffTot = kOffCounts + al256(sizeof(int) * kNoAllocBins);
 constexpr size_t kOffSpt = kOffTot + al256(sizeof(int) * (kNoAllocScanBlocks + 2) + 16);
 constexpr size_t kOffBoxes = kOffSpt + al256(sizeof(float4) * kNoAllocMaxPoints);
-constexpr size_t kNoAllocScratchBytes = kOffBoxes + al256(sizeof(float4) * 2 * kNoAllocBoxes);  // ~2.4 MB
+constexpr size_t kOffCyl = kOffBoxes + al256(sizeof(float4) * 2 * kNoAllocBoxes);
+constexpr size_t kNoAllocScratchBytes = kOffCyl + al256(sizeof(float4) * 2 * ((kNoAllocMaxPoints + 31) / 32));  // ~2.5 MB
 
 }  // namespace
 
@@ -786,6 +921,7 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
     S.tot = (int*)(base + kOffTot);
     S.spt = (float4*)(base + kOffSpt);
     S.blo = (float4*)(base + kOffBoxes);
+    S.cyl = (float4*)(base + kOffCyl);
 
     const long long npts = n_points;
     const int L = dim == 3 ? kNoAllocL3 : kNoAllocL2;

@@ -95,6 +95,50 @@ def test_distance_single_point_and_far_cloud():
     assert np.array_equal(rec.argmin(), a_o) and np.array_equal(rec.d(), d_o)
 
 
+def _leaf_shape_clouds(dim):
+    """Clouds whose 32-point leaves are degenerate for the leaves' bounding
+    cylinders: collinear points, points on a grid-aligned plane or line (zero
+    half-height, with nodes exactly on it), coincident points, a leaf of one
+    point, and clusters far apart (leaves spanning a gap)."""
+    rng = np.random.default_rng(5)
+    t = np.linspace(-0.9, 0.9, 300)
+    if dim == 3:
+        line = np.stack([t, 0.5 * t + 0.1, -0.25 * t], 1)
+        plane = np.stack([rng.uniform(-0.9, 0.9, 600), rng.uniform(-0.9, 0.9, 600), np.full(600, 0.25)], 1)
+        lattice = np.stack(np.meshgrid(np.linspace(-1, 1, 9), np.linspace(-1, 1, 9), [0.0]), -1).reshape(-1, 3)
+        same = np.tile([[0.2, -0.3, 0.4]], (70, 1))
+        clusters = np.concatenate([rng.normal(0, 0.01, (40, 3)) + c for c in
+                                   ([-0.8, -0.8, -0.8], [0.8, 0.7, -0.6], [0.0, 0.9, 0.9])])
+        one = np.array([[0.31, 0.47, -0.53]])
+    else:
+        line = np.stack([t, 0.5 * t + 0.1], 1)
+        plane = np.stack([rng.uniform(-0.9, 0.9, 600), np.full(600, 0.25)], 1)
+        lattice = np.stack(np.meshgrid(np.linspace(-1, 1, 17), [0.0]), -1).reshape(-1, 2)
+        same = np.tile([[0.2, -0.3]], (70, 1))
+        clusters = np.concatenate([rng.normal(0, 0.01, (40, 2)) + c for c in ([-0.8, -0.8], [0.8, 0.7], [0.0, 0.9])])
+        one = np.array([[0.31, 0.47]])
+    return {"line": line, "plane": plane, "lattice": lattice, "same": same, "clusters": clusters,
+            "one_extra": np.concatenate([same[:32], one])}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_distance_degenerate_leaves_bit_exact(dim, prec):
+    """Leaves of degenerate shape (see _leaf_shape_clouds) prune with their
+    bounding cylinders exactly as the oracle's brute force decides: argmin and
+    d bit-exact on every node."""
+    n = 25 if dim == 3 else 65
+    for name, pts in _leaf_shape_clouds(dim).items():
+        rec, P = make(dim, n, prec, 0, 1)
+        rec.load_cloud(pts)
+        rec.build_distance()
+        d_o, a_o = O.distance(P, pts)
+        d_o = d_o.astype(np.float32).astype(np.float64) if prec == 32 else d_o
+        assert np.array_equal(rec.argmin(), a_o), name
+        assert np.array_equal(rec.d(), d_o), name
+        rec.close()
+
+
 def test_distance_torus_128_sampled():
     """Torus workload size (20k points, 128^3): sampled nodes vs brute force."""
     g = synth.cube_grid(3, 128)
