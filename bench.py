@@ -696,12 +696,35 @@ def run_batched(args, slr, torch):
     for r in recs:
         r.close()
     same = its == seq_iters and bat_state == seq_state
+    # persistent: the same set-up, then one persistent graph-captured kernel
+    # advances every job (slr_batch_run, block size autotuned)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(8) as ex:
+        recs = list(ex.map(lambda j: _run_job(slr, j, stream=torch.cuda.Stream()), jobs))
+    torch.cuda.synchronize()
+    t_psetup = time.perf_counter() - t0
+    pits, _ = slr.slr_batch_run([r.ctx for r in recs], autotune=True)
+    threads, graph, tuned_ms = slr.slr_batch_run_info(recs[0].ctx)
+    t_pevolve = time.perf_counter() - t0 - t_psetup
+    per_state = []
+    for j, r in zip(jobs, recs):
+        idx, val = r.extract(2 * h_of(j))
+        per_state.append((idx.size, float(val.sum())))
+    torch.cuda.synchronize()
+    t_per = time.perf_counter() - t0
+    for r in recs:
+        r.close()
+    psame = pits == seq_iters and per_state == seq_state
     return {"jobs": len(jobs), "workload": "batch mix: 32 2-D (64^2-512^2) + 32 3-D (64^3-192^3), 1k-200k points, "
                                             "Q1/WENO mixed, FP32, band",
             "one_at_a_time": {"reconstructions_per_s": len(jobs) / t_seq, "seconds": t_seq},
             "batched": {"reconstructions_per_s": len(jobs) / t_bat, "seconds": t_bat, "setup_s": t_setup,
                         "evolve_s": t_evolve, "chunk": chunk},
-            "speedup": t_seq / t_bat, "identical_results": bool(same), "iterations": its,
+            "persistent": {"reconstructions_per_s": len(jobs) / t_per, "seconds": t_per, "setup_s": t_psetup,
+                           "evolve_s": t_pevolve, "threads_per_block": threads, "graph_captured": bool(graph),
+                           "autotune_trial_ms": tuned_ms, "identical_results": bool(psame)},
+            "speedup": t_seq / t_bat, "speedup_persistent": t_seq / t_per, "identical_results": bool(same),
+            "iterations": its,
             "input_generation_s": gen_s}
 
 

@@ -188,6 +188,38 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
  * chunk. 0 before any batch. */
 int slr_batch_chunk(const slr_ctx* first_job);
 
+/* Batched form of slr_evolve in one persistent kernel (the batching of many
+ * reconstructions on one GPU stands in for the paper's ranks advancing
+ * subdomains together, §3.3; each job runs Algorithm 1's loop, step 4 of §3,
+ * without the reinitialisation). One cooperative launch, captured in a CUDA
+ * graph, advances every job iteration by iteration: its blocks take work
+ * items (a brick of a 3-D job's band, a group of band-list tiles of a 2-D
+ * job, a slot of candidate cells of the energy of §3.5, a slice of a job's
+ * record and stop test of §4 eq. deltaEn) from one ticket counter, in three
+ * phases per iteration separated by grid barriers. A job whose stop test has
+ * fired contributes no items; the launch ends when every job has stopped.
+ * Each job's state, iteration count and history are bit-identical to those
+ * of slr_evolve on that job alone.
+ * Jobs: initialised (slr_init_u) on the current device, narrow band on,
+ * reinitialisation off, energy_R = 5 in 3-D (else SLR_E_INVALID: use
+ * slr_batch_evolve, which takes any job); FP32 and FP64 jobs run as separate
+ * launches, at most 64 jobs per launch. autotune != 0: the first launches
+ * time the block sizes (128 and 256 threads, two iterations each, twice)
+ * and the rest of the batch keeps the faster; 0: 128 threads. `cuda_stream`
+ * (NULL: the first job's stream) orders the launches; every job's own stream
+ * is synchronised first. iters_out / converged_out: n_jobs entries each, may
+ * be NULL. SLR_E_TIMEOUT if a grid barrier waited longer than its poll limit
+ * (~0.3 s); SLR_E_STATE if a job's device-side check failed. Contexts must
+ * not be used by other threads meanwhile. */
+slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* cuda_stream, int* iters_out,
+                         int* converged_out);
+
+/* The last slr_batch_run whose first job was first_job: threads per block
+ * (128 or 256), whether its launches ran as captured CUDA graphs (1) or were
+ * enqueued directly where capture was refused (0), and the autotuner's best
+ * trial time in ms (0 without autotuning). Any pointer may be NULL. */
+slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* graph, float* tuned_ms);
+
 /* Nodes with |φ| < width, in ascending linear index (the reconstructed zero
  * level set's neighbourhood). idx/u: caller buffers of `cap` entries (either
  * may be NULL to query the count). *n_out = number of such nodes; returns

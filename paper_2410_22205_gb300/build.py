@@ -23,10 +23,15 @@ LIB = os.path.join(PKG, "libslr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-# The brick step instantiates one kernel per launch shape; without implicit
-# FMA contraction every instance rounds each operation as written, so the
-# autotuner's choice cannot change a result.
-FILE_FLAGS = {"slr_brick.cu": ["-fmad=false"]}
+# The per-iteration kernels are compiled without implicit FMA contraction:
+# every multiply-add they want is written as an explicit fma, so each
+# operation rounds as written. The brick step instantiates one kernel per
+# launch shape, and the batched persistent kernel runs the same device code
+# as the per-job kernels; contraction decided per instance would make results
+# depend on the autotuner's choice or differ between a batched and a solo run.
+_NO_FMAD = ["-fmad=false"]
+FILE_FLAGS = {name: _NO_FMAD for name in ("slr_brick.cu", "slr_step.cu", "slr_energy.cu", "slr_batch_f32.cu",
+                                          "slr_batch_f64.cu")}
 
 
 def nvcc() -> str:

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -278,6 +279,10 @@ slr_status ctxless_error_set(slr_status s, const std::string& msg) {
     return s;
 }
 const char* ctxless_error() { return g_ctxless_error.c_str(); }
+}  // namespace slr
+
+namespace slr {
+slr_status cuda_status(slr_ctx* c, cudaError_t e, const char* where) { return cuda_fail(c, e, where); }
 }  // namespace slr
 
 extern "C" {
@@ -710,6 +715,74 @@ slr_status slr_batch_evolve(slr_ctx* const* jobs, int n_jobs, int chunk, void* c
 }
 
 int slr_batch_chunk(const slr_ctx* first_job) { return first_job ? first_job->batch_chunk : 0; }
+
+
+slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* cuda_stream, int* iters_out,
+                         int* converged_out) {
+    if (!jobs || n_jobs < 1) return SLR_E_INVALID;
+    int dev = -1;
+    for (int j = 0; j < n_jobs; ++j) {
+        slr_ctx* c = jobs[j];
+        if (!c) return SLR_E_INVALID;
+        if (!c->have_u) return fail(c, SLR_E_STATE, "batch_run: a job has no initial level set");
+        if (dev < 0) dev = c->device;
+        if (c->device != dev) return fail(c, SLR_E_INVALID, "batch_run: jobs on different devices");
+        if (!c->cfg.band)
+            return fail(c, SLR_E_INVALID, "batch_run: a job runs on the whole grid (slr_batch_evolve takes it)");
+        if (c->cfg.reinit)
+            return fail(c, SLR_E_INVALID, "batch_run: a job runs the reinitialisation (slr_batch_evolve takes it)");
+        if (c->cfg.dim == 3 && c->cfg.energy_R != 5)
+            return fail(c, SLR_E_INVALID, "batch_run: a 3-D job's energy_R is not 5 (slr_batch_evolve takes it)");
+        for (int i = 0; i < j; ++i)
+            if (jobs[i] == c) return fail(c, SLR_E_INVALID, "batch_run: a job is listed twice");
+    }
+    slr_ctx* c0 = jobs[0];
+    DeviceGuard g(dev);
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c0->stream;
+    // groups of one storage type and at most 64 jobs, in the caller's order
+    int shape = -1, graph = 1;
+    float tuned = 0.f;
+    for (int prec : {32, 64}) {
+        std::vector<slr_ctx*> grp;
+        for (int j = 0; j < n_jobs; ++j)
+            if (jobs[j]->cfg.precision == prec) grp.push_back(jobs[j]);
+        for (size_t b = 0; b < grp.size(); b += 64) {
+            const int m = (int)std::min<size_t>(64, grp.size() - b);
+            int sh = autotune ? -1 : 0, gr = 0;
+            float tm = 0.f;
+            const slr_status s = prec == 32 ? batch_run_f32(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm)
+                                            : batch_run_f64(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm);
+            if (s == SLR_E_TIMEOUT) return fail(c0, s, "batch_run: a grid barrier of the batched kernel waited too long");
+            if (s == SLR_E_STATE) return fail(c0, s, "batch_run: a device-side check failed in a job");
+            if (s == SLR_E_NOMEM) return fail(c0, s, "batch_run: allocation failed");
+            if (s != SLR_OK) {
+                if (grp[b] != c0 && !grp[b]->err.empty()) c0->err = grp[b]->err;
+                return s;
+            }
+            if (shape < 0) {
+                shape = sh;
+                tuned = tm;
+            }
+            graph = graph && gr;
+        }
+    }
+    c0->batch_threads = shape == 1 ? 256 : 128;
+    c0->batch_graph = graph;
+    c0->batch_tuned_ms = tuned;
+    for (int j = 0; j < n_jobs; ++j) {
+        if (iters_out) iters_out[j] = jobs[j]->batch_iters;
+        if (converged_out) converged_out[j] = jobs[j]->batch_converged;
+    }
+    return SLR_OK;
+}
+
+slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* graph, float* tuned_ms) {
+    if (!first_job) return SLR_E_INVALID;
+    if (threads) *threads = first_job->batch_threads;
+    if (graph) *graph = first_job->batch_graph;
+    if (tuned_ms) *tuned_ms = first_job->batch_tuned_ms;
+    return SLR_OK;
+}
 
 slr_status slr_step_async(slr_ctx* c, int n_steps, double energy_override) {
     if (!c) return SLR_E_INVALID;

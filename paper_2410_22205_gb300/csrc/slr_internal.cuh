@@ -174,6 +174,11 @@ struct slr_ctx {
 
     bool have_cloud = false, have_d = false, have_u = false;
     int batch_chunk = 0;  // chunk of the last slr_batch_evolve this context led (autotuned or given)
+    // slr_batch_run: this job's iterations and stop reason; as the first job,
+    // the block size, graph use and autotuning trial time of the run it led
+    int batch_iters = 0, batch_converged = 0;
+    int batch_threads = 0, batch_graph = 0;
+    float batch_tuned_ms = 0.f;
     std::string err;
     long long launches = 0;
 
@@ -252,16 +257,39 @@ long long full_step_blocks(const slr_ctx* c);
 slr_status evolve_prepare(slr_ctx* c);
 slr_status evolve_launch(slr_ctx* c);
 cudaError_t launch_gather_status(slr_ctx* c, DevState* const* states, int n, int* out, cudaStream_t st);
+// a failed CUDA call of a context's operation: the message goes to the
+// context, the status is SLR_E_CUDA (slr_api.cu)
+slr_status cuda_status(slr_ctx* c, cudaError_t e, const char* where);
+// the batched persistent kernel (slr_batch.cuh) for one group of at most 64
+// jobs of one storage type: shape_io in/out (-1: autotune), graph_out,
+// tuned_ms out
+slr_status batch_run_f32(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
+                         float* tuned_ms);
+slr_status batch_run_f64(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
+                         float* tuned_ms);
 
 // ---------------------------------------------------------------------------
 // device numerics
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 
+// Global loads of the fields read by the numerics below. A per-job kernel
+// reads data that no block writes during its launch, through the read-only
+// path. The batched persistent kernel reads fields that other blocks wrote
+// earlier in the same launch, before a grid barrier; its translation unit
+// defines SLR_COHERENT_LOADS, and the loads become plain cached loads
+// (ld.global.ca), which the barrier's acquire orders after those writes.
+#ifdef SLR_COHERENT_LOADS
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) {
+    return __ldca(p);
+}
+#else
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) {
     return __ldg(p);
 }
+#endif
 
 // §3: centred difference along one axis; one-sided first order on the
 // domain boundary (the paper is silent there).

@@ -15,18 +15,9 @@
 // never re-enter, so G̃^n ⊆ G̃^{n-1} and scanning L^{n-1} finds the whole band.
 #include "slr_compact.cuh"
 #include "slr_internal.cuh"
+#include "slr_step.cuh"
 
 namespace slr {
-
-// node index -> (i, j, k); 32-bit arithmetic (grids hold at most 2^31-1 nodes)
-template <typename T>
-__device__ __forceinline__ void decode(const Params<T>& P, long long idx, int& i, int& j, int& k) {
-    const int id = (int)idx;
-    const int q = id / P.n0;
-    i = id - q * P.n0;
-    k = q / P.n1;
-    j = q - k * P.n1;
-}
 
 // fused band rebuild + SL update + cut (band mode). Work is handed out per
 // warp: a ticket is a tile of kStepTile consecutive entries of L^{n-1} (four
@@ -52,56 +43,13 @@ __global__ void __launch_bounds__(kStepBlock, (INTERP == 1 ? (sizeof(T) == 8 ? 2
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->band_count[(n + 1) & 1] = ntiles ? ds->band_next : 0;
     if (ntiles == 0) return;
     const int per = (ntiles + kRecordBlocks - 1) / kRecordBlocks;  // tiles per record-block slice
-    const unsigned lt = (1u << lane) - 1u;
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&ds->ticket, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        constexpr int H = kStepTile / 32;
-        int idx[H];
-        T v[H];
-        bool inb[H], valid[H];
-        unsigned m[H];
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            const int e = t * kStepTile + h * 32 + lane;
-            valid[h] = e < cnt_in;
-            idx[h] = valid[h] ? Lin[e] : 0;
-            v[h] = valid[h] ? uin[idx[h]] : T(0);
-            inb[h] = valid[h] && (fabs(v[h]) < P.gamma);
-            m[h] = __ballot_sync(0xffffffffu, inb[h]);
-        }
-        {
-            unsigned run = (unsigned)(ds->band_base[t / per] + tile_off[t]);
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const unsigned pos = run + __popc(m[h] & lt);
-                if (inb[h]) {
-                    if (pos < (unsigned)band_cap)
-                        Lout[pos] = idx[h];
-                    else
-                        atomicOr(&ds->error, kErrBandOffset);  // offsets not prepared for this band
-                }
-                run += (unsigned)__popc(m[h]);
-            }
-        }
-        T dabs = T(0);
-#pragma unroll 1
-        for (int h = 0; h < H; ++h) {
-            if (!valid[h]) continue;
-            T out = v[h];
-            if (inb[h]) {
-                int i, j, k;
-                decode(P, idx[h], i, j, k);
-                out = sl_update<T, DIM, INTERP>(P, uin, d, Ep, i, j, k, idx[h], v[h]);
-                out = fmin(fmax(out, -P.gamma), P.gamma);  // eq. cut
-            }
-            uout[idx[h]] = out;
-            dabs += fabs(out - v[h]);
-        }
-        dabs = warp_sum(dabs);
-        if (lane == 0) part_dphi[t] = (double)dabs;
+        band_tile<T, DIM, INTERP>(P, uin, uout, d, Lin, Lout, tile_off, ds->band_base, band_cap, cnt_in, per, t, Ep,
+                                  part_dphi, ds);
     }
 }
 

@@ -31,7 +31,7 @@ SLR_FIELD_U, SLR_FIELD_D, SLR_FIELD_ARGMIN = 0, 1, 2
 EXPORTS = [
     "slr_config_default", "slr_create", "slr_load_cloud", "slr_build_distance", "slr_build_distance_fsm",
     "slr_set_distance", "slr_init_u",
-    "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_batch_chunk", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
+    "slr_step", "slr_step_async", "slr_evolve", "slr_batch_evolve", "slr_batch_chunk", "slr_batch_run", "slr_batch_run_info", "slr_extract", "slr_get_field", "slr_get_band", "slr_energy", "slr_diagnostics",
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches", "slr_brick_shape", "slr_brick_shape_set", "slr_probe_fma",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error", "slr_selftest_barrier",
@@ -144,6 +144,8 @@ def lib():
                 "slr_evolve": (C.c_int, [_vp, _ip, _ip]),
                 "slr_batch_evolve": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
                 "slr_batch_chunk": (C.c_int, [_vp]),
+                "slr_batch_run": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
+                "slr_batch_run_info": (C.c_int, [_vp, _ip, _ip, C.POINTER(C.c_float)]),
                 "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
                 "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
                 "slr_get_band": (C.c_int, [_vp, _i64p, C.c_int64, _i64p]),
@@ -354,6 +356,26 @@ def slr_batch_evolve(ctxs, chunk=8, stream=None):
     s = lib().slr_batch_evolve(arr, n, int(chunk), C.c_void_p(stream) if stream else None, it, cv)
     _check(ctxs[0] if n else None, s)
     return list(it), [bool(x) for x in cv]
+
+
+def slr_batch_run(ctxs, autotune=True, stream=None):
+    """Evolve several narrow-band contexts together in one persistent kernel
+    launch (graph-captured); returns (iters, converged) per context."""
+    n = len(ctxs)
+    arr = (_vp * n)(*ctxs)
+    it = (C.c_int * n)()
+    cv = (C.c_int * n)()
+    s = lib().slr_batch_run(arr, n, 1 if autotune else 0, C.c_void_p(stream) if stream else None, it, cv)
+    _check(ctxs[0] if n else None, s)
+    return list(it), [bool(x) for x in cv]
+
+
+def slr_batch_run_info(ctx):
+    """(threads per block, graph-captured, autotuner's best trial ms) of the
+    last slr_batch_run that ctx led."""
+    th, gr, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
+    _check(ctx, lib().slr_batch_run_info(ctx, C.byref(th), C.byref(gr), C.byref(ms)))
+    return th.value, bool(gr.value), ms.value
 
 
 def slr_batch_chunk(ctx):
