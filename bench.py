@@ -704,7 +704,7 @@ def run_batched(args, slr, torch):
     torch.cuda.synchronize()
     t_psetup = time.perf_counter() - t0
     pits, _ = slr.slr_batch_run([r.ctx for r in recs], autotune=True)
-    threads, graph, tuned_ms = slr.slr_batch_run_info(recs[0].ctx)
+    shape = slr.slr_batch_run_info(recs[0].ctx)
     t_pevolve = time.perf_counter() - t0 - t_psetup
     per_state = []
     for j, r in zip(jobs, recs):
@@ -721,8 +721,7 @@ def run_batched(args, slr, torch):
             "batched": {"reconstructions_per_s": len(jobs) / t_bat, "seconds": t_bat, "setup_s": t_setup,
                         "evolve_s": t_evolve, "chunk": chunk},
             "persistent": {"reconstructions_per_s": len(jobs) / t_per, "seconds": t_per, "setup_s": t_psetup,
-                           "evolve_s": t_pevolve, "threads_per_block": threads, "graph_captured": bool(graph),
-                           "autotune_trial_ms": tuned_ms, "identical_results": bool(psame)},
+                           "evolve_s": t_pevolve, "launch_shape": shape, "identical_results": bool(psame)},
             "speedup": t_seq / t_bat, "speedup_persistent": t_seq / t_per, "identical_results": bool(same),
             "iterations": its,
             "input_generation_s": gen_s}

@@ -204,8 +204,10 @@ int slr_batch_chunk(const slr_ctx* first_job);
  * reinitialisation off, energy_R = 5 in 3-D (else SLR_E_INVALID: use
  * slr_batch_evolve, which takes any job); FP32 and FP64 jobs run as separate
  * launches, at most 64 jobs per launch. autotune != 0: the first launches
- * time the block sizes (128 and 256 threads, two iterations each, twice)
- * and the rest of the batch keeps the faster; 0: 128 threads. `cuda_stream`
+ * time five launch shapes (128 threads at two register budgets with one or
+ * two bricks per step item, 256 threads with one; one iteration each,
+ * twice) and the rest of the batch keeps the fastest; 0: the first shape
+ * (128 threads, one brick per item). `cuda_stream`
  * (NULL: the first job's stream) orders the launches; every job's own stream
  * is synchronised first. iters_out / converged_out: n_jobs entries each, may
  * be NULL. SLR_E_TIMEOUT if a grid barrier waited longer than its poll limit
@@ -214,11 +216,14 @@ int slr_batch_chunk(const slr_ctx* first_job);
 slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* cuda_stream, int* iters_out,
                          int* converged_out);
 
-/* The last slr_batch_run whose first job was first_job: threads per block
- * (128 or 256), whether its launches ran as captured CUDA graphs (1) or were
- * enqueued directly where capture was refused (0), and the autotuner's best
- * trial time in ms (0 without autotuning). Any pointer may be NULL. */
-slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* graph, float* tuned_ms);
+/* The last slr_batch_run whose first job was first_job: the launch shape
+ * it ran with (threads per block, resident blocks per SM, bricks of a 3-D
+ * job per step item), whether its launches ran as captured CUDA graphs (1)
+ * or were enqueued directly where capture was refused (0), and the
+ * autotuner's best trial time in ms (0 without autotuning). Any pointer may
+ * be NULL. */
+slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* blocks_per_sm, int* bricks_per_item,
+                              int* graph, float* tuned_ms);
 
 /* Nodes with |φ| < width, in ascending linear index (the reconstructed zero
  * level set's neighbourhood). idx/u: caller buffers of `cap` entries (either

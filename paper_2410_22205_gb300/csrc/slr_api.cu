@@ -740,7 +740,7 @@ slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* c
     DeviceGuard g(dev);
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c0->stream;
     // groups of one storage type and at most 64 jobs, in the caller's order
-    int shape = -1, graph = 1;
+    int shape = -1, graph = 1, threads = 0, blocks = 0, bpi = 0;
     float tuned = 0.f;
     for (int prec : {32, 64}) {
         std::vector<slr_ctx*> grp;
@@ -748,10 +748,11 @@ slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* c
             if (jobs[j]->cfg.precision == prec) grp.push_back(jobs[j]);
         for (size_t b = 0; b < grp.size(); b += 64) {
             const int m = (int)std::min<size_t>(64, grp.size() - b);
-            int sh = autotune ? -1 : 0, gr = 0;
+            int sh = autotune ? -1 : 0, gr = 0, th = 0, bl = 0, bp = 0;
             float tm = 0.f;
-            const slr_status s = prec == 32 ? batch_run_f32(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm)
-                                            : batch_run_f64(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm);
+            const slr_status s = prec == 32
+                                     ? batch_run_f32(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm, &th, &bl, &bp)
+                                     : batch_run_f64(grp.data() + b, m, autotune != 0, st, &sh, &gr, &tm, &th, &bl, &bp);
             if (s == SLR_E_TIMEOUT) return fail(c0, s, "batch_run: a grid barrier of the batched kernel waited too long");
             if (s == SLR_E_STATE) return fail(c0, s, "batch_run: a device-side check failed in a job");
             if (s == SLR_E_NOMEM) return fail(c0, s, "batch_run: allocation failed");
@@ -762,11 +763,16 @@ slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* c
             if (shape < 0) {
                 shape = sh;
                 tuned = tm;
+                threads = th;
+                blocks = bl;
+                bpi = bp;
             }
             graph = graph && gr;
         }
     }
-    c0->batch_threads = shape == 1 ? 256 : 128;
+    c0->batch_threads = threads;
+    c0->batch_blocks = blocks;
+    c0->batch_bpi = bpi;
     c0->batch_graph = graph;
     c0->batch_tuned_ms = tuned;
     for (int j = 0; j < n_jobs; ++j) {
@@ -776,9 +782,12 @@ slr_status slr_batch_run(slr_ctx* const* jobs, int n_jobs, int autotune, void* c
     return SLR_OK;
 }
 
-slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* graph, float* tuned_ms) {
+slr_status slr_batch_run_info(const slr_ctx* first_job, int* threads, int* blocks_per_sm, int* bricks_per_item,
+                              int* graph, float* tuned_ms) {
     if (!first_job) return SLR_E_INVALID;
     if (threads) *threads = first_job->batch_threads;
+    if (blocks_per_sm) *blocks_per_sm = first_job->batch_blocks;
+    if (bricks_per_item) *bricks_per_item = first_job->batch_bpi;
     if (graph) *graph = first_job->batch_graph;
     if (tuned_ms) *tuned_ms = first_job->batch_tuned_ms;
     return SLR_OK;

@@ -4,26 +4,32 @@
 // Every job is one run of Algorithm 1's loop (arXiv 2410.22205, §3: step 4,
 // the SL update of §3.1-§3.2 with the band and cut of §3.8, then the energy
 // of §3.5 and the stop test of §4 eq. deltaEn), without the
-// reinitialisation. The kernel advances all jobs together, iteration by
-// iteration, in three phases separated by grid barriers:
-//   0. step:   one work item per active brick of a 3-D job (the brick step
-//              of slr_brick.cuh) or per NT/32 tiles of 128 band-list
-//              entries of a 2-D job (the list step of slr_step.cuh);
-//   1. energy: one work item per slot of 1024 candidate cells of every job,
-//              plus, for a 2-D job, its tiles' band-member counts;
-//   2. record: kRecordBlocks slices per job; the block that finishes a
-//              job's last slice does its bookkeeping and stop test.
-// Blocks take work items from one ticket counter; a phase's items are the
-// concatenation of the running jobs' items (jobs whose stop test has fired
-// have none), so large and small jobs share the GPU without one launch per
-// job. The barriers give up after a poll limit and report kErrBarrier,
-// which the host returns as SLR_E_TIMEOUT.
+// reinitialisation. One iteration of a job is three phases of work items:
+//   0. step:   one item per active brick of a 3-D job (the brick step of
+//              slr_brick.cuh), or per NT/32 tiles of 128 band-list entries
+//              of a 2-D job (the list step of slr_step.cuh);
+//   1. energy: one item per slot of 1024 candidate cells, after, for a 2-D
+//              job, the items that count its tiles' band members;
+//   2. record: kRecordBlocks slices; the block that finishes a job's last
+//              slice does its bookkeeping and stop test.
+// The items of all jobs form one ticket sequence, iteration by iteration and
+// phase by phase (jobs in a fixed order inside a phase), and the blocks of
+// the launch take tickets from one counter. An item waits only for its own
+// job: a step item for the job's record of the previous iteration, an
+// energy item for all of the job's step items, a record item for all of its
+// energy items (per-job completion counters). Every wait is on items with
+// smaller tickets, taken by blocks that are resident (a cooperative launch),
+// so the sequence always advances; jobs are at different phases at the same
+// time and no grid-wide barrier exists. A wait gives up after a poll limit
+// and reports kErrBarrier, which the host returns as SLR_E_TIMEOUT. Items of
+// a job whose stop test has fired are no-ops, and the blocks leave once every
+// job has stopped.
 //
 // The per-item device code is the per-job kernels' own (brick_compute,
 // band_tile, energy_slot, tile_count, record_slice), compiled like them
 // without implicit FMA contraction and with the reductions' summation trees
 // kept, so each job's results are bit-identical to its solo run. Fields that
-// other blocks wrote before a barrier are read with coherent loads
+// other blocks wrote before a wait are read with coherent loads
 // (SLR_COHERENT_LOADS, L2 loads of the partials, TMA after a proxy fence).
 #pragma once
 
@@ -67,31 +73,30 @@ struct BatchHot {
     double* part_dphi;
     int band_cap;
     int dim, interp;
+    int ntc;            // 2-D: tile-count items that open its energy phase
 };
 
 template <typename T>
 struct BatchParams {
     BatchHot<T> job[kBatchMaxJobs];
+    int pre[3][kBatchMaxJobs + 1];  // per phase: prefix over jobs of the items of one iteration
+    long long per_iter;             // items of one iteration (all phases)
 };
 static_assert(sizeof(BatchParams<double>) + 64 <= 32764, "batch parameters fit the kernel-parameter space");
 
-// per-job data read rarely: in global memory (tensor maps 64-byte aligned)
-struct __align__(64) BatchCold {
+// per-job data read rarely: in global memory (CUtensorMap carries its own alignment)
+struct BatchCold {
     CUtensorMap tm[3];  // u buffer 0, u buffer 1, d (3-D jobs staged by TMA)
     RecordArgs rec;
 };
 
 struct BatchCtl {
-    unsigned bar[2];           // grid barrier: arrivals, generation
-    int err;                   // kErrBarrier / kErrStage
-    int iters;                 // iterations this launch ran (block 0)
-    unsigned long long ticket; // work-item tickets of all phases of the launch
-};
-
-// block size x resident blocks per SM the register budget allows
-template <typename T, int NT>
-struct BatchOcc {
-    static constexpr int v = sizeof(T) == 4 ? 768 / NT : (NT == 128 ? 3 : 1);
+    unsigned long long ticket;     // next work item of the launch
+    int err;                       // kErrBarrier / kErrStage
+    int pad;
+    int step_done[kBatchMaxJobs];  // per job: step items completed in this launch
+    int energy_done[kBatchMaxJobs];
+    int rec_done[kBatchMaxJobs];   // per job: iterations whose record is complete
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -105,72 +110,62 @@ __device__ __forceinline__ X vload(const X* p) {
     return *(const volatile X*)p;
 }
 
-// Grid-wide barrier of the cooperative launch (the protocol of grid_barrier,
-// with its result word in dynamic shared memory: the kernel keeps no static
-// shared memory, so that six blocks of 128 threads fit an SM). A wait
-// longer than the poll limit, or an error bit set by another block, makes
-// every block see false.
-__device__ __forceinline__ bool batch_barrier(unsigned* bar, int* err, int* s_ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long polls = 0;
-            while (*vgen == gen) {
-                if (++polls > kBarrierSpinLimit || (*(volatile int*)err & kErrBarrier)) {
-                    ok = 0;
-                    atomicOr(err, kErrBarrier);
-                    break;
-                }
-                __nanosleep(64);
-            }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: wait until *cnt >= need (an acquire load: the counted items'
+// writes are visible after it), the job has stopped, or another block
+// reported an error; false after the poll limit (kErrBarrier is then set
+// for every block to see).
+__device__ __forceinline__ bool batch_wait(const int* cnt, int need, const DevState* ds, int* err) {
+    long long polls = 0;
+    while (ld_acquire(cnt) < need) {
+        if (ld_acquire(&ds->stop)) return true;
+        if (vload(err) & kErrBarrier) return false;
+        if (++polls > kBarrierSpinLimit) {
+            atomicOr(err, kErrBarrier);
+            return false;
         }
-        __threadfence();
-        *s_ok = ok;
+        __nanosleep(64);
     }
-    __syncthreads();
-    return *s_ok != 0;
+    return true;
 }
 
-// work items of job J in phase ph (0 while its stop flag is set)
-template <typename T, int NT>
-__device__ __forceinline__ int batch_items(const BatchHot<T>& J, int ph) {
-    constexpr int W = NT / 32;
-    const DevState* ds = J.ds;
-    if (vload(&ds->stop)) return 0;
-    if (ph == 2) return kRecordBlocks;
-    if (J.dim == 3) return ph == 0 ? J.A.nbricks : J.nslots;
-    const int n = vload(&ds->n);
-    if (ph == 0) {
-        // at least one item: item 0 also publishes the size of the band it writes
-        const int nt = (vload(&ds->band_count[n & 1]) + kStepTile - 1) / kStepTile;
-        const int it = (nt + W - 1) / W;
-        return it > 0 ? it : 1;
-    }
-    const int nt = (vload(&ds->band_count[(n + 1) & 1]) + kStepTile - 1) / kStepTile;
-    return (nt + W - 1) / W + J.nslots;
-}
+// item words in shared memory (the brick step's ticket area, 32 bytes)
+enum {
+    kItJob = 0,  // job of the current item
+    kItLoc,      // its index within the job's items of the phase
+    kItPhIt,     // phase | iteration << 2 (iteration -1: past the launch's end)
+    kItFlags,    // kFlOk: wait passed / staged; kFlStop: the job has stopped; kFlPar: staging parity
+    kItKey,      // the last (iteration, phase, job) whose wait this block passed
+    kItDone,     // completion to publish for the previous item: step j, energy 64 + j, or -1
+    kItTk0,      // two ticket slots: the current ticket and the next one, by turns
+    kItTk1
+};
+enum { kFlOk = 1, kFlStop = 2, kFlPar = 4 };
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, BatchOcc<T, NT>::v)
+// One launch shape of the batch kernel: NT threads per block, OCC resident
+// blocks per SM asked of the register allocator (80 registers at NT = 128,
+// OCC = 6 in FP32; 96 at OCC = 5), and bpi bricks per step item of a 3-D job
+// (a run-time argument). Thread 0 decodes the current ticket and waits for
+// its dependency while thread 32 publishes the previous item's completion
+// and thread 64 takes the next ticket, so the three latencies overlap.
+template <typename T, int NT, int OCC>
+__global__ void __launch_bounds__(NT, OCC)
     k_batch(const __grid_constant__ BatchParams<T> BP, const BatchCold* __restrict__ cold, BatchCtl* ctl, int njobs,
-            int max_iters) {
+            int max_iters, int bpi) {
     using S = BrickSmem<T, 1>;
     using G = BoxGeom;
     constexpr int W = NT / 32;
+    static_assert(NT >= 96, "three threads in distinct warps run the item bookkeeping");
     static_assert(sizeof(EnergyWs<T>) <= S::kBar && sizeof(RecordWs) <= S::kBar, "workspaces fit the brick area");
+    static_assert(kItTk1 < 8, "item words fit the ticket area");
     extern __shared__ __align__(128) unsigned char smem[];
     // [0, kBar): one item's scratch (brick boxes and lists, or the energy or
-    // record workspace); kBar: the staging barrier; kTicket: the item (job,
-    // index) and the grid barrier's result; kBytes: the prefix of the jobs'
-    // item counts
+    // record workspace); kBar: the staging barrier; kTicket: the item words
     T* su = reinterpret_cast<T*>(smem);
     T* sd = reinterpret_cast<T*>(smem + G::BoxN * (int)sizeof(T));
     unsigned short* s_list = reinterpret_cast<unsigned short*>(smem + S::kList);
@@ -178,8 +173,7 @@ __global__ void __launch_bounds__(NT, BatchOcc<T, NT>::v)
     int* s_cnt = reinterpret_cast<int*>(smem + S::kCnt);
     EnergyWs<T>& ews = *reinterpret_cast<EnergyWs<T>*>(smem);
     RecordWs& rws = *reinterpret_cast<RecordWs*>(smem);
-    int* s_item = reinterpret_cast<int*>(smem + S::kTicket);
-    int* s_pre = reinterpret_cast<int*>(smem + S::kBytes);
+    int* s_it = reinterpret_cast<int*>(smem + S::kTicket);
     const unsigned bar = smem_addr(smem + S::kBar);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
@@ -188,191 +182,248 @@ __global__ void __launch_bounds__(NT, BatchOcc<T, NT>::v)
         for (int j = 0; j < njobs; ++j)
             if (BP.job[j].dim == 3 && BP.job[j].A.tma)
                 for (int m = 0; m < 3; ++m) fence_tensormap_acquire(&cold[j].tm[m]);
+        s_it[kItFlags] = 0;
+        s_it[kItKey] = -1;
+        s_it[kItDone] = -1;
+        s_it[kItTk0] = (int)atomicAdd(&ctl->ticket, 1u);
     }
     __syncthreads();
-    unsigned long long tbase = 0;  // tickets taken before this phase (the same in every block)
-    unsigned tpar = 0;             // thread 0: parity of the staging barrier's next completion
-    int it = 0;
-    for (; it < max_iters; ++it) {
-        bool any = true;
-        for (int ph = 0; ph < 3 && any; ++ph) {
-            if (tid < njobs) s_pre[tid + 1] = batch_items<T, NT>(BP.job[tid], ph);
-            __syncthreads();
-            if (tid == 0) {
-                s_pre[0] = 0;
-                for (int j = 1; j <= njobs; ++j) s_pre[j] += s_pre[j - 1];
-            }
-            __syncthreads();
-            const int total = s_pre[njobs];
-            if (ph == 0 && total == 0) {
-                any = false;  // every job has stopped (every block sees the same state)
-                break;
-            }
-            for (;;) {
-                if (tid == 0) {
-                    const long long t = (long long)(atomicAdd(&ctl->ticket, 1ull) - tbase);
-                    int jj = -1, loc = 0;
-                    if (t < total) {
-                        int lo = 0, hi = njobs;  // s_pre[lo] <= t < s_pre[hi]
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (s_pre[mid] <= t)
-                                lo = mid;
-                            else
-                                hi = mid;
-                        }
-                        jj = lo;
-                        loc = (int)(t - s_pre[lo]);
+    const unsigned end = (unsigned)max_iters * (unsigned)BP.per_iter;  // the host keeps it below 2^31
+    int cur_iter = -1;
+    for (int slot = 0;; slot ^= 1) {
+        if (tid == 0) {
+            // ---- decode the current ticket: iteration, phase, job, index ----
+            const unsigned t = (unsigned)s_it[kItTk0 + slot];
+            int iter = -1, ph = 0, j = 0, r = 0;
+            if (t < end) {
+                iter = (int)(t / (unsigned)BP.per_iter);
+                r = (int)(t - (unsigned)iter * (unsigned)BP.per_iter);
+                if (r >= BP.pre[0][njobs]) {
+                    r -= BP.pre[0][njobs];
+                    ph = 1;
+                    if (r >= BP.pre[1][njobs]) {
+                        r -= BP.pre[1][njobs];
+                        ph = 2;
                     }
-                    s_item[0] = jj;
-                    s_item[1] = loc;
                 }
-                __syncthreads();
-                const int j = s_item[0], loc = s_item[1];
-                if (j < 0) break;
-                const BatchHot<T>& J = BP.job[j];
-                DevState* ds = J.ds;
-                const int n = vload(&ds->n);
-                if (ph == 0 && J.dim == 3) {
-                    // ---- a brick of a 3-D job ----
-                    const Params<T> P = J.P;
-                    const BrickArgs<T> A = J.A;
-                    const int b = __ldg(A.bricks + loc);
-                    if (__ldcg(A.bcnt + b) != 0) {
-                        const T* uin = (n & 1) ? J.ub1 : J.ub0;
-                        T* uout = (n & 1) ? J.ub0 : J.ub1;
-                        const T Ep = (T)vload(&ds->Ep);
-                        const T invEp = Ep > T(0) ? T(1) / Ep : T(0);
-                        const int bxi = b % A.nbx, q = b / A.nbx;
-                        const int ox = bxi * kBX - kHalo, oy = (q % A.nby) * kBY - kHalo, oz = (q / A.nby) * kBZ - kHalo;
-                        bool staged = true;
-                        if (A.tma) {
-                            if (tid == 0) {
-                                // the boxes' rows were written through the generic proxy
-                                // by other blocks before the last barrier, and this
-                                // block's generic accesses of the scratch area ended at
-                                // the last block barrier
-                                fence_proxy_async_global();
-                                fence_proxy_async();
-                                mbar_expect_tx(bar, (unsigned)((G::BoxN + G::DBoxN) * sizeof(T)));
-                                tma_load_3d(smem_addr(su), &cold[j].tm[n & 1], bar, ox, oy, oz);
-                                tma_load_3d(smem_addr(sd), &cold[j].tm[2], bar, ox, oy + kHalo - 1, oz + kHalo - 1);
-                                long long w = 0;
-                                while (!mbar_try_wait(bar, tpar) && ++w < kStageWaitLimit) {
-                                }
-                                staged = w < kStageWaitLimit;
-                                if (!staged) {
-                                    long long w2 = 0;  // the copies in flight: a second bounded wait
-                                    while (!mbar_try_wait(bar, tpar) && ++w2 < kStageWaitLimit) {
-                                    }
-                                }
-                                tpar ^= 1u;
-                            }
-                        } else {
-                            brick_stage_copy<T, NT>(P, uin, J.d, su, sd, ox, oy, oz);
-                        }
-                        if (__syncthreads_or(!staged)) {
-                            if (tid == 0) {
-                                atomicOr(&ds->error, kErrStage);
-                                atomicOr(&ctl->err, kErrStage | kErrBarrier);  // the other blocks leave their barrier
-                            }
-                            return;
-                        }
-                        if (J.interp)
-                            brick_compute<T, 1, 1, NT>(P, A, su, sd, uin, uout, J.d, ds, Ep, invEp, b, ox, oy, oz,
-                                                       s_list, s_abs, s_cnt);
-                        else
-                            brick_compute<T, 0, 1, NT>(P, A, su, sd, uin, uout, J.d, ds, Ep, invEp, b, ox, oy, oz,
-                                                       s_list, s_abs, s_cnt);
-                    }
-                } else if (ph == 0) {
-                    // ---- NT/32 tiles of a 2-D job's band list, one per warp ----
-                    const Params<T> P = J.P;
-                    const int cnt_in = vload(&ds->band_count[n & 1]);
-                    const int ntiles = (cnt_in + kStepTile - 1) / kStepTile;
-                    if (loc == 0 && tid == 0) ds->band_count[(n + 1) & 1] = ntiles ? vload(&ds->band_next) : 0;
-                    const int t = loc * W + warp;
-                    if (t < ntiles) {
-                        const T* uin = (n & 1) ? J.ub1 : J.ub0;
-                        T* uout = (n & 1) ? J.ub0 : J.ub1;
-                        const int* Lin = (n & 1) ? J.L1 : J.L0;
-                        int* Lout = (n & 1) ? J.L0 : J.L1;
-                        const T Ep = (T)vload(&ds->Ep);
-                        const int per = (ntiles + kRecordBlocks - 1) / kRecordBlocks;
-                        if (J.interp)
-                            band_tile<T, 2, 1>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap,
-                                               cnt_in, per, t, Ep, J.part_dphi, ds);
-                        else
-                            band_tile<T, 2, 0>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap,
-                                               cnt_in, per, t, Ep, J.part_dphi, ds);
-                    }
-                } else if (ph == 1) {
-                    // ---- energy slots (and a 2-D job's tile counts) on u^{n+1} ----
-                    const Params<T> P = J.P;
-                    const EnergyArgs<T> E = J.E;
-                    const int sel = (n + 1) & 1;
-                    const T* u = sel ? J.ub1 : J.ub0;
-                    if (J.dim == 3) {
-                        if (J.interp)
-                            energy_slot<T, 3, 1, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
-                        else
-                            energy_slot<T, 3, 0, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
-                    } else {
-                        const int nb = vload(&ds->band_count[sel]);
-                        const int ntb = (nb + kStepTile - 1) / kStepTile;
-                        const int ntc = (ntb + W - 1) / W;
-                        if (loc < ntc) {
-                            const int t = loc * W + warp;
-                            if (t < ntb) tile_count<T>(P, u, sel ? J.L1 : J.L0, nb, t, J.tile_off);
-                        } else if (J.interp) {
-                            energy_slot<T, 2, 1, 0, NT>(P, u, J.d, J.cells, J.ncells, loc - ntc, E, J.part_e, ews);
-                        } else {
-                            energy_slot<T, 2, 0, 0, NT>(P, u, J.d, J.cells, J.ncells, loc - ntc, E, J.part_e, ews);
-                        }
-                    }
+                int lo = 0, hi = njobs;  // pre[ph][lo] <= r < pre[ph][hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (BP.pre[ph][mid] <= r)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                j = lo;
+                r -= BP.pre[ph][lo];
+                // ---- wait for this job's previous phase (once per iteration,
+                // phase and job in a block: the job's stop flag cannot change
+                // meanwhile) ----
+                const int key = (iter * 3 + ph) * kBatchMaxJobs + j;
+                int fl = s_it[kItFlags] & kFlPar;
+                if (key == s_it[kItKey]) {
+                    fl |= kFlOk | (s_it[kItFlags] & kFlStop);
                 } else {
-                    // ---- a record slice ----
-                    record_slice<NT>(cold[j].rec, ds, loc, kRecordBlocks, rws);
+                    const DevState* ds = BP.job[j].ds;
+                    bool ok;
+                    if (ph == 0)
+                        ok = iter == 0 || batch_wait(&ctl->rec_done[j], iter, ds, &ctl->err);
+                    else if (ph == 1)
+                        ok = batch_wait(&ctl->step_done[j], (iter + 1) * (BP.pre[0][j + 1] - BP.pre[0][j]), ds,
+                                        &ctl->err);
+                    else
+                        ok = batch_wait(&ctl->energy_done[j], (iter + 1) * (BP.pre[1][j + 1] - BP.pre[1][j]), ds,
+                                        &ctl->err);
+                    fl |= (ok ? kFlOk : 0) | (ld_acquire(&ds->stop) ? kFlStop : 0);
+                    s_it[kItKey] = ok ? key : -1;
                 }
-                __syncthreads();
+                s_it[kItFlags] = fl;
             }
-            tbase += (unsigned long long)total + gridDim.x;  // every block took one ticket past the end
-            if (!batch_barrier(ctl->bar, &ctl->err, s_item + 2)) return;
+            s_it[kItPhIt] = ph | (iter << 2);
+            s_it[kItJob] = j;
+            s_it[kItLoc] = r;
+        } else if (tid == 32) {
+            // ---- the previous item's completion: its writes ended at the
+            // last block barrier; fence, then count it (release) ----
+            const int dn = s_it[kItDone];
+            if (dn >= 0) {
+                __threadfence();
+                atomicAdd(dn < kBatchMaxJobs ? &ctl->step_done[dn] : &ctl->energy_done[dn - kBatchMaxJobs], 1);
+                s_it[kItDone] = -1;
+            }
+        } else if (tid == 64) {
+            // ---- the next ticket; it depends on nothing the current item
+            // produces (waits point to smaller tickets only) ----
+            s_it[kItTk0 + (slot ^ 1)] = (int)atomicAdd(&ctl->ticket, 1u);
         }
-        if (!any) break;
+        __syncthreads();
+        const int phit = s_it[kItPhIt];
+        const int iter = phit >> 2;
+        if (iter < 0) break;  // past the launch's last iteration
+        if (iter != cur_iter) {
+            // a new iteration for this block: leave if every job has stopped
+            cur_iter = iter;
+            if (__syncthreads_and(tid >= njobs || vload(&BP.job[tid].ds->stop) != 0)) break;
+        }
+        if (!(s_it[kItFlags] & kFlOk)) return;
+        const int ph = phit & 3, j = s_it[kItJob], loc = s_it[kItLoc];
+        const BatchHot<T>& J = BP.job[j];
+        DevState* ds = J.ds;
+        if (!(s_it[kItFlags] & kFlStop)) {
+            const int n = vload(&ds->n);
+            if (ph == 0 && J.dim == 3) {
+                // ---- bpi bricks of a 3-D job ----
+                const Params<T>& P = J.P;
+                const BrickArgs<T>& A = J.A;
+                const int b_end = min((loc + 1) * bpi, A.nbricks);
+                for (int bq = loc * bpi; bq < b_end; ++bq) {
+                    const int b = __ldg(A.bricks + bq);
+                    if (__ldcg(A.bcnt + b) == 0) continue;
+                    const T* uin = (n & 1) ? J.ub1 : J.ub0;
+                    T* uout = (n & 1) ? J.ub0 : J.ub1;
+                    const T Ep = (T)vload(&ds->Ep);
+                    const T invEp = Ep > T(0) ? T(1) / Ep : T(0);
+                    const int bxi = b % A.nbx, q = b / A.nbx;
+                    const int ox = bxi * kBX - kHalo, oy = (q % A.nby) * kBY - kHalo, oz = (q / A.nby) * kBZ - kHalo;
+                    if (A.tma) {
+                        if (tid == 0) {
+                            // the boxes' rows were written through the generic proxy
+                            // by other blocks before the wait, and this block's
+                            // generic accesses of the scratch area ended at the last
+                            // block barrier
+                            fence_proxy_async_global();
+                            fence_proxy_async();
+                            mbar_expect_tx(bar, (unsigned)((G::BoxN + G::DBoxN) * sizeof(T)));
+                            tma_load_3d(smem_addr(su), &cold[j].tm[n & 1], bar, ox, oy, oz);
+                            tma_load_3d(smem_addr(sd), &cold[j].tm[2], bar, ox, oy + kHalo - 1, oz + kHalo - 1);
+                            const int fl = s_it[kItFlags];
+                            const unsigned par = (fl & kFlPar) ? 1u : 0u;
+                            long long w = 0;
+                            while (!mbar_try_wait(bar, par) && ++w < kStageWaitLimit) {
+                            }
+                            const bool staged = w < kStageWaitLimit;
+                            if (!staged) {
+                                long long w2 = 0;  // the copies in flight: a second bounded wait
+                                while (!mbar_try_wait(bar, par) && ++w2 < kStageWaitLimit) {
+                                }
+                            }
+                            s_it[kItFlags] = ((fl ^ kFlPar) & ~kFlOk) | (staged ? kFlOk : 0);
+                        }
+                    } else {
+                        brick_stage_copy<T, NT>(P, uin, J.d, su, sd, ox, oy, oz);
+                    }
+                    __syncthreads();
+                    if (!(s_it[kItFlags] & kFlOk)) {
+                        if (tid == 0) {
+                            atomicOr(&ds->error, kErrStage);
+                            atomicOr(&ctl->err, kErrStage | kErrBarrier);  // the waiting blocks leave
+                        }
+                        return;
+                    }
+                    if (J.interp)
+                        brick_compute<T, 1, 1, NT>(P, A, su, sd, uin, uout, J.d, ds, Ep, invEp, b, ox, oy, oz,
+                                                   s_list, s_abs, s_cnt);
+                    else
+                        brick_compute<T, 0, 1, NT>(P, A, su, sd, uin, uout, J.d, ds, Ep, invEp, b, ox, oy, oz,
+                                                   s_list, s_abs, s_cnt);
+                    __syncthreads();  // the boxes are free for the next brick
+                }
+            } else if (ph == 0) {
+                // ---- NT/32 tiles of a 2-D job's band list, one per warp ----
+                const Params<T>& P = J.P;
+                const int cnt_in = vload(&ds->band_count[n & 1]);
+                const int ntiles = (cnt_in + kStepTile - 1) / kStepTile;
+                if (loc == 0 && tid == 0) ds->band_count[(n + 1) & 1] = ntiles ? vload(&ds->band_next) : 0;
+                const int t = loc * W + warp;
+                if (t < ntiles) {
+                    const T* uin = (n & 1) ? J.ub1 : J.ub0;
+                    T* uout = (n & 1) ? J.ub0 : J.ub1;
+                    const int* Lin = (n & 1) ? J.L1 : J.L0;
+                    int* Lout = (n & 1) ? J.L0 : J.L1;
+                    const T Ep = (T)vload(&ds->Ep);
+                    const int per = (ntiles + kRecordBlocks - 1) / kRecordBlocks;
+                    if (J.interp)
+                        band_tile<T, 2, 1>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap, cnt_in,
+                                           per, t, Ep, J.part_dphi, ds);
+                    else
+                        band_tile<T, 2, 0>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap, cnt_in,
+                                           per, t, Ep, J.part_dphi, ds);
+                }
+            } else if (ph == 1) {
+                // ---- energy slots (after a 2-D job's tile counts) on u^{n+1} ----
+                const Params<T>& P = J.P;
+                const EnergyArgs<T>& E = J.E;
+                const int sel = (n + 1) & 1;
+                const T* u = sel ? J.ub1 : J.ub0;
+                if (J.dim == 3) {
+                    if (J.interp)
+                        energy_slot<T, 3, 1, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
+                    else
+                        energy_slot<T, 3, 0, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
+                } else if (loc < J.ntc) {
+                    const int nb = vload(&ds->band_count[sel]);
+                    const int t = loc * W + warp;
+                    if (t < (nb + kStepTile - 1) / kStepTile) tile_count<T>(P, u, sel ? J.L1 : J.L0, nb, t, J.tile_off);
+                } else if (J.interp) {
+                    energy_slot<T, 2, 1, 0, NT>(P, u, J.d, J.cells, J.ncells, loc - J.ntc, E, J.part_e, ews);
+                } else {
+                    energy_slot<T, 2, 0, 0, NT>(P, u, J.d, J.cells, J.ncells, loc - J.ntc, E, J.part_e, ews);
+                }
+            } else {
+                // ---- a record slice; the last one completes the iteration ----
+                const bool last = record_slice<NT>(cold[j].rec, ds, loc, kRecordBlocks, rws);
+                if (last && tid == 0) {
+                    __threadfence();
+                    atomicAdd(&ctl->rec_done[j], 1);
+                }
+            }
+        }
+        // this item's completion, published by thread 32 at the top of the
+        // next pass (after the barrier below; every way out of the loop
+        // passes through that top)
+        if (tid == 0) s_it[kItDone] = ph == 0 ? j : (ph == 1 ? kBatchMaxJobs + j : -1);
+        __syncthreads();
     }
-    if (blockIdx.x == 0 && tid == 0) ctl->iters = it;
 }
 
-// dynamic shared memory of k_batch<T, NT>
+// dynamic shared memory of k_batch
 template <typename T>
 constexpr int batch_smem() {
-    return BrickSmem<T, 1>::kBytes + (kBatchMaxJobs + 1) * (int)sizeof(int);
+    return BrickSmem<T, 1>::kBytes;
 }
 
 // ---------------------------------------------------------------------------
 // host side: one group of at most kBatchMaxJobs jobs of storage type T
 // ---------------------------------------------------------------------------
-constexpr int kBatchShapes = 2;
-constexpr int kBatchNT[kBatchShapes] = {128, 256};
-constexpr int kBatchTuneIters = 2;      // iterations of each autotuning launch
+// Launch shapes the autotuner chooses between: threads per block, resident
+// blocks per SM (the register budget: FP32 80 or 96 registers at 128
+// threads; FP64 168 or 255), bricks per step item
+constexpr int kBatchShapes = 5;
+struct BatchShape {
+    int nt, inst, bpi;  // inst: 0 = <128, hi occ>, 1 = <128, lo occ>, 2 = <256, ...>
+};
+constexpr BatchShape kBatchShape[kBatchShapes] = {{128, 0, 1}, {128, 0, 2}, {128, 1, 1}, {128, 1, 2}, {256, 2, 1}};
+template <typename T>
+struct BatchInstOcc {
+    static constexpr int hi = sizeof(T) == 4 ? 6 : 3, lo = sizeof(T) == 4 ? 5 : 2, wide = sizeof(T) == 4 ? 3 : 1;
+};
+constexpr int kBatchTuneIters = 1;      // iterations of each autotuning launch
 constexpr int kBatchChunk = 1 << 20;    // iterations of a launch after autotuning (all jobs stop first)
 
-template <typename T, int NT>
-cudaError_t batch_kernel_setup(int device, int* occ) {
-    auto kern = k_batch<T, NT>;
+template <typename T, int NT, int OCC>
+cudaError_t batch_kernel_setup(int* occ) {
+    auto kern = k_batch<T, NT, OCC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<T>());
     if (e != cudaSuccess) return e;
     int o = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, batch_smem<T>());
     *occ = o;
-    (void)device;
     return e;
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int OCC>
 cudaError_t batch_enqueue(const BatchParams<T>& bp, const BatchCold* cold, BatchCtl* ctl, int njobs, int iters,
-                          int grid, cudaStream_t st) {
+                          int bpi, int grid, cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)grid);
@@ -384,29 +435,34 @@ cudaError_t batch_enqueue(const BatchParams<T>& bp, const BatchCold* cold, Batch
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch<T, NT>, bp, cold, ctl, njobs, iters);
+    return cudaLaunchKernelEx(&cfg, k_batch<T, NT, OCC>, bp, cold, ctl, njobs, iters, bpi);
 }
 
 // Advance jobs[0..n) (band mode, no reinitialisation, 3-D energy R = 5; all
 // of storage type T, on one device) until each has stopped. shape_io: -1 to
-// autotune the block size, else the index of kBatchNT to use; receives the
-// one used. graph_out: 1 if the launches ran as captured graphs.
+// autotune the launch shape, else the index into kBatchShape; receives the
+// one used. graph_out: 1 if the launches ran as captured graphs; threads,
+// resident blocks per SM and bricks per item of the shape used.
 template <typename T>
 slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
-                           float* tuned_ms) {
+                           float* tuned_ms, int* threads_out, int* blocks_out, int* bpi_out) {
     slr_ctx* c0 = jobs[0];
     std::vector<int> order(n);
     for (int j = 0; j < n; ++j) order[j] = j;
-    // the costliest items first, so a phase ends on small items: 3-D WENO,
-    // then 3-D Q1, then 2-D (the results do not depend on the order)
+    // the costliest items first, so that the sequence of one phase ends on
+    // small items: 3-D WENO, then 3-D Q1, then 2-D (results do not depend on it)
     auto rank = [&](int j) { return jobs[j]->cfg.dim == 3 ? (jobs[j]->cfg.interp ? 0 : 1) : 2; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rank(a) < rank(b); });
-    BatchParams<T>* bp = new BatchParams<T>();
+    // one parameter block per launch shape (its item counts depend on the
+    // shape: NT/32 tiles per 2-D item, bpi bricks per 3-D item)
+    std::vector<BatchParams<T>*> bp(kBatchShapes, nullptr);
+    for (auto& x : bp) x = new BatchParams<T>();
     std::vector<BatchCold> hcold(n);
     memset(hcold.data(), 0, sizeof(BatchCold) * n);
     for (int q = 0; q < n; ++q) {
         slr_ctx* c = jobs[order[q]];
-        BatchHot<T>& J = bp->job[q];
+        BatchHot<T> J;
+        memset(&J, 0, sizeof(J));
         J.P = make_params<T>(c);
         const double p = c->cfg.p;
         const int p_kind = p == 1.0 ? 1 : (p == 2.0 ? 2 : 0);
@@ -426,7 +482,6 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         J.band_cap = (int)c->band_cap;
         J.dim = c->cfg.dim;
         J.interp = c->cfg.interp;
-        memset(&J.A, 0, sizeof(J.A));
         if (c->cfg.dim == 3) {
             const BrickState& B = c->brick;
             J.A.nbricks = (int)B.nbricks;
@@ -445,13 +500,30 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
             hcold[q].tm[2] = B.tm_d;
         }
         hcold[q].rec = record_args(c, 1, 1, p, p_kind);
+        for (int sh = 0; sh < kBatchShapes; ++sh) {
+            // items per iteration: the band of a job without reinitialisation
+            // only shrinks, so a 2-D job's tiles are bounded by its list capacity
+            const int W = kBatchShape[sh].nt / 32, bpi = kBatchShape[sh].bpi;
+            BatchHot<T> Js = J;
+            const int cap_tiles = (int)((c->band_cap + kStepTile - 1) / kStepTile);
+            Js.ntc = c->cfg.dim == 3 ? 0 : (cap_tiles + W - 1) / W;
+            const int s_items = c->cfg.dim == 3 ? (J.A.nbricks + bpi - 1) / bpi : std::max(1, Js.ntc);
+            const int e_items = Js.ntc + J.nslots;
+            BatchParams<T>& B = *bp[sh];
+            B.job[q] = Js;
+            B.pre[0][q + 1] = B.pre[0][q] + s_items;
+            B.pre[1][q + 1] = B.pre[1][q] + e_items;
+            B.pre[2][q + 1] = B.pre[2][q] + kRecordBlocks;
+        }
     }
+    for (int sh = 0; sh < kBatchShapes; ++sh)
+        bp[sh]->per_iter = (long long)bp[sh]->pre[0][n] + bp[sh]->pre[1][n] + bp[sh]->pre[2][n];
     BatchCold* dcold = nullptr;
     BatchCtl* dctl = nullptr;
     DevState** dstates = nullptr;
     int* dstat = nullptr;
     int* hstat = nullptr;
-    cudaGraphExec_t gx[kBatchShapes][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t gx[kBatchShapes][2] = {};
     cudaEvent_t ev[2] = {nullptr, nullptr};
     auto cleanup = [&]() {
         for (auto& r : gx)
@@ -464,7 +536,7 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         if (dstates) dev_free(c0, dstates);
         if (dstat) dev_free(c0, dstat);
         if (hstat) cudaFreeHost(hstat);
-        delete bp;
+        for (auto b : bp) delete b;
     };
     dcold = (BatchCold*)dev_alloc(c0, sizeof(BatchCold) * n);
     dctl = (BatchCtl*)dev_alloc(c0, sizeof(BatchCtl));
@@ -486,9 +558,11 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         if (e == cudaSuccess) e = cudaMemsetAsync(&jobs[j]->ds->converged, 0, sizeof(int), st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    int occ[kBatchShapes] = {0, 0};
-    if (e == cudaSuccess) e = batch_kernel_setup<T, 128>(c0->device, &occ[0]);
-    if (e == cudaSuccess) e = batch_kernel_setup<T, 256>(c0->device, &occ[1]);
+    using O = BatchInstOcc<T>;
+    int occ[3] = {0, 0, 0};  // resident blocks per SM of each kernel instance
+    if (e == cudaSuccess) e = batch_kernel_setup<T, 128, O::hi>(&occ[0]);
+    if (e == cudaSuccess) e = batch_kernel_setup<T, 128, O::lo>(&occ[1]);
+    if (e == cudaSuccess) e = batch_kernel_setup<T, 256, O::wide>(&occ[2]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
     if (e != cudaSuccess) {
@@ -496,13 +570,22 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         return cuda_status(c0, e, "batch_run");
     }
     // one launch: reset the control words, the kernel, the jobs' status
-    // words gathered into one array and copied to pinned host memory
+    // words gathered into one array and copied to pinned host memory. The
+    // tickets are 32-bit: a launch covers at most 2^31 items.
     auto enqueue = [&](int sh, int iters) -> cudaError_t {
+        const BatchShape& S = kBatchShape[sh];
+        const long long cap = 0x7fffffffll / std::max(1ll, bp[sh]->per_iter);
+        iters = (int)std::min<long long>(iters, std::max(1ll, cap));
         cudaError_t r = cudaMemsetAsync(dctl, 0, sizeof(BatchCtl), st);
-        const int grid = occ[sh] * c0->num_sms;
-        if (r == cudaSuccess)
-            r = sh == 0 ? batch_enqueue<T, 128>(*bp, dcold, dctl, n, iters, grid, st)
-                        : batch_enqueue<T, 256>(*bp, dcold, dctl, n, iters, grid, st);
+        const int grid = occ[S.inst] * c0->num_sms;
+        if (r == cudaSuccess) {
+            if (S.inst == 0)
+                r = batch_enqueue<T, 128, O::hi>(*bp[sh], dcold, dctl, n, iters, S.bpi, grid, st);
+            else if (S.inst == 1)
+                r = batch_enqueue<T, 128, O::lo>(*bp[sh], dcold, dctl, n, iters, S.bpi, grid, st);
+            else
+                r = batch_enqueue<T, 256, O::wide>(*bp[sh], dcold, dctl, n, iters, S.bpi, grid, st);
+        }
         if (r == cudaSuccess) r = launch_gather_status(c0, dstates, n, dstat, st);
         if (r == cudaSuccess) r = cudaMemcpyAsync(dstat + 4 * n, &dctl->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
         if (r == cudaSuccess)
@@ -556,10 +639,11 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         return all;
     };
     if (tune) {
-        // each shape twice, kBatchTuneIters iterations per launch, in
-        // alternation; the least device time per launch wins (the iterations
-        // and results do not depend on the shape)
-        float ms_of[kBatchShapes] = {1e30f, 1e30f};
+        // each shape twice, kBatchTuneIters iterations per launch, in turns;
+        // the least device time per launch wins (the iterations and results
+        // do not depend on the shape)
+        float ms_of[kBatchShapes];
+        for (auto& x : ms_of) x = 1e30f;
         for (int rep = 0; rep < 2 && !done && e == cudaSuccess; ++rep)
             for (int sh = kBatchShapes - 1; sh >= 0 && !done && e == cudaSuccess; --sh) {
                 e = cudaEventRecord(ev[0], st);
@@ -573,7 +657,9 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
                     if (ms < ms_of[sh]) ms_of[sh] = ms;
                 }
             }
-        shape = ms_of[0] <= ms_of[1] ? 0 : 1;
+        shape = 0;
+        for (int sh = 1; sh < kBatchShapes; ++sh)
+            if (ms_of[sh] < ms_of[shape]) shape = sh;
         best_ms = ms_of[shape];
     }
     while (!done && e == cudaSuccess) {
@@ -593,6 +679,9 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
     *shape_io = shape;
     *graph_out = graphs ? 1 : 0;
     *tuned_ms = best_ms;
+    *threads_out = kBatchShape[shape].nt;
+    *blocks_out = occ[kBatchShape[shape].inst];
+    *bpi_out = kBatchShape[shape].bpi;
     cleanup();
     return status;
 }

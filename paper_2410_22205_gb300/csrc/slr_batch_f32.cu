@@ -7,8 +7,8 @@
 namespace slr {
 
 slr_status batch_run_f32(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
-                         float* tuned_ms) {
-    return batch_run_group<float>(jobs, n, tune, st, shape_io, graph_out, tuned_ms);
+                         float* tuned_ms, int* threads, int* blocks, int* bpi) {
+    return batch_run_group<float>(jobs, n, tune, st, shape_io, graph_out, tuned_ms, threads, blocks, bpi);
 }
 
 }  // namespace slr

@@ -480,12 +480,13 @@ struct RecordWs {
 // (all NT threads of the block calling), then, in the block that finishes
 // the job's last slice, the bookkeeping. The FP64 sums follow the tree of
 // kRecordThreads threads whatever NT; the tile offsets are integers.
+// Returns true in the block that did the bookkeeping.
 template <int NT>
-__device__ __forceinline__ void record_slice(const RecordArgs& A, DevState* ds, int blk, int G, RecordWs& ws) {
+__device__ __forceinline__ bool record_slice(const RecordArgs& A, DevState* ds, int blk, int G, RecordWs& ws) {
     static_assert(kRecordThreads % NT == 0 && NT >= 64, "the block size divides kRecordThreads");
     constexpr int V = kRecordThreads / NT;
     constexpr int VW = kRecordThreads / 32;
-    if (A.mode == 1 && ds->stop) return;
+    if (A.mode == 1 && ds->stop) return false;
     const int n = ds->n;
     long long ntiles = 0;
     if (A.mode == 1) {
@@ -572,7 +573,7 @@ __device__ __forceinline__ void record_slice(const RecordArgs& A, DevState* ds, 
     __syncthreads();
     const bool last = ws.last != 0;
     __syncthreads();  // ws is reused by the caller's next item
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     // the stop test's window of earlier energies:
     // hist[t] = E_2 at iteration (nn - k) + t for t < k (nn, k as below)
@@ -656,6 +657,7 @@ __device__ __forceinline__ void record_slice(const RecordArgs& A, DevState* ds, 
         }
     }
     __syncthreads();  // ws is reused by the caller's next item
+    return true;
 }
 
 // host side (slr_energy.cu): the quadrature scalars and the record

@@ -177,7 +177,7 @@ struct slr_ctx {
     // slr_batch_run: this job's iterations and stop reason; as the first job,
     // the block size, graph use and autotuning trial time of the run it led
     int batch_iters = 0, batch_converged = 0;
-    int batch_threads = 0, batch_graph = 0;
+    int batch_threads = 0, batch_blocks = 0, batch_bpi = 0, batch_graph = 0;
     float batch_tuned_ms = 0.f;
     std::string err;
     long long launches = 0;
@@ -261,12 +261,13 @@ cudaError_t launch_gather_status(slr_ctx* c, DevState* const* states, int n, int
 // context, the status is SLR_E_CUDA (slr_api.cu)
 slr_status cuda_status(slr_ctx* c, cudaError_t e, const char* where);
 // the batched persistent kernel (slr_batch.cuh) for one group of at most 64
-// jobs of one storage type: shape_io in/out (-1: autotune), graph_out,
-// tuned_ms out
+// jobs of one storage type: shape_io in/out (-1: autotune); out: graph use,
+// the autotuner's best trial time, and the shape's threads per block,
+// resident blocks per SM and bricks per item
 slr_status batch_run_f32(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
-                         float* tuned_ms);
+                         float* tuned_ms, int* threads, int* blocks, int* bpi);
 slr_status batch_run_f64(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
-                         float* tuned_ms);
+                         float* tuned_ms, int* threads, int* blocks, int* bpi);
 
 // ---------------------------------------------------------------------------
 // device numerics

@@ -145,7 +145,7 @@ def lib():
                 "slr_batch_evolve": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
                 "slr_batch_chunk": (C.c_int, [_vp]),
                 "slr_batch_run": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, _ip, _ip]),
-                "slr_batch_run_info": (C.c_int, [_vp, _ip, _ip, C.POINTER(C.c_float)]),
+                "slr_batch_run_info": (C.c_int, [_vp, _ip, _ip, _ip, _ip, C.POINTER(C.c_float)]),
                 "slr_extract": (C.c_int, [_vp, C.c_double, _i64p, _dp, C.c_int64, _i64p]),
                 "slr_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
                 "slr_get_band": (C.c_int, [_vp, _i64p, C.c_int64, _i64p]),
@@ -371,11 +371,13 @@ def slr_batch_run(ctxs, autotune=True, stream=None):
 
 
 def slr_batch_run_info(ctx):
-    """(threads per block, graph-captured, autotuner's best trial ms) of the
-    last slr_batch_run that ctx led."""
-    th, gr, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
-    _check(ctx, lib().slr_batch_run_info(ctx, C.byref(th), C.byref(gr), C.byref(ms)))
-    return th.value, bool(gr.value), ms.value
+    """Launch shape of the last slr_batch_run that ctx led: dict of threads
+    per block, resident blocks per SM, bricks per item, graph capture and
+    the autotuner's best trial time (ms)."""
+    th, bl, bp, gr, ms = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0), C.c_float(0.0)
+    _check(ctx, lib().slr_batch_run_info(ctx, C.byref(th), C.byref(bl), C.byref(bp), C.byref(gr), C.byref(ms)))
+    return {"threads_per_block": th.value, "blocks_per_sm": bl.value, "bricks_per_item": bp.value,
+            "graph_captured": bool(gr.value), "autotune_trial_ms": ms.value}
 
 
 def slr_batch_chunk(ctx):

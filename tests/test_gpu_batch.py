@@ -80,9 +80,13 @@ def test_batch_run_equals_solo_runs(autotune):
     solo = _solo(KINDS)
     jobs = [_job(k, i) for i, k in enumerate(KINDS)]
     its, convs = slr.slr_batch_run([j.ctx for j in jobs], autotune=bool(autotune))
-    threads, graph, ms = slr.slr_batch_run_info(jobs[0].ctx)
-    assert threads == 128 if not autotune else threads in (128, 256)
-    assert (ms > 0.0) == bool(autotune)
+    info = slr.slr_batch_run_info(jobs[0].ctx)
+    if autotune:
+        assert info["threads_per_block"] in (128, 256) and info["bricks_per_item"] in (1, 2)
+    else:
+        assert info["threads_per_block"] == 128 and info["bricks_per_item"] == 1
+    assert info["blocks_per_sm"] >= 1
+    assert (info["autotune_trial_ms"] > 0.0) == bool(autotune)
     _check(jobs, its, convs, solo)
     for j in jobs:
         j.close()
