@@ -204,10 +204,10 @@ int slr_batch_chunk(const slr_ctx* first_job);
  * reinitialisation off, energy_R = 5 in 3-D (else SLR_E_INVALID: use
  * slr_batch_evolve, which takes any job); FP32 and FP64 jobs run as separate
  * launches, at most 64 jobs per launch. autotune != 0: the first launches
- * time five launch shapes (128 threads at two register budgets with one or
- * two bricks per step item, 256 threads with one; one iteration each,
- * twice) and the rest of the batch keeps the fastest; 0: the first shape
- * (128 threads, one brick per item). `cuda_stream`
+ * time seven launch shapes (128 threads at two register budgets with one,
+ * two or four bricks per step item, 256 threads with one; one iteration
+ * each, twice) and the rest of the batch keeps the fastest; 0: the first
+ * shape (128 threads, one brick per item). `cuda_stream`
  * (NULL: the first job's stream) orders the launches; every job's own stream
  * is synchronised first. iters_out / converged_out: n_jobs entries each, may
  * be NULL. SLR_E_TIMEOUT if a grid barrier waited longer than its poll limit

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(NT, OCC)
                             s_it[kItFlags] = ((fl ^ kFlPar) & ~kFlOk) | (staged ? kFlOk : 0);
                         }
                     } else {
-                        brick_stage_copy<T, NT>(P, uin, J.d, su, sd, ox, oy, oz);
+                        brick_stage_copy<T, NT, false>(P, uin, J.d, su, sd, ox, oy, oz);
                     }
                     __syncthreads();
                     if (!(s_it[kItFlags] & kFlOk)) {
@@ -397,12 +397,14 @@ constexpr int batch_smem() {
 // ---------------------------------------------------------------------------
 // Launch shapes the autotuner chooses between: threads per block, resident
 // blocks per SM (the register budget: FP32 80 or 96 registers at 128
-// threads; FP64 168 or 255), bricks per step item
-constexpr int kBatchShapes = 5;
+// threads; FP64 168 or 255), bricks per step item (more bricks per item
+// spread the item's bookkeeping; fewer even out the end of a phase)
+constexpr int kBatchShapes = 7;
 struct BatchShape {
     int nt, inst, bpi;  // inst: 0 = <128, hi occ>, 1 = <128, lo occ>, 2 = <256, ...>
 };
-constexpr BatchShape kBatchShape[kBatchShapes] = {{128, 0, 1}, {128, 0, 2}, {128, 1, 1}, {128, 1, 2}, {256, 2, 1}};
+constexpr BatchShape kBatchShape[kBatchShapes] = {{128, 0, 1}, {128, 0, 2}, {128, 1, 1}, {128, 1, 2},
+                                                   {256, 2, 1}, {128, 0, 4}, {128, 1, 4}};
 template <typename T>
 struct BatchInstOcc {
     static constexpr int hi = sizeof(T) == 4 ? 6 : 3, lo = sizeof(T) == 4 ? 5 : 2, wide = sizeof(T) == 4 ? 3 : 1;

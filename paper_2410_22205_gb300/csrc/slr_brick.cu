@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NT, BrickOcc<T, INTERP, NT>::v)
                 }
                 phases ^= 1u << st;
             } else {
-                brick_stage_copy<T, NT>(P, uin, d, su, sd, ox, oy, oz);
+                brick_stage_copy<T, NT, true>(P, uin, d, su, sd, ox, oy, oz);
             }
             if (__syncthreads_or(!staged)) {
                 if (tid == 0) atomicOr(&ds->error, kErrStage);

@@ -299,26 +299,56 @@ struct BrickOcc {
 
 // Step 1 without TMA: the u box (24x16x16) and the d box (24x10x10) of the
 // brick whose u box starts at node (ox, oy, oz), by 4- or 8-byte cp.async
-// copies; nodes outside the grid are zero-filled.
-template <typename T, int NT>
+// copies; nodes outside the grid are zero-filled. The boxes are rows of 24
+// nodes along x. ROWS: each warp takes whole rows, lanes 0..23 one node each,
+// so a row's y/z test and address are computed once per row (the per-job
+// step: 6% (WENO) and 13% (Q1) shorter than the flat form on such grids).
+// Otherwise the threads take consecutive nodes of the flattened box, all
+// lanes busy (the batched kernel, where the row form measured 6% slower).
+// Both fill the same shared memory.
+template <typename T, int NT, bool ROWS>
 __device__ __forceinline__ void brick_stage_copy(const Params<T>& P, const T* uin, const T* __restrict__ d, T* su,
                                                  T* sd, int ox, int oy, int oz) {
     using G = BoxGeom;
-    static_assert(kBox == 16, "row decode of the u box assumes 16 rows per plane");
-    for (int e = threadIdx.x; e < G::BoxN; e += NT) {
-        const int r = e / G::X;
-        const int x = ox + (e - r * G::X), y = oy + (r & 15), z = oz + (r >> 4);
-        const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
-        const T* src = in ? uin + (x + P.is1 * y + P.is2 * z) : uin;
-        cp_async_zfill<(int)sizeof(T)>(smem_addr(su + e), src, in);
-    }
-    for (int e = threadIdx.x; e < G::DBoxN; e += NT) {
-        const int r = e / G::X;
-        const int x = ox + (e - r * G::X);
-        const int y = oy + kHalo - 1 + r % kDY, z = oz + kHalo - 1 + r / kDY;
-        const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
-        const T* src = in ? d + (x + P.is1 * y + P.is2 * z) : d;
-        cp_async_zfill<(int)sizeof(T)>(smem_addr(sd + e), src, in);
+    constexpr int W = NT / 32;
+    static_assert(G::X == 24 && kBox == 16 && kDY == 10, "row layout of the staged boxes");
+    if (ROWS) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane < G::X) {
+            const int x = ox + lane;
+            const bool xin = x >= 0 && x < P.n0;
+            // u box: row r = y + 16 z (y, z from 0), origin (ox, oy, oz)
+            for (int r = warp; r < kBox * kBox; r += W) {
+                const int y = oy + (r & 15), z = oz + (r >> 4);
+                const bool in = xin && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
+                const T* src = in ? uin + (x + P.is1 * y + P.is2 * z) : uin;
+                cp_async_zfill<(int)sizeof(T)>(smem_addr(su + r * G::X + lane), src, in);
+            }
+            // d box: row r = y + 10 z, origin (ox, oy + kHalo - 1, oz + kHalo - 1)
+            for (int r = warp; r < kDY * kDY; r += W) {
+                const int ry = r / kDY;
+                const int y = oy + kHalo - 1 + (r - ry * kDY), z = oz + kHalo - 1 + ry;
+                const bool in = xin && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
+                const T* src = in ? d + (x + P.is1 * y + P.is2 * z) : d;
+                cp_async_zfill<(int)sizeof(T)>(smem_addr(sd + r * G::X + lane), src, in);
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < G::BoxN; e += NT) {
+            const int r = e / G::X;
+            const int x = ox + (e - r * G::X), y = oy + (r & 15), z = oz + (r >> 4);
+            const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
+            const T* src = in ? uin + (x + P.is1 * y + P.is2 * z) : uin;
+            cp_async_zfill<(int)sizeof(T)>(smem_addr(su + e), src, in);
+        }
+        for (int e = threadIdx.x; e < G::DBoxN; e += NT) {
+            const int r = e / G::X;
+            const int x = ox + (e - r * G::X);
+            const int y = oy + kHalo - 1 + r % kDY, z = oz + kHalo - 1 + r / kDY;
+            const bool in = x >= 0 && x < P.n0 && y >= 0 && y < P.n1 && z >= 0 && z < P.n2;
+            const T* src = in ? d + (x + P.is1 * y + P.is2 * z) : d;
+            cp_async_zfill<(int)sizeof(T)>(smem_addr(sd + e), src, in);
+        }
     }
     cp_async_wait_all();
 }
