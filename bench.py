@@ -186,13 +186,28 @@ def cfg_kw():
     return dict(p=2.0, delta=1.0)
 
 
-def sha_of_kernels():
+# the sources each dominant kernel is compiled from (its translation unit and
+# the headers it includes): profiles/traffic.json holds DRAM counters only
+# for the hash of these files, so any change to the kernel voids them
+KERNEL_SOURCES = {
+    "k_step_brick": ["slr_brick.cu", "slr_brick.cuh", "slr_compact.cuh", "slr_internal.cuh"],
+    "k_step_band": ["slr_step.cu", "slr_step.cuh", "slr_compact.cuh", "slr_internal.cuh"],
+    "k_energy": ["slr_energy.cu", "slr_energy.cuh", "slr_compact.cuh", "slr_internal.cuh"],
+}
+
+
+def sha_of_kernel(name):
+    """Hash of the sources of kernel `name` (every csrc file if unknown) and
+    of the C ABI header they include."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_22205_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    files = KERNEL_SOURCES.get(name.split("<")[0], sorted(os.listdir(csrc)))
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
+    with open(os.path.join(ROOT, "include", "slr.h"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -412,7 +427,7 @@ def run_gpu(args):
     front = 1.5 * 4 * math.pi * 0.81 / ((2.0 / (n - 1)) ** 2)
     kernel = {"name": names[dom], "kind": [("step_weno" if interp else "step_q1"), "energy"][dom],
               "front_cells": front, "bytes_per_node": 20.0 if band else 12.0}
-    sha = sha_of_kernels()
+    sha = sha_of_kernel(names[dom])
     roof = roofline_for(kernel, float(kmean[dom]), mean_band, peaks, sha, probe)
     roof["kernel_share_of_step"] = float(kmean[dom] / np.mean(pstep_ms))
     roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
