@@ -32,6 +32,8 @@
 // between the scratch field W and the output buffer; the last kernel writes
 // the cut result into both φ buffers and W, so that the three agree outside
 // the next Ḡ, as the sweeps of the next iteration assume.
+#include <cstring>
+
 #include "slr_internal.cuh"
 
 namespace slr {
@@ -353,10 +355,20 @@ __global__ void __launch_bounds__(kRB) k_reinit_prep(Params<T> P, const T* ub0, 
 // one forward-Euler sweep of eq. reinit, Y = X - Δτ sign(φ̃)(|∇X|_G - 1), on
 // Ḡ; phase 0 reads W and writes the output buffer, phase 1 the reverse (the
 // output buffer is the one the SL step wrote, picked by the iteration parity)
+// Programmatic dependent launch: a sweep (and the final kernel) lets the
+// next kernel of the chain start as soon as every block of its own grid has
+// started, and waits for the previous kernel's completion only where it
+// reads that kernel's output. The list of Ḡ and its flags, written before
+// the first sweep, are read before the wait, so the next launch's latency
+// and those loads overlap the end of the previous sweep.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kRB) k_reinit_sweep(Params<T> P, T* ub0, T* ub1, T* W, int phase, const int* L0,
                                                       const int* L1, const unsigned char* __restrict__ rfl, T dtau,
                                                       DevState* ds) {
+    pdl_trigger();
     if (ds->stop) return;
     const int n = ds->n;
     const int sel = (n + 1) & 1;
@@ -370,6 +382,7 @@ __global__ void __launch_bounds__(kRB) k_reinit_sweep(Params<T> P, T* ub0, T* ub
     // grid): all their loads are issued before any store
     constexpr int K = 4;
     const long long S = (long long)gridDim.x * blockDim.x;
+    bool waited = false;
     for (long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; p0 < cnt; p0 += K * S) {
         int j[K];
         unsigned f[K];
@@ -380,6 +393,10 @@ __global__ void __launch_bounds__(kRB) k_reinit_sweep(Params<T> P, T* ub0, T* ub
             const bool v = p < cnt;
             j[k] = v ? G[p] : 0;
             f[k] = v ? (unsigned)rfl[p] : 1u;
+        }
+        if (!waited) {
+            pdl_wait();  // X is the previous sweep's output
+            waited = true;
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -427,7 +444,9 @@ template <typename T>
 __global__ void __launch_bounds__(kRB) k_reinit_final(Params<T> P, T* ub0, T* ub1, T* W, int M, const int* L0,
                                                       const int* L1, double* part, DevState* ds) {
     __shared__ double s[kRB / 32];
+    pdl_trigger();
     if (ds->stop) return;
+    pdl_wait();  // R is the last sweep's output
     const int n = ds->n;
     const int sel = (n + 1) & 1;
     const int* __restrict__ G = sel ? L1 : L0;
@@ -513,11 +532,30 @@ cudaError_t reinit_t(slr_ctx* c) {
     // sweep m reads X_m and writes Y_m: W -> out, out -> W, ... ; the output
     // buffer is picked on the device by the iteration parity, so both
     // orders are captured and each kernel selects its own
-    for (int m = 0; m < M; ++m)
-        k_reinit_sweep<T, DIM><<<grid, kRB, 0, c->stream>>>(P, u0, u1, W, m & 1, c->band[0], c->band[1], c->rflags,
-                                                             dtau, c->ds);
-    k_reinit_final<T><<<grid, kRB, 0, c->stream>>>(P, u0, u1, W, M, c->band[0], c->band[1], c->part_dphi_r, c->ds);
+    // the first sweep depends fully on the interface step (it reads the flags
+    // that kernel writes); the later sweeps and the final kernel are
+    // programmatic dependents of the kernel before them
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kRB);
+    lc.stream = c->stream;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    for (int m = 0; m < M && e == cudaSuccess; ++m) {
+        lc.attrs = m == 0 ? nullptr : pdl;
+        lc.numAttrs = m == 0 ? 0 : 1;
+        e = cudaLaunchKernelEx(&lc, k_reinit_sweep<T, DIM>, P, u0, u1, W, m & 1, (const int*)c->band[0],
+                               (const int*)c->band[1], (const unsigned char*)c->rflags, dtau, c->ds);
+    }
+    lc.attrs = M > 0 ? pdl : nullptr;
+    lc.numAttrs = M > 0 ? 1 : 0;
+    if (e == cudaSuccess)
+        e = cudaLaunchKernelEx(&lc, k_reinit_final<T>, P, u0, u1, W, M, (const int*)c->band[0],
+                               (const int*)c->band[1], c->part_dphi_r, c->ds);
     c->launches += kReinitFixedKernels + M;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
