@@ -29,6 +29,16 @@ constexpr int kErrBarrier = 2;       // a grid-wide barrier of a cooperative ker
 constexpr int kErrStage = 4;         // a shared-memory staging wait of the brick step gave up
 constexpr long long kBarrierSpinLimit = 1ll << 22;  // polls of one barrier wait (~0.3 s with the sleeps)
 
+// Programmatic dependent launch (griddepcontrol): pdl_trigger lets the next
+// kernel of the stream, launched with the programmatic-serialization
+// attribute, be scheduled once every block of this grid has started;
+// pdl_wait returns once the previous kernel has completed and its writes are
+// visible. Both are no-ops for a kernel launched without the attribute.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // Grid-wide barrier of a cooperative launch (every block co-resident).
 // bar[0] counts the arrivals, bar[1] is the generation; both start at 0.
 // Writes before the barrier are visible to loads after it that bypass L1

@@ -355,14 +355,13 @@ __global__ void __launch_bounds__(kRB) k_reinit_prep(Params<T> P, const T* ub0, 
 // one forward-Euler sweep of eq. reinit, Y = X - Δτ sign(φ̃)(|∇X|_G - 1), on
 // Ḡ; phase 0 reads W and writes the output buffer, phase 1 the reverse (the
 // output buffer is the one the SL step wrote, picked by the iteration parity)
-// Programmatic dependent launch: a sweep (and the final kernel) lets the
-// next kernel of the chain start as soon as every block of its own grid has
-// started, and waits for the previous kernel's completion only where it
-// reads that kernel's output. The list of Ḡ and its flags, written before
-// the first sweep, are read before the wait, so the next launch's latency
-// and those loads overlap the end of the previous sweep.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Programmatic dependent launch (pdl_trigger, pdl_wait): a sweep (and the
+// final kernel) lets the next kernel of the chain start as soon as every
+// block of its own grid has started, and waits for the previous kernel's
+// completion only where it reads that kernel's output. The list of Ḡ and its
+// flags, written before the first sweep, are read before the wait, so the
+// next launch's latency and those loads overlap the end of the previous
+// sweep.
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kRB) k_reinit_sweep(Params<T> P, T* ub0, T* ub1, T* W, int phase, const int* L0,
