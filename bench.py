@@ -416,9 +416,14 @@ def run_gpu(args):
     kern = np.array(kern_ms)
     tname = "float" if prec == 32 else "double"
     iname = "WENO" if interp else "Q1"
-    # the list step runs with the reinitialisation (its band can leave the bricks of the initial band)
-    step_name = (f"k_step_band<{tname},3,{iname}>" if args.reinit else
-                 f"k_step_brick<{tname},{iname},{'band' if band else 'whole grid'}>")
+    # the list step runs with the reinitialisation (its band can leave the bricks of the initial band) and,
+    # by the library's rule, for a band run with Q1 on rows that TMA cannot stage; the bricks otherwise
+    try:
+        brick_info = rec.brick_shape()
+    except slr.SlrError:
+        brick_info = None
+    step_name = (f"k_step_brick<{tname},{iname},{'band' if band else 'whole grid'}>" if brick_info else
+                 f"k_step_band<{tname},3,{iname}>")
     names = [step_name,
              f"k_energy<{tname},3,{iname},R=5> (front cells + quadrature)", "k_record"]
     kmean = kern.mean(axis=0)
@@ -433,12 +438,10 @@ def run_gpu(args):
     roof["kernels_ms"] = {nm: float(v) for nm, v in zip(names, kmean)}
     roof["kernels_timed"] = (f"{kprof} further steps with an event between the kernels captured in the graph "
                              f"({float(np.mean(pstep_ms)):.4f} ms per step with the events)")
-    try:
-        bt, bs, bms = rec.brick_shape()
+    if brick_info:
+        bt, bs, bms = brick_info
         roof["launch_shape"] = {"threads_per_block": bt, "stages": bs, "autotune_trial_ms": bms,
                                 "chosen_by": "the brick step's autotuner at init (fastest of 4 shapes on φ^0)"}
-    except slr.SlrError:
-        pass
     iter_lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
     if args.reinit:
         roof["phases_ms"] = {k: float(v) for k, v in
@@ -474,7 +477,7 @@ def run_gpu(args):
                 bt, bs, bms = r2.brick_shape()
                 variants[label]["launch_shape"] = {"threads_per_block": bt, "stages": bs}
             except slr.SlrError:
-                pass
+                variants[label]["step"] = "list step (k_step_band)"
             if want_err and not rei:
                 records.append(record_step(r2, label, n, prec, interp, band))
             r2.close()

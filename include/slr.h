@@ -87,6 +87,11 @@ typedef struct {
                          * first neighbours after every SL step (needs band = 1); 0: off (default) */
     int reinit_sweeps;  /* pseudo-time sweeps of eq. reinit; 0 -> 4(γ/h + 1) */
     double reinit_dtau; /* pseudo-time step Δτ; 0 -> h/2 (at most h/sqrt(dim)) */
+    int step_kind;      /* SL step of a 3-D run without reinitialisation: 1 = on bricks staged in shared memory,
+                         * 2 = on the band list (the only kind in 2-D and with reinitialisation); 0 (default) =
+                         * by the rule measured on GB300: the list step for a band run with the Q1 interpolator
+                         * on a grid whose rows are not a multiple of 16 bytes (no TMA staging), bricks
+                         * otherwise. The kind changes timing only within the tolerances of the step. */
 } slr_config;
 
 void slr_config_default(slr_config* cfg);

@@ -314,6 +314,7 @@ void slr_config_default(slr_config* cfg) {
     cfg->reinit = 0;
     cfg->reinit_sweeps = 0;
     cfg->reinit_dtau = 0.0;
+    cfg->step_kind = 0;
 }
 
 slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* cuda_stream, slr_ctx** out) {
@@ -363,6 +364,9 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
     if (k.reinit_sweeps < 0 || k.reinit_sweeps > 10000) return bad("reinit_sweeps must be in 0..10000");
     if (!(k.reinit_dtau >= 0.0) || !(k.reinit_dtau <= h / sqrt((double)k.dim) * (1.0 + 1e-12)))
         return bad("reinit_dtau must be in [0, h/sqrt(dim)]");
+    if (k.step_kind < 0 || k.step_kind > 2) return bad("step_kind must be 0, 1 or 2");
+    if (k.step_kind == 1 && (k.dim != 3 || k.reinit))
+        return bad("step_kind 1 (bricks) needs a 3-D run without reinitialisation");
     c->h = h;
     c->dt = k.dt > 0.0 ? k.dt : h / 4.0;
     c->gamma = k.gamma > 0.0 ? k.gamma : (k.dim == 2 ? 4.0 : 6.0) * h;

@@ -5,11 +5,12 @@
 // the SL update of §3.1-§3.2 with the band and cut of §3.8, then the energy
 // of §3.5 and the stop test of §4 eq. deltaEn), without the
 // reinitialisation. One iteration of a job is three phases of work items:
-//   0. step:   one item per active brick of a 3-D job (the brick step of
-//              slr_brick.cuh), or per NT/32 tiles of 128 band-list entries
-//              of a 2-D job (the list step of slr_step.cuh);
-//   1. energy: one item per slot of 1024 candidate cells, after, for a 2-D
-//              job, the items that count its tiles' band members;
+//   0. step:   one item per bpi active bricks of a 3-D job on the brick
+//              step (slr_brick.cuh), or per NT/32 tiles of 128 band-list
+//              entries of a job on the list step (slr_step.cuh: 2-D, and 3-D
+//              where the step-kind rule picks it);
+//   1. energy: one item per slot of 1024 candidate cells, after, for a job on
+//              the list step, the items that count its tiles' band members;
 //   2. record: kRecordBlocks slices; the block that finishes a job's last
 //              slice does its bookkeeping and stop test.
 // The items of all jobs form one ticket sequence, iteration by iteration and
@@ -73,7 +74,8 @@ struct BatchHot {
     double* part_dphi;
     int band_cap;
     int dim, interp;
-    int ntc;            // 2-D: tile-count items that open its energy phase
+    int bricked;        // 3-D brick step; else the list step (2-D, or 3-D by the step-kind rule)
+    int ntc;            // list step: tile-count items that open its energy phase
 };
 
 template <typename T>
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(NT, OCC)
         mbar_init(bar, 1);
         fence_mbar_init();
         for (int j = 0; j < njobs; ++j)
-            if (BP.job[j].dim == 3 && BP.job[j].A.tma)
+            if (BP.job[j].bricked && BP.job[j].A.tma)
                 for (int m = 0; m < 3; ++m) fence_tensormap_acquire(&cold[j].tm[m]);
         s_it[kItFlags] = 0;
         s_it[kItKey] = -1;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(NT, OCC)
         DevState* ds = J.ds;
         if (!(s_it[kItFlags] & kFlStop)) {
             const int n = vload(&ds->n);
-            if (ph == 0 && J.dim == 3) {
+            if (ph == 0 && J.bricked) {
                 // ---- bpi bricks of a 3-D job ----
                 const Params<T>& P = J.P;
                 const BrickArgs<T>& A = J.A;
@@ -329,7 +331,8 @@ __global__ void __launch_bounds__(NT, OCC)
                     __syncthreads();  // the boxes are free for the next brick
                 }
             } else if (ph == 0) {
-                // ---- NT/32 tiles of a 2-D job's band list, one per warp ----
+                // ---- NT/32 tiles of the band list (2-D, or a 3-D job on the
+                // list step), one per warp ----
                 const Params<T>& P = J.P;
                 const int cnt_in = vload(&ds->band_count[n & 1]);
                 const int ntiles = (cnt_in + kStepTile - 1) / kStepTile;
@@ -342,28 +345,36 @@ __global__ void __launch_bounds__(NT, OCC)
                     int* Lout = (n & 1) ? J.L0 : J.L1;
                     const T Ep = (T)vload(&ds->Ep);
                     const int per = (ntiles + kRecordBlocks - 1) / kRecordBlocks;
-                    if (J.interp)
+                    if (J.dim == 3) {
+                        if (J.interp)
+                            band_tile<T, 3, 1>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap,
+                                               cnt_in, per, t, Ep, J.part_dphi, ds);
+                        else
+                            band_tile<T, 3, 0>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap,
+                                               cnt_in, per, t, Ep, J.part_dphi, ds);
+                    } else if (J.interp) {
                         band_tile<T, 2, 1>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap, cnt_in,
                                            per, t, Ep, J.part_dphi, ds);
-                    else
+                    } else {
                         band_tile<T, 2, 0>(P, uin, uout, J.d, Lin, Lout, J.tile_off, ds->band_base, J.band_cap, cnt_in,
                                            per, t, Ep, J.part_dphi, ds);
+                    }
                 }
             } else if (ph == 1) {
-                // ---- energy slots (after a 2-D job's tile counts) on u^{n+1} ----
+                // ---- energy slots (after a list-step job's tile counts) on u^{n+1} ----
                 const Params<T>& P = J.P;
                 const EnergyArgs<T>& E = J.E;
                 const int sel = (n + 1) & 1;
                 const T* u = sel ? J.ub1 : J.ub0;
-                if (J.dim == 3) {
-                    if (J.interp)
-                        energy_slot<T, 3, 1, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
-                    else
-                        energy_slot<T, 3, 0, 5, NT>(P, u, J.d, J.cells, J.ncells, loc, E, J.part_e, ews);
-                } else if (loc < J.ntc) {
+                if (loc < J.ntc) {
                     const int nb = vload(&ds->band_count[sel]);
                     const int t = loc * W + warp;
                     if (t < (nb + kStepTile - 1) / kStepTile) tile_count<T>(P, u, sel ? J.L1 : J.L0, nb, t, J.tile_off);
+                } else if (J.dim == 3) {
+                    if (J.interp)
+                        energy_slot<T, 3, 1, 5, NT>(P, u, J.d, J.cells, J.ncells, loc - J.ntc, E, J.part_e, ews);
+                    else
+                        energy_slot<T, 3, 0, 5, NT>(P, u, J.d, J.cells, J.ncells, loc - J.ntc, E, J.part_e, ews);
                 } else if (J.interp) {
                     energy_slot<T, 2, 1, 0, NT>(P, u, J.d, J.cells, J.ncells, loc - J.ntc, E, J.part_e, ews);
                 } else {
@@ -484,7 +495,8 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
         J.band_cap = (int)c->band_cap;
         J.dim = c->cfg.dim;
         J.interp = c->cfg.interp;
-        if (c->cfg.dim == 3) {
+        J.bricked = brick_mode(c) ? 1 : 0;
+        if (J.bricked) {
             const BrickState& B = c->brick;
             J.A.nbricks = (int)B.nbricks;
             J.A.bricks = B.list;
@@ -508,8 +520,8 @@ slr_status batch_run_group(slr_ctx* const* jobs, int n, int tune, cudaStream_t s
             const int W = kBatchShape[sh].nt / 32, bpi = kBatchShape[sh].bpi;
             BatchHot<T> Js = J;
             const int cap_tiles = (int)((c->band_cap + kStepTile - 1) / kStepTile);
-            Js.ntc = c->cfg.dim == 3 ? 0 : (cap_tiles + W - 1) / W;
-            const int s_items = c->cfg.dim == 3 ? (J.A.nbricks + bpi - 1) / bpi : std::max(1, Js.ntc);
+            Js.ntc = J.bricked ? 0 : (cap_tiles + W - 1) / W;
+            const int s_items = J.bricked ? (J.A.nbricks + bpi - 1) / bpi : std::max(1, Js.ntc);
             const int e_items = Js.ntc + J.nslots;
             BatchParams<T>& B = *bp[sh];
             B.job[q] = Js;

@@ -321,7 +321,18 @@ struct BandOf {
 
 }  // namespace
 
-bool brick_mode(const slr_ctx* c) { return c->cfg.dim == 3 && !c->cfg.reinit; }
+// The brick step for 3-D runs without reinitialisation (where the band cannot
+// leave the bricks of G̃^0), by cfg.step_kind. By rule (0): bricks, except a
+// band run with the Q1 interpolator on a grid whose rows are not a multiple
+// of 16 bytes. Such rows cannot be staged by TMA, and on GB300 the list step
+// measured faster there (one iteration at 131^3: 62 against 69 µs; at 189^3:
+// 89 against 102 µs), while WENO and TMA-staged grids favour the bricks.
+bool brick_mode(const slr_ctx* c) {
+    if (c->cfg.dim != 3 || c->cfg.reinit) return false;
+    if (c->cfg.step_kind != 0) return c->cfg.step_kind == 1;
+    const bool tma_rows = (c->cfg.n[0] * (long long)c->tsize) % 16 == 0;
+    return !c->cfg.band || c->cfg.interp == 1 || tma_rows;
+}
 
 // Active bricks of field u (normally φ^0 in u[0]), the per-brick counters
 // and partials (keyed by brick id over the whole grid, so the Δ_φ sum does

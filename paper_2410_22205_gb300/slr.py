@@ -71,6 +71,7 @@ class slr_config(C.Structure):
         ("reinit", C.c_int),
         ("reinit_sweeps", C.c_int),
         ("reinit_dtau", C.c_double),
+        ("step_kind", C.c_int),
     ]
 
 

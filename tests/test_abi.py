@@ -75,6 +75,9 @@ def test_new_entry_points_check_their_arguments_without_a_device():
     dict(gamma=0.01, beta=0.02),
     dict(max_iters=100000),
     dict(stop_k=1024),
+    dict(step_kind=3),
+    dict(step_kind=1, dim=2, n=(64, 64, 1), lo=(-1.0, -1.0), hi=(1.0, 1.0)),
+    dict(step_kind=1, reinit=1),
 ])
 def test_create_rejects_invalid_config(bad):
     cfg = slr.slr_config_default(**bad)

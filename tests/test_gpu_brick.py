@@ -30,6 +30,7 @@ def _make(n, prec, interp, band, **kw):
     shape = (n,) * 3 if isinstance(n, int) else tuple(n)
     lo = (-1.0,) * 3
     hi = tuple(-1.0 + 2.0 * (shape[a] - 1) / (shape[0] - 1) for a in range(3))
+    kw.setdefault("step_kind", 1)  # the brick step on every grid (by rule, Q1 band runs on ragged rows take the list step)
     rec = slr.Reconstruction(dim=3, n=shape, lo=lo, hi=hi, precision=prec, interp=interp, band=band, **kw)
     okw = {k: v for k, v in kw.items() if k in ("p", "delta")}
     P = O.params(3, shape, lo, hi, interp=interp, band=band, prec=prec, **okw)
