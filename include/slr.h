@@ -459,6 +459,15 @@ typedef struct slr_server slr_server;
 slr_status slr_server_create(size_t hbm_budget, int max_active, int setup_threads, const slr_allocator* alloc,
                              slr_server** out);
 
+/* Admission order of queued requests (the paper has no counterpart): 0 (the
+ * default) the oldest first; 1 the least estimated set-up time less the time
+ * the request has waited, so that small requests pass a large one whose
+ * distance grid would hold the set-up threads, and a large request still gets
+ * its turn once it has waited about its estimate (4 ns per grid node plus
+ * 20 ns per point). Either way a request is admitted only while a slot and
+ * its share of the HBM budget are free. SLR_E_INVALID for another value. */
+slr_status slr_server_set_policy(slr_server* s, int policy);
+
 /* Queue one reconstruction: cfg as for slr_create, the cloud (host, copied),
  * φ^0 = |x - c| - r with sphere = {cx, cy, cz, r}; the job then runs to the
  * stopping criterion of §4. *ticket identifies it. */

@@ -2,8 +2,10 @@
 //
 // Requests (a configuration, a host point cloud and a sphere for φ^0) are
 // queued by slr_server_submit. Worker threads drive the device:
-//  - setup (setup_threads of them): each admits the next queued request, in
-//    order, while an active slot and enough of the HBM budget are free,
+//  - setup (setup_threads of them): each admits a queued request while an
+//    active slot and enough of the HBM budget are free (policy 0: the oldest;
+//    policy 1: the least estimated set-up time less its waiting time, so that
+//    small requests pass large ones without starving them),
 //    creates the job's context on its own stream, copies the cloud, builds
 //    the exact distance grid and φ^0, and hands the job to the iteration
 //    thread. Several set-ups run at once, so a large request's distance grid
@@ -46,6 +48,7 @@ struct Job {
     int64_t npts = 0;
     double sphere[4] = {0, 0, 0, 0};
     size_t bytes = 0;
+    double setup_est_ms = 0.0;  // estimated set-up time (the exact distance grid dominates it)
     bool holds_budget = false;  // admitted and its share not yet returned
     slr_ctx* ctx = nullptr;
     std::atomic<int> state{kQueued};
@@ -70,6 +73,14 @@ size_t job_bytes(const slr_config& c, int64_t npts) {
     return grid + cloud;
 }
 
+// estimated set-up time of a job in ms: the exact distance grid takes about
+// 4 ns per node on GB300 (65 ms at 256^3 with 1M points), the cloud's index
+// a few ns per point
+double setup_estimate_ms(const slr_config& c, int64_t npts) {
+    const double N = (double)c.n[0] * (double)c.n[1] * (double)(c.dim == 3 ? c.n[2] : 1);
+    return 4e-6 * N + 2e-5 * (double)npts;
+}
+
 }  // namespace
 
 struct slr_server {
@@ -78,6 +89,7 @@ struct slr_server {
     int max_active = 16;
     int device = 0;
     int rounds_per_check = 4;
+    int policy = 0;  // admission order: 0 first come, 1 least estimated set-up less waiting time
     slr_allocator al{};
     bool have_al = false;
     std::mutex mu;
@@ -96,7 +108,30 @@ struct slr_server {
 
     void setup_loop();
     void iter_loop();
+    // the queued job to admit now (index into queue), or -1 (caller holds mu)
+    long pick() const;
 };
+
+long slr_server::pick() const {
+    if (queue.empty() || active >= max_active) return -1;
+    auto fits = [&](const Job& j) { return used + j.bytes <= budget || active == 0; };
+    if (policy == 0) return fits(*queue.front()) ? 0 : -1;
+    // estimate less waiting time = estimate + submit time - now: the order by
+    // estimate + submit time, which does not change while the jobs wait
+    long best = -1;
+    double best_key = 0.0;
+    for (size_t i = 0; i < queue.size(); ++i) {
+        const Job& j = *queue[i];
+        if (!fits(j)) continue;
+        const double key =
+            j.setup_est_ms + std::chrono::duration<double, std::milli>(j.t_submit.time_since_epoch()).count();
+        if (best < 0 || key < best_key) {
+            best = (long)i;
+            best_key = key;
+        }
+    }
+    return best;
+}
 
 void slr_server::setup_loop() {
     cudaSetDevice(device);
@@ -104,15 +139,15 @@ void slr_server::setup_loop() {
         std::shared_ptr<Job> j;
         {
             std::unique_lock<std::mutex> lk(mu);
+            long at = -1;
             cv.wait(lk, [&] {
                 if (stop) return true;
-                if (queue.empty()) return false;
-                const auto& f = queue.front();
-                return active < max_active && (used + f->bytes <= budget || active == 0);
+                at = pick();
+                return at >= 0;
             });
             if (stop) return;
-            j = queue.front();
-            queue.pop_front();
+            j = queue[(size_t)at];
+            queue.erase(queue.begin() + at);
             used += j->bytes;
             ++active;
             j->holds_budget = true;
@@ -279,6 +314,16 @@ slr_status slr_server_create(size_t hbm_budget, int max_active, int setup_thread
     return SLR_OK;
 }
 
+slr_status slr_server_set_policy(slr_server* s, int policy) {
+    if (!s || policy < 0 || policy > 1) return SLR_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->policy = policy;
+    }
+    s->cv.notify_all();
+    return SLR_OK;
+}
+
 slr_status slr_server_submit(slr_server* s, const slr_config* cfg, const double* xyz, int64_t n_points,
                              const double sphere[4], uint64_t* ticket) {
     if (!s || !cfg || !xyz || n_points < 1 || !sphere || !ticket) return SLR_E_INVALID;
@@ -288,6 +333,7 @@ slr_status slr_server_submit(slr_server* s, const slr_config* cfg, const double*
     j->xyz.assign(xyz, xyz + (size_t)n_points * cfg->dim);
     for (int a = 0; a < 4; ++a) j->sphere[a] = sphere[a];
     j->bytes = job_bytes(*cfg, n_points);
+    j->setup_est_ms = setup_estimate_ms(*cfg, n_points);
     j->t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

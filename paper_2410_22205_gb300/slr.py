@@ -35,7 +35,7 @@ EXPORTS = [
     "slr_export_state", "slr_import_state", "slr_set_profiling", "slr_last_iteration_times",
     "slr_last_iteration_phases", "slr_kernel_launches", "slr_brick_shape", "slr_brick_shape_set", "slr_probe_fma",
     "slr_last_error", "slr_destroy", "slr_distance_grid_noalloc", "slr_cloud_spacing", "slr_l1_error", "slr_selftest_barrier",
-    "slr_server_create", "slr_server_submit", "slr_server_poll", "slr_server_timing", "slr_server_release",
+    "slr_server_create", "slr_server_set_policy", "slr_server_submit", "slr_server_poll", "slr_server_timing", "slr_server_release",
     "slr_server_last_error",
     "slr_server_destroy", "slr_multirun_default", "slr_reconstruct",
 ]
@@ -173,6 +173,7 @@ def lib():
                 "slr_multirun_default": (None, [C.POINTER(slr_multirun_config)]),
                 "slr_reconstruct": (C.c_int, [C.POINTER(slr_multirun_config), _dp, C.c_int64, C.POINTER(slr_allocator),
                                               _vp, C.POINTER(_vp), C.POINTER(slr_multirun_report)]),
+                "slr_server_set_policy": (C.c_int, [_vp, C.c_int]),
                 "slr_server_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(slr_allocator),
                                                 C.POINTER(_vp)]),
                 "slr_server_timing": (C.c_int, [_vp, C.c_uint64, _dp, _dp, _dp]),
@@ -499,12 +500,19 @@ def _check_srv(srv, status):
         raise SlrError(status, msg.decode() if msg else "")
 
 
-def slr_server_create(hbm_budget, max_active=16, allocator=None, setup_threads=1):
+def slr_server_create(hbm_budget, max_active=16, allocator=None, setup_threads=1, policy=0):
+    """A continuous-batching server; policy 0 admits the oldest request first,
+    1 the least estimated set-up time less its waiting time."""
     h = C.c_void_p()
     al = C.byref(allocator.struct if hasattr(allocator, "struct") else allocator) if allocator is not None else None
     s = lib().slr_server_create(int(hbm_budget), int(max_active), int(setup_threads), al, C.byref(h))
     if s != SLR_OK:
         raise SlrError(s, "server creation failed")
+    if policy:
+        s = lib().slr_server_set_policy(h.value, int(policy))
+        if s != SLR_OK:
+            lib().slr_server_destroy(h.value)
+            raise SlrError(s, "invalid server policy")
     return h.value
 
 

@@ -505,10 +505,13 @@ def test_batch_evolve_equals_solo_runs(chunk):
         assert np.array_equal(j.diagnostics()["e2"], e2)
 
 
-def test_server_results_equal_solo_runs():
+@pytest.mark.parametrize("policy", [0, 1])
+def test_server_results_equal_solo_runs(policy):
     """Continuous batching: jobs submitted into a running mix (at most 3
     admitted at once, a tight memory budget) finish with exactly the state,
-    iteration count and energies of the same job run alone."""
+    iteration count and energies of the same job run alone, whether the
+    server admits the oldest request first (policy 0) or the least estimated
+    set-up first (policy 1)."""
     import time
 
     slr = _slr()
@@ -526,7 +529,7 @@ def test_server_results_equal_solo_runs():
         it, conv = r.evolve()
         solo.append((it, r.u(), r.diagnostics()["e2"]))
         r.close()
-    srv = slr.slr_server_create(64 << 20, max_active=3, setup_threads=2)
+    srv = slr.slr_server_create(64 << 20, max_active=3, setup_threads=2, policy=policy)
     try:
         tickets = []
         for cfg, pts in specs:
