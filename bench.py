@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--fullgrid", action="store_true",
                     help="time the whole-grid step (band off) instead of the narrow band")
     ap.add_argument("--reinit", action="store_true",
-                    help="time the iteration with the reinitialisation of §3.7 (Algorithm 1 step 4d) on")
+                    help="time the iteration with the reinitialisation of §3.7 (Algorithm 1) on")
     ap.add_argument("--batch-jobs", type=int, default=64, help="jobs of the batched mix (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=15.0,
                     help="length of each Poisson serving stream (0: skip)")
@@ -540,7 +540,7 @@ def run_e2e(args, cloud, slr, torch, reinit=0):
     """Whole jobs through the public API with host buffers: pinned host cloud
     -> load (H2D) -> exact distance grid -> φ^0 -> evolve to the stop test ->
     extract |φ| < 2h (D2H). Timed by the host clock around each job. With
-    reinit = 1 every iteration also runs Algorithm 1 step 4d (§3.7), so the
+    reinit = 1 every iteration also runs the reinitialisation of Algorithm 1 (§3.7), so the
     band follows the front; the error on the cloud (eq. errCloud) of the
     result is reported next to the rate."""
     pinned = torch.empty(cloud.shape, dtype=torch.float64, pin_memory=True)
@@ -551,7 +551,7 @@ def run_e2e(args, cloud, slr, torch, reinit=0):
     for j in range(args.e2e_jobs + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        # Algorithm 1 with step 4d runs the paper's first-run parameters (p = 1,
+        # Algorithm 1 with the reinitialisation runs the paper's first-run parameters (p = 1,
         # δ = 0: the front moves Δt|∇d| = h/4 per step towards the cloud)
         # and may need more than 100 iterations to cross the gap at 256^3
         kw = dict(p=1.0, delta=0.0, max_iters=400) if reinit else cfg_kw()

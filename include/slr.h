@@ -83,7 +83,7 @@ typedef struct {
     int stop_k;         /* running-mean window k_max, default 10, at most 1023 */
     int min_iters;      /* default 10 */
     int max_iters;      /* default 100 */
-    int reinit;         /* 1: Algorithm 1 step 4d, the reinitialisation of §3.7 on the band and its
+    int reinit;         /* 1: the reinitialisation of Algorithm 1 (§3.7) on the band and its
                          * first neighbours after every SL step (needs band = 1); 0: off (default) */
     int reinit_sweeps;  /* pseudo-time sweeps of eq. reinit; 0 -> 4(γ/h + 1) */
     double reinit_dtau; /* pseudo-time step Δτ; 0 -> h/2 (at most h/sqrt(dim)) */
@@ -154,7 +154,7 @@ slr_status slr_cloud_spacing(slr_ctx* ctx, const int64_t* sample, int64_t m, dou
  * the diagnostics. Needs d (build or set) first. */
 slr_status slr_init_u(slr_ctx* ctx, int kind, const double* params, const double* u0_host);
 
-/* Run n_steps iterations of Algorithm 1 step 4 (band, SL update §3.1, cut)
+/* Run n_steps iterations of Algorithm 1 (band, SL update §3.1, cut)
  * without the stopping test, each followed by the FP64 energy of the new
  * state. energy_override >= 0 uses that value as E_p in the scale factor
  * (d/E_p)^(p-1) of every step; < 0 uses the computed E_p(φ^n). */
@@ -195,7 +195,7 @@ int slr_batch_chunk(const slr_ctx* first_job);
 
 /* Batched form of slr_evolve in one persistent kernel (the batching of many
  * reconstructions on one GPU stands in for the paper's ranks advancing
- * subdomains together, §3.3; each job runs Algorithm 1's loop, step 4 of §3,
+ * subdomains together, §3.3; each job runs the loop of Algorithm 1 (§3)
  * without the reinitialisation). One cooperative launch, captured in a CUDA
  * graph, advances every job iteration by iteration: its blocks take work
  * items (a brick of a 3-D job's band, a group of band-list tiles of a 2-D

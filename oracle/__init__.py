@@ -323,7 +323,7 @@ def stop(E2, n, kmax=10, tol=1e-4, min_iters=10, max_iters=100):
 
 
 def evolve(P, u0, d, R=5, tol=1e-4, kmax=10, min_iters=10, max_iters=100, reinit=False, sweeps=0, dtau=0.0):
-    """Algorithm 1 loop (§4 stop rule); with reinit, step 4d (§3.7) after every SL step."""
+    """Algorithm 1 loop (§4 stop rule); with reinit, the reinitialisation (§3.7) after every SL step."""
     u = np.array(u0, dtype=np.float64, copy=True)
     d, dp = _d(d)
     E2 = np.zeros(max_iters + 1)

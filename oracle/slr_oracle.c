@@ -599,7 +599,7 @@ void or_sl_nodes(const or_params* g, const double* u, const double* d, double Ep
     for (long long t = 0; t < m; ++t) out[t] = or_sl_node(g, u, d, Ep, nodes[t], flags ? flags + t : NULL);
 }
 
-/* Algorithm 1, steps 4a, 4c and the cut of 4d (no reinitialisation) */
+/* One iteration of Algorithm 1 without the reinitialisation: band, SL update, cut */
 double or_sl_step(const or_params* g, const double* u, const double* d, double Ep, double* u_out, int* flags_out) {
     long long N = or_num_nodes(g);
     long long slab = g->n[0] * g->n[1];
@@ -798,7 +798,7 @@ int or_stop(const double* E2, int n, int kmax, double tol, int min_iters, int ma
 }
 
 /* ------------------------------------------------------------------ */
-/* §3.7 reinitialisation (Algorithm 1 step 4d)                          */
+/* §3.7 reinitialisation (Algorithm 1)                                  */
 /* ------------------------------------------------------------------ */
 
 /* The paper runs the constrained reinitialisation of Hartmann, Meinke and
@@ -1199,7 +1199,7 @@ int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, doub
         }
         double dphi = or_sl_step(g, u, d, Ep, next, NULL);
         if (reinit) {
-            /* Algorithm 1 step 4d; Δ_φ then measures the whole update */
+            /* the reinitialisation of Algorithm 1; Δ_φ then measures the whole update */
             or_reinit(g, u, next, sweeps, dtau, re, NULL);
             double acc = 0.0;
             for (long long i = 0; i < N; ++i) acc += fabs(re[i] - u[i]);

@@ -106,7 +106,7 @@ double or_scale_factor(const or_params* g, double dj, double Ep);
 double or_sl_node(const or_params* g, const double* u, const double* d, double Ep,
                   long long idx, int* flags);
 
-/* Algorithm 1 step 4c + cut: u_out on every node. In band mode the nodes
+/* The SL update of Algorithm 1 and the cut: u_out on every node. In band mode the nodes
  * of eq. subgrid are updated, then every node is cut (eq. cut); in whole-grid
  * mode every node is updated and nothing is cut. flags_out (may be NULL):
  * per-node flags. Returns Δ_φ = h^dim Σ |u_out - u| (§4, L1 of the update). */
@@ -143,7 +143,7 @@ long long or_reinit(const or_params* g, const double* phi_band, const double* ph
                     double* out, unsigned char* flags_out);
 int or_reinit_sweeps(const or_params* g);
 
-/* or_evolve with Algorithm 1 step 4d (reinit != 0): after each SL step and
+/* or_evolve with the reinitialisation of Algorithm 1 (reinit != 0): after each SL step and
  * cut, or_reinit with the step's band; Δ_φ then covers the whole update. */
 int or_evolve_reinit(const or_params* g, double* u, const double* d, int R, double stop_tol, int kmax,
                      int min_iters, int max_iters, int reinit, int sweeps, double dtau, double* E2_hist,

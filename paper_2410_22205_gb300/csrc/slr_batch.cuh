@@ -1,8 +1,8 @@
 // Batched evolution of many independent reconstructions in one persistent,
 // cooperative, graph-captured kernel (k_batch).
 //
-// Every job is one run of Algorithm 1's loop (arXiv 2410.22205, §3: step 4,
-// the SL update of §3.1-§3.2 with the band and cut of §3.8, then the energy
+// Every job is one run of Algorithm 1's loop (arXiv 2410.22205, §3: the
+// band, the SL update of §3.1-§3.2 with the band and cut of §3.8, then the energy
 // of §3.5 and the stop test of §4 eq. deltaEn), without the
 // reinitialisation. One iteration of a job is three phases of work items:
 //   0. step:   one item per bpi active bricks of a 3-D job on the brick

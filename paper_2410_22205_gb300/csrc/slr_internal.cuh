@@ -230,7 +230,7 @@ cudaError_t launch_extract(slr_ctx* c, double width, long long* idx_dev, double*
 slr_status init_after_u(slr_ctx* c, cudaError_t e);
 // §3.6 initial data into an FP64 device field (ext: N bytes of scratch); see slr_initdata.cu
 cudaError_t launch_init_marking(slr_ctx* c, double gamma_s, double* phi_dev, unsigned char* ext_dev);
-// Algorithm 1 step 4d (§3.7) after launch_step; see slr_reinit.cu
+// the reinitialisation of Algorithm 1 (§3.7) after launch_step; see slr_reinit.cu
 cudaError_t launch_reinit(slr_ctx* c);
 int reinit_grid(const slr_ctx* c);
 int reinit_sweeps(const slr_ctx* c);

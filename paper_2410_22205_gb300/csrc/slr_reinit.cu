@@ -1,4 +1,4 @@
-// Algorithm 1 step 4d: the reinitialisation of §3.7 on Ḡ^n (the band G̃^n of
+// The reinitialisation of Algorithm 1 (§3.7) on Ḡ^n (the band G̃^n of
 // the SL step and its face neighbours), then eq. cut.
 //
 // Besides φ^{n+1} it leaves the next step's scan list (Ḡ^n, ascending node

@@ -1,4 +1,4 @@
-"""GPU parity of Algorithm 1 step 4d, the reinitialisation of §3.7 (SL step,
+"""GPU parity of the reinitialisation of Algorithm 1, §3.7 (SL step,
 then reinitialisation on the band and its first neighbours, then eq. cut),
 through the C ABI against the FP64 oracle.
 
@@ -88,7 +88,7 @@ def test_reinit_iteration_parity(dim, n, prec, interp):
 
 
 def test_evolve_with_reinit_matches_oracle_fp64():
-    """Algorithm 1 with step 4d, 2-D, FP64 Q1, p = 1, 60 iterations: the GPU
+    """Algorithm 1 with the reinitialisation, 2-D, FP64 Q1, p = 1, 60 iterations: the GPU
     trajectory follows the oracle's; E_2 history within 1e-9 relative."""
     rec, P = make(2, 64, 64, 0, p=1.0, delta=0.0, max_iters=60, min_iters=60)
     pts = synth.circle_uniform(400, 0.45)
