@@ -108,7 +108,7 @@ slr_status slr_create(const slr_config* cfg, const slr_allocator* alloc, void* c
  * n_points rows of `dim` FP64 coordinates, row-major. n_points >= 1. */
 slr_status slr_load_cloud(slr_ctx* ctx, const double* xyz, int64_t n_points);
 
-/* Algorithm 1 step 2 / §3.4: d(x_j) = min_Q |x_j - Q| on every node, exact,
+/* Algorithm 1, §3.4: d(x_j) = min_Q |x_j - Q| on every node, exact,
  * with argmin (the lowest point index on ties). Needs slr_load_cloud. The
  * minimiser is decided in FP64; d is stored in the configured precision. */
 slr_status slr_build_distance(slr_ctx* ctx);
@@ -136,7 +136,7 @@ slr_status slr_set_distance(slr_ctx* ctx, const double* d_host);
  * m indices. Exact distances (FP64), summed in sample order. */
 slr_status slr_cloud_spacing(slr_ctx* ctx, const int64_t* sample, int64_t m, double* h_s);
 
-/* Algorithm 1 step 3: initial level set φ^0.
+/* Algorithm 1, §3.6: initial level set φ^0.
  *  kind 0 (sphere): params = {cx, cy, cz, r}; φ^0 = |x - c| - r (FP64, rounded to storage);
  *  kind 1 (array):  u0_host = FP64 values of all nodes;
  *  kind 2 (§3.6, from the cloud): params = {γ_S}: nodes on the grid boundary
