@@ -197,8 +197,8 @@ KERNEL_SOURCES = {
 
 
 def sha_of_kernel(name):
-    """Hash of the sources of kernel `name` (every csrc file if unknown) and
-    of the C ABI header they include."""
+    """Hash of the sources of kernel `name`: its translation unit and the
+    headers its device code uses (every csrc file if the name is unknown)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_22205_gb300", "csrc")
     files = KERNEL_SOURCES.get(name.split("<")[0], sorted(os.listdir(csrc)))
@@ -206,8 +206,6 @@ def sha_of_kernel(name):
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
-    with open(os.path.join(ROOT, "include", "slr.h"), "rb") as f:
-        h.update(f.read())
     return h.hexdigest()[:16]
 
 
