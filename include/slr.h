@@ -353,14 +353,16 @@ slr_status slr_probe_fma(int precision, int64_t trips, double* tflops_out, doubl
 /* Release all device memory of the context and the context itself. NULL is a no-op. */
 void slr_destroy(slr_ctx* ctx);
 
-/* Failure-detection check of the bounded grid barrier that the cooperative
- * fast-sweeping kernel uses between planes (the paper has no counterpart).
- * Runs the barrier alone in a two-block cooperative launch on the current
- * device. unreachable = 0: a normal barrier, SLR_OK. unreachable = 1: a
- * barrier that no block completes; every wait gives up after its poll limit
- * (about 0.3 s) and the call returns SLR_E_TIMEOUT, the device staying usable.
- * SLR_E_CUDA when cooperative launch is unavailable; slr_last_error(NULL)
- * gives the reason. */
+/* Failure-detection check of the bounded waits (the paper has no
+ * counterpart), on the current device. unreachable = 0: the grid barrier
+ * that the cooperative fast-sweeping kernel uses between planes, alone in a
+ * two-block cooperative launch, SLR_OK. unreachable = 1: a barrier that no
+ * block completes; every wait gives up after its poll limit (about 0.3 s)
+ * and the call returns SLR_E_TIMEOUT, the device staying usable.
+ * unreachable = 2: the batched kernel's per-job dependency wait (slr_batch_run)
+ * on a counter that no work item completes, SLR_E_TIMEOUT after its poll
+ * limit. SLR_E_INVALID for another mode; SLR_E_CUDA when cooperative launch
+ * is unavailable; slr_last_error(NULL) gives the reason. */
 slr_status slr_selftest_barrier(int unreachable);
 
 /* §4: the L^1 norm of the error against an exact signed distance,

@@ -943,18 +943,21 @@ slr_status slr_get_field(slr_ctx* c, int which, void* host_out, int64_t cap) {
 
 slr_status slr_selftest_barrier(int unreachable) {
     ctxless_error_clear();
+    if (unreachable < 0 || unreachable > 2) return ctxless_error_set(SLR_E_INVALID, "selftest_barrier: mode 0, 1 or 2");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return ctxless_error_set(SLR_E_CUDA, "selftest_barrier: no usable current device");
     }
     int err = 0;
-    cudaError_t e = barrier_selftest(dev, unreachable ? 1 : 0, &err);
+    cudaError_t e = unreachable == 2 ? batch_wait_selftest(&err) : barrier_selftest(dev, unreachable, &err);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return ctxless_error_set(SLR_E_CUDA, std::string("selftest_barrier: ") + cudaGetErrorString(e));
     }
-    if (err & kErrBarrier) return ctxless_error_set(SLR_E_TIMEOUT, "selftest_barrier: the barrier's wait ran out");
+    if (err & kErrBarrier)
+        return ctxless_error_set(SLR_E_TIMEOUT, unreachable == 2 ? "selftest_barrier: the batched kernel's wait ran out"
+                                                                 : "selftest_barrier: the barrier's wait ran out");
     return SLR_OK;
 }
 

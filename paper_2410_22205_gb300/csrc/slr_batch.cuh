@@ -122,10 +122,10 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // writes are visible after it), the job has stopped, or another block
 // reported an error; false after the poll limit (kErrBarrier is then set
 // for every block to see).
-__device__ __forceinline__ bool batch_wait(const int* cnt, int need, const DevState* ds, int* err) {
+__device__ __forceinline__ bool batch_wait(const int* cnt, int need, const int* stop, int* err) {
     long long polls = 0;
     while (ld_acquire(cnt) < need) {
-        if (ld_acquire(&ds->stop)) return true;
+        if (ld_acquire(stop)) return true;
         if (vload(err) & kErrBarrier) return false;
         if (++polls > kBarrierSpinLimit) {
             atomicOr(err, kErrBarrier);
@@ -229,13 +229,13 @@ __global__ void __launch_bounds__(NT, OCC)
                     const DevState* ds = BP.job[j].ds;
                     bool ok;
                     if (ph == 0)
-                        ok = iter == 0 || batch_wait(&ctl->rec_done[j], iter, ds, &ctl->err);
+                        ok = iter == 0 || batch_wait(&ctl->rec_done[j], iter, &ds->stop, &ctl->err);
                     else if (ph == 1)
-                        ok = batch_wait(&ctl->step_done[j], (iter + 1) * (BP.pre[0][j + 1] - BP.pre[0][j]), ds,
-                                        &ctl->err);
+                        ok = batch_wait(&ctl->step_done[j], (iter + 1) * (BP.pre[0][j + 1] - BP.pre[0][j]),
+                                        &ds->stop, &ctl->err);
                     else
-                        ok = batch_wait(&ctl->energy_done[j], (iter + 1) * (BP.pre[1][j + 1] - BP.pre[1][j]), ds,
-                                        &ctl->err);
+                        ok = batch_wait(&ctl->energy_done[j], (iter + 1) * (BP.pre[1][j + 1] - BP.pre[1][j]),
+                                        &ds->stop, &ctl->err);
                     fl |= (ok ? kFlOk : 0) | (ld_acquire(&ds->stop) ? kFlStop : 0);
                     s_it[kItKey] = ok ? key : -1;
                 }
@@ -395,6 +395,13 @@ __global__ void __launch_bounds__(NT, OCC)
         if (tid == 0) s_it[kItDone] = ph == 0 ? j : (ph == 1 ? kBatchMaxJobs + j : -1);
         __syncthreads();
     }
+}
+
+// Failure-detection check of the dependency wait above: one thread waits
+// for a counter that nothing increments (no stop flag set), so the wait
+// runs out after its poll limit and sets kErrBarrier in *err.
+__global__ void k_batch_wait_selftest(const int* words, int* err) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) batch_wait(words, 1, words + 1, err);
 }
 
 // dynamic shared memory of k_batch

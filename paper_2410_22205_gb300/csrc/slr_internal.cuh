@@ -278,6 +278,9 @@ slr_status batch_run_f32(slr_ctx* const* jobs, int n, int tune, cudaStream_t st,
                          float* tuned_ms, int* threads, int* blocks, int* bpi);
 slr_status batch_run_f64(slr_ctx* const* jobs, int n, int tune, cudaStream_t st, int* shape_io, int* graph_out,
                          float* tuned_ms, int* threads, int* blocks, int* bpi);
+// the batched kernel's dependency wait on a counter that nothing completes
+// (slr_batch_f32.cu); *err_out receives its error bits
+cudaError_t batch_wait_selftest(int* err_out);
 
 // ---------------------------------------------------------------------------
 // device numerics

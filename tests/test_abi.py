@@ -46,6 +46,7 @@ def test_new_entry_points_check_their_arguments_without_a_device():
     assert L.slr_batch_chunk(None) == 0
     assert L.slr_batch_run(None, 0, 0, None, None, None) == slr.SLR_E_INVALID
     assert L.slr_server_set_policy(None, 1) == slr.SLR_E_INVALID
+    assert L.slr_selftest_barrier(3) == slr.SLR_E_INVALID
     assert L.slr_batch_run_info(None, None, None, None, None, None) == slr.SLR_E_INVALID
     out = slr.C.c_double(0.0)
     assert L.slr_l1_error(None, 0, None, None, slr.C.byref(out)) == slr.SLR_E_INVALID
