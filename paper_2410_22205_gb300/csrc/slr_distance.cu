@@ -345,8 +345,12 @@ __device__ __forceinline__ float warp_minf(float v) {
     return v;
 }
 
+// Each warp owns a tile of 64 nodes, two per lane: node a and node b one step
+// further along the last axis (z in 3-D, y in 2-D). The pair shares its other
+// coordinates, so the screen shares two of its three FMAs per point, and one
+// walk of the tree, one leaf staging and one stack serve twice the nodes.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, int* aout) {
+__global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, int* aout) {
     __shared__ int s_stack[8][kStack];
     __shared__ float4 s_leaf[8][32];  // a leaf's points about the leaf centre, |q'|^2 in .w
     __shared__ int s_pid[8][32];      // their input indices
@@ -361,41 +365,67 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
     int tk = (int)(r / A.ty);
     int i, j, k;
     if (DIM == 3) {
-        i = ti * 2 + (lane & 1);
-        j = tj * 4 + ((lane >> 1) & 3);
-        k = tk * 4 + (lane >> 3);
+        i = ti * 4 + (lane & 3);
+        j = tj * 4 + ((lane >> 2) & 3);
+        k = tk * 4 + ((lane >> 4) << 1);
     } else {
         i = ti * 8 + (lane & 7);
-        j = tj * 4 + (lane >> 3);
+        j = tj * 8 + ((lane >> 3) << 1);
         k = 0;
     }
-    bool valid = i < A.n0 && j < A.n1 && k < A.n2;
+    // the pair axis: its node count, node a's index along it
+    const int np_ = DIM == 3 ? A.n2 : A.n1;
+    const int pa_ = DIM == 3 ? k : j;
+    bool valid_a = i < A.n0 && j < A.n1 && k < A.n2;
+    bool valid_b = valid_a && pa_ + 1 < np_;
     i = i < A.n0 ? i : A.n0 - 1;
     j = j < A.n1 ? j : A.n1 - 1;
     k = k < A.n2 ? k : A.n2 - 1;
+    const int pa = pa_ < np_ ? pa_ : np_ - 1;
+    const int pb = pa + 1 < np_ ? pa + 1 : np_ - 1;
+    const long long idx_a = (long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k);
+    const long long idx_b = idx_a + (long long)(pb - pa) * (DIM == 3 ? (long long)A.n0 * A.n1 : (long long)A.n0);
     if (A.mask) {
         // only the listed nodes; a warp with none of them has nothing to do
-        valid = valid && A.mask[(long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k)];
-        if (!__any_sync(0xffffffffu, valid)) return;
+        valid_a = valid_a && A.mask[idx_a];
+        valid_b = valid_b && A.mask[idx_b];
+        if (!__any_sync(0xffffffffu, valid_a || valid_b)) return;
     }
-    // exact node coordinates (lo + i*h, no contraction) and FP32 offsets from lo
+    // exact node coordinates (lo + i*h, no contraction): x, the shared second
+    // coordinate s (y in 3-D), the pair coordinates za, zb (z in 3-D, y in 2-D);
+    // FP32 offsets from lo
+    const double loP = DIM == 3 ? A.lo2 : A.lo1;
     const double x = __dadd_rn(A.lo0, __dmul_rn((double)i, A.h));
-    const double y = __dadd_rn(A.lo1, __dmul_rn((double)j, A.h));
-    const double z = DIM == 3 ? __dadd_rn(A.lo2, __dmul_rn((double)k, A.h)) : 0.0;
-    const float xf = (float)(x - A.lo0), yf = (float)(y - A.lo1), zf = DIM == 3 ? (float)(z - A.lo2) : 0.f;
-    const float tlx = warp_minf(xf), tly = warp_minf(yf), tlz = warp_minf(zf);
-    const float thx = warp_maxf(xf), thy = warp_maxf(yf), thz = warp_maxf(zf);
+    const double s = DIM == 3 ? __dadd_rn(A.lo1, __dmul_rn((double)j, A.h)) : 0.0;
+    const double za = __dadd_rn(loP, __dmul_rn((double)pa, A.h));
+    const double zb = __dadd_rn(loP, __dmul_rn((double)pb, A.h));
+    const float xf = (float)(x - A.lo0), sf = DIM == 3 ? (float)(s - A.lo1) : 0.f;
+    const float zaf = (float)(za - loP), zbf = (float)(zb - loP);
+    // the tile's box in (x, y, z) order
+    float tlx, tly, tlz, thx, thy, thz;
+    tlx = warp_minf(xf);
+    thx = warp_maxf(xf);
+    if (DIM == 3) {
+        tly = warp_minf(sf);
+        thy = warp_maxf(sf);
+        tlz = warp_minf(zaf);
+        thz = warp_maxf(zbf);
+    } else {
+        tly = warp_minf(zaf);
+        thy = warp_maxf(zbf);
+        tlz = thz = 0.f;
+    }
     // the FP32 screen's margin, 1.2e-6 (extent + d): the FP32 offsets and
     // squared distances err by ~1e-7 extent, the FP32 square roots of the
     // bounds below by ~1e-7 d; bounds only screen, the decision is FP64
     const float mscale = 1.2e-6f;
     const float extf = (float)A.extent;
 
-    double best = INFINITY;
-    int bi = 0x7fffffff;
-    float thr = INFINITY;    // squared FP32 screen of this lane
-    float lbound = INFINITY; // this lane's best plus the error margin (FP32)
-    float wb2 = INFINITY;    // squared warp bound
+    double best_a = INFINITY, best_b = INFINITY;
+    int bi_a = 0x7fffffff, bi_b = 0x7fffffff;
+    float thr_a = INFINITY, thr_b = INFINITY;  // squared FP32 screens
+    float lb_a = INFINITY, lb_b = INFINITY;    // bests plus the error margin (FP32)
+    float wb2 = INFINITY;                      // squared warp bound
     float4* leaf = s_leaf[wib];
     int* lpid = s_pid[wib];
 
@@ -408,10 +438,10 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
         unsigned m = __ballot_sync(0xffffffffu, ex);
         int np = __popc(m);
         int rank = 0;
-        for (int s = 0; s < 32; ++s) {
-            float o = __shfl_sync(0xffffffffu, d2, s);
-            bool oex = (m >> s) & 1u;
-            if (oex && (o < d2 || (o == d2 && s < lane))) ++rank;
+        for (int s2 = 0; s2 < 32; ++s2) {
+            float o = __shfl_sync(0xffffffffu, d2, s2);
+            bool oex = (m >> s2) & 1u;
+            if (oex && (o < d2 || (o == d2 && s2 < lane))) ++rank;
         }
         if (ex) stack[np - 1 - rank] = (top << 27) | (int)c;
         sp = np;
@@ -428,31 +458,42 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
             // as no lane's bound exceeds the warp bound
             const float4 blo_ = A.blo[A.off[0] + id], bhi_ = A.bhi[A.off[0] + id];
             // per-lane test: skip the leaf when its box, or else its cylinder,
-            // is beyond every lane's own bound
+            // is beyond both nodes' own bounds of every lane
             {
+                const float loP_ = DIM == 3 ? blo_.z : blo_.y, hiP_ = DIM == 3 ? bhi_.z : bhi_.y;
                 const float gx = fmaxf(0.f, fmaxf(blo_.x - xf, xf - bhi_.x));
-                const float gy = fmaxf(0.f, fmaxf(blo_.y - yf, yf - bhi_.y));
-                const float gz = fmaxf(0.f, fmaxf(blo_.z - zf, zf - bhi_.z));
-                const float lb2 = lbound * lbound;
-                bool need = !(gx * gx + gy * gy + gz * gz > lb2);
-                if (!__any_sync(0xffffffffu, need)) continue;
+                const float gs = DIM == 3 ? fmaxf(0.f, fmaxf(blo_.y - sf, sf - bhi_.y)) : 0.f;
+                const float gza = fmaxf(0.f, fmaxf(loP_ - zaf, zaf - hiP_));
+                const float gzb = fmaxf(0.f, fmaxf(loP_ - zbf, zbf - hiP_));
+                const float g2 = fmaf(gx, gx, gs * gs);
+                bool need_a = !(fmaf(gza, gza, g2) > lb_a * lb_a);
+                bool need_b = !(fmaf(gzb, gzb, g2) > lb_b * lb_b);
+                if (!__any_sync(0xffffffffu, need_a || need_b)) continue;
                 // the distance to a point of the leaf is at least that to the
                 // cylinder: its axial excess over the half-height and its
                 // radial excess over the radius, orthogonal components
                 const float4 cc = A.cyl[2 * id], cn = A.cyl[2 * id + 1];
-                const float wx = xf - cc.x, wy = yf - cc.y, wz = zf - cc.z;
-                const float an = fmaf(wx, cn.x, fmaf(wy, cn.y, wz * cn.z));
-                const float px = fmaf(-an, cn.x, wx), py = fmaf(-an, cn.y, wy), pz = fmaf(-an, cn.z, wz);
-                const float ga = fmaxf(0.f, fabsf(an) - cc.w);
-                const float gb = fmaxf(0.f, sqrtf(fmaf(px, px, fmaf(py, py, pz * pz))) - cn.w);
-                need = need && !(fmaf(ga, ga, gb * gb) > lb2);
-                if (!__any_sync(0xffffffffu, need)) continue;
+                const float ccP = DIM == 3 ? cc.z : cc.y, cnP = DIM == 3 ? cn.z : cn.y;
+                const float wx = xf - cc.x, ws = DIM == 3 ? sf - cc.y : 0.f;
+                const float cnS = DIM == 3 ? cn.y : 0.f;
+                const float wza = zaf - ccP, wzb = zbf - ccP;
+                const float ans = fmaf(wx, cn.x, ws * cnS);
+                const float ana = fmaf(wza, cnP, ans), anb = fmaf(wzb, cnP, ans);
+                const float pxa = fmaf(-ana, cn.x, wx), psa = fmaf(-ana, cnS, ws), pza = fmaf(-ana, cnP, wza);
+                const float pxb = fmaf(-anb, cn.x, wx), psb = fmaf(-anb, cnS, ws), pzb = fmaf(-anb, cnP, wzb);
+                const float gaa = fmaxf(0.f, fabsf(ana) - cc.w), gab = fmaxf(0.f, fabsf(anb) - cc.w);
+                const float gra = fmaxf(0.f, sqrtf(fmaf(pxa, pxa, fmaf(psa, psa, pza * pza))) - cn.w);
+                const float grb = fmaxf(0.f, sqrtf(fmaf(pxb, pxb, fmaf(psb, psb, pzb * pzb))) - cn.w);
+                need_a = need_a && !(fmaf(gaa, gaa, gra * gra) > lb_a * lb_a);
+                need_b = need_b && !(fmaf(gab, gab, grb * grb) > lb_b * lb_b);
+                if (!__any_sync(0xffffffffu, need_a || need_b)) continue;
             }
             // The screen works about the leaf centre c: with u = x - c and
             // q' = q - c, |x - q|^2 = |u|^2 + (|q'|^2 - 2 u.q'), three FMAs per
-            // point. Rounding u, q' and the expanded form moves the squared
-            // distance by at most ~16 ulp (|x - q|^2 + e^2), e the diagonal of
-            // the leaf's box; the screens widen by 4e-6 (thr + e^2) for it.
+            // point, the pair coordinate's last, so that nodes a and b share
+            // the first two. Rounding u, q' and the expanded form moves the
+            // squared distance by at most ~16 ulp (|x - q|^2 + e^2), e the
+            // diagonal of the leaf's box; the screens widen by 4e-6 (thr + e^2).
             const float cx = 0.5f * (blo_.x + bhi_.x), cy = 0.5f * (blo_.y + bhi_.y), cz = 0.5f * (blo_.z + bhi_.z);
             const float ex_ = bhi_.x - blo_.x, ey_ = bhi_.y - blo_.y, ez_ = bhi_.z - blo_.z;
             const float we2 = kWide * (ex_ * ex_ + ey_ * ey_ + ez_ * ez_);
@@ -466,50 +507,79 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
                 lpid[lane] = __float_as_int(p.w);
             }
             __syncwarp();
-            const float ux = xf - cx, uy = yf - cy, uz = zf - cz;
-            const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-            const float ax = -2.f * ux, ay = -2.f * uy, az = -2.f * uz;
-            if (best == INFINITY) {
-                // first leaf of this lane: an FP32 minimum bounds the exact best,
-                // so only points within the margin of it need the FP64 check
-                float m2 = INFINITY;
-                for (int s = 0; s < cnt; ++s) {
-                    const float4 q = leaf[s];
-                    m2 = fminf(m2, fmaf(ax, q.x, fmaf(ay, q.y, fmaf(az, q.z, q.w))));
+            const float cP = DIM == 3 ? cz : cy;
+            const float ux = xf - cx, us = DIM == 3 ? sf - cy : 0.f, uza = zaf - cP, uzb = zbf - cP;
+            const float uxs = fmaf(ux, ux, us * us);
+            const float uua = fmaf(uza, uza, uxs), uub = fmaf(uzb, uzb, uxs);
+            const float ax = -2.f * ux, as = -2.f * us, aza = -2.f * uza, azb = -2.f * uzb;
+            if (best_a == INFINITY) {
+                // first leaf of the pair (both bests are unset until one is
+                // screened): an FP32 minimum bounds each exact best, so only
+                // points within the margin of it need the FP64 check
+                float m2a = INFINITY, m2b = INFINITY;
+                for (int t = 0; t < cnt; ++t) {
+                    const float4 q = leaf[t];
+                    const float qP = DIM == 3 ? q.z : q.y;
+                    const float cm = DIM == 3 ? fmaf(ax, q.x, fmaf(as, q.y, q.w)) : fmaf(ax, q.x, q.w);
+                    m2a = fminf(m2a, fmaf(aza, qP, cm));
+                    m2b = fminf(m2b, fmaf(azb, qP, cm));
                 }
-                m2 = fmaf(fmaxf(0.f, m2 + uu), 1.f + kWide, we2);
-                const float md = sqrtf(m2);
-                const float lim = md + 2.0f * mscale * (extf + md);
-                thr = lim * lim * 1.00001f;
+                m2a = fmaf(fmaxf(0.f, m2a + uua), 1.f + kWide, we2);
+                m2b = fmaf(fmaxf(0.f, m2b + uub), 1.f + kWide, we2);
+                const float mda = sqrtf(m2a), mdb = sqrtf(m2b);
+                const float lima = mda + 2.0f * mscale * (extf + mda), limb = mdb + 2.0f * mscale * (extf + mdb);
+                thr_a = lima * lima * 1.00001f;
+                thr_b = limb * limb * 1.00001f;
             }
-            // this leaf's screen, moved to the side of the expanded form
-            float tl = fmaf(thr, 1.f + kWide, we2) - uu;
-            for (int s = 0; s < cnt; ++s) {
-                const float4 q = leaf[s];
-                const float sc = fmaf(ax, q.x, fmaf(ay, q.y, fmaf(az, q.z, q.w)));
-                if (sc <= tl) {
-                    const int pid = lpid[s];
+            // this leaf's screens, moved to the side of the expanded form
+            float tla = fmaf(thr_a, 1.f + kWide, we2) - uua;
+            float tlb = fmaf(thr_b, 1.f + kWide, we2) - uub;
+            for (int t = 0; t < cnt; ++t) {
+                const float4 q = leaf[t];
+                const float qP = DIM == 3 ? q.z : q.y;
+                const float cm = DIM == 3 ? fmaf(ax, q.x, fmaf(as, q.y, q.w)) : fmaf(ax, q.x, q.w);
+                const bool ca = fmaf(aza, qP, cm) <= tla, cb = fmaf(azb, qP, cm) <= tlb;
+                if (ca || cb) {
+                    const int pid = lpid[t];
                     const double* Q = A.pts + (long long)pid * DIM;
                     const double ex = __dsub_rn(x, Q[0]);
-                    const double ey = __dsub_rn(y, Q[1]);
-                    double s2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+                    const double ex2 = __dmul_rn(ex, ex);
+                    double sxy = 0.0;
                     if (DIM == 3) {
-                        const double ez = __dsub_rn(z, Q[2]);
-                        s2 = __dadd_rn(s2, __dmul_rn(ez, ez));
+                        const double ey = __dsub_rn(s, Q[1]);
+                        sxy = __dadd_rn(ex2, __dmul_rn(ey, ey));
                     }
-                    if (s2 < best || (s2 == best && pid < bi)) {
-                        best = s2;
-                        bi = pid;
-                        const float bdist = sqrtf((float)s2);
-                        const float lim = bdist + mscale * (extf + bdist);
-                        thr = lim * lim * 1.00001f;
-                        lbound = lim * 1.00001f;
-                        tl = fmaf(thr, 1.f + kWide, we2) - uu;
+                    const double qz = Q[DIM - 1];
+                    if (ca) {
+                        const double ez = __dsub_rn(za, qz);
+                        const double s2 = DIM == 3 ? __dadd_rn(sxy, __dmul_rn(ez, ez)) : __dadd_rn(ex2, __dmul_rn(ez, ez));
+                        if (s2 < best_a || (s2 == best_a && pid < bi_a)) {
+                            best_a = s2;
+                            bi_a = pid;
+                            const float bdist = sqrtf((float)s2);
+                            const float lim = bdist + mscale * (extf + bdist);
+                            thr_a = lim * lim * 1.00001f;
+                            lb_a = lim * 1.00001f;
+                            tla = fmaf(thr_a, 1.f + kWide, we2) - uua;
+                        }
+                    }
+                    if (cb) {
+                        const double ez = __dsub_rn(zb, qz);
+                        const double s2 = DIM == 3 ? __dadd_rn(sxy, __dmul_rn(ez, ez)) : __dadd_rn(ex2, __dmul_rn(ez, ez));
+                        if (s2 < best_b || (s2 == best_b && pid < bi_b)) {
+                            best_b = s2;
+                            bi_b = pid;
+                            const float bdist = sqrtf((float)s2);
+                            const float lim = bdist + mscale * (extf + bdist);
+                            thr_b = lim * lim * 1.00001f;
+                            lb_b = lim * 1.00001f;
+                            tlb = fmaf(thr_b, 1.f + kWide, we2) - uub;
+                        }
                     }
                 }
             }
             __syncwarp();
-            const float wb = warp_maxf(lbound);
+            const float wb = warp_maxf(fmaxf(lb_a, lb_b));
             wb2 = wb * wb;
         } else {
             if (box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]) > wb2) continue;
@@ -526,19 +596,22 @@ __global__ void __launch_bounds__(256, 5) k_dist_search(SearchArgs A, T* dout, i
                 break;
             }
             int rank = 0;
-            for (int s = 0; s < 32; ++s) {
-                const float o = __shfl_sync(0xffffffffu, d2, s);
-                if (((m >> s) & 1u) && (o < d2 || (o == d2 && s < lane))) ++rank;
+            for (int s2 = 0; s2 < 32; ++s2) {
+                const float o = __shfl_sync(0xffffffffu, d2, s2);
+                if (((m >> s2) & 1u) && (o < d2 || (o == d2 && s2 < lane))) ++rank;
             }
             if (pass) stack[sp + np - 1 - rank] = (cl << 27) | (int)c;
             sp += np;
             __syncwarp();
         }
     }
-    if (valid) {
-        const long long idx = (long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k);
-        dout[idx] = (T)sqrt(best);
-        aout[idx] = bi;
+    if (valid_a) {
+        dout[idx_a] = (T)sqrt(best_a);
+        aout[idx_a] = bi_a;
+    }
+    if (valid_b) {
+        dout[idx_b] = (T)sqrt(best_b);
+        aout[idx_b] = bi_b;
     }
 }
 
@@ -724,13 +797,14 @@ static SearchArgs search_args(int dim, const int64_t n[3], const double lo[3], d
     A.n0 = (int)n[0];
     A.n1 = (int)n[1];
     A.n2 = dim == 3 ? (int)n[2] : 1;
+    // k_dist_search's tiles: 4x4x4 nodes in 3-D, 8x8 in 2-D
     if (dim == 3) {
-        A.tx = (A.n0 + 1) / 2;
+        A.tx = (A.n0 + 3) / 4;
         A.ty = (A.n1 + 3) / 4;
         A.tz = (A.n2 + 3) / 4;
     } else {
         A.tx = (A.n0 + 7) / 8;
-        A.ty = (A.n1 + 3) / 4;
+        A.ty = (A.n1 + 7) / 8;
         A.tz = 1;
     }
     A.lo0 = lo[0];
