@@ -44,6 +44,9 @@ constexpr int kMaxLevels = 8;
 constexpr int kStack = 256;
 // widening of the exact search's FP32 screen for its expanded form (about 67 ulp)
 constexpr float kWide = 4e-6f;
+// block size and resident blocks per SM of the exact search
+constexpr int kSearchThreads = 256;
+constexpr int kSearchMinBlocks = 4;
 
 __device__ __forceinline__ unsigned long long enc_double(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -335,6 +338,11 @@ __device__ __forceinline__ float box_dist2(float tlx, float tly, float tlz, floa
     return gx * gx + gy * gy + gz * gz;
 }
 
+__device__ __forceinline__ float tile_box_dist2(const float4* tb, float4 lo, float4 hi) {
+    const float4 tl = tb[0], th = tb[1];
+    return box_dist2(tl.x, tl.y, tl.z, th.x, th.y, th.z, lo, hi);
+}
+
 __device__ __forceinline__ float warp_maxf(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -345,25 +353,19 @@ __device__ __forceinline__ float warp_minf(float v) {
     return v;
 }
 
-// Each warp owns a tile of 64 nodes, two per lane: node a and node b one step
-// further along the last axis (z in 3-D, y in 2-D). The pair shares its other
-// coordinates, so the screen shares two of its three FMAs per point, and one
-// walk of the tree, one leaf staging and one stack serve twice the nodes.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, int* aout) {
-    __shared__ int s_stack[8][kStack];
-    __shared__ float4 s_leaf[8][32];  // a leaf's points about the leaf centre, |q'|^2 in .w
-    __shared__ int s_pid[8][32];      // their input indices
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long ntiles = (long long)A.tx * A.ty * A.tz;
-    if (tile >= ntiles) return;
-    int* stack = s_stack[wib];
-    int ti = (int)(tile % A.tx);
-    long long r = tile / A.tx;
-    int tj = (int)(r % A.ty);
-    int tk = (int)(r / A.ty);
-    int i, j, k;
+// The two nodes of lane `lane` in tile `tile` of k_dist_search: node a at
+// (i, j, k), node b one step further along the last axis (z in 3-D, y in 2-D);
+// pa, pb their indices along it. Out-of-grid nodes are clamped onto the grid
+// (they only widen the tile) and marked invalid, as are unlisted nodes under a
+// mask; idx_a, idx_b are the nodes' linear indices.
+template <int DIM>
+__device__ __forceinline__ void pair_node(const SearchArgs& A, long long tile, int lane, int& i, int& j, int& k,
+                                          int& pa, int& pb, long long& idx_a, long long& idx_b, bool& valid_a,
+                                          bool& valid_b) {
+    const int ti = (int)(tile % A.tx);
+    const long long r = tile / A.tx;
+    const int tj = (int)(r % A.ty);
+    const int tk = (int)(r / A.ty);
     if (DIM == 3) {
         i = ti * 4 + (lane & 3);
         j = tj * 4 + ((lane >> 2) & 3);
@@ -373,23 +375,44 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
         j = tj * 8 + ((lane >> 3) << 1);
         k = 0;
     }
-    // the pair axis: its node count, node a's index along it
     const int np_ = DIM == 3 ? A.n2 : A.n1;
     const int pa_ = DIM == 3 ? k : j;
-    bool valid_a = i < A.n0 && j < A.n1 && k < A.n2;
-    bool valid_b = valid_a && pa_ + 1 < np_;
+    valid_a = i < A.n0 && j < A.n1 && k < A.n2;
+    valid_b = valid_a && pa_ + 1 < np_;
     i = i < A.n0 ? i : A.n0 - 1;
     j = j < A.n1 ? j : A.n1 - 1;
     k = k < A.n2 ? k : A.n2 - 1;
-    const int pa = pa_ < np_ ? pa_ : np_ - 1;
-    const int pb = pa + 1 < np_ ? pa + 1 : np_ - 1;
-    const long long idx_a = (long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k);
-    const long long idx_b = idx_a + (long long)(pb - pa) * (DIM == 3 ? (long long)A.n0 * A.n1 : (long long)A.n0);
+    pa = pa_ < np_ ? pa_ : np_ - 1;
+    pb = pa + 1 < np_ ? pa + 1 : np_ - 1;
+    idx_a = (long long)i + (long long)A.n0 * ((long long)j + (long long)A.n1 * k);
+    idx_b = idx_a + (long long)(pb - pa) * (DIM == 3 ? (long long)A.n0 * A.n1 : (long long)A.n0);
     if (A.mask) {
-        // only the listed nodes; a warp with none of them has nothing to do
         valid_a = valid_a && A.mask[idx_a];
         valid_b = valid_b && A.mask[idx_b];
-        if (!__any_sync(0xffffffffu, valid_a || valid_b)) return;
+    }
+}
+
+// Each warp owns a tile of 64 nodes, two per lane: node a and node b one step
+// further along the last axis (z in 3-D, y in 2-D). The pair shares its other
+// coordinates, so the screen shares two of its three FMAs per point, and one
+// walk of the tree, one leaf staging and one stack serve twice the nodes.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_search(SearchArgs A, T* dout, int* aout) {
+    __shared__ int s_stack[kSearchThreads / 32][kStack];
+    __shared__ float4 s_leaf[kSearchThreads / 32][32];  // a leaf's points about the leaf centre, |q'|^2 in .w
+    __shared__ int s_pid[kSearchThreads / 32][32];      // their input indices
+    __shared__ float4 s_tbox[kSearchThreads / 32][2];  // the tile's box (low and high corners)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (tile >= (long long)A.tx * A.ty * A.tz) return;
+    int* stack = s_stack[wib];
+    int i, j, k, pa, pb;
+    {
+        long long idx_a, idx_b;
+        bool valid_a, valid_b;
+        pair_node<DIM>(A, tile, lane, i, j, k, pa, pb, idx_a, idx_b, valid_a, valid_b);
+        // a warp with none of its nodes listed has nothing to do
+        if (A.mask && !__any_sync(0xffffffffu, valid_a || valid_b)) return;
     }
     // exact node coordinates (lo + i*h, no contraction): x, the shared second
     // coordinate s (y in 3-D), the pair coordinates za, zb (z in 3-D, y in 2-D);
@@ -401,19 +424,27 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
     const double zb = __dadd_rn(loP, __dmul_rn((double)pb, A.h));
     const float xf = (float)(x - A.lo0), sf = DIM == 3 ? (float)(s - A.lo1) : 0.f;
     const float zaf = (float)(za - loP), zbf = (float)(zb - loP);
-    // the tile's box in (x, y, z) order
-    float tlx, tly, tlz, thx, thy, thz;
-    tlx = warp_minf(xf);
-    thx = warp_maxf(xf);
-    if (DIM == 3) {
-        tly = warp_minf(sf);
-        thy = warp_maxf(sf);
-        tlz = warp_minf(zaf);
-        thz = warp_maxf(zbf);
-    } else {
-        tly = warp_minf(zaf);
-        thy = warp_maxf(zbf);
-        tlz = thz = 0.f;
+    // the tile's box in (x, y, z) order, kept in shared memory for the
+    // interior nodes' tests (registers are the scarce resource here)
+    {
+        float tlx, tly, tlz, thx, thy, thz;
+        tlx = warp_minf(xf);
+        thx = warp_maxf(xf);
+        if (DIM == 3) {
+            tly = warp_minf(sf);
+            thy = warp_maxf(sf);
+            tlz = warp_minf(zaf);
+            thz = warp_maxf(zbf);
+        } else {
+            tly = warp_minf(zaf);
+            thy = warp_maxf(zbf);
+            tlz = thz = 0.f;
+        }
+        if (lane == 0) {
+            s_tbox[wib][0] = make_float4(tlx, tly, tlz, 0.f);
+            s_tbox[wib][1] = make_float4(thx, thy, thz, 0.f);
+        }
+        __syncwarp();
     }
     // the FP32 screen's margin, 1.2e-6 (extent + d): the FP32 offsets and
     // squared distances err by ~1e-7 extent, the FP32 square roots of the
@@ -434,7 +465,7 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
         const int top = A.nlevels - 1;
         long long c = lane;
         bool ex = c < A.cnt[top];
-        float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[top] + c], A.bhi[A.off[top] + c]) : INFINITY;
+        float d2 = ex ? tile_box_dist2(s_tbox[wib], A.blo[A.off[top] + c], A.bhi[A.off[top] + c]) : INFINITY;
         unsigned m = __ballot_sync(0xffffffffu, ex);
         int np = __popc(m);
         int rank = 0;
@@ -528,8 +559,8 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
                 m2b = fmaf(fmaxf(0.f, m2b + uub), 1.f + kWide, we2);
                 const float mda = sqrtf(m2a), mdb = sqrtf(m2b);
                 const float lima = mda + 2.0f * mscale * (extf + mda), limb = mdb + 2.0f * mscale * (extf + mdb);
-                thr_a = lima * lima * 1.00001f;
-                thr_b = limb * limb * 1.00001f;
+                thr_a = lima * lima * 1.000002f;
+                thr_b = limb * limb * 1.000002f;
             }
             // this leaf's screens, moved to the side of the expanded form
             float tla = fmaf(thr_a, 1.f + kWide, we2) - uua;
@@ -558,8 +589,8 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
                             bi_a = pid;
                             const float bdist = sqrtf((float)s2);
                             const float lim = bdist + mscale * (extf + bdist);
-                            thr_a = lim * lim * 1.00001f;
-                            lb_a = lim * 1.00001f;
+                            thr_a = lim * lim * 1.000002f;
+                            lb_a = lim * 1.000002f;
                             tla = fmaf(thr_a, 1.f + kWide, we2) - uua;
                         }
                     }
@@ -571,8 +602,8 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
                             bi_b = pid;
                             const float bdist = sqrtf((float)s2);
                             const float lim = bdist + mscale * (extf + bdist);
-                            thr_b = lim * lim * 1.00001f;
-                            lb_b = lim * 1.00001f;
+                            thr_b = lim * lim * 1.000002f;
+                            lb_b = lim * 1.000002f;
                             tlb = fmaf(thr_b, 1.f + kWide, we2) - uub;
                         }
                     }
@@ -582,11 +613,11 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
             const float wb = warp_maxf(fmaxf(lb_a, lb_b));
             wb2 = wb * wb;
         } else {
-            if (box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]) > wb2) continue;
+            if (tile_box_dist2(s_tbox[wib], A.blo[A.off[lvl] + id], A.bhi[A.off[lvl] + id]) > wb2) continue;
             const int cl = lvl - 1;
             const long long c = id * 32 + lane;
             const bool ex = c < A.cnt[cl];
-            float d2 = ex ? box_dist2(tlx, tly, tlz, thx, thy, thz, A.blo[A.off[cl] + c], A.bhi[A.off[cl] + c])
+            float d2 = ex ? tile_box_dist2(s_tbox[wib], A.blo[A.off[cl] + c], A.bhi[A.off[cl] + c])
                           : INFINITY;
             const bool pass = ex && d2 <= wb2;
             const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -605,6 +636,10 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
             __syncwarp();
         }
     }
+    // the nodes' indices again (cheaper than keeping them through the walk)
+    long long idx_a, idx_b;
+    bool valid_a, valid_b;
+    pair_node<DIM>(A, tile, lane, i, j, k, pa, pb, idx_a, idx_b, valid_a, valid_b);
     if (valid_a) {
         dout[idx_a] = (T)sqrt(best_a);
         aout[idx_a] = bi_a;
@@ -618,8 +653,8 @@ __global__ void __launch_bounds__(256, 4) k_dist_search(SearchArgs A, T* dout, i
 template <typename T, int DIM>
 static void launch_search(slr_ctx* c, const SearchArgs& A) {
     long long ntiles = (long long)A.tx * A.ty * A.tz;
-    long long blocks = (ntiles * 32 + 255) / 256;
-    k_dist_search<T, DIM><<<(unsigned)blocks, 256, 0, c->stream>>>(A, (T*)c->d, c->argmin);
+    long long blocks = (ntiles * 32 + kSearchThreads - 1) / kSearchThreads;
+    k_dist_search<T, DIM><<<(unsigned)blocks, kSearchThreads, 0, c->stream>>>(A, (T*)c->d, c->argmin);
     c->launches += 1;
 }
 
@@ -865,11 +900,11 @@ cudaError_t distance_on_marked(slr_ctx* c, const unsigned char* mask, double* do
         SearchArgs A = search_args(c, X);
         A.mask = mask;
         const long long ntiles = (long long)A.tx * A.ty * A.tz;
-        const unsigned blocks = (unsigned)((ntiles * 32 + 255) / 256);
+        const unsigned blocks = (unsigned)((ntiles * 32 + kSearchThreads - 1) / kSearchThreads);
         if (c->cfg.dim == 3)
-            k_dist_search<double, 3><<<blocks, 256, 0, c->stream>>>(A, dout, c->argmin);
+            k_dist_search<double, 3><<<blocks, kSearchThreads, 0, c->stream>>>(A, dout, c->argmin);
         else
-            k_dist_search<double, 2><<<blocks, 256, 0, c->stream>>>(A, dout, c->argmin);
+            k_dist_search<double, 2><<<blocks, kSearchThreads, 0, c->stream>>>(A, dout, c->argmin);
         c->launches += 1;
         e = cudaGetLastError();
     }
@@ -1022,17 +1057,17 @@ extern "C" slr_status slr_distance_grid_noalloc(int dim, const int64_t n[3], con
     }
     SearchArgs A = search_args(dim, n, lo, h, pts_dev, npts, X);
     long long ntiles = (long long)A.tx * A.ty * A.tz;
-    unsigned sblocks = (unsigned)((ntiles * 32 + 255) / 256);
+    unsigned sblocks = (unsigned)((ntiles * 32 + kSearchThreads - 1) / kSearchThreads);
     if (precision == 32) {
         if (dim == 3)
-            k_dist_search<float, 3><<<sblocks, 256, 0, st>>>(A, (float*)d_dev, argmin_dev);
+            k_dist_search<float, 3><<<sblocks, kSearchThreads, 0, st>>>(A, (float*)d_dev, argmin_dev);
         else
-            k_dist_search<float, 2><<<sblocks, 256, 0, st>>>(A, (float*)d_dev, argmin_dev);
+            k_dist_search<float, 2><<<sblocks, kSearchThreads, 0, st>>>(A, (float*)d_dev, argmin_dev);
     } else {
         if (dim == 3)
-            k_dist_search<double, 3><<<sblocks, 256, 0, st>>>(A, (double*)d_dev, argmin_dev);
+            k_dist_search<double, 3><<<sblocks, kSearchThreads, 0, st>>>(A, (double*)d_dev, argmin_dev);
         else
-            k_dist_search<double, 2><<<sblocks, 256, 0, st>>>(A, (double*)d_dev, argmin_dev);
+            k_dist_search<double, 2><<<sblocks, kSearchThreads, 0, st>>>(A, (double*)d_dev, argmin_dev);
     }
     int hflag = 0;
     int* flag = S.flag;
