@@ -626,10 +626,13 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
                 if (lane == 0) atomicOr(A.flag, 4);
                 break;
             }
+            // each passing child's rank among the passing ones (nearest last
+            // on the stack, ties by lane), over the set bits of the ballot only
             int rank = 0;
-            for (int s2 = 0; s2 < 32; ++s2) {
-                const float o = __shfl_sync(0xffffffffu, d2, s2);
-                if (((m >> s2) & 1u) && (o < d2 || (o == d2 && s2 < lane))) ++rank;
+            for (unsigned mm = m; mm; mm &= mm - 1) {
+                const int o = __ffs(mm) - 1;
+                const float od = __shfl_sync(0xffffffffu, d2, o);
+                if (od < d2 || (od == d2 && o < lane)) ++rank;
             }
             if (pass) stack[sp + np - 1 - rank] = (cl << 27) | (int)c;
             sp += np;
