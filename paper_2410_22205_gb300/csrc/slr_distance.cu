@@ -660,8 +660,8 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             const float4 chi = ex ? A.bhi[A.off[cl] + c] : make_float4(0.f, 0.f, 0.f, 0.f);
             float d2 = ex ? tile_box_dist2(s_tbox[wib], clo, chi) : INFINITY;
             bool pass = ex && d2 <= wb2;
-            if (cl == 0 && pass) {
-                // a leaf is pushed only if it lies within the bound of one of
+            if (pass) {
+                // a child is pushed only if it lies within the bound of one of
                 // the sub-tiles: no node is nearer to it than its sub-tile's
                 // box, and no node's own bound exceeds its sub-tile's
                 bool near = false;
