@@ -353,11 +353,16 @@ __device__ __forceinline__ float warp_minf(float v) {
     return v;
 }
 
-// the sub-tile (0..7) of lane `lane` in k_dist_search's tile: lanes that
-// differ only in bits 0 and 2 (3-D: x and y within 2x2) or 0 and 1 (2-D: x
-// within 4) share one
+// Sub-tiles of k_dist_search's tile: with 8, lanes that differ only in bits
+// 0 and 2 (3-D: 2x2 in x and y) or 0 and 1 (2-D: 4 in x) share one; with 16,
+// lanes that differ only in bit 0 (2 in x). kSubSecond is the second bit.
+constexpr int kSubTiles = 8;
+template <int DIM>
+constexpr int kSubSecond = kSubTiles == 16 ? 0 : (DIM == 3 ? 4 : 2);
+
 template <int DIM>
 __device__ __forceinline__ int sub_of(int lane) {
+    if (kSubTiles == 16) return lane >> 1;
     return DIM == 3 ? (((lane >> 1) & 1) | ((lane >> 2) & 6)) : (lane >> 2);
 }
 
@@ -410,9 +415,9 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
     __shared__ float4 s_leaf[kSearchThreads / 32][32];  // a leaf's points about the leaf centre, |q'|^2 in .w
     __shared__ int s_pid[kSearchThreads / 32][32];      // their input indices
     __shared__ float4 s_tbox[kSearchThreads / 32][2];  // the tile's box (low and high corners)
-    // the tile's eight sub-tiles of 2x2x2 nodes (4x2 in 2-D, four lanes each):
-    // low corner with the largest pruning bound of their nodes in .w, high corner
-    __shared__ float4 s_sub[kSearchThreads / 32][8][2];
+    // the tile's sub-tiles (kSubTiles): low corner with the largest pruning
+    // bound of their nodes in .w, high corner
+    __shared__ float4 s_sub[kSearchThreads / 32][kSubTiles][2];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (tile >= (long long)A.tx * A.ty * A.tz) return;
@@ -455,7 +460,7 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             s_tbox[wib][0] = make_float4(tlx, tly, tlz, 0.f);
             s_tbox[wib][1] = make_float4(thx, thy, thz, 0.f);
         }
-        // the sub-tile of this lane: the lanes that differ in bits kSubX1, kSubX2
+        // the box of this lane's sub-tile
         float slx = fminf(xf, __shfl_xor_sync(0xffffffffu, xf, 1));
         float shx = fmaxf(xf, __shfl_xor_sync(0xffffffffu, xf, 1));
         float sly = DIM == 3 ? sf : zaf, shy = DIM == 3 ? sf : zbf;
@@ -464,13 +469,15 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
         shy = fmaxf(shy, __shfl_xor_sync(0xffffffffu, shy, 1));
         slz = fminf(slz, __shfl_xor_sync(0xffffffffu, slz, 1));
         shz = fmaxf(shz, __shfl_xor_sync(0xffffffffu, shz, 1));
-        constexpr int X2 = DIM == 3 ? 4 : 2;
-        slx = fminf(slx, __shfl_xor_sync(0xffffffffu, slx, X2));
-        shx = fmaxf(shx, __shfl_xor_sync(0xffffffffu, shx, X2));
-        sly = fminf(sly, __shfl_xor_sync(0xffffffffu, sly, X2));
-        shy = fmaxf(shy, __shfl_xor_sync(0xffffffffu, shy, X2));
-        slz = fminf(slz, __shfl_xor_sync(0xffffffffu, slz, X2));
-        shz = fmaxf(shz, __shfl_xor_sync(0xffffffffu, shz, X2));
+        constexpr int X2 = kSubSecond<DIM>;
+        if (X2) {
+            slx = fminf(slx, __shfl_xor_sync(0xffffffffu, slx, X2));
+            shx = fmaxf(shx, __shfl_xor_sync(0xffffffffu, shx, X2));
+            sly = fminf(sly, __shfl_xor_sync(0xffffffffu, sly, X2));
+            shy = fmaxf(shy, __shfl_xor_sync(0xffffffffu, shy, X2));
+            slz = fminf(slz, __shfl_xor_sync(0xffffffffu, slz, X2));
+            shz = fmaxf(shz, __shfl_xor_sync(0xffffffffu, shz, X2));
+        }
         if ((lane & (1 | X2)) == 0) {
             s_sub[wib][sub_of<DIM>(lane)][0] = make_float4(slx, sly, slz, INFINITY);
             s_sub[wib][sub_of<DIM>(lane)][1] = make_float4(shx, shy, shz, 0.f);
@@ -641,11 +648,11 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
                 }
             }
             {
-                // the sub-tiles' bounds: the largest of their four lanes' own
-                constexpr int X2 = DIM == 3 ? 4 : 2;
+                // the sub-tiles' bounds: the largest of their lanes' own
+                constexpr int X2 = kSubSecond<DIM>;
                 float v = fmaxf(lb_a, lb_b);
                 v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-                v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, X2));
+                if (X2) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, X2));
                 if ((lane & (1 | X2)) == 0) s_sub[wib][sub_of<DIM>(lane)][0].w = v;
             }
             __syncwarp();
@@ -666,7 +673,7 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
                 // box, and no node's own bound exceeds its sub-tile's
                 bool near = false;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
+                for (int t = 0; t < kSubTiles; ++t) {
                     const float4 sl = s_sub[wib][t][0], sh = s_sub[wib][t][1];
                     near = near || !(box_dist2(sl.x, sl.y, sl.z, sh.x, sh.y, sh.z, clo, chi) > sl.w * sl.w);
                 }
