@@ -152,6 +152,20 @@ def test_distance_torus_128_sampled():
     assert np.array_equal(rec.d()[nodes], d_o.astype(np.float32).astype(np.float64))
 
 
+@pytest.mark.parametrize("dim,n,npts", [(3, (45, 38, 29), 6000), (2, (203, 157), 4000)])
+def test_distance_surface_cloud_ragged_whole_grid(dim, n, npts):
+    """A surface cloud deep enough for three hierarchy levels on a grid whose
+    sizes are no multiple of the search's warp tile (4x4x4 nodes in 3-D, 8x8
+    in 2-D): every node, d and argmin, against the oracle's k-d search."""
+    rec, P = make(dim, n, 32, 1, 1)
+    pts = synth.torus_cloud(npts, 0.5, 0.2, 0.002, 3) if dim == 3 else synth.circle_noisy(npts, 0.6, 0.003, 3)
+    rec.load_cloud(pts)
+    rec.build_distance()
+    d_o, a_o = O.distance(P, pts, method="kd")
+    assert np.array_equal(rec.argmin(), a_o)
+    assert np.array_equal(rec.d(), d_o.astype(np.float32).astype(np.float64))
+
+
 # ---------------------------------------------------------------- init, band
 
 @pytest.mark.parametrize("prec", [32, 64])
