@@ -581,10 +581,13 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             const float uxs = fmaf(ux, ux, us * us);
             const float uua = fmaf(uza, uza, uxs), uub = fmaf(uzb, uzb, uxs);
             const float ax = -2.f * ux, as = -2.f * us, aza = -2.f * uza, azb = -2.f * uzb;
-            if (best_a == INFINITY) {
-                // first leaf of the pair (both bests are unset until one is
-                // screened): an FP32 minimum bounds each exact best, so only
-                // points within the margin of it need the FP64 check
+            // The leaf's FP32 minimum first: it bounds the distance of the
+            // leaf's nearest point, and any point beyond the margin of it is
+            // strictly farther than that point, so only points within the
+            // margin (and within the node's own best) need the FP64 check,
+            // however the leaf's points are ordered.
+            float tla, tlb;
+            {
                 float m2a = INFINITY, m2b = INFINITY;
                 for (int t = 0; t < cnt; ++t) {
                     const float4 q = leaf[t];
@@ -597,12 +600,10 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
                 m2b = fmaf(fmaxf(0.f, m2b + uub), 1.f + kWide, we2);
                 const float mda = sqrtf(m2a), mdb = sqrtf(m2b);
                 const float lima = mda + 2.0f * mscale * (extf + mda), limb = mdb + 2.0f * mscale * (extf + mdb);
-                thr_a = lima * lima * 1.000002f;
-                thr_b = limb * limb * 1.000002f;
+                // this leaf's screens, moved to the side of the expanded form
+                tla = fmaf(fminf(thr_a, lima * lima * 1.000002f), 1.f + kWide, we2) - uua;
+                tlb = fmaf(fminf(thr_b, limb * limb * 1.000002f), 1.f + kWide, we2) - uub;
             }
-            // this leaf's screens, moved to the side of the expanded form
-            float tla = fmaf(thr_a, 1.f + kWide, we2) - uua;
-            float tlb = fmaf(thr_b, 1.f + kWide, we2) - uub;
             for (int t = 0; t < cnt; ++t) {
                 const float4 q = leaf[t];
                 const float qP = DIM == 3 ? q.z : q.y;
