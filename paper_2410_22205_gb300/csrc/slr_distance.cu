@@ -12,18 +12,22 @@
 //     (centre, unit axis along the leaf's least-variance direction,
 //     half-height, radius): on a surface cloud a leaf is a thin patch, and
 //     the cylinder bounds the distance to it far more tightly than its box;
-//  4. one warp per tile of 32 grid nodes (2x4x4 in 3-D, 8x4 in 2-D): a
-//     depth-first walk of the hierarchy, nearest child first, pruning boxes
-//     farther from the tile than the warp's worst current best. A leaf is
-//     screened only if, for some lane, both its box and its cylinder lie
-//     within that lane's bound. At the leaves
-//     each lane screens the 32 points in FP32 and re-checks in FP64 — with the
-//     oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 + (z-qz)^2 without
-//     contraction — every point whose FP32 distance is within a safety
-//     margin of its best. Ties go to the lowest point index.
+//  4. one warp per tile of 64 grid nodes (4x4x4 in 3-D, 8x8 in 2-D), two
+//     nodes per lane one step apart along the last axis: a depth-first walk
+//     of the hierarchy, nearest child first. A child box is pushed only if it
+//     lies within the bound of the whole tile and of one of its eight 2x2x2
+//     sub-tiles (each sub-tile's bound the largest current best of its
+//     nodes); a popped leaf is screened only if, for some node, both its box
+//     and its cylinder lie within that node's bound. At a screened leaf each
+//     lane first takes the leaf's FP32 minimum for each node, then re-checks
+//     in FP64 — with the oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 +
+//     (z-qz)^2 without contraction — every point whose FP32 distance is
+//     within a safety margin of both that minimum and the node's best. Ties
+//     go to the lowest point index.
 // The FP32 screen only discards points whose true distance exceeds the
-// lane's best by more than the FP32 error bound (margin 1e-6 x (extent + d),
-// ~10x the worst rounding), so the FP64 decision is exact.
+// node's best (or the leaf's nearest) by more than the FP32 error bound
+// (margin 1.2e-6 x (extent + d), about 6x the worst rounding), so the FP64
+// decision is exact.
 #include <math.h>
 #include <string.h>
 
