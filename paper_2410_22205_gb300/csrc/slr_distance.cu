@@ -19,11 +19,12 @@
 //     sub-tiles (each sub-tile's bound the largest current best of its
 //     nodes); a popped leaf is screened only if, for some node, both its box
 //     and its cylinder lie within that node's bound. At a screened leaf each
-//     lane first takes the leaf's FP32 minimum for each node, then re-checks
-//     in FP64 — with the oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 +
-//     (z-qz)^2 without contraction — every point whose FP32 distance is
-//     within a safety margin of both that minimum and the node's best. Ties
-//     go to the lowest point index.
+//     lane first takes the leaf's FP32 minimum for each node (a leaf whose
+//     minimum passes no node's screen ends there), then re-checks in FP64 —
+//     with the oracle's exact arithmetic, (x-qx)^2 + (y-qy)^2 + (z-qz)^2
+//     without contraction — every point whose FP32 distance is within a
+//     safety margin of both that minimum and the node's best. Ties go to the
+//     lowest point index.
 // The FP32 screen only discards points whose true distance exceeds the
 // node's best (or the leaf's nearest) by more than the FP32 error bound
 // (margin 1.2e-6 x (extent + d), about 6x the worst rounding), so the FP64
@@ -592,21 +593,24 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             // however the leaf's points are ordered.
             float tla, tlb;
             {
-                float m2a = INFINITY, m2b = INFINITY;
+                float s2a = INFINITY, s2b = INFINITY;
                 for (int t = 0; t < cnt; ++t) {
                     const float4 q = leaf[t];
                     const float qP = DIM == 3 ? q.z : q.y;
                     const float cm = DIM == 3 ? fmaf(ax, q.x, fmaf(as, q.y, q.w)) : fmaf(ax, q.x, q.w);
-                    m2a = fminf(m2a, fmaf(aza, qP, cm));
-                    m2b = fminf(m2b, fmaf(azb, qP, cm));
+                    s2a = fminf(s2a, fmaf(aza, qP, cm));
+                    s2b = fminf(s2b, fmaf(azb, qP, cm));
                 }
-                m2a = fmaf(fmaxf(0.f, m2a + uua), 1.f + kWide, we2);
-                m2b = fmaf(fmaxf(0.f, m2b + uub), 1.f + kWide, we2);
+                const float m2a = fmaf(fmaxf(0.f, s2a + uua), 1.f + kWide, we2);
+                const float m2b = fmaf(fmaxf(0.f, s2b + uub), 1.f + kWide, we2);
                 const float mda = sqrtf(m2a), mdb = sqrtf(m2b);
                 const float lima = mda + 2.0f * mscale * (extf + mda), limb = mdb + 2.0f * mscale * (extf + mdb);
                 // this leaf's screens, moved to the side of the expanded form
                 tla = fmaf(fminf(thr_a, lima * lima * 1.000002f), 1.f + kWide, we2) - uua;
                 tlb = fmaf(fminf(thr_b, limb * limb * 1.000002f), 1.f + kWide, we2) - uub;
+                // the second pass computes the same screen values: when no
+                // node's smallest one passes, no point of the leaf does
+                if (!__any_sync(0xffffffffu, s2a <= tla || s2b <= tlb)) continue;
             }
             for (int t = 0; t < cnt; ++t) {
                 const float4 q = leaf[t];
