@@ -574,11 +574,16 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             const long long base = id * 32;
             long long rem = A.npts - base;
             const int cnt = rem < 32 ? (int)rem : 32;
+            // a ragged last leaf is padded with points at infinite distance,
+            // which no screen passes, so both passes run over 32 points
             if (lane < cnt) {
                 const float4 p = A.spt[base + lane];
                 const float qx = p.x - cx, qy = p.y - cy, qz = p.z - cz;
                 leaf[lane] = make_float4(qx, qy, qz, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
                 lpid[lane] = __float_as_int(p.w);
+            } else {
+                leaf[lane] = make_float4(0.f, 0.f, 0.f, INFINITY);
+                lpid[lane] = 0x7fffffff;
             }
             __syncwarp();
             const float cP = DIM == 3 ? cz : cy;
@@ -594,7 +599,8 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
             float tla, tlb;
             {
                 float s2a = INFINITY, s2b = INFINITY;
-                for (int t = 0; t < cnt; ++t) {
+#pragma unroll 8
+                for (int t = 0; t < 32; ++t) {
                     const float4 q = leaf[t];
                     const float qP = DIM == 3 ? q.z : q.y;
                     const float cm = DIM == 3 ? fmaf(ax, q.x, fmaf(as, q.y, q.w)) : fmaf(ax, q.x, q.w);
@@ -612,7 +618,8 @@ __global__ void __launch_bounds__(kSearchThreads, kSearchMinBlocks) k_dist_searc
                 // node's smallest one passes, no point of the leaf does
                 if (!__any_sync(0xffffffffu, s2a <= tla || s2b <= tlb)) continue;
             }
-            for (int t = 0; t < cnt; ++t) {
+#pragma unroll 4
+            for (int t = 0; t < 32; ++t) {
                 const float4 q = leaf[t];
                 const float qP = DIM == 3 ? q.z : q.y;
                 const float cm = DIM == 3 ? fmaf(ax, q.x, fmaf(as, q.y, q.w)) : fmaf(ax, q.x, q.w);
